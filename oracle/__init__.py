@@ -1,0 +1,193 @@
+"""CSGV oracle: plain single-threaded CPU encoder / decoder (ctypes over ``csgv_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU-baseline leg are
+the only callers. The GPU library never imports this package and shares no code with it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "csgv_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+OP_PARENT, OP_NX, OP_NY, OP_NZ, OP_ADV, OP_LAST, OP_DELTA = range(7)
+OP_ALL = 0x7F
+CODER_PLAIN, CODER_RANS = 0, 1
+FLAG_NO_STOP = 1
+ERR_ARG, ERR_FORMAT, ERR_OOM, ERR_CORRUPT = -1, -2, -3, -5
+
+NODE_DTYPE = np.dtype([("level", "<i4"), ("morton", "<u4"), ("op", "<i4"), ("stop", "<i4"),
+                       ("delta", "<u4"), ("label", "<u4"), ("k", "<u4")])
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        super().__init__(f"oracle error {code} {what}".strip())
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so next to its source (gcc, plain C11)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-fPIC", "-shared", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P, U32, SZ = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_size_t
+        lib.oracle_encode_volume.argtypes = [P, P, U32, U32, U32, U32, ctypes.POINTER(P), ctypes.POINTER(SZ)]
+        lib.oracle_decode_brick.argtypes = [P, SZ, U32, U32, P]
+        lib.oracle_decode_volume.argtypes = [P, SZ, P]
+        lib.oracle_brick_nodes.argtypes = [P, SZ, U32, P, U32, P]
+        lib.oracle_brick_symbols.argtypes = [P, SZ, U32, P, U32, P]
+        lib.oracle_delta_nibbles.argtypes = [U32, P]
+        lib.oracle_rans_quantize.argtypes = [P, P]
+        lib.oracle_pack_single_brick.argtypes = [U32, U32, U32, U32, P, U32, P, U32, U32, ctypes.POINTER(P),
+                                                 ctypes.POINTER(SZ)]
+        lib.oracle_free.argtypes = [P]
+        for f in ("oracle_encode_volume", "oracle_decode_brick", "oracle_decode_volume", "oracle_brick_nodes",
+                  "oracle_brick_symbols", "oracle_delta_nibbles", "oracle_rans_quantize", "oracle_pack_single_brick"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _take(ptr: ctypes.c_void_p, size: int) -> np.ndarray:
+    out = np.frombuffer(ctypes.string_at(ptr, size), dtype=np.uint8).copy()
+    _load().oracle_free(ptr)
+    return out
+
+
+def encode_volume(V: np.ndarray, log2b: int, op_mask: int = OP_ALL, coder: int = CODER_PLAIN,
+                  flags: int = 0) -> np.ndarray:
+    """Encode a (z, y, x) uint32 volume; returns the encoded bytes as a uint8 array."""
+    V = np.ascontiguousarray(V, dtype=np.uint32)
+    assert V.ndim == 3
+    dims = (ctypes.c_uint32 * 3)(V.shape[2], V.shape[1], V.shape[0])
+    ptr, size = ctypes.c_void_p(), ctypes.c_size_t()
+    rc = _load().oracle_encode_volume(V.ctypes.data, dims, log2b, op_mask, coder, flags, ctypes.byref(ptr),
+                                      ctypes.byref(size))
+    if rc:
+        raise OracleError(rc, "encode")
+    return _take(ptr, size.value)
+
+
+def header(vol: np.ndarray) -> dict:
+    h = np.frombuffer(vol[:128].tobytes(), dtype="<u4")
+    L = int(h[5])
+    b = 1 << L
+    dims = (int(h[2]), int(h[3]), int(h[4]))
+    nb = tuple((d + b - 1) // b for d in dims)
+    return {"magic": int(h[0]), "version": int(h[1]), "dims": dims, "log2b": L, "b": b, "op_mask": int(h[6]),
+            "coder": int(h[7]), "flags": int(h[8]), "n_bricks": int(h[9]), "max_pal": int(h[10]),
+            "max_sym": int(h[11]), "freq": [int(x) for x in h[12:28]], "records_words": int(h[28]),
+            "bricks_per_axis": nb}
+
+
+def decode_brick(vol: np.ndarray, brick_id: int, lod: int = 0) -> np.ndarray:
+    """Labels of one brick at level of detail lod, shape (n, n, n) with n = b >> lod (z, y, x)."""
+    vol = np.ascontiguousarray(vol, dtype=np.uint8)
+    n = header(vol)["b"] >> lod
+    out = np.empty((max(n, 1),) * 3, dtype=np.uint32)
+    rc = _load().oracle_decode_brick(vol.ctypes.data, vol.size, brick_id, lod, out.ctypes.data)
+    if rc:
+        raise OracleError(rc, f"decode brick {brick_id}")
+    return out
+
+
+def decode_brick_status(vol: np.ndarray, brick_id: int, lod: int = 0) -> int:
+    """Status code (0 or negative) of decoding one brick."""
+    vol = np.ascontiguousarray(vol, dtype=np.uint8)
+    n = header(vol)["b"] >> lod
+    out = np.empty((max(n, 1),) * 3, dtype=np.uint32)
+    return int(_load().oracle_decode_brick(vol.ctypes.data, vol.size, brick_id, lod, out.ctypes.data))
+
+
+def decode_volume(vol: np.ndarray) -> np.ndarray:
+    vol = np.ascontiguousarray(vol, dtype=np.uint8)
+    dx, dy, dz = header(vol)["dims"]
+    out = np.empty((dz, dy, dx), dtype=np.uint32)
+    rc = _load().oracle_decode_volume(vol.ctypes.data, vol.size, out.ctypes.data)
+    if rc:
+        raise OracleError(rc, "decode volume")
+    return out
+
+
+def brick_nodes(vol: np.ndarray, brick_id: int) -> np.ndarray:
+    vol = np.ascontiguousarray(vol, dtype=np.uint8)
+    b = header(vol)["b"]
+    cap = sum(8 ** l for l in range(b.bit_length()))
+    out = np.zeros(cap, dtype=NODE_DTYPE)
+    n = ctypes.c_uint32()
+    rc = _load().oracle_brick_nodes(vol.ctypes.data, vol.size, brick_id, out.ctypes.data, cap, ctypes.byref(n))
+    if rc:
+        raise OracleError(rc, f"nodes of brick {brick_id}")
+    return out[: n.value]
+
+
+def brick_symbols(vol: np.ndarray, brick_id: int) -> np.ndarray:
+    vol = np.ascontiguousarray(vol, dtype=np.uint8)
+    S = ctypes.c_uint32()
+    rc = _load().oracle_brick_symbols(vol.ctypes.data, vol.size, brick_id, None, 0, ctypes.byref(S))
+    if rc:
+        raise OracleError(rc, "symbols")
+    out = np.zeros(S.value, dtype=np.uint8)
+    _load().oracle_brick_symbols(vol.ctypes.data, vol.size, brick_id, out.ctypes.data, S.value, ctypes.byref(S))
+    return out
+
+
+def brick_record(vol: np.ndarray, brick_id: int) -> dict:
+    """Header fields and palette of one brick record."""
+    h = header(vol)
+    starts_off = 128
+    a = int(np.frombuffer(vol[starts_off + 4 * brick_id: starts_off + 4 * brick_id + 8].tobytes(), "<u4")[0])
+    e = int(np.frombuffer(vol[starts_off + 4 * brick_id: starts_off + 4 * brick_id + 8].tobytes(), "<u4")[1])
+    rec_off = (128 + 4 * (h["n_bricks"] + 1) + 15) & ~15
+    r = vol[rec_off + 4 * a: rec_off + 4 * e]
+    w = np.frombuffer(r.tobytes(), dtype="<u4")
+    n_pal, S, cb, nd = (int(x) for x in w[:4])
+    ns = min(S, 32) if h["coder"] == CODER_RANS else 0
+    pal = w[4 + ns: 4 + ns + n_pal].copy()
+    return {"n_pal": n_pal, "n_sym": S, "coded_bytes": cb, "n_delta": nd, "palette": pal, "words": e - a,
+            "offset_words": a}
+
+
+def delta_nibbles(delta: int) -> list:
+    out = (ctypes.c_uint8 * 16)()
+    n = _load().oracle_delta_nibbles(delta, out)
+    return [int(out[i]) for i in range(n)]
+
+
+def rans_quantize(counts) -> np.ndarray:
+    c = np.ascontiguousarray(np.asarray(counts, dtype=np.uint64))
+    f = np.zeros(16, dtype=np.uint32)
+    rc = _load().oracle_rans_quantize(c.ctypes.data, f.ctypes.data)
+    if rc:
+        raise OracleError(rc, "quantize")
+    return f
+
+
+def pack_single_brick(log2b: int, sym, palette, n_delta: int, op_mask: int = OP_ALL, coder: int = CODER_PLAIN,
+                      flags: int = 0) -> np.ndarray:
+    """A one-brick volume whose record holds exactly the given symbols and palette."""
+    s = np.ascontiguousarray(np.asarray(sym, dtype=np.uint8))
+    p = np.ascontiguousarray(np.asarray(palette, dtype=np.uint32))
+    ptr, size = ctypes.c_void_p(), ctypes.c_size_t()
+    rc = _load().oracle_pack_single_brick(log2b, op_mask, coder, flags, s.ctypes.data, s.size,
+                                          p.ctypes.data if p.size else None, p.size, n_delta, ctypes.byref(ptr),
+                                          ctypes.byref(size))
+    if rc:
+        raise OracleError(rc, "pack")
+    return _take(ptr, size.value)

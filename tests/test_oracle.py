@@ -1,0 +1,377 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU needed).
+
+- lossless round trip (the encoding is lossless: Results "CSGV results", Methods "Compressed
+  segmentation volumes"), for every brick size, coder, operation subset and padding case;
+- hand-derived operation streams for small bricks (tests/golden/), from the operation
+  definitions (Supplementary Fig. "CSGV ablation" caption) and the readings stated there;
+- palette = the brick's distinct labels with unlimited delta (Methods, "Compressed segmentation
+  volumes": unlimited back references eliminate palette duplicates);
+- stop bits mark constant subtrees (Results, "CSGV results");
+- coarse levels of detail = mode pyramid recomputed from V with numpy (Results, "Ray marching");
+- delta entries: closed-form counts, octal digits, at most 7 entries for 64^3 bricks (Methods);
+- brute force: every legal operation choice on tiny bricks decodes to V;
+- rANS: round trip and size within 1% (+ state overhead) of the ideal code length;
+- corruption rules: each malformed stream is rejected.
+"""
+import math
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from streams import (OP_ADV, OP_DELTA, OP_LAST, OP_NX, OP_NY, OP_PARENT, StreamEnumerator, golden_volume,
+                     load_golden, mode_pyramid, morton_to_xyz, octal_digits, padded_brick, uniform_pyramid)
+
+ABLATION_MASKS = [  # palette advance + each prefix of (parent, x, y, z, last, delta)
+    (1 << OP_ADV),
+    (1 << OP_ADV) | 0b1,
+    (1 << OP_ADV) | 0b11,
+    (1 << OP_ADV) | 0b111,
+    (1 << OP_ADV) | 0b1111,
+    (1 << OP_ADV) | 0b1111 | (1 << OP_LAST),
+    0x7F,
+]
+
+
+@pytest.fixture(scope="module")
+def small_volume():
+    return synth.fill(synth.small(dims=(40, 24, 20), seed=7, diameter=10.0, bg=0.2))
+
+
+# ---------------------------------------------------------------- round trip (lossless)
+
+@pytest.mark.parametrize("log2b", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("coder", [oracle.CODER_PLAIN, oracle.CODER_RANS])
+def test_roundtrip_lossless(small_volume, log2b, coder):
+    enc = oracle.encode_volume(small_volume, log2b, coder=coder)
+    assert np.array_equal(oracle.decode_volume(enc), small_volume)
+
+
+@pytest.mark.parametrize("mask", ABLATION_MASKS)
+def test_roundtrip_every_operation_prefix(small_volume, mask):
+    for coder in (oracle.CODER_PLAIN, oracle.CODER_RANS):
+        enc = oracle.encode_volume(small_volume, 3, op_mask=mask, coder=coder)
+        assert np.array_equal(oracle.decode_volume(enc), small_volume)
+        h = oracle.header(enc)
+        # no disabled operation appears in any brick
+        for bid in range(0, h["n_bricks"], 7):
+            ops = set(int(o) for o in oracle.brick_nodes(enc, bid)["op"])
+            assert all((mask >> o) & 1 for o in ops)
+
+
+def test_roundtrip_without_stop_bits(small_volume):
+    enc = oracle.encode_volume(small_volume, 3, flags=oracle.FLAG_NO_STOP)
+    assert np.array_equal(oracle.decode_volume(enc), small_volume)
+    nodes = oracle.brick_nodes(enc, 0)
+    assert (nodes["stop"] == 0).all()
+    assert len(nodes) == sum(8 ** l for l in range(4))  # every node of every level is emitted
+
+
+def test_roundtrip_ragged_and_degenerate():
+    rng = np.random.default_rng(3)
+    for dims in [(1, 1, 1), (3, 1, 2), (17, 9, 5), (33, 2, 31)]:
+        V = rng.integers(0, 4, size=dims[::-1], dtype=np.uint32) * np.uint32(0x9E3779B1)
+        for log2b in (1, 2, 3):
+            enc = oracle.encode_volume(V, log2b)
+            assert np.array_equal(oracle.decode_volume(enc), V)
+    # all-distinct labels (palette as long as the brick) and the full uint32 range
+    V = (np.arange(8 ** 3, dtype=np.uint64) * 2654435761 % (1 << 32)).astype(np.uint32).reshape(8, 8, 8)
+    V[0, 0, 0] = 0xFFFFFFFF
+    enc = oracle.encode_volume(V, 3, coder=oracle.CODER_RANS)
+    assert np.array_equal(oracle.decode_volume(enc), V)
+    assert oracle.brick_record(enc, 0)["n_pal"] == len(np.unique(V))
+
+
+def test_uniform_brick_is_one_symbol():
+    V = np.full((32, 32, 32), 123456789, dtype=np.uint32)
+    enc = oracle.encode_volume(V, 5)
+    sym = oracle.brick_symbols(enc, 0)
+    assert list(sym) == [OP_ADV | 8]
+    rec = oracle.brick_record(enc, 0)
+    assert list(rec["palette"]) == [123456789]
+
+
+# ---------------------------------------------------------------- hand-derived fixtures
+
+@pytest.mark.parametrize("name", ["brick4_xsplit_stop.txt", "brick4_x1_neighbours.txt", "brick2_corner.txt"])
+def test_golden_streams(name):
+    g = load_golden(name)
+    V = golden_volume(g)
+    enc = oracle.encode_volume(V, int(g["log2b"][0]))
+    assert [int(s) for s in oracle.brick_symbols(enc, 0)] == [int(s) for s in g["symbols"]]
+    assert [int(p) for p in oracle.brick_record(enc, 0)["palette"]] == [int(p) for p in g["palette"]]
+    assert np.array_equal(oracle.decode_volume(enc), V)
+    # the same stream packed by hand decodes to V too
+    packed = oracle.pack_single_brick(int(g["log2b"][0]), [int(s) for s in g["symbols"]],
+                                      [int(p) for p in g["palette"]], 0)
+    assert np.array_equal(oracle.decode_brick(packed, 0), V)
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_palette_is_distinct_labels_with_unlimited_delta(small_volume):
+    for log2b in (3, 4, 5):
+        enc = oracle.encode_volume(small_volume, log2b)
+        h = oracle.header(enc)
+        for bid in range(h["n_bricks"]):
+            pal = oracle.brick_record(enc, bid)["palette"]
+            brick = padded_brick(small_volume, 1 << log2b, bid)
+            assert len(pal) == len(set(pal.tolist())), "palette duplicate"
+            assert set(pal.tolist()) == set(np.unique(brick).tolist())
+
+
+def test_palette_without_delta_may_hold_duplicates(small_volume):
+    mask = 0x7F & ~(1 << OP_DELTA)
+    enc = oracle.encode_volume(small_volume, 4, op_mask=mask)
+    dup = 0
+    for bid in range(oracle.header(enc)["n_bricks"]):
+        pal = oracle.brick_record(enc, bid)["palette"].tolist()
+        brick = padded_brick(small_volume, 16, bid)
+        assert set(pal) == set(np.unique(brick).tolist())
+        dup += len(pal) - len(set(pal))
+    assert dup > 0  # the paper's motivation for unlimited delta
+
+
+def test_stop_bit_subtrees_are_uniform(small_volume):
+    for log2b in (3, 4):
+        b = 1 << log2b
+        enc = oracle.encode_volume(small_volume, log2b)
+        for bid in range(oracle.header(enc)["n_bricks"]):
+            brick = padded_brick(small_volume, b, bid)
+            uni = uniform_pyramid(brick)
+            for nd in oracle.brick_nodes(enc, bid):
+                l, m = int(nd["level"]), int(nd["morton"])
+                x, y, z = morton_to_xyz(m, l)
+                s = b >> l
+                sub = brick[z * s:(z + 1) * s, y * s:(y + 1) * s, x * s:(x + 1) * s]
+                if nd["stop"]:
+                    assert (sub == nd["label"]).all()
+                # the canonical encoder sets the stop bit exactly on constant non-finest nodes
+                assert bool(nd["stop"]) == (l < log2b and bool(uni[l][z, y, x]))
+
+
+def test_emitted_node_labels_are_the_mode_pyramid(small_volume):
+    enc = oracle.encode_volume(small_volume, 4)
+    for bid in range(oracle.header(enc)["n_bricks"]):
+        pyr = mode_pyramid(padded_brick(small_volume, 16, bid))
+        for nd in oracle.brick_nodes(enc, bid):
+            x, y, z = morton_to_xyz(int(nd["morton"]), int(nd["level"]))
+            assert int(nd["label"]) == int(pyr[int(nd["level"])][z, y, x])
+
+
+@pytest.mark.parametrize("coder", [oracle.CODER_PLAIN, oracle.CODER_RANS])
+def test_coarse_lod_is_mode_pyramid(small_volume, coder):
+    for log2b in (2, 3, 4, 5):
+        b = 1 << log2b
+        enc = oracle.encode_volume(small_volume, log2b, coder=coder)
+        for bid in range(oracle.header(enc)["n_bricks"]):
+            pyr = mode_pyramid(padded_brick(small_volume, b, bid))
+            for lod in range(log2b + 1):
+                assert np.array_equal(oracle.decode_brick(enc, bid, lod), pyr[log2b - lod])
+
+
+def test_morton_order_within_levels(small_volume):
+    enc = oracle.encode_volume(small_volume, 4)
+    nodes = oracle.brick_nodes(enc, 3)
+    for l in range(5):
+        ms = nodes["morton"][nodes["level"] == l]
+        assert (np.diff(ms.astype(np.int64)) > 0).all()
+    assert (np.diff(nodes["level"]) >= 0).all()
+
+
+# ---------------------------------------------------------------- delta entries
+
+def test_delta_entry_counts_closed_form():
+    worst = sum(8 ** l for l in range(7))  # nodes of a 64^3 brick: 299593
+    assert worst == 299593
+    for d in list(range(1, 5000)) + list(range(worst - 5000, worst + 1)):
+        e = oracle.delta_nibbles(d)
+        assert len(e) == math.ceil(d.bit_length() / 3)
+        assert [x & 7 for x in e] == octal_digits(d)  # payloads are the octal digits, MSB first
+        assert all(x & 8 for x in e[:-1]) and not (e[-1] & 8)
+        if d < 8:
+            assert len(e) == 1
+    assert len(oracle.delta_nibbles(worst)) == 7  # "7 entries for a 64^3 brick"
+    assert 7 * 4 < 32  # fewer bits than a duplicated 32-bit palette entry
+
+
+def test_delta_references_decode():
+    # a 2^3 brick whose stream uses deltas 2 and 3 explicitly (all ADV palette + back refs)
+    pal = [10, 20, 30]
+    sym = [OP_ADV]  # root = 10
+    sym += [OP_ADV, OP_ADV]  # voxels 0, 1 -> 20, 30 (palette now 10, 20, 30; k = 3)
+    sym += [OP_DELTA, 3]  # voxel 2 -> palette[3 - 3] = 10
+    sym += [OP_DELTA, 2]  # voxel 3 -> 20
+    sym += [OP_DELTA, 1]  # voxel 4 -> 30 (delta 1 is legal, same as last)
+    sym += [OP_LAST, OP_PARENT, OP_PARENT]  # voxels 5, 6, 7 -> 30, 10, 10
+    vol = oracle.pack_single_brick(1, sym, pal, 3)
+    got = oracle.decode_brick(vol, 0).reshape(-1)
+    assert got.tolist() == [20, 30, 10, 20, 30, 30, 10, 10]
+
+
+# ---------------------------------------------------------------- brute force
+
+def _tiny_bricks():
+    rng = np.random.default_rng(11)
+    out = []
+    for b in (2, 4):
+        for n_labels in (1, 2, 3):
+            for _ in range(3):
+                B = rng.integers(0, n_labels, size=(b, b, b)).astype(np.uint32) + 1
+                if b == 4:  # blocky 4^3 bricks so that stop bits and neighbours occur
+                    B = np.repeat(np.repeat(np.repeat(rng.integers(1, n_labels + 1, size=(2, 2, 2)), 2, 0), 2, 1), 2, 2)
+                    B = B.astype(np.uint32)
+                    B[rng.integers(0, 4), rng.integers(0, 4), rng.integers(0, 4)] = rng.integers(1, n_labels + 1)
+                out.append(B)
+    return out
+
+
+@pytest.mark.parametrize("coder", [oracle.CODER_PLAIN, oracle.CODER_RANS])
+def test_brute_force_every_legal_choice_decodes(coder):
+    rng = random.Random(5)
+    total = 0
+    for B in _tiny_bricks():
+        L = B.shape[0].bit_length() - 1
+        en = StreamEnumerator(B)
+        streams = en.count_and_enumerate(limit=3000) if B.shape[0] == 2 else None
+        if streams is None:
+            streams = [en.sample(rng) for _ in range(300)]
+        for sym, pal, nd in streams:
+            vol = oracle.pack_single_brick(L, sym, pal, nd, coder=coder)
+            assert np.array_equal(oracle.decode_brick(vol, 0), B)
+            total += 1
+    assert total > 2000
+
+
+def test_brute_force_operation_subsets():
+    rng = random.Random(6)
+    for B in _tiny_bricks()[9:]:
+        for mask in ABLATION_MASKS:
+            en = StreamEnumerator(B, op_mask=mask)
+            for _ in range(40):
+                sym, pal, nd = en.sample(rng)
+                vol = oracle.pack_single_brick(2, sym, pal, nd, op_mask=mask)
+                assert np.array_equal(oracle.decode_brick(vol, 0), B)
+
+
+def test_enumerator_canonical_choice_matches_encoder():
+    for B in _tiny_bricks():
+        L = B.shape[0].bit_length() - 1
+        sym, pal, nd = StreamEnumerator(B).canonical_first()
+        enc = oracle.encode_volume(B, L)
+        assert list(oracle.brick_symbols(enc, 0)) == sym
+        assert oracle.brick_record(enc, 0)["palette"].tolist() == pal
+
+
+# ---------------------------------------------------------------- rANS
+
+def test_rans_quantize_invariants():
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        counts = rng.integers(0, 1000, size=16) * (rng.random(16) < 0.7)
+        counts[rng.integers(0, 16)] += 1
+        f = oracle.rans_quantize(counts)
+        assert f.sum() == 4096
+        assert ((counts > 0) == (f > 0)).all()
+    f = oracle.rans_quantize([0] * 4 + [5] + [0] * 11)
+    assert f[4] == 4096 and f.sum() == 4096
+
+
+def test_rans_size_within_entropy_bound(small_volume):
+    enc = oracle.encode_volume(small_volume, 4, coder=oracle.CODER_RANS)
+    h = oracle.header(enc)
+    f = np.array(h["freq"], dtype=np.float64)
+    for bid in range(h["n_bricks"]):
+        sym = oracle.brick_symbols(enc, bid)
+        ideal_bits = float(-np.log2(f[sym] / 4096.0).sum())
+        rec = oracle.brick_record(enc, bid)
+        coded_bits = 8 * rec["coded_bytes"]
+        n_states = min(len(sym), 32)
+        # the final states carry up to 32 bits each; words are whole 16-bit units
+        assert coded_bits <= 1.01 * ideal_bits + 32 * n_states + 16
+        assert coded_bits + 32 * n_states >= ideal_bits - 1e-6
+
+
+def test_rans_many_lengths_roundtrip():
+    rng = random.Random(9)
+    for S in list(range(1, 80)) + [127, 128, 129, 1000]:
+        # a legal stream: root ADV then PARENT everywhere on a 2^3 .. grid is too short; use a
+        # single 2^3 brick plus DELTA digits to reach arbitrary lengths is not legal either, so
+        # check the coder alone through pack + symbol read-back
+        sym = [rng.choice([0, 0, 0, 4, 5, 8, 12, 6, 1]) for _ in range(S)]
+        vol = oracle.pack_single_brick(1, sym, [1], 0, coder=oracle.CODER_RANS)
+        assert list(oracle.brick_symbols(vol, 0)) == sym
+
+
+# ---------------------------------------------------------------- corruption rules
+
+def _golden_stream():
+    g = load_golden("brick4_x1_neighbours.txt")
+    return [int(s) for s in g["symbols"]], [int(p) for p in g["palette"]]
+
+
+def _status(sym, pal, nd=0, mask=0x7F, flags=0, coder=oracle.CODER_PLAIN, lod=0):
+    vol = oracle.pack_single_brick(2, sym, pal, nd, op_mask=mask, flags=flags, coder=coder)
+    return oracle.decode_brick_status(vol, 0, lod)
+
+
+@pytest.mark.parametrize("coder", [oracle.CODER_PLAIN, oracle.CODER_RANS])
+def test_corrupt_streams_rejected(coder):
+    sym, pal = _golden_stream()
+    C = oracle.ERR_CORRUPT
+    assert _status(sym, pal, coder=coder) == 0
+    bad = []
+    s = list(sym); s[5] = 7; bad.append((s, pal, 0, 0x7F, 0))                       # reserved op 7
+    bad.append((sym, pal, 0, 0x7F & ~(1 << OP_NY), 0))                              # disabled op used
+    s = list(sym); s[0] = OP_PARENT; bad.append((s, pal, 0, 0x7F, 0))               # parent at the root
+    s = list(sym); s[0] = OP_LAST; bad.append((s, pal, 0, 0x7F, 0))                 # last with empty palette
+    s = list(sym); s[12] = OP_NY; bad.append((s, pal, 0, 0x7F, 0))                  # (1,1,0): y odd -> no NY
+    s = list(sym); s[10] = OP_NX; bad.append((s, pal, 0, 0x7F, 0))                  # (1,0,0): x odd -> no NX
+    s = list(sym); s[2] = OP_ADV; bad.append((s, pal, 0, 0x7F, 0))                  # ADV beyond the palette
+    bad.append((sym, pal + [7], 0, 0x7F, 0))                                        # palette entry unused
+    s = list(sym); s[10] = OP_LAST | 8; bad.append((s, pal, 0, 0x7F, 0))            # stop bit at finest level
+    bad.append((sym + [0], pal, 0, 0x7F, 0))                                        # trailing symbol
+    bad.append((sym[:-1], pal, 0, 0x7F, 0))                                         # missing symbol
+    bad.append((sym, pal, 1, 0x7F, 0))                                              # delta count mismatch
+    s = list(sym[:10]) + [OP_DELTA, 3] + sym[11:]; bad.append((s, pal, 1, 0x7F, 0)) # delta 3 > k = 2
+    s = list(sym[:10]) + [OP_DELTA, 0] + sym[11:]; bad.append((s, pal, 1, 0x7F, 0)) # delta 0
+    s = list(sym[:10]) + [OP_DELTA] + [8] * 7 + [1] + sym[11:]; bad.append((s, pal, 1, 0x7F, 0))  # 8 entries
+    s = list(sym[:-1]) + [OP_DELTA, 9]; bad.append((s, pal, 1, 0x7F, 0))            # delta runs off the end
+    bad.append((sym, pal, 0, 0x7F, oracle.FLAG_NO_STOP))                            # stop bit while disabled
+    for s, p, nd, mask, flags in bad:
+        assert _status(s, p, nd, mask, flags, coder) == C, (s, p, nd, mask, flags)
+
+
+def test_long_legal_delta_chain_accepted():
+    sym, pal = _golden_stream()
+    # replace the LAST at (1,0,0) (palette index 1 = k - 1) by delta 1 written with 7 entries:
+    # leading zero groups are not minimal but legal
+    s = list(sym[:10]) + [OP_DELTA] + [8] * 6 + [1] + sym[11:]
+    assert _status(s, pal, 1) == 0
+
+
+def test_volume_format_checks(small_volume):
+    enc = oracle.encode_volume(small_volume, 3)
+    assert oracle.decode_brick_status(enc, 0) == 0
+    bad = enc.copy(); bad[0] ^= 1
+    assert oracle.decode_brick_status(bad, 0) == oracle.ERR_FORMAT
+    bad = enc.copy(); bad[4] = 2
+    assert oracle.decode_brick_status(bad, 0) == oracle.ERR_FORMAT
+    bad = enc.copy(); bad[36] ^= 1  # n_bricks inconsistent with dims
+    assert oracle.decode_brick_status(bad, 0) == oracle.ERR_FORMAT
+    bad = enc.copy(); bad[128 + 4] ^= 4  # start of brick 1 moved: both neighbours' extents break
+    assert oracle.decode_brick_status(bad, 0) == oracle.ERR_FORMAT
+    assert oracle.decode_brick_status(enc, 10 ** 6) == oracle.ERR_ARG
+
+
+# ---------------------------------------------------------------- compression sanity
+
+def test_compression_rate_in_paper_band():
+    V = synth.fill(synth.c1())
+    enc = oracle.encode_volume(V, 5, coder=oracle.CODER_RANS)
+    ratio = enc.size / V.nbytes
+    # the paper reports 1-3 % typical and up to ~5 % for dense 32-bit data; a synthetic volume with
+    # 40 cells must land well inside (0.05 %, 10 %)
+    assert 0.0005 < ratio < 0.10, ratio
