@@ -1,0 +1,334 @@
+#!/usr/bin/env python3
+"""Benchmark: brick-parallel decode of a CSGV-compressed 512^3 segmentation volume (32^3 bricks).
+
+One step = decode every brick of the volume (4096 bricks, 134M voxels) from the device-resident
+encoding into a 512 MiB uint32 brick cache, with the batched persistent decoder. Prints one JSON
+line (rank 0). `--impl reference` times the CPU oracle on the host cores instead (bounded sample).
+
+Timing: W untimed warm-up steps; K timed steps, each a CUDA-event pair on the launching stream
+around the decode; the L2 is flushed (256 MiB write) before every step, outside the event pair;
+barrier + synchronize on both sides of the timed region; max over ranks. Clocks are sampled with
+nvidia-smi while the timed steps run.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+B_LOG2 = 5
+CODER_RANS = 1
+METRIC = "decoded Gvoxel/s"
+UNIT = "Gvoxel/s"
+WORKLOAD = "512^3 uint32 Voronoi volume (~20k cells, 10% background), 32^3 bricks (4096), rANS, all operations"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def make_workload():
+    import synth
+    import paper_2609_36898_gb300 as vc
+    spec = synth.c2()
+    t = time.time()
+    V = synth.fill(spec)
+    t_gen = time.time() - t
+    t = time.time()
+    enc = vc.vc_encode_volume(V, B_LOG2, op_mask=0x7F, coder=CODER_RANS)
+    t_enc = time.time() - t
+    return spec, V, enc, t_gen, t_enc
+
+
+def algorithmic_bytes(enc: np.ndarray, n_bricks: int, edge: int) -> int:
+    """Per launch: Brick Starts entry + record bytes + queue item (id + slot) + decoded labels."""
+    h = np.frombuffer(enc[:128].tobytes(), dtype="<u4")
+    records_words = int(h[28])
+    return 4 * n_bricks + 4 * records_words + 8 * n_bricks + 4 * edge ** 3 * n_bricks
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_src_hash: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "decode_batched_512cube_b32_rans.json")
+    try:
+        d = json.load(open(p))
+        if d.get("kernel_source_sha256") == kernel_src_hash:
+            return d.get("dram_bytes_per_launch_full_workload")
+    except Exception:
+        pass
+    return None
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("decode.cu", "vc_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2609_36898_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def oracle_rate(enc: np.ndarray, seconds: float, max_bricks: int):
+    """Single-threaded oracle decode on a bounded sample of the workload's bricks."""
+    import oracle
+    n_b = 0
+    t0 = time.perf_counter()
+    while n_b < max_bricks and time.perf_counter() - t0 < seconds:
+        oracle.decode_brick(enc, n_b % 4096, 0)
+        n_b += 1
+    dt = time.perf_counter() - t0
+    vox = n_b * (1 << (3 * B_LOG2))
+    return vox / dt / 1e9, n_b, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    spec, V, enc, _, _ = make_workload()
+    import oracle
+    oracle.build()
+    total_vox, total_t, nb = 0, 0.0, 0
+    for _ in range(args.warmup):
+        oracle.decode_brick(enc, 0, 0)
+    per_step = max(1.0, 20.0 / max(1, args.steps))
+    for _ in range(args.steps):
+        r, n_b, dt = oracle_rate(enc, per_step, 4096)
+        total_vox += n_b * 32 ** 3
+        total_t += dt
+        nb += n_b
+    value = total_vox / total_t / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total_t / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "bricks_per_step": 4096, "sample": "bounded"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{nb} bricks of the 512^3 volume, ~{per_step:.0f} s per step, single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    import paper_2609_36898_gb300 as vc
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec, V, enc, t_gen, t_enc = make_workload()
+    vol = vc.Volume(enc, device=local)
+    n = vol.n_bricks
+    e = vol.b
+    ids = torch.arange(n, dtype=torch.int32, device=dev)
+    cache = torch.empty(n * e ** 3, dtype=torch.int32, device=dev)
+    status = torch.zeros(vc.VC_STATUS_WORDS, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    mode = vc.MODES[args.mode]
+
+    def step():
+        vc.vc_decode_bricks(vol.handle, ids.data_ptr(), n, ids.data_ptr(), cache.data_ptr(), 0, mode,
+                            status.data_ptr(), stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    if int(status[0]) != 0:
+        raise RuntimeError(f"decode status {status.tolist()}")
+    # correctness spot check of the warm-up output against the generator (lossless)
+    got = cache[: e ** 3].cpu().numpy().view(np.uint32).reshape(e, e, e)
+    assert np.array_equal(got, V[:e, :e, :e]), "decoded brick 0 differs from the input volume"
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k)
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [s.elapsed_time(t) for s, t in zip(starts, ends)]
+    dev_s = sum(step_ms) / 1000.0
+    if world > 1:
+        t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dev_s = float(t.item())
+    if int(status[0]) != 0:
+        raise RuntimeError(f"decode status {status.tolist()}")
+    vox_per_step = n * e ** 3
+    value = world * vox_per_step * args.steps / dev_s / 1e9
+    algo = algorithmic_bytes(enc, n, e)
+    avg_launch_s = dev_s / args.steps
+    peak, peak_kind = measured_peak()
+    achieved = algo / avg_launch_s / 1e9
+    traffic = ncu_traffic(kernel_hash())
+
+    # other schedules on the same data (context): plain = one launch per brick, grid = one launch
+    modes = {}
+    for mname in ("plain", "grid", "batched"):
+        m = vc.MODES[mname]
+        reps = 2 if mname == "plain" else 5
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(3)
+            ev0.record(stream)
+            vc.vc_decode_bricks(vol.handle, ids.data_ptr(), n, ids.data_ptr(), cache.data_ptr(), 0, m,
+                                status.data_ptr(), stream.cuda_stream)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            tot += ev0.elapsed_time(ev1)
+        modes[mname] = vox_per_step * reps / (tot / 1000.0) / 1e9
+
+    # end to end through the host entry point: ids host->device, decode, labels device->host (pinned)
+    ids_h = torch.arange(n, dtype=torch.int32).numpy().view(np.uint32)
+    labels_h = torch.empty(n * e ** 3, dtype=torch.int32, pin_memory=True)
+    labels_np = labels_h.numpy().view(np.uint32)
+    e2e_steps = max(2, min(args.steps, 5))
+    vc.vc_decode_bricks_host(vol.handle, ids_h, 0, mode, labels_np, stream.cuda_stream)  # warm-up / allocation
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        st = vc.vc_decode_bricks_host(vol.handle, ids_h, 0, mode, labels_np, stream.cuda_stream)
+        if st != 0:
+            raise RuntimeError(f"host decode status {st}")
+    e2e_s = time.perf_counter() - t0
+    e2e_val = world * vox_per_step * e2e_steps / e2e_s / 1e9
+    assert np.array_equal(labels_np[: e ** 3].reshape(e, e, e), V[:e, :e, :e])
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            r, nb, dt = oracle_rate(enc, 15.0, 4096)
+            cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"first {nb} bricks of the same 512^3 volume decoded single-threaded in {dt:.1f} s"}
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * dev_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "bricks_per_step": n, "voxels_per_step": vox_per_step,
+                       "schedule": args.mode, "encoded_bytes": int(enc.size),
+                       "bits_per_voxel": 8.0 * enc.size / V.size, "l2": "flushed before every step (256 MiB write)",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": algo, "kernel": f"decode_batched_kernel<5,rans>"},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
+                    "d2h_bytes_per_step": 4 * n * e ** 3 + 4},
+            "gpu_launches": args.steps * (n if args.mode == "plain" else 1),
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+            "schedules_gvoxel_s": modes,
+            "wall_s_timed_region": wall,
+            "prep_s": {"generate": t_gen, "encode": t_enc},
+        }
+        print(json.dumps(out))
+    vol.release()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="batched", choices=["plain", "grid", "batched"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

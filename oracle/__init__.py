@@ -56,6 +56,9 @@ def _load():
         lib.oracle_rans_quantize.argtypes = [P, P]
         lib.oracle_pack_single_brick.argtypes = [U32, U32, U32, U32, P, U32, P, U32, U32, ctypes.POINTER(P),
                                                  ctypes.POINTER(SZ)]
+        lib.oracle_pack_bricks.argtypes = [U32, U32, U32, U32, U32, P, P, P, P, P, ctypes.POINTER(P),
+                                           ctypes.POINTER(SZ)]
+        lib.oracle_pack_bricks.restype = ctypes.c_int
         lib.oracle_free.argtypes = [P]
         for f in ("oracle_encode_volume", "oracle_decode_brick", "oracle_decode_volume", "oracle_brick_nodes",
                   "oracle_brick_symbols", "oracle_delta_nibbles", "oracle_rans_quantize", "oracle_pack_single_brick"):
@@ -190,4 +193,21 @@ def pack_single_brick(log2b: int, sym, palette, n_delta: int, op_mask: int = OP_
                                           ctypes.byref(size))
     if rc:
         raise OracleError(rc, "pack")
+    return _take(ptr, size.value)
+
+
+def pack_bricks(log2b: int, streams, op_mask: int = OP_ALL, coder: int = CODER_PLAIN, flags: int = 0) -> np.ndarray:
+    """A volume of len(streams) bricks along x; streams = [(symbols, palette, n_delta), ...]."""
+    sym = np.ascontiguousarray(np.concatenate([np.asarray(s, dtype=np.uint8) for s, _, _ in streams]))
+    S = np.array([len(s) for s, _, _ in streams], dtype=np.uint32)
+    pals = [np.asarray(p, dtype=np.uint32) for _, p, _ in streams]
+    pal = np.ascontiguousarray(np.concatenate(pals)) if sum(p.size for p in pals) else np.zeros(1, np.uint32)
+    npal = np.array([p.size for p in pals], dtype=np.uint32)
+    nd = np.array([d for _, _, d in streams], dtype=np.uint32)
+    ptr, size = ctypes.c_void_p(), ctypes.c_size_t()
+    rc = _load().oracle_pack_bricks(log2b, op_mask, coder, flags, len(streams), sym.ctypes.data, S.ctypes.data,
+                                    pal.ctypes.data, npal.ctypes.data, nd.ctypes.data, ctypes.byref(ptr),
+                                    ctypes.byref(size))
+    if rc:
+        raise OracleError(rc, "pack_bricks")
     return _take(ptr, size.value)

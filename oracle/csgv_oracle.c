@@ -800,3 +800,96 @@ int oracle_pack_single_brick(uint32_t log2b, uint32_t op_mask, uint32_t coder, u
   *out_size = size;
   return 0;
 }
+
+/* Assemble a volume of n bricks along x (dims b*n x b x b) from caller-made symbol streams and
+ * palettes, concatenated: brick i has S_each[i] symbols, npal_each[i] palette entries and
+ * nd_each[i] delta operations. The rANS table is quantised from all bricks' symbols. */
+int oracle_pack_bricks(uint32_t log2b, uint32_t op_mask, uint32_t coder, uint32_t flags, uint32_t n,
+                       const uint8_t* sym, const uint32_t* S_each, const uint32_t* pal, const uint32_t* npal_each,
+                       const uint32_t* nd_each, uint8_t** out_bytes, size_t* out_size) {
+  if (log2b < 1 || log2b > 6 || n == 0) return O_ERR_ARG;
+  uint64_t counts[16] = {0};
+  uint64_t total_sym = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (S_each[i] == 0) return O_ERR_ARG;
+    for (uint32_t k = 0; k < S_each[i]; ++k) {
+      if (sym[total_sym + k] > 15) return O_ERR_ARG;
+      counts[sym[total_sym + k]]++;
+    }
+    total_sym += S_each[i];
+  }
+  uint32_t freq[16] = {0};
+  if (coder == CODER_RANS) oracle_rans_quantize(counts, freq);
+  uint8_t** rec = (uint8_t**)calloc(n, sizeof(uint8_t*));
+  uint32_t* rw = (uint32_t*)calloc(n, sizeof(uint32_t));
+  if (!rec || !rw) { free(rec); free(rw); return O_ERR_OOM; }
+  int rc = 0;
+  uint64_t so = 0, po = 0, words_total = 0;
+  uint32_t max_pal = 0, max_sym = 0;
+  for (uint32_t i = 0; i < n && !rc; ++i) {
+    const uint8_t* s = sym + so;
+    const uint32_t* p = pal + po;
+    uint32_t S = S_each[i], np = npal_each[i];
+    uint32_t ns = 0, cb;
+    uint32_t states[RANS_LANES];
+    uint16_t* words = NULL;
+    if (coder == CODER_RANS) {
+      words = (uint16_t*)malloc(((size_t)S + 1) * sizeof(uint16_t));
+      if (!words) { rc = O_ERR_OOM; break; }
+      long nw = rans_encode(s, S, freq, states, words);
+      if (nw < 0) { free(words); rc = O_ERR_ARG; break; }
+      cb = (uint32_t)(2 * nw);
+      ns = S < RANS_LANES ? S : RANS_LANES;
+    } else {
+      cb = (S + 1) / 2;
+    }
+    size_t bytes = 16 + 4 * (size_t)ns + 4 * (size_t)np + cb;
+    size_t padded = (bytes + 15) & ~(size_t)15;
+    uint8_t* r = (uint8_t*)calloc(padded, 1);
+    if (!r) { free(words); rc = O_ERR_OOM; break; }
+    wr32(r, np); wr32(r + 4, S); wr32(r + 8, cb); wr32(r + 12, nd_each[i]);
+    uint8_t* q = r + 16;
+    for (uint32_t l = 0; l < ns; ++l, q += 4) wr32(q, states[l]);
+    for (uint32_t k = 0; k < np; ++k, q += 4) wr32(q, p[k]);
+    if (coder == CODER_RANS) {
+      for (uint32_t w = 0; w < cb / 2; ++w) { q[2 * w] = (uint8_t)words[w]; q[2 * w + 1] = (uint8_t)(words[w] >> 8); }
+    } else {
+      for (uint32_t k = 0; k < S; ++k) q[k / 2] |= (uint8_t)((s[k] & 15u) << (4 * (k & 1)));
+    }
+    free(words);
+    rec[i] = r;
+    rw[i] = (uint32_t)(padded / 4);
+    words_total += rw[i];
+    if (np > max_pal) max_pal = np;
+    if (S > max_sym) max_sym = S;
+    so += S;
+    po += np;
+  }
+  if (!rc) {
+    size_t rec_off = (O_HEADER_BYTES + 4 * ((size_t)n + 1) + 15) & ~(size_t)15;
+    size_t size = rec_off + 4 * (size_t)words_total;
+    uint8_t* o = (uint8_t*)calloc(size, 1);
+    if (!o) rc = O_ERR_OOM;
+    else {
+      uint32_t b = 1u << log2b;
+      wr32(o + 0, O_MAGIC); wr32(o + 4, O_VERSION);
+      wr32(o + 8, b * n); wr32(o + 12, b); wr32(o + 16, b);
+      wr32(o + 20, log2b); wr32(o + 24, op_mask); wr32(o + 28, coder); wr32(o + 32, flags);
+      wr32(o + 36, n); wr32(o + 40, max_pal); wr32(o + 44, max_sym);
+      for (int s = 0; s < 16; ++s) wr32(o + 48 + 4 * s, freq[s]);
+      wr32(o + 112, (uint32_t)words_total);
+      uint32_t acc = 0;
+      for (uint32_t i = 0; i < n; ++i) {
+        wr32(o + O_HEADER_BYTES + 4 * (size_t)i, acc);
+        memcpy(o + rec_off + 4 * (size_t)acc, rec[i], 4 * (size_t)rw[i]);
+        acc += rw[i];
+      }
+      wr32(o + O_HEADER_BYTES + 4 * (size_t)n, acc);
+      *out_bytes = o;
+      *out_size = size;
+    }
+  }
+  for (uint32_t i = 0; i < n; ++i) free(rec[i]);
+  free(rec); free(rw);
+  return rc;
+}

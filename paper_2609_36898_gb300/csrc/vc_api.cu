@@ -1,0 +1,276 @@
+// Host side of the C ABI: volume loading and validation, decode dispatch, release.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "vc_internal.h"
+
+using namespace vc;
+
+namespace {
+
+inline uint32_t le32(const uint8_t* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+void free_volume(Volume* v) {
+  if (!v) return;
+  DeviceGuard g(v->device);
+  cudaDeviceSynchronize();
+  cudaFree(v->d_file);
+  cudaFree(v->d_tables);
+  cudaFree(v->d_host_ids);
+  cudaFree(v->d_host_slots);
+  cudaFree(v->d_host_cache);
+  cudaFree(v->d_host_status);
+  v->kind = 0;
+  delete v;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vc_status_string(vc_status s) {
+  switch (s) {
+    case VC_OK: return "ok";
+    case VC_ERR_ARG: return "invalid argument";
+    case VC_ERR_FORMAT: return "invalid volume format";
+    case VC_ERR_OOM: return "out of memory";
+    case VC_ERR_CUDA: return "CUDA error";
+    case VC_ERR_CORRUPT: return "corrupt brick record";
+    case VC_ERR_TIMEOUT: return "device wait timed out";
+    case VC_ERR_BUSY: return "busy";
+    case VC_ERR_UNSUPPORTED: return "unsupported by this build";
+    default: return "unknown status";
+  }
+}
+
+vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, void* cuda_stream, vc_volume** out) {
+  if (!out) return VC_ERR_ARG;
+  *out = nullptr;
+  if (!host_bytes) return VC_ERR_ARG;
+  const uint8_t* p = static_cast<const uint8_t*>(host_bytes);
+  if (nbytes < kHeaderBytes) return VC_ERR_FORMAT;
+  if (le32(p) != kMagic || le32(p + 4) != kVersion) return VC_ERR_FORMAT;
+  uint32_t dims[3] = {le32(p + 8), le32(p + 12), le32(p + 16)};
+  const uint32_t L = le32(p + 20), op_mask = le32(p + 24), coder = le32(p + 28), flags = le32(p + 32);
+  const uint32_t n_bricks = le32(p + 36), hdr_max_pal = le32(p + 40), hdr_max_sym = le32(p + 44);
+  uint32_t freq[16];
+  for (int s = 0; s < 16; ++s) freq[s] = le32(p + 48 + 4 * s);
+  const uint32_t records_words = le32(p + 112);
+  if (L < 1 || L > 6) return VC_ERR_FORMAT;
+  if (!(op_mask & (1u << 4)) || (op_mask & ~0x7Fu)) return VC_ERR_FORMAT;
+  if (coder > 1 || (flags & ~kFlagNoStop)) return VC_ERR_FORMAT;
+  const uint32_t b = 1u << L;
+  uint32_t nb[3];
+  uint64_t nbt = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (dims[a] == 0) return VC_ERR_FORMAT;
+    nb[a] = (dims[a] + b - 1) / b;
+    nbt *= nb[a];
+  }
+  if (nbt != n_bricks) return VC_ERR_FORMAT;
+  if (coder == 1) {
+    uint32_t sum = 0;
+    for (int s = 0; s < 16; ++s) sum += freq[s];
+    if (sum != kRansM) return VC_ERR_FORMAT;
+  }
+  const size_t starts_bytes = 4 * ((size_t)n_bricks + 1);
+  const size_t rec_off = (kHeaderBytes + starts_bytes + 15) & ~(size_t)15;
+  if (nbytes < rec_off + 4 * (size_t)records_words) return VC_ERR_FORMAT;
+  // Brick Starts and every record's sizes
+  const uint8_t* st = p + kHeaderBytes;
+  const uint8_t* rec = p + rec_off;
+  uint32_t max_pal = 0, max_sym = 0, max_delta = 0, max_words = 0;
+  uint32_t prev = le32(st);
+  if (prev != 0) return VC_ERR_FORMAT;
+  for (uint32_t i = 0; i < n_bricks; ++i) {
+    const uint32_t a = le32(st + 4 * (size_t)i), e = le32(st + 4 * ((size_t)i + 1));
+    if (e < a || e > records_words || (a & 3u) || (e & 3u) || e - a < 4) return VC_ERR_FORMAT;
+    const uint8_t* r = rec + 4 * (size_t)a;
+    const uint32_t n_pal = le32(r), S = le32(r + 4), cb = le32(r + 8), nd = le32(r + 12);
+    if (S == 0) return VC_ERR_FORMAT;
+    const uint64_t ns = coder == 1 ? std::min<uint32_t>(S, kRansLanes) : 0;
+    const uint64_t need = 16 + 4 * ns + 4 * (uint64_t)n_pal + cb;
+    if (((need + 15) & ~(uint64_t)15) != 4 * (uint64_t)(e - a)) return VC_ERR_FORMAT;
+    if (coder == 0 && cb != (S + 1) / 2) return VC_ERR_FORMAT;
+    if (coder == 1 && (cb & 1u)) return VC_ERR_FORMAT;
+    if (nd > S) return VC_ERR_FORMAT;
+    max_pal = std::max(max_pal, n_pal);
+    max_sym = std::max(max_sym, S);
+    max_delta = std::max(max_delta, nd);
+    max_words = std::max(max_words, e - a);
+  }
+  if (le32(st + 4 * (size_t)n_bricks) != records_words) return VC_ERR_FORMAT;
+  if (max_pal > hdr_max_pal || max_sym > hdr_max_sym) return VC_ERR_FORMAT;
+  if (max_pal > kMaxIdx16) return VC_ERR_UNSUPPORTED;  // palette indices are kept in 16 bits
+
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return VC_ERR_ARG;
+  DeviceGuard g(device);
+  SmemLayout sl;
+  vc_status rc = compute_layout(L, coder, max_sym, max_pal, max_delta, max_words, device, &sl);
+  if (rc != VC_OK) return rc;
+
+  Volume* v = new (std::nothrow) Volume();
+  if (!v) return VC_ERR_OOM;
+  v->kind = kHandleVolume;
+  v->device = device;
+  for (int a = 0; a < 3; ++a) { v->dims[a] = dims[a]; v->nb[a] = nb[a]; }
+  v->L = L; v->op_mask = op_mask; v->coder = coder; v->flags = flags; v->n_bricks = n_bricks;
+  v->max_pal = max_pal; v->max_sym = max_sym; v->max_delta = max_delta; v->max_rec_words = max_words;
+  v->encoded_bytes = nbytes;
+  const size_t file_bytes = rec_off + 4 * (size_t)records_words;
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaMalloc(&v->d_file, file_bytes) != cudaSuccess) { cudaGetLastError(); delete v; return VC_ERR_OOM; }
+  if (cudaMalloc(&v->d_tables, 4096 + 64 * 4) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(v->d_file);
+    delete v;
+    return VC_ERR_OOM;
+  }
+  v->device_bytes = file_bytes + 4096 + 64 * 4;
+  // rANS tables: slot -> symbol, then freq[16] and cum[17]
+  std::vector<uint8_t> tab(4096 + 64 * 4, 0);
+  if (coder == 1) {
+    uint32_t cum = 0;
+    for (int s = 0; s < 16; ++s) {
+      for (uint32_t k = 0; k < freq[s]; ++k) tab[cum + k] = (uint8_t)s;
+      cum += freq[s];
+    }
+    uint32_t fc[33];
+    fc[16] = 0;
+    for (int s = 0; s < 16; ++s) { fc[s] = freq[s]; fc[17 + s] = fc[16 + s] + freq[s]; }
+    std::memcpy(tab.data() + 4096, fc, sizeof(fc));
+  }
+  bool ok = cudaMemcpyAsync(v->d_file, p, file_bytes, cudaMemcpyHostToDevice, stream) == cudaSuccess &&
+            cudaMemcpyAsync(v->d_tables, tab.data(), tab.size(), cudaMemcpyHostToDevice, stream) == cudaSuccess &&
+            cudaStreamSynchronize(stream) == cudaSuccess;
+  if (!ok) { free_volume(v); return VC_ERR_CUDA; }
+  v->dv.records = reinterpret_cast<const uint32_t*>(v->d_file + rec_off);
+  v->dv.starts = reinterpret_cast<const uint32_t*>(v->d_file + kHeaderBytes);
+  v->dv.rans_sym = v->d_tables;
+  v->dv.rans_fc = reinterpret_cast<const uint32_t*>(v->d_tables + 4096);
+  v->dv.n_bricks = n_bricks;
+  v->dv.L = L;
+  v->dv.op_mask = op_mask;
+  v->dv.coder = coder;
+  v->dv.flags = flags;
+  v->dv.sm = sl;
+  *out = reinterpret_cast<vc_volume*>(v);
+  return VC_OK;
+}
+
+vc_status vc_volume_info_get(const vc_volume* vol, vc_volume_info* info) {
+  const Volume* v = reinterpret_cast<const Volume*>(vol);
+  if (!v || !info || v->kind != kHandleVolume) return VC_ERR_ARG;
+  std::memset(info, 0, sizeof(*info));
+  for (int a = 0; a < 3; ++a) { info->dims[a] = v->dims[a]; info->bricks_per_axis[a] = v->nb[a]; }
+  info->brick_size = 1u << v->L;
+  info->log2b = v->L;
+  info->n_bricks = v->n_bricks;
+  info->op_mask = v->op_mask;
+  info->coder = v->coder;
+  info->flags = v->flags;
+  info->max_pal = v->max_pal;
+  info->max_sym = v->max_sym;
+  info->max_delta = v->max_delta;
+  info->encoded_bytes = v->encoded_bytes;
+  info->device_bytes = v->device_bytes;
+  info->smem_bytes = v->dv.sm.total;
+  info->device = (uint32_t)v->device;
+  return VC_OK;
+}
+
+vc_status vc_decode_bricks(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, const uint32_t* cache_slots,
+                           uint32_t* cache, uint32_t lod, uint32_t mode, int32_t* status_dev, void* cuda_stream) {
+  Volume* v = reinterpret_cast<Volume*>(vol);
+  if (!v || v->kind != kHandleVolume) return VC_ERR_ARG;
+  if (n == 0) return VC_OK;
+  if (!brick_ids || !cache_slots || !cache || !status_dev) return VC_ERR_ARG;
+  if (lod > v->L || mode > VC_MODE_BATCHED) return VC_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(cache) & 15u) return VC_ERR_ARG;
+  DeviceGuard g(v->device);
+  return launch_decode(*v, brick_ids, n, cache_slots, cache, lod, mode, status_dev,
+                       static_cast<cudaStream_t>(cuda_stream));
+}
+
+vc_status vc_decode_bricks_host(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, uint32_t lod, uint32_t mode,
+                                uint32_t* labels_out, int32_t* status_out, void* cuda_stream) {
+  Volume* v = reinterpret_cast<Volume*>(vol);
+  if (!v || v->kind != kHandleVolume || !status_out) return VC_ERR_ARG;
+  *status_out = 0;
+  if (n == 0) return VC_OK;
+  if (!brick_ids || !labels_out || lod > v->L || mode > VC_MODE_BATCHED) return VC_ERR_ARG;
+  DeviceGuard g(v->device);
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  const uint32_t edge = (1u << v->L) >> lod;
+  const size_t words = (size_t)n * edge * edge * edge;
+  if (n > v->host_cap_items) {
+    cudaFree(v->d_host_ids);
+    cudaFree(v->d_host_slots);
+    v->d_host_ids = v->d_host_slots = nullptr;
+    v->host_cap_items = 0;
+    if (cudaMalloc(&v->d_host_ids, 4 * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&v->d_host_slots, 4 * (size_t)n) != cudaSuccess) {
+      cudaGetLastError();
+      return VC_ERR_OOM;
+    }
+    std::vector<uint32_t> iota(n);
+    for (uint32_t i = 0; i < n; ++i) iota[i] = i;
+    if (cudaMemcpy(v->d_host_slots, iota.data(), 4 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess)
+      return VC_ERR_CUDA;
+    v->host_cap_items = n;
+  }
+  if (words > v->host_cap_words) {
+    cudaFree(v->d_host_cache);
+    v->d_host_cache = nullptr;
+    v->host_cap_words = 0;
+    if (cudaMalloc(&v->d_host_cache, 4 * words) != cudaSuccess) { cudaGetLastError(); return VC_ERR_OOM; }
+    v->host_cap_words = words;
+  }
+  if (!v->d_host_status) {
+    if (cudaMalloc(&v->d_host_status, 4 * VC_STATUS_WORDS) != cudaSuccess) { cudaGetLastError(); return VC_ERR_OOM; }
+  }
+  if (cudaMemsetAsync(v->d_host_status, 0, 4 * VC_STATUS_WORDS, stream) != cudaSuccess) return VC_ERR_CUDA;
+  if (cudaMemcpyAsync(v->d_host_ids, brick_ids, 4 * (size_t)n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    return VC_ERR_CUDA;
+  vc_status rc = launch_decode(*v, v->d_host_ids, n, v->d_host_slots, v->d_host_cache, lod, mode, v->d_host_status,
+                               stream);
+  if (rc != VC_OK) return rc;
+  if (cudaMemcpyAsync(labels_out, v->d_host_cache, 4 * words, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+    return VC_ERR_CUDA;
+  int32_t st = 0;
+  if (cudaMemcpyAsync(&st, v->d_host_status, 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess) return VC_ERR_CUDA;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return VC_ERR_CUDA;
+  *status_out = st;
+  return VC_OK;
+}
+
+vc_status vc_release(void* handle) {
+  if (!handle) return VC_OK;
+  uint32_t kind = *static_cast<uint32_t*>(handle);
+  if (kind == kHandleVolume) {
+    free_volume(static_cast<Volume*>(handle));
+    return VC_OK;
+  }
+  return VC_ERR_ARG;
+}
+
+}  // extern "C"

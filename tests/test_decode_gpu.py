@@ -1,0 +1,278 @@
+"""GPU parity: libvc.so's CUDA decoder against the CPU oracle, through the C ABI.
+
+Bit-exact on every brick (integer work): every brick size 2..32, both coders, every operation
+subset, every level of detail, all three schedules; brute-force enumerated legal streams;
+corrupt records (each rule of the format) must raise VC_ERR_CORRUPT for exactly that item; the
+512^3 workload the benchmark times is checked at full size against the generator's voxels (the
+encoding is lossless) and against the oracle on sampled bricks.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from streams import (OP_ADV, OP_DELTA, OP_LAST, OP_NY, OP_PARENT, StreamEnumerator, load_golden, padded_brick)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2609_36898_gb300 as vc  # noqa: E402
+
+MODES = ["plain", "grid", "batched"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    vc._lib_handle()
+
+
+def gpu_decode(enc: np.ndarray, ids, lod=0, mode="batched", slots=None, expect_status=0, cache_slots=None):
+    """Decodes bricks `ids` into slots 0..n-1 (or `slots`); returns (n, e, e, e) labels and status."""
+    vol = vc.Volume(enc, device=0)
+    try:
+        ids_t = torch.as_tensor(np.asarray(ids, dtype=np.int64), dtype=torch.int64).to(torch.int32).cuda()
+        n = ids_t.numel()
+        e = vol.edge(lod)
+        if slots is None:
+            slots = np.arange(n)
+        slots_t = torch.as_tensor(np.asarray(slots, dtype=np.int64)).to(torch.int32).cuda()
+        nslots = int(max(slots)) + 1 if n else 1
+        cache = torch.full((nslots * e ** 3,), -1, dtype=torch.int32, device="cuda")
+        status = torch.zeros(vc.VC_STATUS_WORDS, dtype=torch.int32, device="cuda")
+        vol.decode(ids_t, slots_t, cache, lod=lod, mode=mode, status=status)
+        torch.cuda.synchronize()
+        st = status.cpu().numpy()
+        out = cache.cpu().numpy().view(np.uint32).reshape(nslots, e, e, e)
+        return out, st
+    finally:
+        vol.release()
+
+
+def oracle_bricks(enc, ids, lod=0):
+    return np.stack([oracle.decode_brick(enc, int(i), lod) for i in ids])
+
+
+@pytest.fixture(scope="module")
+def small_volume():
+    return synth.fill(synth.small(dims=(40, 24, 20), seed=7, diameter=10.0, bg=0.2))
+
+
+@pytest.mark.parametrize("log2b", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("coder", [0, 1])
+def test_parity_every_brick_every_lod(small_volume, log2b, coder):
+    enc = oracle.encode_volume(small_volume, log2b, coder=coder)
+    n = oracle.header(enc)["n_bricks"]
+    ids = np.arange(n)
+    for lod in range(log2b + 1):
+        ref = oracle_bricks(enc, ids, lod)
+        for mode in MODES:
+            out, st = gpu_decode(enc, ids, lod, mode)
+            assert st[0] == 0, (mode, lod, st)
+            assert np.array_equal(out, ref), (mode, lod)
+
+
+@pytest.mark.parametrize("mask", [1 << 4, (1 << 4) | 1, (1 << 4) | 0b1111, 0x7F & ~(1 << OP_DELTA),
+                                  0x7F & ~(1 << OP_LAST), 0x7F])
+def test_parity_operation_subsets(small_volume, mask):
+    for coder in (0, 1):
+        for flags in (0, 1):
+            enc = oracle.encode_volume(small_volume, 4, op_mask=mask, coder=coder, flags=flags)
+            ids = np.arange(oracle.header(enc)["n_bricks"])
+            out, st = gpu_decode(enc, ids, 0, "batched")
+            assert st[0] == 0
+            assert np.array_equal(out, oracle_bricks(enc, ids))
+
+
+def test_parity_workload_64cube():
+    V = synth.fill(synth.c1())
+    for coder in (0, 1):
+        enc = oracle.encode_volume(V, 5, coder=coder)
+        for mode in MODES:
+            out, st = gpu_decode(enc, range(8), 0, mode)
+            assert st[0] == 0
+            for i in range(8):
+                assert np.array_equal(out[i], padded_brick(V, 32, i))
+
+
+def _bricks_of(V, b):
+    nz, ny, nx = (s // b for s in V.shape)
+    return V.reshape(nz, b, ny, b, nx, b).transpose(0, 2, 4, 1, 3, 5).reshape(-1, b, b, b)
+
+
+@pytest.mark.parametrize("coder", [0, 1])
+def test_parity_full_size_512cube_batched(coder):
+    """The benchmark's workload at full size: all 4096 bricks, batched schedule."""
+    spec = synth.c2()
+    V = synth.fill(spec)
+    enc = vc.vc_encode_volume(V, 5, coder=coder)
+    ids = np.arange(4096)
+    out, st = gpu_decode(enc, ids, 0, "batched")
+    assert st[0] == 0
+    assert np.array_equal(out, _bricks_of(V, 32))
+    rng = np.random.default_rng(0)
+    for i in rng.choice(4096, size=24, replace=False):
+        assert np.array_equal(out[i], oracle.decode_brick(enc, int(i)))
+    # the same volume encoded by the oracle decodes identically (sampled bricks)
+    sub = V[:64, :64, :]
+    enc2 = oracle.encode_volume(sub, 5, coder=coder)
+    out2, st2 = gpu_decode(enc2, np.arange(64), 0, "grid")
+    assert st2[0] == 0 and np.array_equal(out2, _bricks_of(sub, 32))
+
+
+def test_random_order_duplicates_and_scattered_slots(small_volume):
+    enc = oracle.encode_volume(small_volume, 3, coder=1)
+    n = oracle.header(enc)["n_bricks"]
+    rng = np.random.default_rng(1)
+    ids = rng.integers(0, n, size=300)
+    slots = rng.permutation(1000)[:300]
+    for mode in MODES:
+        out, st = gpu_decode(enc, ids, 0, mode, slots=slots)
+        assert st[0] == 0
+        for i, s in zip(ids, slots):
+            assert np.array_equal(out[s], oracle.decode_brick(enc, int(i)))
+
+
+def test_empty_request_is_noop(small_volume):
+    enc = oracle.encode_volume(small_volume, 3)
+    vol = vc.Volume(enc)
+    try:
+        z = torch.zeros(1, dtype=torch.int32, device="cuda")
+        st = torch.zeros(4, dtype=torch.int32, device="cuda")
+        vc.vc_decode_bricks(vol.handle, z.data_ptr(), 0, z.data_ptr(), z.data_ptr(), 0, 2, st.data_ptr(), 0)
+        torch.cuda.synchronize()
+        assert st.cpu()[0] == 0
+    finally:
+        vol.release()
+
+
+def test_out_of_range_brick_id_reports_arg(small_volume):
+    enc = oracle.encode_volume(small_volume, 3)
+    n = oracle.header(enc)["n_bricks"]
+    for mode in MODES:
+        out, st = gpu_decode(enc, [0, 1, n + 5, 2], 0, mode)
+        assert st[0] == vc.VC_ERR_ARG and st[1] == 2
+        assert np.array_equal(out[0], oracle.decode_brick(enc, 0))
+        assert np.array_equal(out[3], oracle.decode_brick(enc, 2))
+
+
+def test_host_entry_point_matches_device_path(small_volume):
+    enc = oracle.encode_volume(small_volume, 4, coder=1)
+    n = oracle.header(enc)["n_bricks"]
+    vol = vc.Volume(enc)
+    try:
+        for lod in (0, 1):
+            e = 16 >> lod
+            labels = np.empty((n, e, e, e), dtype=np.uint32)
+            st = vc.vc_decode_bricks_host(vol.handle, np.arange(n, dtype=np.uint32), lod, vc.VC_MODE_BATCHED, labels)
+            assert st == 0
+            assert np.array_equal(labels, oracle_bricks(enc, range(n), lod))
+    finally:
+        vol.release()
+
+
+# ------------------------------------------------------------------ brute force
+
+def _tiny_bricks():
+    rng = np.random.default_rng(11)
+    out = []
+    for b in (2, 4):
+        for n_labels in (1, 2, 3):
+            for _ in range(3):
+                if b == 2:
+                    B = rng.integers(1, n_labels + 1, size=(2, 2, 2)).astype(np.uint32)
+                else:
+                    B = np.repeat(np.repeat(np.repeat(rng.integers(1, n_labels + 1, size=(2, 2, 2)), 2, 0), 2, 1), 2, 2)
+                    B = B.astype(np.uint32)
+                    B[rng.integers(0, 4), rng.integers(0, 4), rng.integers(0, 4)] = rng.integers(1, n_labels + 1)
+                out.append(B)
+    return out
+
+
+@pytest.mark.parametrize("coder", [0, 1])
+def test_brute_force_streams_decode_on_gpu(coder):
+    rng = random.Random(5)
+    for B in _tiny_bricks():
+        L = B.shape[0].bit_length() - 1
+        en = StreamEnumerator(B)
+        streams = en.count_and_enumerate(limit=2000) if B.shape[0] == 2 else None
+        if streams is None:
+            streams = [en.sample(rng) for _ in range(300)]
+        enc = oracle.pack_bricks(L, streams, coder=coder)
+        for mode in ("grid", "batched"):
+            out, st = gpu_decode(enc, np.arange(len(streams)), 0, mode)
+            assert st[0] == 0
+            assert (out == B[None]).all()
+        # every level of detail agrees with the oracle replay of the same streams
+        for lod in range(1, L + 1):
+            out, st = gpu_decode(enc, np.arange(len(streams)), lod, "batched")
+            assert st[0] == 0
+            assert np.array_equal(out, oracle_bricks(enc, range(len(streams)), lod))
+
+
+# ------------------------------------------------------------------ corruption
+
+def _corrupt_cases():
+    g = load_golden("brick4_x1_neighbours.txt")
+    sym = [int(s) for s in g["symbols"]]
+    pal = [int(p) for p in g["palette"]]
+    cases = []
+    s = list(sym); s[5] = 7; cases.append((s, pal, 0, 0x7F, 0))
+    cases.append((sym, pal, 0, 0x7F & ~(1 << OP_NY), 0))
+    s = list(sym); s[0] = OP_PARENT; cases.append((s, pal, 0, 0x7F, 0))
+    s = list(sym); s[0] = OP_LAST; cases.append((s, pal, 0, 0x7F, 0))
+    s = list(sym); s[12] = OP_NY; cases.append((s, pal, 0, 0x7F, 0))
+    s = list(sym); s[2] = OP_ADV; cases.append((s, pal, 0, 0x7F, 0))
+    cases.append((sym, pal + [7], 0, 0x7F, 0))
+    s = list(sym); s[10] = OP_LAST | 8; cases.append((s, pal, 0, 0x7F, 0))
+    cases.append((sym + [0], pal, 0, 0x7F, 0))
+    cases.append((sym[:-1], pal, 0, 0x7F, 0))
+    cases.append((sym, pal, 1, 0x7F, 0))
+    s = list(sym[:10]) + [OP_DELTA, 3] + sym[11:]; cases.append((s, pal, 1, 0x7F, 0))
+    s = list(sym[:10]) + [OP_DELTA, 0] + sym[11:]; cases.append((s, pal, 1, 0x7F, 0))
+    s = list(sym[:10]) + [OP_DELTA] + [8] * 7 + [1] + sym[11:]; cases.append((s, pal, 1, 0x7F, 0))
+    s = list(sym[:-1]) + [OP_DELTA, 9]; cases.append((s, pal, 1, 0x7F, 0))
+    cases.append((sym, pal, 0, 0x7F, 1))
+    return sym, pal, cases
+
+
+@pytest.mark.parametrize("coder", [0, 1])
+def test_corrupt_records_flagged_per_item(coder):
+    sym, pal, cases = _corrupt_cases()
+    for s, p, nd, mask, flags in cases:
+        assert oracle.decode_brick_status(oracle.pack_single_brick(2, s, p, nd, op_mask=mask, flags=flags,
+                                                                   coder=coder), 0) == oracle.ERR_CORRUPT
+        # a valid brick, the corrupt one, a valid brick
+        good = (sym, pal, 0)
+        enc = oracle.pack_bricks(2, [good, (s, p, nd), good], op_mask=mask, coder=coder, flags=flags)
+        if mask != 0x7F or flags:
+            # the good stream itself violates the restricted mask / flags: use only the corrupt one
+            enc = oracle.pack_bricks(2, [(s, p, nd)], op_mask=mask, coder=coder, flags=flags)
+            for mode in MODES:
+                _, st = gpu_decode(enc, [0], 0, mode)
+                assert st[0] == vc.VC_ERR_CORRUPT and st[1] == 0, (s, mode)
+            continue
+        for mode in MODES:
+            out, st = gpu_decode(enc, [0, 1, 2], 0, mode)
+            assert st[0] == vc.VC_ERR_CORRUPT and st[1] == 1, (s, p, nd, mode, st)
+            ref = oracle.decode_brick(enc, 0)
+            assert np.array_equal(out[0], ref) and np.array_equal(out[2], ref)
+
+
+def test_rans_corrupt_words_flagged():
+    g = load_golden("brick4_x1_neighbours.txt")
+    sym = [int(s) for s in g["symbols"]] * 1
+    pal = [int(p) for p in g["palette"]]
+    enc = oracle.pack_single_brick(2, sym, pal, 0, coder=1)
+    rec = oracle.brick_record(enc, 0)
+    rec_off = (128 + 8 + 15) & ~15
+    # an initial state below 2^16 is invalid
+    bad = enc.copy()
+    bad[rec_off + 16: rec_off + 20] = 0
+    assert oracle.decode_brick_status(bad, 0) == oracle.ERR_CORRUPT
+    _, st = gpu_decode(bad, [0], 0, "batched")
+    assert st[0] == vc.VC_ERR_CORRUPT
+    assert rec["n_sym"] == len(sym)
