@@ -97,7 +97,7 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   // Brick Starts and every record's sizes
   const uint8_t* st = p + kHeaderBytes;
   const uint8_t* rec = p + rec_off;
-  uint32_t max_pal = 0, max_sym = 0, max_delta = 0, max_words = 0;
+  uint32_t max_pal = 0, max_sym = 0, max_delta = 0, max_words = 0, max_stage = 0;
   uint32_t prev = le32(st);
   if (prev != 0) return VC_ERR_FORMAT;
   for (uint32_t i = 0; i < n_bricks; ++i) {
@@ -116,18 +116,19 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
     max_sym = std::max(max_sym, S);
     max_delta = std::max(max_delta, nd);
     max_words = std::max(max_words, e - a);
+    // bytes the reconstruction kernel stages: the record (plain), or its head and decoded symbols (rANS)
+    const uint32_t stage = coder == 0 ? 4 * (e - a)
+                                      : (uint32_t)(((16 + 4 * ns + 4 * (uint64_t)n_pal) + 15) & ~15ull) +
+                                            (((S + 1) / 2 + 15) & ~15u);
+    max_stage = std::max(max_stage, stage);
   }
   if (le32(st + 4 * (size_t)n_bricks) != records_words) return VC_ERR_FORMAT;
   if (max_pal > hdr_max_pal || max_sym > hdr_max_sym) return VC_ERR_FORMAT;
-  if (max_pal > kMaxIdx16) return VC_ERR_UNSUPPORTED;  // palette indices are kept in 16 bits
+  if (max_pal >= kMaxIdx16) return VC_ERR_UNSUPPORTED;  // palette indices are kept in 16 bits
 
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return VC_ERR_ARG;
   DeviceGuard g(device);
-  SmemLayout sl;
-  vc_status rc = compute_layout(L, coder, max_sym, max_pal, max_delta, max_words, device, &sl);
-  if (rc != VC_OK) return rc;
-
   Volume* v = new (std::nothrow) Volume();
   if (!v) return VC_ERR_OOM;
   v->kind = kHandleVolume;
@@ -135,38 +136,40 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   for (int a = 0; a < 3; ++a) { v->dims[a] = dims[a]; v->nb[a] = nb[a]; }
   v->L = L; v->op_mask = op_mask; v->coder = coder; v->flags = flags; v->n_bricks = n_bricks;
   v->max_pal = max_pal; v->max_sym = max_sym; v->max_delta = max_delta; v->max_rec_words = max_words;
+  v->max_stage = max_stage;
   v->encoded_bytes = nbytes;
+  SmemLayout sl;
+  vc_status rc = compute_layout(*v, device, 256, 2, &sl);
+  if (rc != VC_OK) { delete v; return rc; }
+
+  // the device copy carries 64 zero bytes of slack: 8-nibble windows may read past a record's end
   const size_t file_bytes = rec_off + 4 * (size_t)records_words;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-  if (cudaMalloc(&v->d_file, file_bytes) != cudaSuccess) { cudaGetLastError(); delete v; return VC_ERR_OOM; }
-  if (cudaMalloc(&v->d_tables, 4096 + 64 * 4) != cudaSuccess) {
+  if (cudaMalloc(&v->d_file, file_bytes + 64) != cudaSuccess) { cudaGetLastError(); delete v; return VC_ERR_OOM; }
+  if (cudaMalloc(&v->d_tables, 4 * kRansM) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(v->d_file);
     delete v;
     return VC_ERR_OOM;
   }
-  v->device_bytes = file_bytes + 4096 + 64 * 4;
-  // rANS tables: slot -> symbol, then freq[16] and cum[17]
-  std::vector<uint8_t> tab(4096 + 64 * 4, 0);
+  v->device_bytes = file_bytes + 64 + 4 * kRansM;
+  // rANS table: per slot, symbol | freq << 4 | (slot - cum[symbol]) << 17
+  std::vector<uint32_t> tab(kRansM, 0);
   if (coder == 1) {
     uint32_t cum = 0;
-    for (int s = 0; s < 16; ++s) {
-      for (uint32_t k = 0; k < freq[s]; ++k) tab[cum + k] = (uint8_t)s;
+    for (uint32_t s = 0; s < 16; ++s) {
+      for (uint32_t k = 0; k < freq[s]; ++k) tab[cum + k] = s | (freq[s] << 4) | (k << 17);
       cum += freq[s];
     }
-    uint32_t fc[33];
-    fc[16] = 0;
-    for (int s = 0; s < 16; ++s) { fc[s] = freq[s]; fc[17 + s] = fc[16 + s] + freq[s]; }
-    std::memcpy(tab.data() + 4096, fc, sizeof(fc));
   }
-  bool ok = cudaMemcpyAsync(v->d_file, p, file_bytes, cudaMemcpyHostToDevice, stream) == cudaSuccess &&
-            cudaMemcpyAsync(v->d_tables, tab.data(), tab.size(), cudaMemcpyHostToDevice, stream) == cudaSuccess &&
+  bool ok = cudaMemsetAsync(v->d_file + file_bytes, 0, 64, stream) == cudaSuccess &&
+            cudaMemcpyAsync(v->d_file, p, file_bytes, cudaMemcpyHostToDevice, stream) == cudaSuccess &&
+            cudaMemcpyAsync(v->d_tables, tab.data(), 4 * kRansM, cudaMemcpyHostToDevice, stream) == cudaSuccess &&
             cudaStreamSynchronize(stream) == cudaSuccess;
   if (!ok) { free_volume(v); return VC_ERR_CUDA; }
   v->dv.records = reinterpret_cast<const uint32_t*>(v->d_file + rec_off);
   v->dv.starts = reinterpret_cast<const uint32_t*>(v->d_file + kHeaderBytes);
-  v->dv.rans_sym = v->d_tables;
-  v->dv.rans_fc = reinterpret_cast<const uint32_t*>(v->d_tables + 4096);
+  v->dv.rans_tab = reinterpret_cast<const uint32_t*>(v->d_tables);
   v->dv.n_bricks = n_bricks;
   v->dv.L = L;
   v->dv.op_mask = op_mask;

@@ -14,36 +14,41 @@ constexpr uint32_t kVersion = 1u;
 constexpr uint32_t kHeaderBytes = 128u;
 constexpr uint32_t kRansLanes = 32u;
 constexpr uint32_t kRansM = 4096u;
-constexpr uint32_t kThreads = 256u;       // threads per decoder thread block
-constexpr uint32_t kMaxIdx16 = 0xFFF0u;   // palette indices live in 16-bit grids; above: pending marks
+constexpr uint32_t kMaxIdx8 = 0xFCu;      // palette indices below this fit 8-bit grids (marks above)
+constexpr uint32_t kMaxIdx16 = 0xFFF0u;   // same for 16-bit grids
 constexpr uint32_t kFlagNoStop = 1u;
 constexpr uint32_t kHandleVolume = 0x564F4C31u;  // "VOL1"
+constexpr uint32_t kRansWarps = 16u;      // bricks (warps) per block of the rANS symbol kernel
 
-// Byte offsets of the decoder's shared-memory regions (one brick in flight per thread block).
+// Byte offsets of the reconstruction kernel's shared-memory regions (one brick per block).
 struct SmemLayout {
-  uint32_t stage_off;    // staged record, two buffers of stage_bytes (prefetch in batched mode)
-  uint32_t stage_bytes;  // 0 = records are read from global memory
-  uint32_t nib_off;      // rANS: decoded symbols, two per byte (low nibble first)
-  uint32_t op_off;       // delta bricks: one operation symbol per node (bytes)
+  uint32_t misc_off;     // error flag, items, counters, mbarriers, warp totals, scan scratch
+  uint32_t lut_off;      // parse table: 2 states x 256 byte values (u16)
+  uint32_t stage_off;    // staged record (plain) or record head + decoded symbols (rANS)
+  uint32_t stage_bytes;  // per buffer; 0 = read from global memory
+  uint32_t nstage;       // 1 or 2 buffers (2 = prefetch the next brick in the batched kernel)
+  uint32_t nodes_off;    // node-indexed operation symbols, 8 per u32 (delta bricks only)
+  uint32_t nodes_words;
   uint32_t mask_off;     // adv_mask, del_mask, adv_pre, del_pre: 4 x nwords u32
   uint32_t nwords;
   uint32_t dlist_off;    // delta values of the brick's delta operations
-  uint32_t grid_off;     // G (u16 palette index) then R (u16 rank) for levels 0..L-1
-  uint32_t ncells;
-  uint32_t chunk_off;    // per-32-cell masks and prefixes of the level being built
-  uint32_t nchunks;
-  uint32_t parse_off;    // per-thread summaries of the delta-entry parse
-  uint32_t rans_off;     // slot -> symbol table (4096 B) + freq[16] + cum[17]
-  uint32_t misc_off;     // scalars: error flag, item numbers, counters, mbarriers
+  uint32_t dlist_cap;
+  uint32_t g_off;        // palette index per cell of levels 0..L-1 (gt_bytes each)
+  uint32_t r_off;        // rank among the level's stop-0 nodes per cell (u16), levels 0..L-1
+  uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each)
+  uint32_t gt_bytes;     // 1 (max_pal < 252) or 2
   uint32_t total;
+  // rANS symbol kernel
+  uint32_t ws_stride;    // bytes of decoded symbols per request item (workspace)
+  uint32_t a_buf;        // per-warp coded-word buffer bytes
+  uint32_t a_smem;       // dynamic shared memory per block
 };
 
 // Device-side description of a loaded volume, passed by value to the kernels.
 struct DevVolume {
-  const uint32_t* records;  // record area (32-bit words)
-  const uint32_t* starts;   // n_bricks + 1 word offsets
-  const uint8_t* rans_sym;  // 4096 slot -> symbol
-  const uint32_t* rans_fc;  // freq[16], cum[17]
+  const uint32_t* records;   // record area (32-bit words)
+  const uint32_t* starts;    // n_bricks + 1 word offsets
+  const uint32_t* rans_tab;  // 4096 entries: symbol | freq << 4 | (slot - cum) << 17
   uint32_t n_bricks;
   uint32_t L;
   uint32_t op_mask;
@@ -57,10 +62,10 @@ struct Volume {
   int device;
   uint32_t dims[3];
   uint32_t L, op_mask, coder, flags, n_bricks, nb[3];
-  uint32_t max_pal, max_sym, max_delta, max_rec_words;
+  uint32_t max_pal, max_sym, max_delta, max_rec_words, max_stage;
   uint64_t encoded_bytes, device_bytes;
-  uint8_t* d_file;       // device copy of the whole file
-  uint8_t* d_tables;     // rANS tables
+  uint8_t* d_file;       // device copy of the whole file (+ slack)
+  uint8_t* d_tables;     // rANS table
   DevVolume dv;
   // staging for vc_decode_bricks_host
   uint32_t* d_host_ids;
@@ -71,8 +76,7 @@ struct Volume {
 };
 
 // decode.cu
-vc_status compute_layout(uint32_t L, uint32_t coder, uint32_t max_sym, uint32_t max_pal, uint32_t max_delta,
-                         uint32_t max_rec_words, int device, SmemLayout* out);
+vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, SmemLayout* out);
 vc_status launch_decode(const Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
                         uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream);
 
