@@ -133,6 +133,22 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
 /* Fills *info. Host only, no CUDA calls. */
 vc_status vc_volume_info_get(const vc_volume* vol, vc_volume_info* info);
 
+/* How a volume's bricks are mapped onto the GPU (the autotuner's knobs). Paper: decoding runs in
+ * parallel over all requested bricks (Results, "GPU-based rendering pipeline"); the schedule is
+ * this library's choice. */
+typedef struct vc_schedule {
+  uint32_t threads;       /* threads per brick-decoding block: 256, 512 or 1024 (512/1024 for b >= 16) */
+  uint32_t stage_depth;   /* 1 = stage the current brick's record only, 2 = prefetch the next one */
+  uint32_t blocks_per_sm; /* batched schedule: persistent blocks per SM, 0 = as many as fit */
+} vc_schedule;
+
+/* Sets the schedule used by later decode calls on this volume (host only; not while a decode of
+ * this volume is being enqueued from another thread). VC_ERR_UNSUPPORTED if the combination
+ * is not built or its shared memory does not fit; the previous schedule then stays. The default
+ * after loading is {512, 1, 0} for b >= 16 and {256, 1, 0} below. */
+vc_status vc_volume_set_schedule(vc_volume* vol, const vc_schedule* sched);
+vc_status vc_volume_get_schedule(const vc_volume* vol, vc_schedule* sched);
+
 /* Decodes n bricks on `cuda_stream` (the Decompress stage: all requested bricks in parallel,
  * Results "GPU-based rendering pipeline"; Methods "GPU rendering pipeline").
  *   brick_ids   device, n x u32: brick ids (< n_bricks); duplicates allowed
@@ -151,9 +167,9 @@ vc_status vc_volume_info_get(const vc_volume* vol, vc_volume_info* info);
 vc_status vc_decode_bricks(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, const uint32_t* cache_slots,
                            uint32_t* cache, uint32_t lod, uint32_t mode, int32_t* status_dev, void* cuda_stream);
 
-/* Same as vc_decode_bricks with host arrays: copies brick_ids and cache_slots (host, n x u32) to
- * the device, decodes into the volume's own staging cache and copies the labels back to
- * labels_out (host, n * (b >> lod)^3 u32, brick i at offset i * (b >> lod)^3). Synchronous.
+/* Same as vc_decode_bricks with host arrays: copies brick_ids (host, n x u32) to the device,
+ * decodes brick i into slot i of the volume's own device staging cache and copies the labels back
+ * to labels_out (host, n * (b >> lod)^3 u32, brick i at offset i * (b >> lod)^3). Synchronous.
  * *status_out receives the device status word 0. Host buffers are best pinned. The staging
  * buffers are allocated on first use and grow as needed (owned by the volume). */
 vc_status vc_decode_bricks_host(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, uint32_t lod,

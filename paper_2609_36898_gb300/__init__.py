@@ -55,6 +55,10 @@ class vc_volume_info(ctypes.Structure):
     ]
 
 
+class vc_schedule(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_uint32), ("stage_depth", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
+
+
 _lib = None
 
 
@@ -68,6 +72,8 @@ def _lib_handle():
         P, U32, I32, SZ = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32, ctypes.c_size_t
         lib.vc_load_compressed.argtypes = [P, SZ, ctypes.c_int, P, ctypes.POINTER(P)]
         lib.vc_volume_info_get.argtypes = [P, ctypes.POINTER(vc_volume_info)]
+        lib.vc_volume_set_schedule.argtypes = [P, ctypes.POINTER(vc_schedule)]
+        lib.vc_volume_get_schedule.argtypes = [P, ctypes.POINTER(vc_schedule)]
         lib.vc_decode_bricks.argtypes = [P, P, U32, P, P, U32, U32, P, P]
         lib.vc_decode_bricks_host.argtypes = [P, P, U32, U32, U32, P, ctypes.POINTER(I32), P]
         lib.vc_release.argtypes = [P]
@@ -77,7 +83,7 @@ def _lib_handle():
         lib.vc_status_string.argtypes = [I32]
         lib.vc_status_string.restype = ctypes.c_char_p
         for f in ("vc_load_compressed", "vc_volume_info_get", "vc_decode_bricks", "vc_decode_bricks_host",
-                  "vc_release", "vc_encode_volume"):
+                  "vc_release", "vc_encode_volume", "vc_volume_set_schedule", "vc_volume_get_schedule"):
             getattr(lib, f).restype = I32
         _lib = lib
     return _lib
@@ -102,6 +108,17 @@ def vc_volume_info_get(vol) -> vc_volume_info:
     info = vc_volume_info()
     _check(_lib_handle().vc_volume_info_get(vol, ctypes.byref(info)), "vc_volume_info_get")
     return info
+
+
+def vc_volume_set_schedule(vol, threads: int, stage_depth: int = 2, blocks_per_sm: int = 0) -> None:
+    s = vc_schedule(threads, stage_depth, blocks_per_sm)
+    _check(_lib_handle().vc_volume_set_schedule(vol, ctypes.byref(s)), "vc_volume_set_schedule")
+
+
+def vc_volume_get_schedule(vol) -> tuple:
+    s = vc_schedule()
+    _check(_lib_handle().vc_volume_get_schedule(vol, ctypes.byref(s)), "vc_volume_get_schedule")
+    return (s.threads, s.stage_depth, s.blocks_per_sm)
 
 
 def vc_decode_bricks(vol, brick_ids_ptr: int, n: int, cache_slots_ptr: int, cache_ptr: int, lod: int, mode: int,
@@ -153,6 +170,10 @@ class Volume:
         self.b = int(self.info.brick_size)
         self.L = int(self.info.log2b)
         self.n_bricks = int(self.info.n_bricks)
+
+    def set_schedule(self, threads: int, stage_depth: int = 2, blocks_per_sm: int = 0) -> None:
+        vc_volume_set_schedule(self.handle, threads, stage_depth, blocks_per_sm)
+        self.info = vc_volume_info_get(self.handle)
 
     def edge(self, lod: int = 0) -> int:
         return self.b >> lod

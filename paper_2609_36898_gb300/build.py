@@ -14,8 +14,11 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["decode.cu", "vc_api.cu", "encode.cpp"]
-HEADERS = ["vc_internal.h"]
+# (source, object name, extra flags): the reconstruction kernels are compiled once per thread count
+SOURCES = [("decode.cu", "decode", []), ("decode_nt.cu", "decode_nt256", ["-DVC_NT=256"]),
+           ("decode_nt.cu", "decode_nt512", ["-DVC_NT=512"]), ("decode_nt.cu", "decode_nt1024", ["-DVC_NT=1024"]),
+           ("vc_api.cu", "vc_api", []), ("encode.cpp", "encode", [])]
+HEADERS = ["vc_internal.h", "decode_kernels.cuh"]
 
 
 def _nvcc() -> str:
@@ -45,12 +48,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "vc.h")]
     jobs = []
     objs = []
-    for s in SOURCES:
+    for s, name, extra in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD, s + ".o")
+        obj = os.path.join(BUILD, name + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs + [__file__]):
-            jobs.append([nvcc] + _flags(s) + ["-c", src, "-o", obj])
+            jobs.append([nvcc] + _flags(s) + extra + ["-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

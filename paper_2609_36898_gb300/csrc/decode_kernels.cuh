@@ -1,0 +1,1024 @@
+// Device code of the brick decoder (templates), shared by the per-thread-count translation
+// units. See decode.cu for the design.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "vc_internal.h"
+
+namespace vc {
+namespace dev {
+namespace {
+
+constexpr uint16_t NONE16 = 0xFFFFu;
+enum : uint32_t { OP_PARENT = 0, OP_NX = 1, OP_NY = 2, OP_NZ = 3, OP_ADV = 4, OP_LAST = 5, OP_DELTA = 6 };
+
+struct Params {
+  DevVolume v;
+  const uint32_t* ids;
+  const uint32_t* slots;
+  uint32_t n;
+  uint32_t* cache;
+  uint32_t lod;
+  int32_t* status;
+  uint32_t item_base;
+  const uint8_t* ws;  // decoded rANS symbols, ws_stride bytes per item (nullptr for plain volumes)
+};
+
+template <typename GT>
+struct GridT {
+  static constexpr uint32_t MARK = sizeof(GT) == 1 ? 0xFDu : 0xFFFDu;  // MARK + axis: pending copy
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // bit i -> bit 3i
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0xFF0000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+__device__ __forceinline__ uint32_t compact3(uint32_t v) {  // bit 3i -> bit i
+  v &= 0x09249249u;
+  v = (v ^ (v >> 2)) & 0x030C30C3u;
+  v = (v ^ (v >> 4)) & 0x0300F00Fu;
+  v = (v ^ (v >> 8)) & 0xFF0000FFu;
+  v = (v ^ (v >> 16)) & 0x000003FFu;
+  return v;
+}
+// Offset in the finest grid (x fastest, edge 2^L) of child (0,0,0) of level-(L-1) cell m; additive
+// over disjoint bit sets of m.
+template <int L>
+__device__ __forceinline__ uint32_t flin(uint32_t m) {
+  constexpr uint32_t b = 1u << L;
+  return 2u * ((compact3(m >> 2) * b + compact3(m >> 1)) * b + compact3(m));
+}
+// Morton code m minus one step along axis a (the coordinate must be > 0).
+__device__ __forceinline__ uint32_t morton_dec(uint32_t m, uint32_t a) {
+  const uint32_t ma = 0x09249249u << a;
+  return (((m & ma) - 1u) & ma) | (m & ~ma);
+}
+
+__device__ __forceinline__ void set_err(int* s_err, int code) { *s_err = code; }
+
+__device__ void report(int32_t* status, int code, uint32_t item) {
+  if (atomicCAS(reinterpret_cast<int*>(status), 0, code) == 0) atomicExch(reinterpret_cast<int*>(status) + 1, (int)item);
+}
+
+__device__ __forceinline__ uint32_t nib_at(const uint32_t* w, uint32_t i) { return (w[i >> 3] >> ((i & 7u) << 2)) & 15u; }
+
+// 8 nibbles starting at nibble j of a packed array (two aligned loads and a funnel shift).
+__device__ __forceinline__ uint32_t nib8_at(const uint32_t* w, uint32_t j) {
+  const uint32_t lo = w[j >> 3], hi = w[(j >> 3) + 1];
+  return __funnelshift_r(lo, hi, (j & 7u) << 2);
+}
+// 8 bits starting at bit j of a bit array.
+__device__ __forceinline__ uint32_t bits8_at(const uint32_t* w, uint32_t j) {
+  const uint32_t lo = w[j >> 5], hi = w[(j >> 5) + 1];
+  return __funnelshift_r(lo, hi, j & 31u) & 0xFFu;
+}
+// bit i set iff (nibble i & 7) == v, for the 8 nibbles of x
+__device__ __forceinline__ uint32_t nib_eq8(uint32_t x, uint32_t v) {
+  const uint32_t t = (x & 0x77777777u) ^ (v * 0x11111111u);
+  uint32_t z = ~(t + 0x77777777u) & 0x88888888u;
+  z >>= 3;
+  z = (z | (z >> 3)) & 0x03030303u;
+  z = (z | (z >> 6)) & 0x000F000Fu;
+  z = (z | (z >> 12)) & 0xFFu;
+  return z;
+}
+
+// Inclusive warp scan of two counters.
+__device__ __forceinline__ void warp_scan2(uint32_t& a, uint32_t& b, uint32_t lane) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t na = __shfl_up_sync(0xFFFFFFFFu, a, off), nb = __shfl_up_sync(0xFFFFFFFFu, b, off);
+    if (lane >= (uint32_t)off) { a += na; b += nb; }
+  }
+}
+
+// Exclusive block scan of (a, b); tmp holds 2 * NW + 2 words. Ends with a barrier.
+template <int NT>
+__device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t& pa, uint32_t& pb, uint32_t& ta,
+                                            uint32_t& tb, uint32_t* tmp) {
+  constexpr uint32_t NW = NT / 32;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint32_t ia = a, ib = b;
+  warp_scan2(ia, ib, lane);
+  if (lane == 31) { tmp[warp] = ia; tmp[NW + warp] = ib; }
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t va = lane < NW ? tmp[lane] : 0u, vb = lane < NW ? tmp[NW + lane] : 0u;
+    uint32_t sa = va, sb = vb;
+    warp_scan2(sa, sb, lane);
+    if (lane < NW) { tmp[lane] = sa - va; tmp[NW + lane] = sb - vb; }
+    if (lane == 31) { tmp[2 * NW] = sa; tmp[2 * NW + 1] = sb; }
+  }
+  __syncthreads();
+  pa = tmp[warp] + ia - a;
+  pb = tmp[NW + warp] + ib - b;
+  ta = tmp[2 * NW];
+  tb = tmp[2 * NW + 1];
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
+// Parse table, one u32 per byte value: for start state s in {0, 1} (1 = a delta entry is
+// expected), bits [16 s, 16 s + 13) hold the end state (bit 0), which nibbles are operations
+// (bits 1-2), which are delta operations (bits 3-4) and the operation nibbles themselves,
+// compacted (bits 5-12).
+__device__ __forceinline__ uint32_t parse_entry(uint32_t byte) {
+  uint32_t out = 0;
+#pragma unroll
+  for (uint32_t s = 0; s < 2; ++s) {
+    uint32_t st = s, opm = 0, delm = 0;
+#pragma unroll
+    for (uint32_t h = 0; h < 2; ++h) {
+      const uint32_t v = (byte >> (4 * h)) & 15u;
+      if (st == 0) {
+        opm |= 1u << h;
+        if ((v & 7u) == OP_DELTA) { delm |= 1u << h; st = 1; }
+      } else {
+        st = (v >> 3) & 1u;  // another entry follows
+      }
+    }
+    const uint32_t val = opm == 3u ? byte : (opm == 1u ? (byte & 15u) : (opm == 2u ? (byte >> 4) : 0u));
+    out |= (st | (opm << 1) | (delm << 3) | (val << 5)) << (16 * s);
+  }
+  return out;
+}
+__device__ __forceinline__ uint32_t parse_pick(uint32_t e, uint32_t st) { return (st ? e >> 16 : e) & 0x1FFFu; }
+
+// delta from the entries at nibble i..; 0 when invalid (runs past S or needs an eighth entry)
+__device__ __forceinline__ uint32_t read_delta(const uint32_t* sw, uint32_t i, uint32_t S) {
+  uint32_t d = 0;
+#pragma unroll 1
+  for (uint32_t e = 0; e < 7u; ++e) {
+    if (i + e >= S) return 0u;
+    const uint32_t v = nib_at(sw, i + e);
+    d = (d << 3) | (v & 7u);
+    if (!(v & 8u)) return d;
+  }
+  return 0u;
+}
+
+struct ParseOut {
+  uint32_t n_nodes;
+  uint32_t n_delta;
+};
+
+// The table entry of byte k of stream word x; bytes past the end of the stream (S nibbles) are
+// masked: a lone low nibble keeps only its own half.
+__device__ __forceinline__ uint32_t parse_byte(const uint32_t* lut, uint32_t x, uint32_t k, uint32_t nib_left) {
+  const uint32_t byte = (x >> (8u * k)) & 0xFFu;
+  uint32_t e = lut[byte];
+  if (nib_left < 2u * k + 2u) {
+    // only the low nibble is part of the stream: recompute for one nibble (rare: last byte)
+    const uint32_t v = byte & 15u;
+    uint32_t out = 0;
+#pragma unroll
+    for (uint32_t s = 0; s < 2; ++s) {
+      uint32_t st = s, opm = 0, delm = 0;
+      if (st == 0) {
+        opm = 1u;
+        if ((v & 7u) == OP_DELTA) { delm = 1u; st = 1; }
+      } else {
+        st = (v >> 3) & 1u;
+      }
+      out |= (st | (opm << 1) | (delm << 3) | ((opm ? v : 0u) << 5)) << (16 * s);
+    }
+    e = out;
+  }
+  return e;
+}
+
+// State of the parse automaton before symbol p0 (0 = an operation is expected), found by looking
+// back to the nearest self-synchronising symbol: after any symbol v in {0..5, 7} the next one is an
+// operation whatever came before (an operation that is not a delta, or a last delta entry), and
+// after 14 a delta entry follows either way. -1 if none lies within 64 symbols.
+__device__ __forceinline__ int lookback_state(const uint32_t* sw, uint32_t p0) {
+  if (p0 == 0) return 0;
+  const uint32_t lim = p0 > 64u ? p0 - 64u : 0u;
+  uint32_t q = p0;
+  int st = -1;
+  while (q > lim) {
+    --q;
+    const uint32_t v = nib_at(sw, q);
+    if (v < 8u && v != 6u) { st = 0; ++q; break; }
+    if (v == 14u) { st = 1; ++q; break; }
+  }
+  if (st < 0) {
+    if (q != 0) return -1;
+    st = 0;  // reached the start of the stream
+  }
+  for (; q < p0; ++q) {
+    const uint32_t v = nib_at(sw, q);
+    st = st == 0 ? (int)((v & 7u) == OP_DELTA) : (int)(v >> 3);
+  }
+  return st;
+}
+
+// Pass B of the parse: from start state st at word w0, writes this thread's node symbols from node
+// index j (8 per u32 through a 64-bit accumulator) and its delta values from index d.
+__device__ __forceinline__ void parse_emit(const uint32_t* sw, uint32_t S, uint32_t w0, uint32_t w1, uint32_t st,
+                                           uint32_t jstart, uint32_t d, uint32_t* nodes, uint32_t nodes_words,
+                                           uint32_t* dlist, uint32_t dcap, const uint32_t* lut) {
+  uint32_t j = jstart;
+  uint64_t acc = 0;
+  for (uint32_t w = w0; w < w1; ++w) {
+    const uint32_t x = sw[w];
+    const uint32_t left = S - 8u * w;
+    const uint32_t nb = left >= 8u ? 4u : (left + 1u) >> 1;
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k) {
+      if (k < nb) {
+        const uint32_t f = parse_pick(parse_byte(lut, x, k, left), st);
+        const uint32_t opm = (f >> 1) & 3u, cnt = __popc(opm);
+        const uint32_t p = j & 7u;
+        acc |= (uint64_t)(f >> 5) << (4u * p);
+        j += cnt;
+        if (p + cnt >= 8u) {  // a word of 8 node symbols is complete
+          const uint32_t wi = (j - cnt) >> 3;
+          if (wi < nodes_words) {
+            if (wi == (jstart >> 3) && (jstart & 7u)) atomicOr(&nodes[wi], (uint32_t)acc);
+            else nodes[wi] = (uint32_t)acc;
+          }
+          acc >>= 32;
+        }
+        const uint32_t delm = (f >> 3) & 3u;
+        if (delm) {
+#pragma unroll
+          for (uint32_t h = 0; h < 2; ++h)
+            if (delm & (1u << h)) {
+              if (d < dcap) dlist[d] = read_delta(sw, 8u * w + 2u * k + h + 1u, S);
+              ++d;
+            }
+        }
+        st = f & 1u;
+      }
+    }
+  }
+  if ((j & 7u) && (j >> 3) < nodes_words) atomicOr(&nodes[j >> 3], (uint32_t)acc);
+}
+
+// Builds nodes[] (8 operation symbols per u32, zero-padded) and dlist[] from the symbol stream.
+// scratch: 8 NT + 2 words, used only when some chunk has no self-synchronising symbol nearby.
+template <int NT>
+__device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes, uint32_t nodes_words,
+                                 uint32_t* dlist, uint32_t dcap, const uint32_t* lut, uint32_t* scan_tmp,
+                                 uint32_t* sum, int* s_err) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint32_t T = (S + 7u) >> 3;  // stream words
+  const uint32_t WP = (T + NT - 1) / NT;
+  const uint32_t w0 = min(tid * WP, T), w1 = min(w0 + WP, T);
+  for (uint32_t w = tid; w < nodes_words; w += NT) nodes[w] = 0u;
+  const int st0 = w0 < w1 ? lookback_state(sw, 8u * w0) : 0;
+  ParseOut out;
+  if (!__syncthreads_or(st0 < 0)) {
+    // fast path: every chunk knows its start state; count, scan, emit
+    uint32_t st = (uint32_t)st0, n = 0, d = 0;
+    for (uint32_t w = w0; w < w1; ++w) {
+      const uint32_t x = sw[w];
+      const uint32_t left = S - 8u * w;
+      const uint32_t nb = left >= 8u ? 4u : (left + 1u) >> 1;
+#pragma unroll
+      for (uint32_t k = 0; k < 4; ++k) {
+        if (k < nb) {
+          const uint32_t f = parse_pick(parse_byte(lut, x, k, left), st);
+          n += __popc((f >> 1) & 3u); d += __popc((f >> 3) & 3u); st = f & 1u;
+        }
+      }
+    }
+    if (w0 < w1 && w1 == T && st != 0) set_err(s_err, VC_ERR_CORRUPT);  // ends inside a delta chain
+    uint32_t jb, db, tn, td;
+    block_scan2<NT>(n, d, jb, db, tn, td, scan_tmp);
+    parse_emit(sw, S, w0, w1, (uint32_t)st0, jb, db, nodes, nodes_words, dlist, dcap, lut);
+    out.n_nodes = tn;
+    out.n_delta = td;
+    __syncthreads();
+    return out;
+  }
+  // general path: summaries for both start states composed by a warp scan
+  uint32_t s0 = 0, s1 = 1, n0 = 0, n1 = 0, d0 = 0, d1 = 0;
+  bool merged = false;
+  for (uint32_t w = w0; w < w1; ++w) {
+    const uint32_t x = sw[w];
+    const uint32_t left = S - 8u * w;
+    const uint32_t nb = left >= 8u ? 4u : (left + 1u) >> 1;
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k) {
+      if (k < nb) {
+        const uint32_t e = parse_byte(lut, x, k, left);
+        const uint32_t f0 = parse_pick(e, s0);
+        n0 += __popc((f0 >> 1) & 3u); d0 += __popc((f0 >> 3) & 3u); s0 = f0 & 1u;
+        if (!merged) {
+          const uint32_t f1 = parse_pick(e, s1);
+          n1 += __popc((f1 >> 1) & 3u); d1 += __popc((f1 >> 3) & 3u); s1 = f1 & 1u;
+          if (s1 == s0) { merged = true; n1 -= n0; d1 -= d0; }  // keep the offsets from here on
+        }
+      }
+    }
+  }
+  if (merged) { n1 += n0; d1 += d0; s1 = s0; }
+  // sum layout (padded by one word per 32 against bank conflicts): end states, n0, n1, d0, d1,
+  // then start state / node base / delta base
+  auto at = [](uint32_t t) { return t + (t >> 5); };
+  constexpr uint32_t SP = NT + NT / 32;
+  sum[at(tid)] = s0 | (s1 << 1);
+  sum[SP + at(tid)] = n0;
+  sum[2 * SP + at(tid)] = n1;
+  sum[3 * SP + at(tid)] = d0;
+  sum[4 * SP + at(tid)] = d1;
+  __syncthreads();
+  if (warp == 0) {
+    constexpr uint32_t PER = NT / 32;
+    uint32_t E0 = 0, E1 = 1, N0 = 0, N1 = 0, D0 = 0, D1 = 0;  // identity
+    for (uint32_t t = lane * PER; t < lane * PER + PER; ++t) {
+      const uint32_t te = sum[at(t)];
+      const uint32_t a0 = E0 ? sum[2 * SP + at(t)] : sum[SP + at(t)], b0 = E0 ? sum[4 * SP + at(t)] : sum[3 * SP + at(t)];
+      const uint32_t a1 = E1 ? sum[2 * SP + at(t)] : sum[SP + at(t)], b1 = E1 ? sum[4 * SP + at(t)] : sum[3 * SP + at(t)];
+      N0 += a0; D0 += b0; E0 = (te >> E0) & 1u;
+      N1 += a1; D1 += b1; E1 = (te >> E1) & 1u;
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t pE0 = __shfl_up_sync(0xFFFFFFFFu, E0, off), pE1 = __shfl_up_sync(0xFFFFFFFFu, E1, off);
+      const uint32_t pN0 = __shfl_up_sync(0xFFFFFFFFu, N0, off), pN1 = __shfl_up_sync(0xFFFFFFFFu, N1, off);
+      const uint32_t pD0 = __shfl_up_sync(0xFFFFFFFFu, D0, off), pD1 = __shfl_up_sync(0xFFFFFFFFu, D1, off);
+      if (lane >= (uint32_t)off) {
+        // prefix p, then this lane's function c from p's end state
+        const uint32_t cE0 = E0, cE1 = E1, cN0 = N0, cN1 = N1, cD0 = D0, cD1 = D1;
+        N0 = pN0 + (pE0 ? cN1 : cN0); D0 = pD0 + (pE0 ? cD1 : cD0); E0 = pE0 ? cE1 : cE0;
+        N1 = pN1 + (pE1 ? cN1 : cN0); D1 = pD1 + (pE1 ? cD1 : cD0); E1 = pE1 ? cE1 : cE0;
+      }
+    }
+    uint32_t xs = __shfl_up_sync(0xFFFFFFFFu, E0, 1), xn = __shfl_up_sync(0xFFFFFFFFu, N0, 1),
+             xd = __shfl_up_sync(0xFFFFFFFFu, D0, 1);
+    if (lane == 0) { xs = 0; xn = 0; xd = 0; }
+    for (uint32_t t = lane * PER; t < lane * PER + PER; ++t) {
+      const uint32_t te = sum[at(t)];
+      const uint32_t tn = xs ? sum[2 * SP + at(t)] : sum[SP + at(t)];
+      const uint32_t td = xs ? sum[4 * SP + at(t)] : sum[3 * SP + at(t)];
+      sum[5 * SP + at(t)] = xs;
+      sum[6 * SP + at(t)] = xn;
+      sum[7 * SP + at(t)] = xd;
+      xn += tn; xd += td; xs = (te >> xs) & 1u;
+    }
+    if (lane == 31) {
+      sum[8 * SP] = xn;
+      sum[8 * SP + 1] = xd;
+      if (xs != 0) set_err(s_err, VC_ERR_CORRUPT);  // the stream ends inside a delta entry chain
+    }
+  }
+  __syncthreads();
+  parse_emit(sw, S, w0, w1, sum[5 * SP + at(tid)], sum[6 * SP + at(tid)], sum[7 * SP + at(tid)], nodes, nodes_words,
+             dlist, dcap, lut);
+  out.n_nodes = sum[8 * SP];
+  out.n_delta = sum[8 * SP + 1];
+  __syncthreads();
+  return out;
+}
+
+struct BrickCtx {
+  const uint32_t* pal;
+  uint32_t n_pal;
+  const uint32_t* nodes;  // 8 operation symbols per u32
+  uint32_t n_nodes;
+  const uint32_t* adv_mask;
+  const uint32_t* del_mask;
+  const uint32_t* adv_pre;
+  const uint32_t* del_pre;
+  const uint32_t* dlist;
+  uint32_t dlist_cap;
+  uint32_t op_mask;
+  int* s_err;
+};
+
+// Palette index of node j with operation o in {ADV, LAST, DELTA}.
+__device__ __forceinline__ uint32_t pal_index(const BrickCtx& c, uint32_t j, uint32_t o) {
+  const uint32_t w = j >> 5, lt = (1u << (j & 31u)) - 1u;
+  const uint32_t k = c.adv_pre[w] + __popc(c.adv_mask[w] & lt);
+  if (o == OP_ADV) {
+    if (k >= c.n_pal) { set_err(c.s_err, VC_ERR_CORRUPT); return 0; }
+    return k;
+  }
+  if (o == OP_LAST) {
+    if (k == 0) { set_err(c.s_err, VC_ERR_CORRUPT); return 0; }
+    return k - 1;
+  }
+  const uint32_t d = c.del_pre[w] + __popc(c.del_mask[w] & lt);
+  const uint32_t delta = d < c.dlist_cap ? c.dlist[d] : 0u;
+  if (delta == 0 || delta > k) { set_err(c.s_err, VC_ERR_CORRUPT); return 0; }
+  return k - delta;
+}
+
+__device__ __forceinline__ uint32_t label_of(const BrickCtx& c, uint32_t idx) {
+  return idx < c.n_pal ? c.pal[idx] : 0u;
+}
+
+// Follows neighbour marks (at most three hops) in a level grid indexed by Morton code.
+template <typename GT>
+__device__ __forceinline__ uint32_t resolve_morton(const GT* G, uint32_t m, uint32_t g, int* s_err) {
+#pragma unroll 1
+  for (int hop = 0; hop < 3 && g >= GridT<GT>::MARK; ++hop) {
+    m = morton_dec(m, g - GridT<GT>::MARK);
+    g = G[m];
+  }
+  if (g >= GridT<GT>::MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
+  return g;
+}
+
+__device__ __forceinline__ void store16(uint32_t* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  *reinterpret_cast<uint4*>(p) = make_uint4(a, b, c, d);
+}
+
+template <typename GT>
+__device__ __forceinline__ void store_pair(GT* fg, uint32_t pos, uint32_t lo, uint32_t hi) {
+  if constexpr (sizeof(GT) == 1) *reinterpret_cast<uint16_t*>(fg + pos) = (uint16_t)(lo | (hi << 8));
+  else *reinterpret_cast<uint32_t*>(fg + pos) = lo | (hi << 16);
+}
+
+// ------------------------------------------------------------------------------------------
+// Decode one brick. head: the record (header, [states], palette) in shared or global memory;
+// sw: its symbols as packed nibbles (u32 aligned); out: destination of (b >> lod)^3 labels.
+template <int L, typename GT, bool RANS, int NT>
+__device__ void decode_brick(const Params& P, const uint32_t* head, const uint32_t* sw, uint32_t* out,
+                             unsigned char* sm, int* s_err) {
+  constexpr uint32_t NW = NT / 32;
+  constexpr uint32_t MARK = GridT<GT>::MARK;
+  const SmemLayout& SL = P.v.sm;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  uint32_t* misc = reinterpret_cast<uint32_t*>(sm + SL.misc_off);
+  uint32_t* wtot = misc + 16;      // NW warp totals (words 16..47)
+  uint32_t* scan_tmp = misc + 48;  // 2 NW + 2 words (48..113)
+
+  const uint32_t n_pal = head[0], S = head[1], nd = head[3];
+  const uint32_t ns = RANS ? (S < 32u ? S : 32u) : 0u;
+
+  BrickCtx c;
+  c.pal = head + 4 + ns;
+  c.n_pal = n_pal;
+  c.op_mask = P.v.op_mask;
+  c.s_err = s_err;
+  uint32_t* dlist = reinterpret_cast<uint32_t*>(sm + SL.dlist_off);
+  c.dlist = dlist;
+  c.dlist_cap = nd < SL.dlist_cap ? nd : SL.dlist_cap;
+
+  // 1. operations per node
+  if (nd == 0) {
+    c.nodes = sw;
+    c.n_nodes = S;
+  } else {
+    uint32_t* nodes = reinterpret_cast<uint32_t*>(sm + SL.nodes_off);
+    // the general parse path borrows the finest grid (not in use yet) for its summaries
+    const ParseOut po = parse_stream<NT>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap,
+                                         reinterpret_cast<const uint32_t*>(sm + SL.lut_off), scan_tmp,
+                                         reinterpret_cast<uint32_t*>(sm + SL.fg_off), s_err);
+    c.nodes = nodes;
+    c.n_nodes = po.n_nodes;
+    if (po.n_delta != nd) set_err(s_err, VC_ERR_CORRUPT);
+  }
+
+  // 2. palette-cursor masks and prefix counts (32 nodes per word)
+  uint32_t* adv_mask = reinterpret_cast<uint32_t*>(sm + SL.mask_off);
+  uint32_t* del_mask = adv_mask + SL.nwords;
+  uint32_t* adv_pre = adv_mask + 2 * SL.nwords;
+  uint32_t* del_pre = adv_mask + 3 * SL.nwords;
+  c.adv_mask = adv_mask; c.del_mask = del_mask; c.adv_pre = adv_pre; c.del_pre = del_pre;
+  {
+    const uint32_t nw32 = (c.n_nodes + 31u) >> 5;
+    const uint32_t per = (nw32 + NT - 1) / NT;
+    const uint32_t a0 = min(tid * per, nw32), a1 = min(a0 + per, nw32);
+    uint32_t sa = 0, sd = 0;
+    for (uint32_t w = a0; w < a1; ++w) {
+      uint32_t am = 0, dm = 0;
+#pragma unroll
+      for (uint32_t k = 0; k < 4; ++k) {
+        const uint32_t x = c.nodes[4u * w + k];
+        am |= nib_eq8(x, OP_ADV) << (8u * k);
+        dm |= nib_eq8(x, OP_DELTA) << (8u * k);
+      }
+      const uint32_t left = c.n_nodes - 32u * w;
+      if (left < 32u) { const uint32_t valid = (1u << left) - 1u; am &= valid; dm &= valid; }
+      adv_mask[w] = am; del_mask[w] = dm;
+      sa += __popc(am); sd += __popc(dm);
+    }
+    if (tid == 0) { adv_mask[nw32] = 0; del_mask[nw32] = 0; }  // read by 8-bit windows at the end
+    uint32_t pa, pd, ta, td;
+    block_scan2<NT>(sa, sd, pa, pd, ta, td, scan_tmp);
+    for (uint32_t w = a0; w < a1; ++w) {
+      adv_pre[w] = pa; del_pre[w] = pd;
+      pa += __popc(adv_mask[w]); pd += __popc(del_mask[w]);
+    }
+    if (tid == 0 && (ta != n_pal || td != nd)) set_err(s_err, VC_ERR_CORRUPT);
+  }
+  __syncthreads();
+
+  // 3. coarse levels
+  const uint32_t Lout = (uint32_t)L - P.lod;
+  const uint32_t last_coarse = Lout < (uint32_t)L ? Lout : (uint32_t)L - 1u;
+  GT* G = reinterpret_cast<GT*>(sm + SL.g_off);
+  uint16_t* R = reinterpret_cast<uint16_t*>(sm + SL.r_off);  // ranks of levels 0..L-2
+  const bool no_stop = (P.v.flags & kFlagNoStop) != 0;
+  constexpr uint32_t b = 1u << L;
+  const bool finest = Lout == (uint32_t)L;
+  GT* fg = reinterpret_cast<GT*>(sm + SL.fg_off);
+  uint16_t* plist = reinterpret_cast<uint16_t*>(sm + SL.list_off);
+  const uint32_t flane = flin<L>(lane);  // finest-grid offset contributed by the lane bits of a cell
+  uint32_t off = 0, Nl = 1, gofs = 0, gofs_prev = 0;
+
+  // pass 1 for cell m of level l: its palette index (or a neighbour mark) into G; true if it is
+  // emitted with stop bit 0. Cells below a stopped node inherit the parent's index.
+  auto cell_pass1 = [&](uint32_t l, uint32_t m, GT* Gl, const GT* Gp, const uint16_t* Rp) -> bool {
+    bool emitted = true;
+    uint32_t j = 0;
+    if (l > 0) {
+      const uint32_t r = Rp[m >> 3];
+      emitted = r != NONE16;
+      j = off + 8u * r + (m & 7u);
+    }
+    uint32_t g = 0;
+    bool nonstop = false;
+    if (!emitted) {
+      g = Gp[m >> 3];
+    } else if (j >= c.n_nodes) {
+      set_err(s_err, VC_ERR_CORRUPT);
+    } else {
+      const uint32_t s = nib_at(c.nodes, j), o = s & 7u, stop = s >> 3;
+      if (o == 7u || !((c.op_mask >> o) & 1u) || (stop && no_stop)) set_err(s_err, VC_ERR_CORRUPT);
+      if (o == OP_PARENT) {
+        if (l == 0) set_err(s_err, VC_ERR_CORRUPT);
+        else g = Gp[m >> 3];
+      } else if (o <= OP_NZ) {
+        const uint32_t a = o - OP_NX;
+        if (((m >> a) & 1u) || (m & (0x09249249u << a)) == 0) set_err(s_err, VC_ERR_CORRUPT);
+        else g = MARK + a;
+      } else if (o != 7u) {
+        g = pal_index(c, j, o);
+      }
+      nonstop = !stop;
+    }
+    Gl[m] = (GT)g;
+    return nonstop;
+  };
+  // pass 2 for cell m: final palette index (marks resolved); on the last level before the finest,
+  // constant 2^3 blocks are written to the finest grid and stop-0 cells listed by rank r.
+  auto cell_pass2 = [&](uint32_t m, GT* Gl, bool feed_finest, uint32_t r) {
+    uint32_t g = Gl[m];
+    if (g >= MARK) {
+      g = resolve_morton<GT>(Gl, m, g, s_err);
+      Gl[m] = (GT)g;
+    }
+    if (feed_finest) {
+      if (r != NONE16) {
+        plist[r] = (uint16_t)m;
+      } else {
+        const uint32_t f0 = flane + flin<L>(m - lane);
+        store_pair<GT>(fg, f0, g, g);
+        store_pair<GT>(fg, f0 + b, g, g);
+        store_pair<GT>(fg, f0 + b * b, g, g);
+        store_pair<GT>(fg, f0 + b * b + b, g, g);
+      }
+    }
+  };
+
+  // levels of at most 64 cells: warp 0 alone, no block barriers
+  uint32_t l = 0;
+  if (warp == 0) {
+    for (; l <= last_coarse && l <= 2u; ++l) {
+      const uint32_t cells = 1u << (3u * l);
+      const bool final_level = l == last_coarse;
+      GT* Gl = G + gofs;
+      const GT* Gp = G + gofs_prev;
+      uint16_t* Rl = R + gofs;
+      const uint16_t* Rp = R + gofs_prev;
+      uint32_t running = 0, lr[2] = {NONE16, NONE16};
+#pragma unroll
+      for (uint32_t k = 0; k < 2; ++k) {
+        const uint32_t m = 32u * k + lane;
+        const bool nonstop = m < cells && cell_pass1(l, m, Gl, Gp, Rp);
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, nonstop);
+        const uint32_t r = nonstop ? running + __popc(bal & lanemask_lt()) : NONE16;
+        if (m < cells && !final_level) Rl[m] = (uint16_t)r;
+        lr[k] = r;
+        running += __popc(bal);
+      }
+      __syncwarp();
+#pragma unroll
+      for (uint32_t k = 0; k < 2; ++k) {
+        const uint32_t m = 32u * k + lane;
+        if (m < cells) cell_pass2(m, Gl, final_level && finest, lr[k]);
+      }
+      __syncwarp();
+      off += Nl;
+      Nl = 8u * running;
+      gofs_prev = gofs;
+      gofs += cells;
+    }
+    if (lane == 0) { misc[8] = off; misc[9] = Nl; misc[10] = gofs; misc[11] = gofs_prev; misc[12] = l; }
+  }
+  __syncthreads();
+  off = misc[8]; Nl = misc[9]; gofs = misc[10]; gofs_prev = misc[11]; l = misc[12];
+
+  // larger levels: every warp owns a contiguous run of cells; ranks are completed with the other
+  // warps' totals after a barrier
+  for (; l <= last_coarse; ++l) {
+    const uint32_t cells = 1u << (3u * l);
+    const uint32_t nwa = min(NW, cells >> 5);
+    const uint32_t cpw = cells / nwa;
+    GT* Gl = G + gofs;
+    const GT* Gp = G + gofs_prev;
+    uint16_t* Rl = R + gofs;
+    const uint16_t* Rp = R + gofs_prev;
+    if (l < last_coarse) {
+      if (warp < nwa) {
+        uint32_t running = 0;
+        for (uint32_t base = warp * cpw; base < (warp + 1) * cpw; base += 32u) {
+          const uint32_t m = base + lane;
+          const bool nonstop = cell_pass1(l, m, Gl, Gp, Rp);
+          const uint32_t bal = __ballot_sync(0xFFFFFFFFu, nonstop);
+          Rl[m] = nonstop ? (uint16_t)(running + __popc(bal & lanemask_lt())) : NONE16;
+          running += __popc(bal);
+        }
+        if (lane == 0) wtot[warp] = running;
+      }
+      __syncthreads();
+      uint32_t total = 0, before = 0;
+      for (uint32_t w = 0; w < nwa; ++w) {
+        const uint32_t t = wtot[w];
+        if (w < warp) before += t;
+        total += t;
+      }
+      if (warp < nwa) {
+        for (uint32_t m = warp * cpw + lane; m < (warp + 1) * cpw; m += 32u) {
+          if (before) {
+            const uint32_t r = Rl[m];
+            if (r != NONE16) Rl[m] = (uint16_t)(r + before);
+          }
+          cell_pass2(m, Gl, false, NONE16);
+        }
+      }
+      __syncthreads();
+      off += Nl;
+      Nl = 8u * total;
+    } else {
+      // the last coarse level: its ranks are needed only to list the finest level's parents, and
+      // stay in registers
+      constexpr uint32_t LC = 1u << (3 * (L - 1));
+      constexpr uint32_t NWA = (LC >> 5) < NW ? (LC >> 5) : NW;
+      constexpr uint32_t CPL = NWA ? LC / (NWA * 32u) : 1u;
+      uint32_t lr[CPL];
+      if (warp < nwa) {
+        uint32_t running = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < CPL; ++k) {
+          const uint32_t m = warp * cpw + 32u * k + lane;
+          const bool nonstop = 32u * k < cpw && cell_pass1(l, m, Gl, Gp, Rp);
+          const uint32_t bal = __ballot_sync(0xFFFFFFFFu, nonstop);
+          lr[k] = nonstop ? running + __popc(bal & lanemask_lt()) : NONE16;
+          running += __popc(bal);
+        }
+        if (lane == 0) wtot[warp] = running;
+      }
+      __syncthreads();
+      uint32_t total = 0, before = 0;
+      for (uint32_t w = 0; w < nwa; ++w) {
+        const uint32_t t = wtot[w];
+        if (w < warp) before += t;
+        total += t;
+      }
+      if (warp < nwa) {
+#pragma unroll
+        for (uint32_t k = 0; k < CPL; ++k) {
+          const uint32_t m = warp * cpw + 32u * k + lane;
+          if (32u * k < cpw) cell_pass2(m, Gl, finest, lr[k] == NONE16 ? NONE16 : lr[k] + before);
+        }
+      }
+      __syncthreads();
+      off += Nl;
+      Nl = 8u * total;
+    }
+    gofs_prev = gofs;
+    gofs += cells;
+  }
+
+  if (finest) {
+    // 4. finest level: the blocks of the listed (stop-0) level-(L-1) cells, from their 8 operations
+    if (tid == 0 && off + Nl != c.n_nodes) set_err(s_err, VC_ERR_CORRUPT);
+    const GT* Gp = G + gofs_prev;
+    const uint32_t nparents = Nl >> 3;
+    for (uint32_t r = tid; r < nparents; r += NT) {
+      const uint32_t m = plist[r];
+      const uint32_t px = compact3(m), py = compact3(m >> 1), pz = compact3(m >> 2);
+      const uint32_t f0 = flin<L>(m);
+      const uint32_t gp = Gp[m];
+      uint32_t v[8];
+      const uint32_t j0 = off + 8u * r;
+      if (j0 + 8u > c.n_nodes) {
+        set_err(s_err, VC_ERR_CORRUPT);
+#pragma unroll
+        for (int o = 0; o < 8; ++o) v[o] = 0;
+      } else {
+        const uint32_t ops = nib8_at(c.nodes, j0);
+        if (ops & 0x88888888u) set_err(s_err, VC_ERR_CORRUPT);  // stop bit at the finest level
+        const uint32_t adv8 = bits8_at(adv_mask, j0), del8 = bits8_at(del_mask, j0);
+        const uint32_t w = j0 >> 5, lt = (1u << (j0 & 31u)) - 1u;
+        const uint32_t k0 = adv_pre[w] + __popc(adv_mask[w] & lt);
+        const uint32_t dd0 = del_pre[w] + __popc(del_mask[w] & lt);
+#pragma unroll
+        for (uint32_t o = 0; o < 8; ++o) {
+          const uint32_t op = (ops >> (4u * o)) & 7u;
+          const uint32_t below = (1u << o) - 1u;
+          uint32_t val = 0;
+          if (op == 7u || !((c.op_mask >> op) & 1u)) {
+            set_err(s_err, VC_ERR_CORRUPT);
+          } else if (op == OP_PARENT) {
+            val = gp;
+          } else if (op <= OP_NZ) {
+            const uint32_t a = op - OP_NX;
+            const uint32_t pc = a == 0 ? px : (a == 1 ? py : pz);
+            if (((o >> a) & 1u) || pc == 0) set_err(s_err, VC_ERR_CORRUPT);
+            else val = MARK + a;
+          } else {
+            const uint32_t k = k0 + __popc(adv8 & below);
+            if (op == OP_ADV) {
+              if (k >= n_pal) set_err(s_err, VC_ERR_CORRUPT);
+              else val = k;
+            } else if (op == OP_LAST) {
+              if (k == 0) set_err(s_err, VC_ERR_CORRUPT);
+              else val = k - 1u;
+            } else {
+              const uint32_t di = dd0 + __popc(del8 & below);
+              const uint32_t delta = di < c.dlist_cap ? dlist[di] : 0u;
+              if (delta == 0 || delta > k) set_err(s_err, VC_ERR_CORRUPT);
+              else val = k - delta;
+            }
+          }
+          v[o] = val;
+        }
+      }
+      store_pair<GT>(fg, f0, v[0], v[1]);
+      store_pair<GT>(fg, f0 + b, v[2], v[3]);
+      store_pair<GT>(fg, f0 + b * b, v[4], v[5]);
+      store_pair<GT>(fg, f0 + b * b + b, v[6], v[7]);
+    }
+    __syncthreads();
+    constexpr uint32_t quads = b * b * b / 4u;
+    for (uint32_t q = tid; q < quads; q += NT) {
+      uint32_t idx[4];
+      if constexpr (sizeof(GT) == 1) {
+        const uint32_t x = reinterpret_cast<const uint32_t*>(fg)[q];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) idx[i] = (x >> (8 * i)) & 0xFFu;
+      } else {
+        const uint2 x = reinterpret_cast<const uint2*>(fg)[q];
+        idx[0] = x.x & 0xFFFFu; idx[1] = x.x >> 16; idx[2] = x.y & 0xFFFFu; idx[3] = x.y >> 16;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (idx[i] >= MARK) {
+          uint32_t pos = 4u * q + (uint32_t)i, g = idx[i];
+#pragma unroll 1
+          for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
+            const uint32_t a = g - MARK;
+            pos -= a == 0 ? 1u : (a == 1 ? b : b * b);
+            g = fg[pos];
+          }
+          if (g >= MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
+          idx[i] = g;
+        }
+      }
+      store16(out + 4u * q, label_of(c, idx[0]), label_of(c, idx[1]), label_of(c, idx[2]), label_of(c, idx[3]));
+    }
+  } else {
+    // coarse level of detail: the level-Lout grid, x fastest
+    const GT* Gl = G + gofs_prev;
+    const uint32_t n = 1u << Lout;
+    const uint32_t total = n * n * n;
+    if (total >= 4u) {
+      for (uint32_t q = tid; q < total / 4u; q += NT) {
+        const uint32_t li = q << 2;
+        uint32_t v[4];
+#pragma unroll
+        for (uint32_t i = 0; i < 4; ++i) {
+          const uint32_t t = li + i;
+          const uint32_t x = t & (n - 1u), y = (t >> Lout) & (n - 1u), z = t >> (2 * Lout);
+          v[i] = label_of(c, Gl[spread3(x) | (spread3(y) << 1) | (spread3(z) << 2)]);
+        }
+        store16(out + li, v[0], v[1], v[2], v[3]);
+      }
+    } else if (tid == 0) {
+      out[0] = label_of(c, Gl[0]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// TMA bulk copies into shared memory, completion on an mbarrier.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after 2^22 polls (far beyond any copy's latency) and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <int NT>
+__device__ __forceinline__ void init_parse_lut(unsigned char* sm, const SmemLayout& SL) {
+  uint32_t* lut = reinterpret_cast<uint32_t*>(sm + SL.lut_off);
+  for (uint32_t i = threadIdx.x; i < 256u; i += NT) lut[i] = parse_entry(i);
+}
+
+// Where one request item's data lives: the record, and the bytes to stage in shared memory.
+struct ItemSrc {
+  const uint32_t* rec;     // record in global memory
+  const uint32_t* stream;  // symbols in global memory (record for plain, workspace for rANS)
+  uint32_t head_bytes;     // staged head (whole record for plain)
+  uint32_t stream_bytes;   // staged symbols after the head (rANS only)
+};
+
+template <bool RANS>
+__device__ __forceinline__ ItemSrc item_src(const Params& P, uint32_t item, uint32_t brick) {
+  ItemSrc s;
+  const uint32_t a = P.v.starts[brick], e = P.v.starts[brick + 1];
+  s.rec = P.v.records + a;
+  if (RANS) {
+    const uint32_t np = s.rec[0], S = s.rec[1];
+    const uint32_t ns = S < 32u ? S : 32u;
+    s.head_bytes = (16u + 4u * ns + 4u * np + 15u) & ~15u;
+    s.stream = reinterpret_cast<const uint32_t*>(P.ws + (size_t)item * P.v.sm.ws_stride);
+    s.stream_bytes = (((S + 1u) >> 1) + 15u) & ~15u;
+  } else {
+    s.head_bytes = (e - a) * 4u;
+    s.stream = s.rec + 4u + s.rec[0];
+    s.stream_bytes = 0;
+  }
+  return s;
+}
+
+// One thread block per request item (grid and per-brick schedules).
+template <int L, typename GT, bool RANS, int NT>
+__global__ void __launch_bounds__(NT) decode_grid_kernel(const __grid_constant__ Params P) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const SmemLayout& SL = P.v.sm;
+  int* s_err = reinterpret_cast<int*>(sm + SL.misc_off);
+  const uint32_t item = P.item_base + blockIdx.x;
+  if (item >= P.n) return;
+  const uint32_t brick = P.ids[item];
+  if (brick >= P.v.n_bricks) {
+    if (threadIdx.x == 0) report(P.status, VC_ERR_ARG, item);
+    return;
+  }
+  if (threadIdx.x == 0) *s_err = 0;
+  init_parse_lut<NT>(sm, SL);
+  const ItemSrc src = item_src<RANS>(P, item, brick);
+  const uint32_t* head = src.rec;
+  const uint32_t* sw = src.stream;
+  if (src.head_bytes + src.stream_bytes <= SL.stage_bytes) {
+    uint4* dst = reinterpret_cast<uint4*>(sm + SL.stage_off);
+    const uint4* h = reinterpret_cast<const uint4*>(src.rec);
+    for (uint32_t i = threadIdx.x; i < src.head_bytes / 16u; i += NT) dst[i] = h[i];
+    const uint4* s = reinterpret_cast<const uint4*>(src.stream);
+    for (uint32_t i = threadIdx.x; i < src.stream_bytes / 16u; i += NT) dst[src.head_bytes / 16u + i] = s[i];
+    // the staged copies' offsets come from the global record (the stage is complete only after
+    // the barrier below)
+    head = reinterpret_cast<const uint32_t*>(sm + SL.stage_off);
+    sw = reinterpret_cast<const uint32_t*>(reinterpret_cast<const unsigned char*>(head) +
+                                           (RANS ? src.head_bytes : 16u + 4u * src.rec[0]));
+  }
+  __syncthreads();
+  const uint32_t edge = (1u << L) >> P.lod;
+  uint32_t* out = P.cache + (size_t)P.slots[item] * edge * edge * edge;
+  decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, s_err);
+  __syncthreads();
+  if (threadIdx.x == 0 && *s_err) report(P.status, *s_err, item);
+}
+
+// Persistent thread blocks pull items from the work counter in status[2]; while one brick is
+// decoded, the next brick's record (and symbols) are already being copied into the other stage
+// buffer by the TMA engine.
+template <int L, typename GT, bool RANS, int NT>
+__global__ void __launch_bounds__(NT) decode_batched_kernel(const __grid_constant__ Params P) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const SmemLayout& SL = P.v.sm;
+  uint32_t* misc = reinterpret_cast<uint32_t*>(sm + SL.misc_off);
+  int* s_err = reinterpret_cast<int*>(misc);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(misc + 4);  // two mbarriers at byte 16
+  uint32_t* counter = reinterpret_cast<uint32_t*>(P.status) + 2;
+  unsigned char* stage[2] = {sm + SL.stage_off, sm + SL.stage_off + SL.stage_bytes};
+  const uint32_t tid = threadIdx.x;
+
+  // thread 0: claims the next item and, if it fits, starts copying its data into stage[buf]
+  auto claim_and_issue = [&](uint32_t buf) {
+    const uint32_t item = atomicAdd(counter, 1u);
+    misc[1 + buf] = item;
+    uint32_t bytes = 0;
+    ItemSrc src{};
+    if (item < P.n) {
+      const uint32_t brick = P.ids[item];
+      if (brick < P.v.n_bricks) {
+        src = item_src<RANS>(P, item, brick);
+        bytes = src.head_bytes + src.stream_bytes;
+        if (bytes > SL.stage_bytes) bytes = 0;
+      }
+    }
+    if (bytes) {
+      fence_proxy_async();
+      mbar_arrive_tx(&bar[buf], bytes);
+      bulk_g2s(stage[buf], src.rec, src.head_bytes, &bar[buf]);
+      if (src.stream_bytes) bulk_g2s(stage[buf] + src.head_bytes, src.stream, src.stream_bytes, &bar[buf]);
+    } else {
+      mbar_arrive_tx(&bar[buf], 0);
+    }
+  };
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  init_parse_lut<NT>(sm, SL);
+  __syncthreads();
+  // stage depth 2: the next item is claimed (and its copy started) while this one is decoded;
+  // depth 1: claimed once this one is done
+  const bool prefetch = SL.nstage == 2;
+  if (tid == 0) claim_and_issue(0);
+  uint32_t parity[2] = {0, 0};
+  uint32_t buf = 0;
+  for (;;) {
+    __syncthreads();
+    const uint32_t item = misc[1 + buf];
+    if (item >= P.n) break;
+    if (tid == 0) {
+      *s_err = 0;
+      if (prefetch) claim_and_issue(buf ^ 1u);
+    }
+    // one warp polls the barrier; the block barrier below publishes the staged bytes to the rest
+    const bool ok = (tid >> 5) != 0 || mbar_wait_bounded(&bar[buf], parity[buf]);
+    parity[buf] ^= 1u;
+    // the decision to give up is taken by the whole block (a barrier follows either way)
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        report(P.status, VC_ERR_TIMEOUT, item);
+        if (prefetch) mbar_wait_bounded(&bar[buf ^ 1u], parity[buf ^ 1u]);  // the prefetch may be in flight
+      }
+      return;
+    }
+    const uint32_t brick = P.ids[item];
+    if (brick >= P.v.n_bricks) {
+      if (tid == 0) report(P.status, VC_ERR_ARG, item);
+    } else {
+      const ItemSrc src = item_src<RANS>(P, item, brick);
+      const bool staged = src.head_bytes + src.stream_bytes <= SL.stage_bytes;
+      const uint32_t* head = staged ? reinterpret_cast<const uint32_t*>(stage[buf]) : src.rec;
+      const uint32_t* sw = !staged ? src.stream
+                                   : (RANS ? reinterpret_cast<const uint32_t*>(stage[buf] + src.head_bytes)
+                                           : head + 4u + head[0]);
+      const uint32_t edge = (1u << L) >> P.lod;
+      uint32_t* out = P.cache + (size_t)P.slots[item] * edge * edge * edge;
+      decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, s_err);
+      __syncthreads();
+      if (tid == 0 && *s_err) report(P.status, *s_err, item);
+    }
+    if (prefetch) {
+      buf ^= 1u;
+    } else {
+      __syncthreads();  // every thread is done with stage[0] before it is refilled
+      if (tid == 0) claim_and_issue(0);
+    }
+  }
+}
+
+}  // namespace
+}  // namespace dev
+}  // namespace vc

@@ -138,8 +138,11 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   v->max_pal = max_pal; v->max_sym = max_sym; v->max_delta = max_delta; v->max_rec_words = max_words;
   v->max_stage = max_stage;
   v->encoded_bytes = nbytes;
+  v->sched.threads = schedule_supported(L, 512) ? 512 : 256;
+  v->sched.stage_depth = 1;
+  v->sched.blocks_per_sm = 0;
   SmemLayout sl;
-  vc_status rc = compute_layout(*v, device, 256, 2, &sl);
+  vc_status rc = compute_layout(*v, device, v->sched.threads, v->sched.stage_depth, &sl);
   if (rc != VC_OK) { delete v; return rc; }
 
   // the device copy carries 64 zero bytes of slack: 8-nibble windows may read past a record's end
@@ -198,6 +201,27 @@ vc_status vc_volume_info_get(const vc_volume* vol, vc_volume_info* info) {
   info->device_bytes = v->device_bytes;
   info->smem_bytes = v->dv.sm.total;
   info->device = (uint32_t)v->device;
+  return VC_OK;
+}
+
+vc_status vc_volume_set_schedule(vc_volume* vol, const vc_schedule* sched) {
+  Volume* v = reinterpret_cast<Volume*>(vol);
+  if (!v || !sched || v->kind != kHandleVolume) return VC_ERR_ARG;
+  if (sched->stage_depth < 1 || sched->stage_depth > 2) return VC_ERR_ARG;
+  if (!schedule_supported(v->L, sched->threads)) return VC_ERR_UNSUPPORTED;
+  DeviceGuard g(v->device);
+  SmemLayout sl;
+  const vc_status rc = compute_layout(*v, v->device, sched->threads, sched->stage_depth, &sl);
+  if (rc != VC_OK) return rc;
+  v->sched = *sched;
+  v->dv.sm = sl;
+  return VC_OK;
+}
+
+vc_status vc_volume_get_schedule(const vc_volume* vol, vc_schedule* sched) {
+  const Volume* v = reinterpret_cast<const Volume*>(vol);
+  if (!v || !sched || v->kind != kHandleVolume) return VC_ERR_ARG;
+  *sched = v->sched;
   return VC_OK;
 }
 

@@ -36,6 +36,7 @@ struct SmemLayout {
   uint32_t g_off;        // palette index per cell of levels 0..L-1 (gt_bytes each)
   uint32_t r_off;        // rank among the level's stop-0 nodes per cell (u16), levels 0..L-1
   uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each)
+  uint32_t list_off;     // cells of level L-1 with stop bit 0, by rank (u16)
   uint32_t gt_bytes;     // 1 (max_pal < 252) or 2
   uint32_t total;
   // rANS symbol kernel
@@ -64,6 +65,7 @@ struct Volume {
   uint32_t L, op_mask, coder, flags, n_bricks, nb[3];
   uint32_t max_pal, max_sym, max_delta, max_rec_words, max_stage;
   uint64_t encoded_bytes, device_bytes;
+  vc_schedule sched;     // threads per block, staging depth, persistent blocks per SM
   uint8_t* d_file;       // device copy of the whole file (+ slack)
   uint8_t* d_tables;     // rANS table
   DevVolume dv;
@@ -76,6 +78,7 @@ struct Volume {
 };
 
 // decode.cu
+bool schedule_supported(uint32_t L, uint32_t threads);
 vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, SmemLayout* out);
 vc_status launch_decode(const Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
                         uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream);
