@@ -102,6 +102,9 @@ typedef int32_t vc_status;
 #define VC_MODE_GRID 1    /* one launch, one thread block per brick */
 #define VC_MODE_BATCHED 2 /* one persistent launch: thread blocks pull bricks from a work counter and
                              prefetch the next brick's record with a bulk copy while decoding */
+#define VC_MODE_PIPELINED 3 /* chunks of bricks flow through three kernels on three library streams:
+                               rANS symbols, reconstruction (finest index grids to a workspace), and
+                               output expansion; the caller's stream waits for all of them */
 
 typedef struct vc_volume vc_volume;
 
@@ -140,12 +143,13 @@ typedef struct vc_schedule {
   uint32_t threads;       /* threads per brick-decoding block: 256, 512 or 1024 (512/1024 for b >= 16) */
   uint32_t stage_depth;   /* 1 = stage the current brick's record only, 2 = prefetch the next one */
   uint32_t blocks_per_sm; /* batched schedule: persistent blocks per SM, 0 = as many as fit */
+  uint32_t chunk;         /* pipelined schedule: bricks per chunk, 0 = 512 */
 } vc_schedule;
 
 /* Sets the schedule used by later decode calls on this volume (host only; not while a decode of
  * this volume is being enqueued from another thread). VC_ERR_UNSUPPORTED if the combination
  * is not built or its shared memory does not fit; the previous schedule then stays. The default
- * after loading is {512, 1, 0} for b >= 16 and {256, 1, 0} below. */
+ * after loading is {256, 1, 0, 512}. */
 vc_status vc_volume_set_schedule(vc_volume* vol, const vc_schedule* sched);
 vc_status vc_volume_get_schedule(const vc_volume* vol, vc_schedule* sched);
 
@@ -157,7 +161,9 @@ vc_status vc_volume_get_schedule(const vc_volume* vol, vc_schedule* sched);
  *               (b >> lod)^3 labels, x fastest; must be 16-byte aligned; caller-owned
  *   lod         level of detail: 0 = finest (b^3 labels), k = level L - k of the brick's hierarchy
  *               (each node the mode of its 2^3 children); 0 <= lod <= L
- *   mode        VC_MODE_PLAIN, VC_MODE_GRID or VC_MODE_BATCHED (same output, different schedule)
+ *   mode        VC_MODE_PLAIN, VC_MODE_GRID, VC_MODE_BATCHED or VC_MODE_PIPELINED (same output,
+ *               different schedule); the pipelined schedule uses the volume's own streams, so calls
+ *               on one volume must not be enqueued from several host threads at once
  *   status_dev  device, VC_STATUS_WORDS int32 (see Conventions); the caller zeroes words 0..1 before
  *               the first call and reads them after synchronising; errors accumulate across calls
  * Returns VC_ERR_ARG for bad host-side arguments and VC_ERR_CUDA if a launch fails; stream-side
@@ -174,6 +180,26 @@ vc_status vc_decode_bricks(vc_volume* vol, const uint32_t* brick_ids, uint32_t n
  * buffers are allocated on first use and grow as needed (owned by the volume). */
 vc_status vc_decode_bricks_host(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, uint32_t lod,
                                 uint32_t mode, uint32_t* labels_out, int32_t* status_out, void* cuda_stream);
+
+/* ---- kernel accounting (diagnostics; the paper has no counterpart) ---- */
+
+typedef struct vc_kernel_stats {
+  uint64_t launches;       /* kernels this library launched for the volume since the last reset */
+  uint32_t timed_calls;    /* grid / batched decode calls timed while profiling was on */
+  uint32_t dropped_calls;  /* calls made while profiling was on that found no free event set */
+  double symbol_ms;        /* summed device time of the rANS symbol kernel of the timed calls */
+  double reconstruct_ms;   /* summed device time of the reconstruction kernel of the timed calls
+                              (for the batched schedule this includes the work-counter reset) */
+} vc_kernel_stats;
+
+/* enable != 0: later grid and batched decode calls on this volume record CUDA timing events on
+ * their stream around the symbol kernel and the reconstruction kernel (up to 256 calls between
+ * resets; the events are the library's). Host only; allocates the events on first use. */
+vc_status vc_volume_set_profiling(vc_volume* vol, int enable);
+
+/* Fills *out. Synchronises on the recorded events, so call it after the timed work was enqueued.
+ * reset != 0 zeroes the counters and frees the event sets for reuse afterwards. */
+vc_status vc_volume_kernel_stats(vc_volume* vol, int reset, vc_kernel_stats* out);
 
 /* Releases a handle returned by this library (a vc_volume); NULL is a no-op. Synchronises the
  * device before freeing device memory. */

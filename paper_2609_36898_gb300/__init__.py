@@ -24,8 +24,8 @@ VC_ERR_TIMEOUT = -6
 VC_ERR_BUSY = -7
 VC_ERR_UNSUPPORTED = -8
 VC_STATUS_WORDS = 4
-VC_MODE_PLAIN, VC_MODE_GRID, VC_MODE_BATCHED = 0, 1, 2
-MODES = {"plain": VC_MODE_PLAIN, "grid": VC_MODE_GRID, "batched": VC_MODE_BATCHED}
+VC_MODE_PLAIN, VC_MODE_GRID, VC_MODE_BATCHED, VC_MODE_PIPELINED = 0, 1, 2, 3
+MODES = {"plain": VC_MODE_PLAIN, "grid": VC_MODE_GRID, "batched": VC_MODE_BATCHED, "pipelined": VC_MODE_PIPELINED}
 
 
 class VCError(RuntimeError):
@@ -56,7 +56,13 @@ class vc_volume_info(ctypes.Structure):
 
 
 class vc_schedule(ctypes.Structure):
-    _fields_ = [("threads", ctypes.c_uint32), ("stage_depth", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
+    _fields_ = [("threads", ctypes.c_uint32), ("stage_depth", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("chunk", ctypes.c_uint32)]
+
+
+class vc_kernel_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("timed_calls", ctypes.c_uint32), ("dropped_calls", ctypes.c_uint32),
+                ("symbol_ms", ctypes.c_double), ("reconstruct_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -77,13 +83,16 @@ def _lib_handle():
         lib.vc_decode_bricks.argtypes = [P, P, U32, P, P, U32, U32, P, P]
         lib.vc_decode_bricks_host.argtypes = [P, P, U32, U32, U32, P, ctypes.POINTER(I32), P]
         lib.vc_release.argtypes = [P]
+        lib.vc_volume_set_profiling.argtypes = [P, ctypes.c_int]
+        lib.vc_volume_kernel_stats.argtypes = [P, ctypes.c_int, ctypes.POINTER(vc_kernel_stats)]
         lib.vc_encode_volume.argtypes = [P, P, U32, U32, U32, U32, U32, ctypes.POINTER(P), ctypes.POINTER(SZ)]
         lib.vc_free_bytes.argtypes = [P]
         lib.vc_free_bytes.restype = None
         lib.vc_status_string.argtypes = [I32]
         lib.vc_status_string.restype = ctypes.c_char_p
         for f in ("vc_load_compressed", "vc_volume_info_get", "vc_decode_bricks", "vc_decode_bricks_host",
-                  "vc_release", "vc_encode_volume", "vc_volume_set_schedule", "vc_volume_get_schedule"):
+                  "vc_release", "vc_encode_volume", "vc_volume_set_schedule", "vc_volume_get_schedule",
+                  "vc_volume_set_profiling", "vc_volume_kernel_stats"):
             getattr(lib, f).restype = I32
         _lib = lib
     return _lib
@@ -110,15 +119,15 @@ def vc_volume_info_get(vol) -> vc_volume_info:
     return info
 
 
-def vc_volume_set_schedule(vol, threads: int, stage_depth: int = 2, blocks_per_sm: int = 0) -> None:
-    s = vc_schedule(threads, stage_depth, blocks_per_sm)
+def vc_volume_set_schedule(vol, threads: int, stage_depth: int = 1, blocks_per_sm: int = 0, chunk: int = 0) -> None:
+    s = vc_schedule(threads, stage_depth, blocks_per_sm, chunk)
     _check(_lib_handle().vc_volume_set_schedule(vol, ctypes.byref(s)), "vc_volume_set_schedule")
 
 
 def vc_volume_get_schedule(vol) -> tuple:
     s = vc_schedule()
     _check(_lib_handle().vc_volume_get_schedule(vol, ctypes.byref(s)), "vc_volume_get_schedule")
-    return (s.threads, s.stage_depth, s.blocks_per_sm)
+    return (s.threads, s.stage_depth, s.blocks_per_sm, s.chunk)
 
 
 def vc_decode_bricks(vol, brick_ids_ptr: int, n: int, cache_slots_ptr: int, cache_ptr: int, lod: int, mode: int,
@@ -136,6 +145,16 @@ def vc_decode_bricks_host(vol, brick_ids: np.ndarray, lod: int, mode: int, label
     _check(_lib_handle().vc_decode_bricks_host(vol, ids.ctypes.data, ids.size, lod, mode, labels_out.ctypes.data,
                                                ctypes.byref(st), ctypes.c_void_p(stream)), "vc_decode_bricks_host")
     return st.value
+
+
+def vc_volume_set_profiling(vol, enable: bool) -> None:
+    _check(_lib_handle().vc_volume_set_profiling(vol, int(bool(enable))), "vc_volume_set_profiling")
+
+
+def vc_volume_kernel_stats(vol, reset: bool = False) -> vc_kernel_stats:
+    st = vc_kernel_stats()
+    _check(_lib_handle().vc_volume_kernel_stats(vol, int(bool(reset)), ctypes.byref(st)), "vc_volume_kernel_stats")
+    return st
 
 
 def vc_release(handle) -> None:
@@ -171,8 +190,8 @@ class Volume:
         self.L = int(self.info.log2b)
         self.n_bricks = int(self.info.n_bricks)
 
-    def set_schedule(self, threads: int, stage_depth: int = 2, blocks_per_sm: int = 0) -> None:
-        vc_volume_set_schedule(self.handle, threads, stage_depth, blocks_per_sm)
+    def set_schedule(self, threads: int, stage_depth: int = 1, blocks_per_sm: int = 0, chunk: int = 0) -> None:
+        vc_volume_set_schedule(self.handle, threads, stage_depth, blocks_per_sm, chunk)
         self.info = vc_volume_info_get(self.handle)
 
     def edge(self, lod: int = 0) -> int:

@@ -37,17 +37,67 @@
 
 namespace vc {
 
-void* pick_kernel_nt256(uint32_t L, bool gt16, bool rans, bool batched);
-void* pick_kernel_nt512(uint32_t L, bool gt16, bool rans, bool batched);
-void* pick_kernel_nt1024(uint32_t L, bool gt16, bool rans, bool batched);
+void* pick_kernel_nt256(uint32_t L, bool gt16, bool rans, bool batched, bool split);
+void* pick_kernel_nt512(uint32_t L, bool gt16, bool rans, bool batched, bool split);
+void* pick_kernel_nt1024(uint32_t L, bool gt16, bool rans, bool batched, bool split);
 
 namespace {
 
 using namespace dev;
 
 // ------------------------------------------------------------------------------------------
-// rANS symbols: one warp per request item. The record's coded words are copied to the warp's
-// shared buffer; each step decodes 32 symbols (symbol i on state i mod 32) and writes 16 bytes.
+// rANS symbols: one warp per request item. Table entry per slot: freq | (slot - cum) << 13 |
+// symbol << 25. Full steps of 32 symbols run without bounds checks; the last step is guarded.
+// Returns true if the stream was consumed exactly and every state ended at 2^16.
+template <bool SMEM>
+__device__ __forceinline__ bool rans_steps(const uint32_t* tab, const uint16_t* words, uint32_t nw, uint32_t S,
+                                           uint32_t x, uint32_t ns, uint8_t* out, uint32_t lane) {
+  const uint32_t lt = lanemask_lt();
+  const uint32_t full = S & ~31u;
+  uint8_t* o = out + (lane >> 1);
+  const bool even = !(lane & 1u);
+  uint32_t ptr = 0;
+  bool bad = false;
+  for (uint32_t base = 0; base < full; base += 32u) {
+    const uint32_t e = tab[x & (kRansM - 1u)];
+    const uint32_t s = e >> 25;
+    x = (e & 0x1FFFu) * (x >> 12) + ((e >> 13) & 0xFFFu);
+    const bool need = x < (1u << 16);
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
+    if (need) {
+      const uint32_t at = ptr + __popc(m & lt);
+      bad |= at >= nw;
+      x = (x << 16) | (uint32_t)words[at < nw ? at : 0u];
+    }
+    ptr += __popc(m);
+    const uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, s, 1);
+    if (even) o[base >> 1] = (uint8_t)(s | (hi << 4));
+  }
+  if (full < S) {
+    const uint32_t i = full + lane;
+    const bool active = i < S;
+    uint32_t s = 0;
+    if (active) {
+      const uint32_t e = tab[x & (kRansM - 1u)];
+      s = e >> 25;
+      x = (e & 0x1FFFu) * (x >> 12) + ((e >> 13) & 0xFFFu);
+    }
+    const bool need = active && x < (1u << 16);
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
+    if (need) {
+      const uint32_t at = ptr + __popc(m & lt);
+      bad |= at >= nw;
+      x = (x << 16) | (uint32_t)words[at < nw ? at : 0u];
+    }
+    ptr += __popc(m);
+    const uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, s, 1);
+    if (active && even) o[full >> 1] = (uint8_t)(s | (i + 1 < S ? hi << 4 : 0u));
+  }
+  bad |= ptr != nw;
+  bad |= lane < ns && x != (1u << 16);
+  return !__any_sync(0xFFFFFFFFu, bad);
+}
+
 __global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_kernel(const __grid_constant__ Params P,
                                                                       uint8_t* ws) {
   extern __shared__ __align__(128) unsigned char sm[];
@@ -64,57 +114,49 @@ __global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_kernel(const __g
   const uint32_t np = rec[0], S = rec[1], cb = rec[2];
   const uint32_t ns = S < 32u ? S : 32u;
   const uint32_t nw = cb >> 1;
-  // copy the coded bytes (16-byte aligned span) into this warp's buffer
+  const uint32_t x0 = lane < ns ? rec[4 + lane] : (1u << 16);
+  const bool bad_state = __any_sync(0xFFFFFFFFu, lane < ns && x0 < (1u << 16));
+  uint8_t* out = ws + (size_t)(item - P.ws_item0) * SL.ws_stride;
+  // the coded bytes (a 16-byte aligned span) go to this warp's shared buffer when they fit
   const uint32_t cofs = 16u + 4u * ns + 4u * np;
   const uint32_t a0 = cofs & ~15u, a1 = (cofs + cb + 15u) & ~15u;
-  unsigned char* buf = sm + 4u * kRansM + warp * SL.a_buf;
-  const uint16_t* words;
+  bool ok;
   if (a1 - a0 <= SL.a_buf) {
+    unsigned char* buf = sm + 4u * kRansM + warp * SL.a_buf;
     const uint4* src = reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(rec) + a0);
     uint4* dst = reinterpret_cast<uint4*>(buf);
     for (uint32_t i = lane; i < (a1 - a0) / 16u; i += 32u) dst[i] = src[i];
     __syncwarp();
-    words = reinterpret_cast<const uint16_t*>(buf + (cofs - a0));
+    ok = rans_steps<true>(tab, reinterpret_cast<const uint16_t*>(buf + (cofs - a0)), nw, S, x0, ns, out, lane);
   } else {
-    words = reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(rec) + cofs);
+    ok = rans_steps<false>(tab, reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(rec) + cofs),
+                           nw, S, x0, ns, out, lane);
   }
-  uint8_t* out = ws + (size_t)item * SL.ws_stride;
-  uint32_t x = lane < ns ? rec[4 + lane] : (1u << 16);
-  bool bad = lane < ns && x < (1u << 16);
-  uint32_t ptr = 0;
-  for (uint32_t base = 0; base < S; base += 32u) {
-    const uint32_t i = base + lane;
-    const bool active = i < S;
-    uint32_t s = 0;
-    if (active) {
-      const uint32_t e = tab[x & (kRansM - 1u)];
-      s = e & 15u;
-      x = ((e >> 4) & 0x1FFFu) * (x >> 12) + (e >> 17);
-    }
-    const bool need = active && x < (1u << 16);
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
-    if (need) {
-      const uint32_t at = ptr + __popc(m & lanemask_lt());
-      if (at < nw) x = (x << 16) | (uint32_t)words[at];
-      else bad = true;
-    }
-    ptr += __popc(m);
-    const uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, s, 1);
-    if (active && !(lane & 1u)) out[i >> 1] = (uint8_t)(s | (i + 1 < S ? hi << 4 : 0u));
-  }
-  if (ptr != nw) bad = true;
-  if (lane < ns && x != (1u << 16)) bad = true;
-  if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) report(P.status, VC_ERR_CORRUPT, item);
+  if ((!ok || bad_state) && lane == 0) report(P.status, VC_ERR_CORRUPT, item);
 }
 
 // ------------------------------------------------------------------------------------------
-void* pick_kernel(uint32_t L, uint32_t threads, bool gt16, bool rans, bool batched) {
+void* pick_kernel(uint32_t L, uint32_t threads, bool gt16, bool rans, bool batched, bool split) {
   switch (threads) {
-    case 256: return pick_kernel_nt256(L, gt16, rans, batched);
-    case 512: return pick_kernel_nt512(L, gt16, rans, batched);
-    case 1024: return pick_kernel_nt1024(L, gt16, rans, batched);
+    case 256: return pick_kernel_nt256(L, gt16, rans, batched, split);
+    case 512: return pick_kernel_nt512(L, gt16, rans, batched, split);
+    case 1024: return pick_kernel_nt1024(L, gt16, rans, batched, split);
     default: return nullptr;
   }
+}
+
+void* pick_output_kernel(uint32_t L, bool gt16) {
+#define VC_OUT(LL) \
+  case LL: return gt16 ? reinterpret_cast<void*>(&output_kernel<LL, uint16_t>) : reinterpret_cast<void*>(&output_kernel<LL, uint8_t>);
+  switch (L) {
+    VC_OUT(1)
+    VC_OUT(2)
+    VC_OUT(3)
+    VC_OUT(4)
+    VC_OUT(5)
+    default: return nullptr;
+  }
+#undef VC_OUT
 }
 
 uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -127,7 +169,8 @@ bool schedule_supported(uint32_t L, uint32_t threads) {
   return (threads == 512 || threads == 1024) && L >= 4;
 }
 
-vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, SmemLayout* out) {
+vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, bool split,
+                         SmemLayout* out) {
   const uint32_t L = v.L;
   if (!schedule_supported(L, threads) || nstage < 1 || nstage > 2) return VC_ERR_UNSUPPORTED;
   int optin = 0;
@@ -138,6 +181,7 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   const uint32_t b = 1u << L;
   const uint32_t ncells = ((1u << (3 * L)) - 1u) / 7u;  // levels 0..L-1
   const uint32_t stream_words = (v.max_sym + 7u) / 8u;
+  const uint32_t psum_bytes = v.max_delta ? 4u * (9u * threads + 64u) : 0u;  // general parse path
   uint32_t o = 0;
   s.misc_off = o; o += 512;
   s.lut_off = o; o += 1024;
@@ -147,12 +191,33 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   s.nodes_off = o; o += v.max_delta ? align16(4 * s.nodes_words) : 0u;
   s.dlist_cap = v.max_delta;
   s.dlist_off = o; o += align16(4 * (v.max_delta ? v.max_delta : 1u));
-  s.g_off = o; o += align16(s.gt_bytes * ncells);
-  const uint32_t ncells_r = ((1u << (3 * (L - 1))) - 1u) / 7u;  // ranks are stored for levels 0..L-2
-  s.r_off = o; o += align16(2 * (ncells_r ? ncells_r : 1u));
-  // the finest grid also hosts the general parse path's summaries (9 NT words, padded)
-  s.fg_off = o; o += align16(std::max<uint32_t>(s.gt_bytes * b * b * b, 4u * (9u * threads + 64u)));
-  s.list_off = o; o += align16(2u << (3 * (L - 1)));  // rank -> cell of the stop-0 level-(L-1) cells
+  const uint32_t levels_off = o;
+  s.g_off = o; o += align16(s.gt_bytes * (ncells + 7u));  // level 1 starts at cell 8 (alignment)
+  // per level l >= 1 below L, one byte per level-(l-1) cell: its children's stop-0 bits
+  const uint32_t ns_bytes = ((1u << (3 * (L - 1))) - 1u) / 7u;
+  s.ns_off = o; o += align16(ns_bytes ? ns_bytes : 1u);
+  // the stop-0 cells of each level by rank, two buffers (even / odd levels)
+  uint32_t cap[2] = {1u, 1u};
+  for (uint32_t l = 0; l + 1 <= L; ++l) cap[l & 1u] = std::max(cap[l & 1u], 1u << (3 * l));
+  s.list0_cap = (cap[0] + 7u) & ~7u;
+  s.list_off = o; o += align16(2u * (s.list0_cap + cap[1]));
+  if (split) {
+    // no finest grid here (it goes to a workspace); the parse summaries borrow the level arrays,
+    // which are not in use yet, extended if they are too small
+    s.fg_off = 0;
+    s.psum_off = levels_off;
+    if (o - levels_off < psum_bytes) o = levels_off + align16(psum_bytes);
+    s.pal_cap = 0;
+    s.pal_off = o;
+  } else {
+    // the finest grid also hosts the general parse path's summaries
+    s.fg_off = o; o += align16(std::max<uint32_t>(s.gt_bytes * b * b * b, psum_bytes));
+    s.psum_off = s.fg_off;
+    // private palette copy (frees the stage early); 256 entries for byte grids
+    s.pal_cap = s.gt_bytes == 1 ? 256u : (v.max_pal <= 1024u ? v.max_pal : 0u);
+    s.pal_off = o; o += align16(4u * s.pal_cap);
+  }
+  s.fg_stride = align16(s.gt_bytes * b * b * b) + 16u;
   const uint32_t fixed = o;
   uint32_t stage = align16(v.max_stage) + 16u;  // slack for 8-nibble windows at the end
   if (fixed + nstage * stage > (uint32_t)optin) stage = 0;
@@ -170,17 +235,95 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   return VC_OK;
 }
 
-vc_status launch_decode(const Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
+namespace {
+
+bool set_smem(void* k, uint32_t bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+}
+
+bool launch_symbols(const Params& P, uint8_t* ws, uint32_t base, uint32_t count, uint32_t smem, cudaStream_t s) {
+  Params PA = P;
+  PA.item_base = base;
+  PA.n = base + count;
+  void* args[] = {&PA, &ws};
+  const uint32_t blocks = (count + kRansWarps - 1) / kRansWarps;
+  return cudaLaunchKernel(reinterpret_cast<void*>(&rans_symbols_kernel), dim3(blocks), dim3(32 * kRansWarps), args,
+                          smem, s) == cudaSuccess;
+}
+
+// The pipelined schedule: chunks of request items flow through the rANS symbol kernel (stream 0),
+// the split reconstruction kernel (stream 1) and the output kernel (stream 2); a ring of
+// workspace slots is reused once the chunk that last used it has moved on.
+vc_status launch_pipelined(Volume& v, Params P, uint32_t n, cudaStream_t stream) {
+  const bool rans = v.coder == 1;
+  const uint32_t nt = v.sched.threads;
+  const SmemLayout& SL = v.sm_split;
+  P.v.sm = SL;
+  void* kf = pick_kernel(v.L, nt, SL.gt_bytes == 2, rans, false, true);
+  void* ko = pick_output_kernel(v.L, SL.gt_bytes == 2);
+  if (!kf || !ko) return VC_ERR_UNSUPPORTED;
+  if (!set_smem(kf, SL.total)) return VC_ERR_CUDA;
+  if (rans && !set_smem(reinterpret_cast<void*>(&rans_symbols_kernel), SL.a_smem)) return VC_ERR_CUDA;
+  const uint32_t chunk = std::max<uint32_t>(1u, v.sched.chunk ? v.sched.chunk : 512u);
+  const uint32_t nchunks = (n + chunk - 1) / chunk;
+  const uint32_t ring = std::min<uint32_t>(kRing, nchunks);
+  uint8_t *ws = nullptr, *fgws = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&fgws), (size_t)ring * chunk * SL.fg_stride, stream) != cudaSuccess ||
+      (rans && cudaMallocAsync(reinterpret_cast<void**>(&ws), (size_t)ring * chunk * SL.ws_stride, stream) != cudaSuccess)) {
+    cudaGetLastError();
+    if (fgws) cudaFreeAsync(fgws, stream);
+    return VC_ERR_OOM;
+  }
+  const cudaStream_t sA = v.aux[0], sF = v.aux[1], sO = v.aux[2];
+  vc_status rc = VC_OK;
+  auto ok = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == VC_OK) rc = VC_ERR_CUDA;
+    return e == cudaSuccess;
+  };
+  ok(cudaEventRecord(v.ev_fork, stream));
+  ok(cudaStreamWaitEvent(sA, v.ev_fork, 0));
+  ok(cudaStreamWaitEvent(sF, v.ev_fork, 0));
+  ok(cudaStreamWaitEvent(sO, v.ev_fork, 0));
+  for (uint32_t k = 0; k < nchunks && rc == VC_OK; ++k) {
+    const uint32_t base = k * chunk, cnt = std::min(chunk, n - base), slot = k % ring;
+    Params Q = P;
+    Q.item_base = base;
+    Q.n = base + cnt;
+    Q.ws_item0 = base;
+    Q.ws = ws ? ws + (size_t)slot * chunk * SL.ws_stride : nullptr;
+    Q.fgws = fgws + (size_t)slot * chunk * SL.fg_stride;
+    if (rans) {
+      if (k >= ring) ok(cudaStreamWaitEvent(sA, v.ev_f[slot], 0));  // symbols slot read by F(k - ring)
+      ok(launch_symbols(Q, const_cast<uint8_t*>(Q.ws), base, cnt, SL.a_smem, sA) ? cudaSuccess : cudaErrorLaunchFailure);
+      ok(cudaEventRecord(v.ev_a[slot], sA));
+      ok(cudaStreamWaitEvent(sF, v.ev_a[slot], 0));
+    }
+    if (k >= ring) ok(cudaStreamWaitEvent(sF, v.ev_o[slot], 0));  // grid slot read by O(k - ring)
+    void* argsF[] = {&Q};
+    ok(cudaLaunchKernel(kf, dim3(cnt), dim3(nt), argsF, SL.total, sF));
+    ok(cudaEventRecord(v.ev_f[slot], sF));
+    ok(cudaStreamWaitEvent(sO, v.ev_f[slot], 0));
+    void* argsO[] = {&Q};
+    ok(cudaLaunchKernel(ko, dim3(cnt), dim3(256), argsO, 0, sO));
+    ok(cudaEventRecord(v.ev_o[slot], sO));
+    v.launches += rans ? 3 : 2;
+  }
+  // join: the caller's stream waits for all three
+  ok(cudaEventRecord(v.ev_join[0], sA));
+  ok(cudaEventRecord(v.ev_join[1], sF));
+  ok(cudaEventRecord(v.ev_join[2], sO));
+  for (int i = 0; i < 3; ++i) ok(cudaStreamWaitEvent(stream, v.ev_join[i], 0));
+  cudaFreeAsync(fgws, stream);
+  if (ws) cudaFreeAsync(ws, stream);
+  return rc;
+}
+
+}  // namespace
+
+vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
                         uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream) {
   if (n == 0) return VC_OK;
   const bool rans = v.coder == 1;
-  const bool batched = mode == VC_MODE_BATCHED;
-  const uint32_t nt = v.sched.threads;
-  void* k = pick_kernel(v.L, nt, v.dv.sm.gt_bytes == 2, rans, batched);
-  if (!k) return VC_ERR_UNSUPPORTED;
-  const uint32_t smem = v.dv.sm.total;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return VC_ERR_CUDA;
   Params P;
   P.v = v.dv;
   P.ids = ids;
@@ -191,6 +334,17 @@ vc_status launch_decode(const Volume& v, const uint32_t* ids, uint32_t n, const 
   P.status = status;
   P.item_base = 0;
   P.ws = nullptr;
+  P.fgws = nullptr;
+  P.ws_item0 = 0;
+  // coarse levels of detail are written by the reconstruction kernel itself
+  if (mode == VC_MODE_PIPELINED && lod == 0) return launch_pipelined(v, P, n, stream);
+  if (mode == VC_MODE_PIPELINED) mode = VC_MODE_GRID;
+  const bool batched = mode == VC_MODE_BATCHED;
+  const uint32_t nt = v.sched.threads;
+  void* k = pick_kernel(v.L, nt, v.dv.sm.gt_bytes == 2, rans, batched, false);
+  if (!k) return VC_ERR_UNSUPPORTED;
+  const uint32_t smem = v.dv.sm.total;
+  if (!set_smem(k, smem)) return VC_ERR_CUDA;
   uint8_t* ws = nullptr;
   if (rans) {
     if (cudaMallocAsync(reinterpret_cast<void**>(&ws), (size_t)n * v.dv.sm.ws_stride, stream) != cudaSuccess) {
@@ -198,33 +352,38 @@ vc_status launch_decode(const Volume& v, const uint32_t* ids, uint32_t n, const 
       return VC_ERR_OOM;
     }
     P.ws = ws;
-    void* ka = reinterpret_cast<void*>(&rans_symbols_kernel);
-    if (cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.dv.sm.a_smem) != cudaSuccess) {
+    if (!set_smem(reinterpret_cast<void*>(&rans_symbols_kernel), v.dv.sm.a_smem)) {
       cudaFreeAsync(ws, stream);
       return VC_ERR_CUDA;
     }
   }
   vc_status rc = VC_OK;
+  // timing events of this call (grid and batched schedules), if profiling is on and a set is free
+  cudaEvent_t* ev = nullptr;
+  if (v.prof && mode != VC_MODE_PLAIN) {
+    if (v.prof_used < kProfCalls) ev = v.prof_ev + 3 * v.prof_used++;
+    else ++v.prof_dropped;
+  }
+  auto mark = [&](int i) { return !ev || cudaEventRecord(ev[i], stream) == cudaSuccess; };
   auto run_symbols = [&](uint32_t base, uint32_t count) -> bool {
     if (!rans) return true;
-    Params PA = P;
-    PA.item_base = base;
-    PA.n = base + count;
-    void* args[] = {&PA, &ws};
-    const uint32_t blocks = (count + kRansWarps - 1) / kRansWarps;
-    return cudaLaunchKernel(reinterpret_cast<void*>(&rans_symbols_kernel), dim3(blocks), dim3(32 * kRansWarps), args,
-                            v.dv.sm.a_smem, stream) == cudaSuccess;
+    if (!launch_symbols(P, ws, base, count, v.dv.sm.a_smem, stream)) return false;
+    ++v.launches;
+    return true;
   };
-  void* args[] = {&P};
+  auto run = [&](dim3 grid) -> bool {
+    void* args[] = {&P};
+    if (cudaLaunchKernel(k, grid, dim3(nt), args, smem, stream) != cudaSuccess) return false;
+    ++v.launches;
+    return true;
+  };
   if (mode == VC_MODE_PLAIN) {
     for (uint32_t i = 0; i < n && rc == VC_OK; ++i) {
       P.item_base = i;
-      if (!run_symbols(i, 1) || cudaLaunchKernel(k, dim3(1), dim3(nt), args, smem, stream) != cudaSuccess)
-        rc = VC_ERR_CUDA;
+      if (!run_symbols(i, 1) || !run(dim3(1))) rc = VC_ERR_CUDA;
     }
   } else if (mode == VC_MODE_GRID) {
-    if (!run_symbols(0, n) || cudaLaunchKernel(k, dim3(n), dim3(nt), args, smem, stream) != cudaSuccess)
-      rc = VC_ERR_CUDA;
+    if (!mark(0) || !run_symbols(0, n) || !mark(1) || !run(dim3(n)) || !mark(2)) rc = VC_ERR_CUDA;
   } else {
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, v.device) != cudaSuccess ||
@@ -235,9 +394,9 @@ vc_status launch_decode(const Volume& v, const uint32_t* ids, uint32_t n, const 
     } else {
       if (v.sched.blocks_per_sm) per_sm = std::min<int>(per_sm, (int)v.sched.blocks_per_sm);
       const uint32_t grid = std::min<uint32_t>(n, (uint32_t)(sms * per_sm));
-      if (!run_symbols(0, n) ||
+      if (!mark(0) || !run_symbols(0, n) ||
           cudaMemsetAsync(reinterpret_cast<uint32_t*>(status) + 2, 0, sizeof(uint32_t), stream) != cudaSuccess ||
-          cudaLaunchKernel(k, dim3(grid), dim3(nt), args, smem, stream) != cudaSuccess)
+          !mark(1) || !run(dim3(grid)) || !mark(2))
         rc = VC_ERR_CUDA;
     }
   }

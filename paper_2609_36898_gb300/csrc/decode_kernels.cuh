@@ -24,6 +24,8 @@ struct Params {
   int32_t* status;
   uint32_t item_base;
   const uint8_t* ws;  // decoded rANS symbols, ws_stride bytes per item (nullptr for plain volumes)
+  uint8_t* fgws;      // split schedule: finest index grids, fg_stride bytes per item
+  uint32_t ws_item0;  // the workspaces hold items ws_item0 .. (a chunk of the request)
 };
 
 template <typename GT>
@@ -83,6 +85,13 @@ __device__ __forceinline__ uint32_t nib8_at(const uint32_t* w, uint32_t j) {
 __device__ __forceinline__ uint32_t bits8_at(const uint32_t* w, uint32_t j) {
   const uint32_t lo = w[j >> 5], hi = w[(j >> 5) + 1];
   return __funnelshift_r(lo, hi, j & 31u) & 0xFFu;
+}
+// bits 4i of z gathered into bits i (8 bits)
+__device__ __forceinline__ uint32_t gather_nib_bits(uint32_t z) {
+  z = (z | (z >> 3)) & 0x03030303u;
+  z = (z | (z >> 6)) & 0x000F000Fu;
+  z = (z | (z >> 12)) & 0xFFu;
+  return z;
 }
 // bit i set iff (nibble i & 7) == v, for the 8 nibbles of x
 __device__ __forceinline__ uint32_t nib_eq8(uint32_t x, uint32_t v) {
@@ -232,9 +241,23 @@ __device__ __forceinline__ void parse_emit(const uint32_t* sw, uint32_t S, uint3
                                            uint32_t* dlist, uint32_t dcap, const uint32_t* lut) {
   uint32_t j = jstart;
   uint64_t acc = 0;
+  auto flush = [&](uint32_t wi) {
+    if (wi < nodes_words) {
+      if (wi == (jstart >> 3) && (jstart & 7u)) atomicOr(&nodes[wi], (uint32_t)acc);
+      else nodes[wi] = (uint32_t)acc;
+    }
+    acc >>= 32;
+  };
   for (uint32_t w = w0; w < w1; ++w) {
     const uint32_t x = sw[w];
     const uint32_t left = S - 8u * w;
+    if (st == 0 && left >= 8u && nib_eq8(x, OP_DELTA) == 0) {
+      // from an operation, 8 symbols none of which can start or continue a delta: 8 operations
+      acc |= (uint64_t)x << (4u * (j & 7u));
+      j += 8;
+      flush((j - 8u) >> 3);
+      continue;
+    }
     const uint32_t nb = left >= 8u ? 4u : (left + 1u) >> 1;
 #pragma unroll
     for (uint32_t k = 0; k < 4; ++k) {
@@ -244,20 +267,13 @@ __device__ __forceinline__ void parse_emit(const uint32_t* sw, uint32_t S, uint3
         const uint32_t p = j & 7u;
         acc |= (uint64_t)(f >> 5) << (4u * p);
         j += cnt;
-        if (p + cnt >= 8u) {  // a word of 8 node symbols is complete
-          const uint32_t wi = (j - cnt) >> 3;
-          if (wi < nodes_words) {
-            if (wi == (jstart >> 3) && (jstart & 7u)) atomicOr(&nodes[wi], (uint32_t)acc);
-            else nodes[wi] = (uint32_t)acc;
-          }
-          acc >>= 32;
-        }
+        if (p + cnt >= 8u) flush((j - cnt) >> 3);  // a word of 8 node symbols is complete
         const uint32_t delm = (f >> 3) & 3u;
         if (delm) {
 #pragma unroll
           for (uint32_t h = 0; h < 2; ++h)
             if (delm & (1u << h)) {
-              if (d < dcap) dlist[d] = read_delta(sw, 8u * w + 2u * k + h + 1u, S);
+              if (d < dcap) dlist[d] = 8u * w + 2u * k + h + 1u;  // first entry; resolved after the parse
               ++d;
             }
         }
@@ -287,6 +303,10 @@ __device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes
     for (uint32_t w = w0; w < w1; ++w) {
       const uint32_t x = sw[w];
       const uint32_t left = S - 8u * w;
+      if (st == 0 && left >= 8u && nib_eq8(x, OP_DELTA) == 0) {
+        n += 8;
+        continue;
+      }
       const uint32_t nb = left >= 8u ? 4u : (left + 1u) >> 1;
 #pragma unroll
       for (uint32_t k = 0; k < 4; ++k) {
@@ -448,9 +468,13 @@ __device__ __forceinline__ void store_pair(GT* fg, uint32_t pos, uint32_t lo, ui
 // ------------------------------------------------------------------------------------------
 // Decode one brick. head: the record (header, [states], palette) in shared or global memory;
 // sw: its symbols as packed nibbles (u32 aligned); out: destination of (b >> lod)^3 labels.
-template <int L, typename GT, bool RANS, int NT>
+// on_stage_free() is called by every thread exactly once, as soon as the staged record is no longer
+// read: right after the finest grid is filled when the palette fits its shared copy, else at the end.
+// SPLIT: the finest index grid goes to fg_global (global memory) and the output pass is left to
+// output_kernel; otherwise the grid lives in shared memory and labels are written here.
+template <int L, typename GT, bool RANS, int NT, bool SPLIT, typename Hook>
 __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32_t* sw, uint32_t* out,
-                             unsigned char* sm, int* s_err) {
+                             unsigned char* sm, int* s_err, Hook&& on_stage_free, GT* fg_global) {
   constexpr uint32_t NW = NT / 32;
   constexpr uint32_t MARK = GridT<GT>::MARK;
   const SmemLayout& SL = P.v.sm;
@@ -465,6 +489,13 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   BrickCtx c;
   c.pal = head + 4 + ns;
   c.n_pal = n_pal;
+  const bool pal_copied = !SPLIT && n_pal <= SL.pal_cap;
+  if (pal_copied) {  // a private copy of the palette frees the stage before the output pass; byte
+                     // grids get 256 entries (zero padded) so that any byte index stays in bounds
+    uint32_t* pc = reinterpret_cast<uint32_t*>(sm + SL.pal_off);
+    for (uint32_t i = tid; i < SL.pal_cap; i += NT) pc[i] = i < n_pal ? c.pal[i] : 0u;
+    c.pal = pc;  // read after the barriers of the steps below
+  }
   c.op_mask = P.v.op_mask;
   c.s_err = s_err;
   uint32_t* dlist = reinterpret_cast<uint32_t*>(sm + SL.dlist_off);
@@ -480,10 +511,13 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     // the general parse path borrows the finest grid (not in use yet) for its summaries
     const ParseOut po = parse_stream<NT>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap,
                                          reinterpret_cast<const uint32_t*>(sm + SL.lut_off), scan_tmp,
-                                         reinterpret_cast<uint32_t*>(sm + SL.fg_off), s_err);
+                                         reinterpret_cast<uint32_t*>(sm + SL.psum_off), s_err);
     c.nodes = nodes;
     c.n_nodes = po.n_nodes;
     if (po.n_delta != nd) set_err(s_err, VC_ERR_CORRUPT);
+    // delta values from their entries, one delta operation per thread (visible after the barriers
+    // of step 2)
+    for (uint32_t d = tid; d < c.dlist_cap; d += NT) dlist[d] = read_delta(sw, dlist[d], S);
   }
 
   // 2. palette-cursor masks and prefix counts (32 nodes per word)
@@ -521,281 +555,284 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   }
   __syncthreads();
 
-  // 3. coarse levels
+  // 3. coarse levels 0..L-1, parent-major. G: palette index per cell (Morton order, levels
+  // 0..L-1). NS: for level l >= 1, one byte per level-(l-1) cell whose bit o says that child o
+  // was emitted with stop bit 0. The stop-0 cells of a level, in rank (= stream) order, go to one
+  // of two lists; the next level's children of rank r are nodes off + 8 r .. off + 8 r + 7.
   const uint32_t Lout = (uint32_t)L - P.lod;
   const uint32_t last_coarse = Lout < (uint32_t)L ? Lout : (uint32_t)L - 1u;
   GT* G = reinterpret_cast<GT*>(sm + SL.g_off);
-  uint16_t* R = reinterpret_cast<uint16_t*>(sm + SL.r_off);  // ranks of levels 0..L-2
+  uint8_t* NS = sm + SL.ns_off;
+  uint16_t* lists[2] = {reinterpret_cast<uint16_t*>(sm + SL.list_off),
+                        reinterpret_cast<uint16_t*>(sm + SL.list_off) + SL.list0_cap};
   const bool no_stop = (P.v.flags & kFlagNoStop) != 0;
   constexpr uint32_t b = 1u << L;
   const bool finest = Lout == (uint32_t)L;
-  GT* fg = reinterpret_cast<GT*>(sm + SL.fg_off);
-  uint16_t* plist = reinterpret_cast<uint16_t*>(sm + SL.list_off);
-  const uint32_t flane = flin<L>(lane);  // finest-grid offset contributed by the lane bits of a cell
-  uint32_t off = 0, Nl = 1, gofs = 0, gofs_prev = 0;
+  GT* fg = SPLIT ? fg_global : reinterpret_cast<GT*>(sm + SL.fg_off);
 
-  // pass 1 for cell m of level l: its palette index (or a neighbour mark) into G; true if it is
-  // emitted with stop bit 0. Cells below a stopped node inherit the parent's index.
-  auto cell_pass1 = [&](uint32_t l, uint32_t m, GT* Gl, const GT* Gp, const uint16_t* Rp) -> bool {
-    bool emitted = true;
-    uint32_t j = 0;
-    if (l > 0) {
-      const uint32_t r = Rp[m >> 3];
-      emitted = r != NONE16;
-      j = off + 8u * r + (m & 7u);
+  // the 8 children (nodes j0 .. j0+7) of a stop-0 cell with index gp at coordinates (px, py, pz):
+  // palette indices or neighbour marks into v, returns the children emitted with stop bit 0
+  auto decode8 = [&](uint32_t j0, uint32_t gp, uint32_t px, uint32_t py, uint32_t pz, bool at_finest,
+                     uint32_t (&v)[8]) -> uint32_t {
+    if (j0 + 8u > c.n_nodes) {
+      set_err(s_err, VC_ERR_CORRUPT);
+#pragma unroll
+      for (int o = 0; o < 8; ++o) v[o] = 0;
+      return 0;
     }
-    uint32_t g = 0;
-    bool nonstop = false;
-    if (!emitted) {
-      g = Gp[m >> 3];
-    } else if (j >= c.n_nodes) {
+    const uint32_t ops = nib8_at(c.nodes, j0);
+    // per-child class masks (SWAR over the 8 operation nibbles)
+    const uint32_t m_nx = nib_eq8(ops, OP_NX), m_ny = nib_eq8(ops, OP_NY), m_nz = nib_eq8(ops, OP_NZ);
+    const uint32_t m_7 = nib_eq8(ops, 7u);
+    const uint32_t m_pal = gather_nib_bits((ops & 0x44444444u) >> 2) & ~m_7;  // advance, last, delta
+    bool bad = ((ops & 0x88888888u) != 0 && (at_finest || no_stop)) || m_7 != 0;
+    // a neighbour copy needs that coordinate even (child bit 0) and > 0
+    bad |= (m_nx & ~(px ? 0x55u : 0u)) | (m_ny & ~(py ? 0x33u : 0u)) | (m_nz & ~(pz ? 0x0Fu : 0u));
+    if (c.op_mask != 0x7Fu) {
+#pragma unroll
+      for (uint32_t o = 0; o < 7; ++o)
+        if (!((c.op_mask >> o) & 1u)) bad |= nib_eq8(ops, o) != 0;
+    }
+    // parent copies and neighbour marks
+#pragma unroll
+    for (uint32_t o = 0; o < 8; ++o) {
+      const uint32_t op = (ops >> (4u * o)) & 7u;
+      v[o] = op == OP_PARENT ? gp : MARK + op - OP_NX;
+    }
+    if (m_pal) {  // palette reads (a minority of nodes): cursor from the masks
+      const uint32_t adv8 = bits8_at(adv_mask, j0), del8 = bits8_at(del_mask, j0);
+      const uint32_t w = j0 >> 5, lt = (1u << (j0 & 31u)) - 1u;
+      const uint32_t k0 = adv_pre[w] + __popc(adv_mask[w] & lt);
+      const uint32_t dd0 = del_pre[w] + __popc(del_mask[w] & lt);
+#pragma unroll
+      for (uint32_t o = 0; o < 8; ++o) {
+        if ((m_pal >> o) & 1u) {
+          const uint32_t op = (ops >> (4u * o)) & 7u;
+          const uint32_t below = (1u << o) - 1u;
+          const uint32_t k = k0 + __popc(adv8 & below);
+          if (op == OP_ADV) {
+            bad |= k >= n_pal;
+            v[o] = k;
+          } else if (op == OP_LAST) {
+            bad |= k == 0u;
+            v[o] = k - 1u;
+          } else {
+            const uint32_t di = dd0 + __popc(del8 & below);
+            const uint32_t delta = di < c.dlist_cap ? dlist[di] : 0u;
+            bad |= delta == 0u || delta > k;
+            v[o] = k - delta;
+          }
+        }
+      }
+    }
+    if (bad) {
+      set_err(s_err, VC_ERR_CORRUPT);
+#pragma unroll
+      for (int o = 0; o < 8; ++o) v[o] = 0;  // keep invalid indices out of the grids
+    }
+    return gather_nib_bits((~ops & 0x88888888u) >> 3);  // children with stop bit 0
+  };
+  auto store8 = [&](GT* dst, const uint32_t (&v)[8]) {  // 8 consecutive cells
+    if constexpr (sizeof(GT) == 1) {
+      *reinterpret_cast<uint2*>(dst) = make_uint2(v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24),
+                                                  v[4] | (v[5] << 8) | (v[6] << 16) | (v[7] << 24));
+    } else {
+      *reinterpret_cast<uint4*>(dst) = make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16),
+                                                  v[6] | (v[7] << 16));
+    }
+  };
+
+  // level 0: the root (node 0) must be a palette advance
+  if (tid == 0) {
+    uint32_t ns0 = 0, g0 = 0;
+    if (c.n_nodes == 0) {
       set_err(s_err, VC_ERR_CORRUPT);
     } else {
-      const uint32_t s = nib_at(c.nodes, j), o = s & 7u, stop = s >> 3;
-      if (o == 7u || !((c.op_mask >> o) & 1u) || (stop && no_stop)) set_err(s_err, VC_ERR_CORRUPT);
-      if (o == OP_PARENT) {
-        if (l == 0) set_err(s_err, VC_ERR_CORRUPT);
-        else g = Gp[m >> 3];
-      } else if (o <= OP_NZ) {
-        const uint32_t a = o - OP_NX;
-        if (((m >> a) & 1u) || (m & (0x09249249u << a)) == 0) set_err(s_err, VC_ERR_CORRUPT);
-        else g = MARK + a;
-      } else if (o != 7u) {
-        g = pal_index(c, j, o);
-      }
-      nonstop = !stop;
+      const uint32_t s0 = nib_at(c.nodes, 0);
+      if ((s0 & 7u) != OP_ADV || n_pal == 0 || ((s0 >> 3) && no_stop)) set_err(s_err, VC_ERR_CORRUPT);
+      ns0 = (s0 >> 3) ? 0u : 1u;
     }
-    Gl[m] = (GT)g;
-    return nonstop;
+    G[0] = (GT)g0;
+    lists[0][0] = 0;
+    misc[8] = ns0;
+  }
+  __syncthreads();
+  const bool root_open = misc[8] != 0;
+  // level grids: the root at 0, level l >= 1 at 8 + (8^l - 8) / 7, so that every 8 siblings are
+  // one aligned 8-cell group (stored with one vector store)
+  uint32_t off = 1, npar = root_open ? 1u : 0u, gofs_prev = 0, gofs = 8, nsofs_prev = 0, nsofs = 0;
+  // is level-l cell p emitted with stop bit 0?  (l >= 1: from the level's NS bytes)
+  auto open_cell = [&](uint32_t l, uint32_t p, uint32_t nso) -> bool {
+    return l == 0 ? root_open : ((NS[nso + (p >> 3)] >> (p & 7u)) & 1u) != 0;
   };
-  // pass 2 for cell m: final palette index (marks resolved); on the last level before the finest,
-  // constant 2^3 blocks are written to the finest grid and stop-0 cells listed by rank r.
-  auto cell_pass2 = [&](uint32_t m, GT* Gl, bool feed_finest, uint32_t r) {
-    uint32_t g = Gl[m];
-    if (g >= MARK) {
-      g = resolve_morton<GT>(Gl, m, g, s_err);
-      Gl[m] = (GT)g;
+  for (uint32_t l = 1; l <= last_coarse; ++l) {
+    const uint32_t parents = 1u << (3u * (l - 1u));
+    GT* Gl = G + gofs;
+    const GT* Gp = G + gofs_prev;
+    uint8_t* NSl = NS + nsofs;  // this level's bytes (indexed by parent)
+    const uint16_t* list_prev = lists[(l - 1u) & 1u];
+    uint16_t* list_cur = lists[l & 1u];
+    // children of stopped (or not emitted) parents inherit the parent's index
+    for (uint32_t p = tid; p < parents; p += NT) {
+      if (!open_cell(l - 1u, p, nsofs_prev)) {
+        const uint32_t g = Gp[p];
+        const uint32_t v[8] = {g, g, g, g, g, g, g, g};
+        store8(Gl + 8u * p, v);
+        NSl[p] = 0;
+      }
     }
-    if (feed_finest) {
-      if (r != NONE16) {
-        plist[r] = (uint16_t)m;
-      } else {
-        const uint32_t f0 = flane + flin<L>(m - lane);
+    // children of stop-0 parents: a contiguous run of ranks per thread
+    const uint32_t per = (npar + NT - 1u) / NT;
+    const uint32_t r0 = min(tid * per, npar), r1 = min(r0 + per, npar);
+    uint32_t cnt = 0;
+    for (uint32_t r = r0; r < r1; ++r) {
+      const uint32_t p = list_prev[r];
+      uint32_t v[8];
+      const uint32_t open8 = decode8(off + 8u * r, Gp[p], compact3(p), compact3(p >> 1), compact3(p >> 2), false, v);
+      store8(Gl + 8u * p, v);
+      NSl[p] = (uint8_t)open8;
+      cnt += __popc(open8);
+    }
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= (uint32_t)o) inc += t;
+    }
+    if (lane == 31) wtot[warp] = inc;
+    __syncthreads();
+    uint32_t base = inc - cnt, total = 0;
+    for (uint32_t w = 0; w < NW; ++w) {
+      const uint32_t t = wtot[w];
+      if (w < warp) base += t;
+      total += t;
+    }
+    // list this level's stop-0 cells by rank; resolve the neighbour marks among the children
+    for (uint32_t r = r0; r < r1; ++r) {
+      const uint32_t p = list_prev[r];
+      uint32_t open8 = NSl[p];
+      while (open8) {
+        const uint32_t o = __ffs(open8) - 1u;
+        open8 &= open8 - 1u;
+        list_cur[base++] = (uint16_t)(8u * p + o);
+      }
+#pragma unroll
+      for (uint32_t o = 0; o < 8; ++o) {
+        const uint32_t m = 8u * p + o;
+        const uint32_t g = Gl[m];
+        if (g >= MARK) Gl[m] = (GT)resolve_morton<GT>(Gl, m, g, s_err);
+      }
+    }
+    __syncthreads();
+    off += 8u * npar;
+    npar = total;
+    gofs_prev = gofs;
+    gofs += 1u << (3u * l);
+    nsofs_prev = nsofs;
+    nsofs += parents;
+  }
+
+  if (finest) {
+    // 4. finest level: constant blocks of stopped level-(L-1) cells, then the 8 operations of each
+    // stop-0 cell (from the rank list)
+    if (tid == 0 && off + 8u * npar != c.n_nodes) set_err(s_err, VC_ERR_CORRUPT);
+    const GT* Gp = G + gofs_prev;
+    constexpr uint32_t pcells = 1u << (3 * (L - 1));
+    constexpr uint32_t PC = (pcells + NT - 1) / NT;
+    const uint32_t ftid = flin<L>(tid & (NT - 1u) & (pcells - 1u));
+#pragma unroll
+    for (uint32_t k = 0; k < PC; ++k) {
+      const uint32_t p = tid + k * NT;  // with NT a power of two, p's bits are tid's plus k * NT's
+      if (p < pcells && !open_cell(L - 1u, p, nsofs_prev)) {
+        const uint32_t g = Gp[p];
+        const uint32_t f0 = pcells > NT ? ftid + flin<L>(k * NT) : flin<L>(p);
         store_pair<GT>(fg, f0, g, g);
         store_pair<GT>(fg, f0 + b, g, g);
         store_pair<GT>(fg, f0 + b * b, g, g);
         store_pair<GT>(fg, f0 + b * b + b, g, g);
       }
     }
-  };
-
-  // levels of at most 64 cells: warp 0 alone, no block barriers
-  uint32_t l = 0;
-  if (warp == 0) {
-    for (; l <= last_coarse && l <= 2u; ++l) {
-      const uint32_t cells = 1u << (3u * l);
-      const bool final_level = l == last_coarse;
-      GT* Gl = G + gofs;
-      const GT* Gp = G + gofs_prev;
-      uint16_t* Rl = R + gofs;
-      const uint16_t* Rp = R + gofs_prev;
-      uint32_t running = 0, lr[2] = {NONE16, NONE16};
-#pragma unroll
-      for (uint32_t k = 0; k < 2; ++k) {
-        const uint32_t m = 32u * k + lane;
-        const bool nonstop = m < cells && cell_pass1(l, m, Gl, Gp, Rp);
-        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, nonstop);
-        const uint32_t r = nonstop ? running + __popc(bal & lanemask_lt()) : NONE16;
-        if (m < cells && !final_level) Rl[m] = (uint16_t)r;
-        lr[k] = r;
-        running += __popc(bal);
-      }
-      __syncwarp();
-#pragma unroll
-      for (uint32_t k = 0; k < 2; ++k) {
-        const uint32_t m = 32u * k + lane;
-        if (m < cells) cell_pass2(m, Gl, final_level && finest, lr[k]);
-      }
-      __syncwarp();
-      off += Nl;
-      Nl = 8u * running;
-      gofs_prev = gofs;
-      gofs += cells;
-    }
-    if (lane == 0) { misc[8] = off; misc[9] = Nl; misc[10] = gofs; misc[11] = gofs_prev; misc[12] = l; }
-  }
-  __syncthreads();
-  off = misc[8]; Nl = misc[9]; gofs = misc[10]; gofs_prev = misc[11]; l = misc[12];
-
-  // larger levels: every warp owns a contiguous run of cells; ranks are completed with the other
-  // warps' totals after a barrier
-  for (; l <= last_coarse; ++l) {
-    const uint32_t cells = 1u << (3u * l);
-    const uint32_t nwa = min(NW, cells >> 5);
-    const uint32_t cpw = cells / nwa;
-    GT* Gl = G + gofs;
-    const GT* Gp = G + gofs_prev;
-    uint16_t* Rl = R + gofs;
-    const uint16_t* Rp = R + gofs_prev;
-    if (l < last_coarse) {
-      if (warp < nwa) {
-        uint32_t running = 0;
-        for (uint32_t base = warp * cpw; base < (warp + 1) * cpw; base += 32u) {
-          const uint32_t m = base + lane;
-          const bool nonstop = cell_pass1(l, m, Gl, Gp, Rp);
-          const uint32_t bal = __ballot_sync(0xFFFFFFFFu, nonstop);
-          Rl[m] = nonstop ? (uint16_t)(running + __popc(bal & lanemask_lt())) : NONE16;
-          running += __popc(bal);
-        }
-        if (lane == 0) wtot[warp] = running;
-      }
-      __syncthreads();
-      uint32_t total = 0, before = 0;
-      for (uint32_t w = 0; w < nwa; ++w) {
-        const uint32_t t = wtot[w];
-        if (w < warp) before += t;
-        total += t;
-      }
-      if (warp < nwa) {
-        for (uint32_t m = warp * cpw + lane; m < (warp + 1) * cpw; m += 32u) {
-          if (before) {
-            const uint32_t r = Rl[m];
-            if (r != NONE16) Rl[m] = (uint16_t)(r + before);
-          }
-          cell_pass2(m, Gl, false, NONE16);
-        }
-      }
-      __syncthreads();
-      off += Nl;
-      Nl = 8u * total;
-    } else {
-      // the last coarse level: its ranks are needed only to list the finest level's parents, and
-      // stay in registers
-      constexpr uint32_t LC = 1u << (3 * (L - 1));
-      constexpr uint32_t NWA = (LC >> 5) < NW ? (LC >> 5) : NW;
-      constexpr uint32_t CPL = NWA ? LC / (NWA * 32u) : 1u;
-      uint32_t lr[CPL];
-      if (warp < nwa) {
-        uint32_t running = 0;
-#pragma unroll
-        for (uint32_t k = 0; k < CPL; ++k) {
-          const uint32_t m = warp * cpw + 32u * k + lane;
-          const bool nonstop = 32u * k < cpw && cell_pass1(l, m, Gl, Gp, Rp);
-          const uint32_t bal = __ballot_sync(0xFFFFFFFFu, nonstop);
-          lr[k] = nonstop ? running + __popc(bal & lanemask_lt()) : NONE16;
-          running += __popc(bal);
-        }
-        if (lane == 0) wtot[warp] = running;
-      }
-      __syncthreads();
-      uint32_t total = 0, before = 0;
-      for (uint32_t w = 0; w < nwa; ++w) {
-        const uint32_t t = wtot[w];
-        if (w < warp) before += t;
-        total += t;
-      }
-      if (warp < nwa) {
-#pragma unroll
-        for (uint32_t k = 0; k < CPL; ++k) {
-          const uint32_t m = warp * cpw + 32u * k + lane;
-          if (32u * k < cpw) cell_pass2(m, Gl, finest, lr[k] == NONE16 ? NONE16 : lr[k] + before);
-        }
-      }
-      __syncthreads();
-      off += Nl;
-      Nl = 8u * total;
-    }
-    gofs_prev = gofs;
-    gofs += cells;
-  }
-
-  if (finest) {
-    // 4. finest level: the blocks of the listed (stop-0) level-(L-1) cells, from their 8 operations
-    if (tid == 0 && off + Nl != c.n_nodes) set_err(s_err, VC_ERR_CORRUPT);
-    const GT* Gp = G + gofs_prev;
-    const uint32_t nparents = Nl >> 3;
-    for (uint32_t r = tid; r < nparents; r += NT) {
-      const uint32_t m = plist[r];
-      const uint32_t px = compact3(m), py = compact3(m >> 1), pz = compact3(m >> 2);
-      const uint32_t f0 = flin<L>(m);
-      const uint32_t gp = Gp[m];
+    const uint16_t* plist = lists[(L - 1u) & 1u];
+    for (uint32_t r = tid; r < npar; r += NT) {
+      const uint32_t p = plist[r];
       uint32_t v[8];
-      const uint32_t j0 = off + 8u * r;
-      if (j0 + 8u > c.n_nodes) {
-        set_err(s_err, VC_ERR_CORRUPT);
-#pragma unroll
-        for (int o = 0; o < 8; ++o) v[o] = 0;
-      } else {
-        const uint32_t ops = nib8_at(c.nodes, j0);
-        if (ops & 0x88888888u) set_err(s_err, VC_ERR_CORRUPT);  // stop bit at the finest level
-        const uint32_t adv8 = bits8_at(adv_mask, j0), del8 = bits8_at(del_mask, j0);
-        const uint32_t w = j0 >> 5, lt = (1u << (j0 & 31u)) - 1u;
-        const uint32_t k0 = adv_pre[w] + __popc(adv_mask[w] & lt);
-        const uint32_t dd0 = del_pre[w] + __popc(del_mask[w] & lt);
-#pragma unroll
-        for (uint32_t o = 0; o < 8; ++o) {
-          const uint32_t op = (ops >> (4u * o)) & 7u;
-          const uint32_t below = (1u << o) - 1u;
-          uint32_t val = 0;
-          if (op == 7u || !((c.op_mask >> op) & 1u)) {
-            set_err(s_err, VC_ERR_CORRUPT);
-          } else if (op == OP_PARENT) {
-            val = gp;
-          } else if (op <= OP_NZ) {
-            const uint32_t a = op - OP_NX;
-            const uint32_t pc = a == 0 ? px : (a == 1 ? py : pz);
-            if (((o >> a) & 1u) || pc == 0) set_err(s_err, VC_ERR_CORRUPT);
-            else val = MARK + a;
-          } else {
-            const uint32_t k = k0 + __popc(adv8 & below);
-            if (op == OP_ADV) {
-              if (k >= n_pal) set_err(s_err, VC_ERR_CORRUPT);
-              else val = k;
-            } else if (op == OP_LAST) {
-              if (k == 0) set_err(s_err, VC_ERR_CORRUPT);
-              else val = k - 1u;
-            } else {
-              const uint32_t di = dd0 + __popc(del8 & below);
-              const uint32_t delta = di < c.dlist_cap ? dlist[di] : 0u;
-              if (delta == 0 || delta > k) set_err(s_err, VC_ERR_CORRUPT);
-              else val = k - delta;
-            }
-          }
-          v[o] = val;
-        }
-      }
+      decode8(off + 8u * r, Gp[p], compact3(p), compact3(p >> 1), compact3(p >> 2), true, v);
+      const uint32_t f0 = flin<L>(p);
       store_pair<GT>(fg, f0, v[0], v[1]);
       store_pair<GT>(fg, f0 + b, v[2], v[3]);
       store_pair<GT>(fg, f0 + b * b, v[4], v[5]);
       store_pair<GT>(fg, f0 + b * b + b, v[6], v[7]);
     }
     __syncthreads();
-    constexpr uint32_t quads = b * b * b / 4u;
-    for (uint32_t q = tid; q < quads; q += NT) {
-      uint32_t idx[4];
-      if constexpr (sizeof(GT) == 1) {
-        const uint32_t x = reinterpret_cast<const uint32_t*>(fg)[q];
+    // neighbour marks of the finest level, resolved per decoded block (at most three hops each), so
+    // that the output pass is a plain gather
+    for (uint32_t r = tid; r < npar; r += NT) {
+      const uint32_t f0 = flin<L>(plist[r]);
+      const uint32_t rows[4] = {f0, f0 + b, f0 + b * b, f0 + b * b + b};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) idx[i] = (x >> (8 * i)) & 0xFFu;
-      } else {
-        const uint2 x = reinterpret_cast<const uint2*>(fg)[q];
-        idx[0] = x.x & 0xFFFFu; idx[1] = x.x >> 16; idx[2] = x.y & 0xFFFFu; idx[3] = x.y >> 16;
-      }
+      for (int h = 0; h < 4; ++h) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (idx[i] >= MARK) {
-          uint32_t pos = 4u * q + (uint32_t)i, g = idx[i];
+        for (uint32_t i = 0; i < 2; ++i) {
+          const uint32_t pos = rows[h] + i;
+          uint32_t g = fg[pos];
+          if (g >= MARK) {
+            uint32_t q = pos;
 #pragma unroll 1
-          for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
-            const uint32_t a = g - MARK;
-            pos -= a == 0 ? 1u : (a == 1 ? b : b * b);
-            g = fg[pos];
+            for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
+              const uint32_t a = g - MARK;
+              q -= a == 0 ? 1u : (a == 1 ? b : b * b);
+              g = fg[q];
+            }
+            if (g >= MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
+            fg[pos] = (GT)g;
           }
-          if (g >= MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
-          idx[i] = g;
         }
       }
-      store16(out + 4u * q, label_of(c, idx[0]), label_of(c, idx[1]), label_of(c, idx[2]), label_of(c, idx[3]));
+    }
+    __syncthreads();
+    if (SPLIT) {
+      on_stage_free();
+      return;
+    }
+    if (pal_copied) on_stage_free();
+    constexpr uint32_t quads = b * b * b / 4u;
+    // resolves the neighbour marks of voxel pos (at most three hops)
+    auto resolve_fg = [&](uint32_t pos, uint32_t g) -> uint32_t {
+#pragma unroll 1
+      for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
+        const uint32_t a = g - MARK;
+        pos -= a == 0 ? 1u : (a == 1 ? b : b * b);
+        g = fg[pos];
+      }
+      if (g >= MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
+      return g;
+    };
+    if constexpr (sizeof(GT) == 1) {
+      if (pal_copied) {
+        // byte grid and a 256-entry palette copy: every index is in bounds, marks are rare
+        const uint32_t* fg32 = reinterpret_cast<const uint32_t*>(fg);
+#pragma unroll 4
+        for (uint32_t q = tid; q < quads; q += NT) {
+          const uint32_t x = fg32[q];  // marks were resolved above
+          store16(out + 4u * q, c.pal[x & 0xFFu], c.pal[(x >> 8) & 0xFFu], c.pal[(x >> 16) & 0xFFu], c.pal[x >> 24]);
+        }
+      } else {
+        const uint32_t* fg32 = reinterpret_cast<const uint32_t*>(fg);
+        for (uint32_t q = tid; q < quads; q += NT) {
+          const uint32_t x = fg32[q];
+          uint32_t idx[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) idx[i] = resolve_fg(4u * q + (uint32_t)i, (x >> (8 * i)) & 0xFFu);
+          store16(out + 4u * q, label_of(c, idx[0]), label_of(c, idx[1]), label_of(c, idx[2]), label_of(c, idx[3]));
+        }
+      }
+    } else {
+      for (uint32_t q = tid; q < quads; q += NT) {
+        const uint2 x = reinterpret_cast<const uint2*>(fg)[q];
+        const uint32_t idx[4] = {resolve_fg(4u * q, x.x & 0xFFFFu), resolve_fg(4u * q + 1u, x.x >> 16),
+                                 resolve_fg(4u * q + 2u, x.y & 0xFFFFu), resolve_fg(4u * q + 3u, x.y >> 16)};
+        store16(out + 4u * q, label_of(c, idx[0]), label_of(c, idx[1]), label_of(c, idx[2]), label_of(c, idx[3]));
+      }
     }
   } else {
     // coarse level of detail: the level-Lout grid, x fastest
@@ -817,6 +854,10 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     } else if (tid == 0) {
       out[0] = label_of(c, Gl[0]);
     }
+  }
+  if (!finest || !pal_copied) {
+    __syncthreads();
+    on_stage_free();
   }
 }
 
@@ -876,7 +917,7 @@ __device__ __forceinline__ ItemSrc item_src(const Params& P, uint32_t item, uint
     const uint32_t np = s.rec[0], S = s.rec[1];
     const uint32_t ns = S < 32u ? S : 32u;
     s.head_bytes = (16u + 4u * ns + 4u * np + 15u) & ~15u;
-    s.stream = reinterpret_cast<const uint32_t*>(P.ws + (size_t)item * P.v.sm.ws_stride);
+    s.stream = reinterpret_cast<const uint32_t*>(P.ws + (size_t)(item - P.ws_item0) * P.v.sm.ws_stride);
     s.stream_bytes = (((S + 1u) >> 1) + 15u) & ~15u;
   } else {
     s.head_bytes = (e - a) * 4u;
@@ -887,7 +928,7 @@ __device__ __forceinline__ ItemSrc item_src(const Params& P, uint32_t item, uint
 }
 
 // One thread block per request item (grid and per-brick schedules).
-template <int L, typename GT, bool RANS, int NT>
+template <int L, typename GT, bool RANS, int NT, bool SPLIT>
 __global__ void __launch_bounds__(NT) decode_grid_kernel(const __grid_constant__ Params P) {
   extern __shared__ __align__(128) unsigned char sm[];
   const SmemLayout& SL = P.v.sm;
@@ -919,7 +960,8 @@ __global__ void __launch_bounds__(NT) decode_grid_kernel(const __grid_constant__
   __syncthreads();
   const uint32_t edge = (1u << L) >> P.lod;
   uint32_t* out = P.cache + (size_t)P.slots[item] * edge * edge * edge;
-  decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, s_err);
+  GT* fgg = SPLIT ? reinterpret_cast<GT*>(P.fgws + (size_t)(item - P.ws_item0) * SL.fg_stride) : nullptr;
+  decode_brick<L, GT, RANS, NT, SPLIT>(P, head, sw, out, sm, s_err, [] {}, fgg);
   __syncthreads();
   if (threadIdx.x == 0 && *s_err) report(P.status, *s_err, item);
 }
@@ -927,7 +969,7 @@ __global__ void __launch_bounds__(NT) decode_grid_kernel(const __grid_constant__
 // Persistent thread blocks pull items from the work counter in status[2]; while one brick is
 // decoded, the next brick's record (and symbols) are already being copied into the other stage
 // buffer by the TMA engine.
-template <int L, typename GT, bool RANS, int NT>
+template <int L, typename GT, bool RANS, int NT, bool SPLIT>
 __global__ void __launch_bounds__(NT) decode_batched_kernel(const __grid_constant__ Params P) {
   extern __shared__ __align__(128) unsigned char sm[];
   const SmemLayout& SL = P.v.sm;
@@ -995,6 +1037,7 @@ __global__ void __launch_bounds__(NT) decode_batched_kernel(const __grid_constan
       return;
     }
     const uint32_t brick = P.ids[item];
+    bool released = false;
     if (brick >= P.v.n_bricks) {
       if (tid == 0) report(P.status, VC_ERR_ARG, item);
     } else {
@@ -1006,19 +1049,88 @@ __global__ void __launch_bounds__(NT) decode_batched_kernel(const __grid_constan
                                            : head + 4u + head[0]);
       const uint32_t edge = (1u << L) >> P.lod;
       uint32_t* out = P.cache + (size_t)P.slots[item] * edge * edge * edge;
-      decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, s_err);
+      // depth 1: the next item's copy starts as soon as this brick's stage is free
+      GT* fgg = SPLIT ? reinterpret_cast<GT*>(P.fgws + (size_t)(item - P.ws_item0) * SL.fg_stride) : nullptr;
+      decode_brick<L, GT, RANS, NT, SPLIT>(P, head, sw, out, sm, s_err, [&] {
+        if (!prefetch && tid == 0) claim_and_issue(0);
+        released = true;
+      }, fgg);
       __syncthreads();
       if (tid == 0 && *s_err) report(P.status, *s_err, item);
     }
     if (prefetch) {
       buf ^= 1u;
-    } else {
+    } else if (!released) {
       __syncthreads();  // every thread is done with stage[0] before it is refilled
       if (tid == 0) claim_and_issue(0);
     }
   }
 }
 
+
+// ------------------------------------------------------------------------------------------
+// Output expansion for the split schedule: one block per request item turns the finest index
+// grid (written by the split reconstruction kernel) into labels, 16 bytes per store. Neighbour
+// marks (rare) are resolved by walking at most three hops in the grid.
+template <int L, typename GT>
+__global__ void __launch_bounds__(256) output_kernel(const __grid_constant__ Params P) {
+  constexpr uint32_t b = 1u << L;
+  constexpr uint32_t MARK = GridT<GT>::MARK;
+  constexpr uint32_t PAL_SMEM = 2048;
+  __shared__ uint32_t pal_s[PAL_SMEM];
+  const uint32_t item = P.item_base + blockIdx.x;
+  if (item >= P.n) return;
+  const uint32_t brick = P.ids[item];
+  if (brick >= P.v.n_bricks) return;  // reported by the reconstruction kernel
+  const uint32_t* rec = P.v.records + P.v.starts[brick];
+  const uint32_t n_pal = rec[0], S = rec[1];
+  const uint32_t ns = P.v.coder == 1 ? (S < 32u ? S : 32u) : 0u;
+  const uint32_t* pal_g = rec + 4 + ns;
+  const bool in_smem = n_pal <= PAL_SMEM;
+  if (in_smem) {
+    const uint32_t lim = sizeof(GT) == 1 ? 256u : n_pal;  // byte grids: pad so any index is in bounds
+    for (uint32_t i = threadIdx.x; i < lim; i += 256u) pal_s[i] = i < n_pal ? pal_g[i] : 0u;
+  }
+  __syncthreads();
+  const GT* fg = reinterpret_cast<const GT*>(P.fgws + (size_t)(item - P.ws_item0) * P.v.sm.fg_stride);
+  uint32_t* out = P.cache + (size_t)P.slots[item] * b * b * b;
+  auto resolve = [&](uint32_t pos, uint32_t g) -> uint32_t {
+#pragma unroll 1
+    for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
+      const uint32_t a = g - MARK;
+      pos -= a == 0 ? 1u : (a == 1 ? b : b * b);
+      g = fg[pos];
+    }
+    return g >= MARK ? 0u : g;  // a mark chain longer than three hops was reported as corrupt
+  };
+  auto label = [&](uint32_t idx) -> uint32_t {
+    if (sizeof(GT) == 1 && in_smem) return pal_s[idx];
+    return idx < n_pal ? (in_smem ? pal_s[idx] : pal_g[idx]) : 0u;
+  };
+  constexpr uint32_t quads = b * b * b / 4u;
+  if constexpr (sizeof(GT) == 1) {
+    const uint32_t* fg32 = reinterpret_cast<const uint32_t*>(fg);
+#pragma unroll 4
+    for (uint32_t q = threadIdx.x; q < quads; q += 256u) {
+      uint32_t x = fg32[q];
+      if (__vcmpgeu4(x, 0xFDFDFDFDu)) {
+        uint32_t y = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) y |= resolve(4u * q + (uint32_t)i, (x >> (8 * i)) & 0xFFu) << (8 * i);
+        x = y;
+      }
+      store16(out + 4u * q, label(x & 0xFFu), label((x >> 8) & 0xFFu), label((x >> 16) & 0xFFu), label(x >> 24));
+    }
+  } else {
+    const uint2* fg64 = reinterpret_cast<const uint2*>(fg);
+#pragma unroll 2
+    for (uint32_t q = threadIdx.x; q < quads; q += 256u) {
+      const uint2 x = fg64[q];
+      store16(out + 4u * q, label(resolve(4u * q, x.x & 0xFFFFu)), label(resolve(4u * q + 1u, x.x >> 16)),
+              label(resolve(4u * q + 2u, x.y & 0xFFFFu)), label(resolve(4u * q + 3u, x.y >> 16)));
+    }
+  }
+}
 }  // namespace
 }  // namespace dev
 }  // namespace vc

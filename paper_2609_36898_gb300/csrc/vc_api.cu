@@ -28,10 +28,50 @@ struct DeviceGuard {
   }
 };
 
+void destroy_pipeline(Volume* v) {
+  for (int i = 0; i < 3; ++i) {
+    if (v->aux[i]) cudaStreamDestroy(v->aux[i]);
+    if (v->ev_join[i]) cudaEventDestroy(v->ev_join[i]);
+  }
+  if (v->ev_fork) cudaEventDestroy(v->ev_fork);
+  for (uint32_t i = 0; i < kRing; ++i) {
+    if (v->ev_a[i]) cudaEventDestroy(v->ev_a[i]);
+    if (v->ev_f[i]) cudaEventDestroy(v->ev_f[i]);
+    if (v->ev_o[i]) cudaEventDestroy(v->ev_o[i]);
+  }
+}
+
+bool create_pipeline(Volume* v) {
+  bool ok = true;
+  for (int i = 0; i < 3; ++i) {
+    ok = ok && cudaStreamCreateWithFlags(&v->aux[i], cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&v->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
+  }
+  ok = ok && cudaEventCreateWithFlags(&v->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (uint32_t i = 0; i < kRing; ++i) {
+    ok = ok && cudaEventCreateWithFlags(&v->ev_a[i], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&v->ev_f[i], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&v->ev_o[i], cudaEventDisableTiming) == cudaSuccess;
+  }
+  return ok;
+}
+
+vc_status layouts_for(Volume* v, const vc_schedule& sc, SmemLayout* fused, SmemLayout* split) {
+  vc_status rc = compute_layout(*v, v->device, sc.threads, sc.stage_depth, false, fused);
+  if (rc == VC_OK) rc = compute_layout(*v, v->device, sc.threads, 1, true, split);
+  return rc;
+}
+
 void free_volume(Volume* v) {
   if (!v) return;
   DeviceGuard g(v->device);
   cudaDeviceSynchronize();
+  destroy_pipeline(v);
+  if (v->prof_ev) {
+    for (uint32_t i = 0; i < 3 * kProfCalls; ++i)
+      if (v->prof_ev[i]) cudaEventDestroy(v->prof_ev[i]);
+    delete[] v->prof_ev;
+  }
   cudaFree(v->d_file);
   cudaFree(v->d_tables);
   cudaFree(v->d_host_ids);
@@ -138,30 +178,37 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   v->max_pal = max_pal; v->max_sym = max_sym; v->max_delta = max_delta; v->max_rec_words = max_words;
   v->max_stage = max_stage;
   v->encoded_bytes = nbytes;
-  v->sched.threads = schedule_supported(L, 512) ? 512 : 256;
+  v->sched.threads = 256;
   v->sched.stage_depth = 1;
   v->sched.blocks_per_sm = 0;
-  SmemLayout sl;
-  vc_status rc = compute_layout(*v, device, v->sched.threads, v->sched.stage_depth, &sl);
+  v->sched.chunk = 512;
+  SmemLayout sl, sls;
+  vc_status rc = layouts_for(v, v->sched, &sl, &sls);
   if (rc != VC_OK) { delete v; return rc; }
+  v->sm_split = sls;
+  if (!create_pipeline(v)) {
+    cudaGetLastError();
+    destroy_pipeline(v);
+    delete v;
+    return VC_ERR_CUDA;
+  }
 
   // the device copy carries 64 zero bytes of slack: 8-nibble windows may read past a record's end
   const size_t file_bytes = rec_off + 4 * (size_t)records_words;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-  if (cudaMalloc(&v->d_file, file_bytes + 64) != cudaSuccess) { cudaGetLastError(); delete v; return VC_ERR_OOM; }
+  if (cudaMalloc(&v->d_file, file_bytes + 64) != cudaSuccess) { cudaGetLastError(); free_volume(v); return VC_ERR_OOM; }
   if (cudaMalloc(&v->d_tables, 4 * kRansM) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(v->d_file);
-    delete v;
+    free_volume(v);
     return VC_ERR_OOM;
   }
   v->device_bytes = file_bytes + 64 + 4 * kRansM;
-  // rANS table: per slot, symbol | freq << 4 | (slot - cum[symbol]) << 17
+  // rANS table: per slot, freq[symbol] | (slot - cum[symbol]) << 13 | symbol << 25
   std::vector<uint32_t> tab(kRansM, 0);
   if (coder == 1) {
     uint32_t cum = 0;
     for (uint32_t s = 0; s < 16; ++s) {
-      for (uint32_t k = 0; k < freq[s]; ++k) tab[cum + k] = s | (freq[s] << 4) | (k << 17);
+      for (uint32_t k = 0; k < freq[s]; ++k) tab[cum + k] = freq[s] | (k << 13) | (s << 25);
       cum += freq[s];
     }
   }
@@ -210,11 +257,13 @@ vc_status vc_volume_set_schedule(vc_volume* vol, const vc_schedule* sched) {
   if (sched->stage_depth < 1 || sched->stage_depth > 2) return VC_ERR_ARG;
   if (!schedule_supported(v->L, sched->threads)) return VC_ERR_UNSUPPORTED;
   DeviceGuard g(v->device);
-  SmemLayout sl;
-  const vc_status rc = compute_layout(*v, v->device, sched->threads, sched->stage_depth, &sl);
+  SmemLayout sl, sls;
+  const vc_status rc = layouts_for(v, *sched, &sl, &sls);
   if (rc != VC_OK) return rc;
   v->sched = *sched;
+  if (!v->sched.chunk) v->sched.chunk = 512;
   v->dv.sm = sl;
+  v->sm_split = sls;
   return VC_OK;
 }
 
@@ -231,7 +280,7 @@ vc_status vc_decode_bricks(vc_volume* vol, const uint32_t* brick_ids, uint32_t n
   if (!v || v->kind != kHandleVolume) return VC_ERR_ARG;
   if (n == 0) return VC_OK;
   if (!brick_ids || !cache_slots || !cache || !status_dev) return VC_ERR_ARG;
-  if (lod > v->L || mode > VC_MODE_BATCHED) return VC_ERR_ARG;
+  if (lod > v->L || mode > VC_MODE_PIPELINED) return VC_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(cache) & 15u) return VC_ERR_ARG;
   DeviceGuard g(v->device);
   return launch_decode(*v, brick_ids, n, cache_slots, cache, lod, mode, status_dev,
@@ -244,7 +293,7 @@ vc_status vc_decode_bricks_host(vc_volume* vol, const uint32_t* brick_ids, uint3
   if (!v || v->kind != kHandleVolume || !status_out) return VC_ERR_ARG;
   *status_out = 0;
   if (n == 0) return VC_OK;
-  if (!brick_ids || !labels_out || lod > v->L || mode > VC_MODE_BATCHED) return VC_ERR_ARG;
+  if (!brick_ids || !labels_out || lod > v->L || mode > VC_MODE_PIPELINED) return VC_ERR_ARG;
   DeviceGuard g(v->device);
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   const uint32_t edge = (1u << v->L) >> lod;
@@ -287,6 +336,52 @@ vc_status vc_decode_bricks_host(vc_volume* vol, const uint32_t* brick_ids, uint3
   if (cudaMemcpyAsync(&st, v->d_host_status, 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess) return VC_ERR_CUDA;
   if (cudaStreamSynchronize(stream) != cudaSuccess) return VC_ERR_CUDA;
   *status_out = st;
+  return VC_OK;
+}
+
+vc_status vc_volume_set_profiling(vc_volume* vol, int enable) {
+  Volume* v = reinterpret_cast<Volume*>(vol);
+  if (!v || v->kind != kHandleVolume) return VC_ERR_ARG;
+  if (enable && !v->prof_ev) {
+    DeviceGuard g(v->device);
+    v->prof_ev = new (std::nothrow) cudaEvent_t[3 * kProfCalls]();
+    if (!v->prof_ev) return VC_ERR_OOM;
+    for (uint32_t i = 0; i < 3 * kProfCalls; ++i) {
+      if (cudaEventCreate(&v->prof_ev[i]) != cudaSuccess) {
+        cudaGetLastError();
+        for (uint32_t j = 0; j < i; ++j) cudaEventDestroy(v->prof_ev[j]);
+        delete[] v->prof_ev;
+        v->prof_ev = nullptr;
+        return VC_ERR_CUDA;
+      }
+    }
+  }
+  v->prof = enable != 0;
+  return VC_OK;
+}
+
+vc_status vc_volume_kernel_stats(vc_volume* vol, int reset, vc_kernel_stats* out) {
+  Volume* v = reinterpret_cast<Volume*>(vol);
+  if (!v || v->kind != kHandleVolume || !out) return VC_ERR_ARG;
+  DeviceGuard g(v->device);
+  std::memset(out, 0, sizeof(*out));
+  out->launches = v->launches;
+  out->timed_calls = v->prof_used;
+  out->dropped_calls = v->prof_dropped;
+  for (uint32_t c = 0; c < v->prof_used; ++c) {
+    cudaEvent_t* e = v->prof_ev + 3 * c;
+    float a = 0.f, b = 0.f;
+    if (cudaEventSynchronize(e[2]) != cudaSuccess || cudaEventElapsedTime(&a, e[0], e[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&b, e[1], e[2]) != cudaSuccess)
+      return VC_ERR_CUDA;
+    out->symbol_ms += a;
+    out->reconstruct_ms += b;
+  }
+  if (reset) {
+    v->launches = 0;
+    v->prof_used = 0;
+    v->prof_dropped = 0;
+  }
   return VC_OK;
 }
 

@@ -19,6 +19,7 @@ constexpr uint32_t kMaxIdx16 = 0xFFF0u;   // same for 16-bit grids
 constexpr uint32_t kFlagNoStop = 1u;
 constexpr uint32_t kHandleVolume = 0x564F4C31u;  // "VOL1"
 constexpr uint32_t kRansWarps = 16u;      // bricks (warps) per block of the rANS symbol kernel
+constexpr uint32_t kRing = 3u;            // pipelined schedule: workspace slots (chunks in flight)
 
 // Byte offsets of the reconstruction kernel's shared-memory regions (one brick per block).
 struct SmemLayout {
@@ -34,9 +35,14 @@ struct SmemLayout {
   uint32_t dlist_off;    // delta values of the brick's delta operations
   uint32_t dlist_cap;
   uint32_t g_off;        // palette index per cell of levels 0..L-1 (gt_bytes each)
-  uint32_t r_off;        // rank among the level's stop-0 nodes per cell (u16), levels 0..L-1
+  uint32_t ns_off;       // per level, one byte per parent cell: which children have stop bit 0
   uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each)
-  uint32_t list_off;     // cells of level L-1 with stop bit 0, by rank (u16)
+  uint32_t psum_off;     // summaries of the general parse path (aliases idle regions)
+  uint32_t fg_stride;    // split schedule: bytes per item of the finest-grid workspace
+  uint32_t list_off;     // stop-0 cells by rank (u16), two buffers: even / odd levels
+  uint32_t list0_cap;    // entries of the even-level buffer
+  uint32_t pal_off;      // private copy of the brick's palette
+  uint32_t pal_cap;      // entries it can hold (0 = palettes are read from the stage)
   uint32_t gt_bytes;     // 1 (max_pal < 252) or 2
   uint32_t total;
   // rANS symbol kernel
@@ -49,7 +55,7 @@ struct SmemLayout {
 struct DevVolume {
   const uint32_t* records;   // record area (32-bit words)
   const uint32_t* starts;    // n_bricks + 1 word offsets
-  const uint32_t* rans_tab;  // 4096 entries: symbol | freq << 4 | (slot - cum) << 17
+  const uint32_t* rans_tab;  // 4096 entries: freq | (slot - cum) << 13 | symbol << 25
   uint32_t n_bricks;
   uint32_t L;
   uint32_t op_mask;
@@ -65,7 +71,10 @@ struct Volume {
   uint32_t L, op_mask, coder, flags, n_bricks, nb[3];
   uint32_t max_pal, max_sym, max_delta, max_rec_words, max_stage;
   uint64_t encoded_bytes, device_bytes;
-  vc_schedule sched;     // threads per block, staging depth, persistent blocks per SM
+  vc_schedule sched;     // threads per block, staging depth, persistent blocks per SM, chunk
+  SmemLayout sm_split;   // layout of the split reconstruction kernel (pipelined schedule)
+  cudaStream_t aux[3];   // pipelined schedule: symbol, reconstruction and output streams
+  cudaEvent_t ev_fork, ev_join[3], ev_a[kRing], ev_f[kRing], ev_o[kRing];
   uint8_t* d_file;       // device copy of the whole file (+ slack)
   uint8_t* d_tables;     // rANS table
   DevVolume dv;
@@ -75,12 +84,22 @@ struct Volume {
   uint32_t* d_host_cache;
   int32_t* d_host_status;
   size_t host_cap_items, host_cap_words;
+  // kernel accounting: launches are always counted; with prof set, each grid / batched decode call
+  // records three timing events (before the symbol kernel, between, after the reconstruction)
+  uint64_t launches;
+  bool prof;
+  cudaEvent_t* prof_ev;    // kProfCalls x 3
+  uint32_t prof_used;      // calls recorded since the last reset
+  uint32_t prof_dropped;   // calls not recorded (ring full)
 };
+
+constexpr uint32_t kProfCalls = 256;
 
 // decode.cu
 bool schedule_supported(uint32_t L, uint32_t threads);
-vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, SmemLayout* out);
-vc_status launch_decode(const Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
+vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, bool split,
+                         SmemLayout* out);
+vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
                         uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream);
 
 }  // namespace vc
