@@ -181,6 +181,30 @@ vc_status vc_decode_bricks(vc_volume* vol, const uint32_t* brick_ids, uint32_t n
 vc_status vc_decode_bricks_host(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, uint32_t lod,
                                 uint32_t mode, uint32_t* labels_out, int32_t* status_out, void* cuda_stream);
 
+/* ---- decode without allocation (the paper has no counterpart) ----
+ * For callers that must not allocate device memory while decoding: code that runs inside CUDA
+ * stream capture, real-time loops that cannot wait for the allocator, processes whose device
+ * memory is reserved up front. vc_decode_bricks allocates the rANS symbol workspace per call
+ * (stream-ordered); this entry point uses one statically reserved device array of
+ * VC_NOALLOC_WS_BYTES per device instead and allocates nothing (no cudaMalloc, no cudaMallocAsync,
+ * no library that allocates).
+ *   Same arguments, output and status reporting as vc_decode_bricks, with mode VC_MODE_GRID or
+ *   VC_MODE_BATCHED only (VC_ERR_ARG otherwise).
+ *   Size limit: for rANS volumes, n x (16 * ceil(ceil(max_sym / 2) / 16) + 16) bytes must fit in
+ *   VC_NOALLOC_WS_BYTES, else VC_ERR_ARG and nothing is enqueued; plain-coded volumes use no
+ *   workspace and have no limit.
+ *   Zeroing: the workspace needs none; as for vc_decode_bricks, the caller zeroes status words
+ *   0..1 before the first call.
+ *   Set-up: the first call on a device (with that device current) looks up the array's device
+ *   address once; make that first call outside any stream capture.
+ *   Concurrency: all calls on one device share the one workspace, so calls whose work may
+ *   overlap on the GPU (other streams, other host threads) race on it and corrupt each other's
+ *   output; order them on one stream or with events. */
+#define VC_NOALLOC_WS_BYTES (32u << 20)
+vc_status vc_decode_bricks_noalloc(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, const uint32_t* cache_slots,
+                                   uint32_t* cache, uint32_t lod, uint32_t mode, int32_t* status_dev,
+                                   void* cuda_stream);
+
 /* ---- kernel accounting (diagnostics; the paper has no counterpart) ---- */
 
 typedef struct vc_kernel_stats {

@@ -81,6 +81,7 @@ def _lib_handle():
         lib.vc_volume_set_schedule.argtypes = [P, ctypes.POINTER(vc_schedule)]
         lib.vc_volume_get_schedule.argtypes = [P, ctypes.POINTER(vc_schedule)]
         lib.vc_decode_bricks.argtypes = [P, P, U32, P, P, U32, U32, P, P]
+        lib.vc_decode_bricks_noalloc.argtypes = [P, P, U32, P, P, U32, U32, P, P]
         lib.vc_decode_bricks_host.argtypes = [P, P, U32, U32, U32, P, ctypes.POINTER(I32), P]
         lib.vc_release.argtypes = [P]
         lib.vc_volume_set_profiling.argtypes = [P, ctypes.c_int]
@@ -92,7 +93,7 @@ def _lib_handle():
         lib.vc_status_string.restype = ctypes.c_char_p
         for f in ("vc_load_compressed", "vc_volume_info_get", "vc_decode_bricks", "vc_decode_bricks_host",
                   "vc_release", "vc_encode_volume", "vc_volume_set_schedule", "vc_volume_get_schedule",
-                  "vc_volume_set_profiling", "vc_volume_kernel_stats"):
+                  "vc_volume_set_profiling", "vc_volume_kernel_stats", "vc_decode_bricks_noalloc"):
             getattr(lib, f).restype = I32
         _lib = lib
     return _lib
@@ -135,6 +136,14 @@ def vc_decode_bricks(vol, brick_ids_ptr: int, n: int, cache_slots_ptr: int, cach
     _check(_lib_handle().vc_decode_bricks(vol, ctypes.c_void_p(brick_ids_ptr), n, ctypes.c_void_p(cache_slots_ptr),
                                           ctypes.c_void_p(cache_ptr), lod, mode, ctypes.c_void_p(status_ptr),
                                           ctypes.c_void_p(stream)), "vc_decode_bricks")
+
+
+def vc_decode_bricks_noalloc(vol, brick_ids_ptr: int, n: int, cache_slots_ptr: int, cache_ptr: int, lod: int,
+                             mode: int, status_ptr: int, stream: int = 0) -> None:
+    _check(_lib_handle().vc_decode_bricks_noalloc(vol, ctypes.c_void_p(brick_ids_ptr), n,
+                                                  ctypes.c_void_p(cache_slots_ptr), ctypes.c_void_p(cache_ptr), lod,
+                                                  mode, ctypes.c_void_p(status_ptr), ctypes.c_void_p(stream)),
+           "vc_decode_bricks_noalloc")
 
 
 def vc_decode_bricks_host(vol, brick_ids: np.ndarray, lod: int, mode: int, labels_out: np.ndarray,

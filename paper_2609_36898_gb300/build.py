@@ -17,7 +17,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (source, object name, extra flags): the reconstruction kernels are compiled once per thread count
 SOURCES = [("decode.cu", "decode", []), ("decode_nt.cu", "decode_nt256", ["-DVC_NT=256"]),
            ("decode_nt.cu", "decode_nt512", ["-DVC_NT=512"]), ("decode_nt.cu", "decode_nt1024", ["-DVC_NT=1024"]),
-           ("vc_api.cu", "vc_api", []), ("encode.cpp", "encode", [])]
+           ("vc_api.cu", "vc_api", []), ("decode_noalloc.cu", "decode_noalloc", []), ("encode.cpp", "encode", [])]
 HEADERS = ["vc_internal.h", "decode_kernels.cuh"]
 
 

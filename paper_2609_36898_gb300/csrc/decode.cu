@@ -322,6 +322,12 @@ vc_status launch_pipelined(Volume& v, Params P, uint32_t n, cudaStream_t stream)
 
 vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
                         uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream) {
+  return launch_decode_ws(v, ids, n, slots, cache, lod, mode, status, stream, nullptr, 0);
+}
+
+vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
+                           uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream, uint8_t* ws_ext,
+                           size_t ws_cap) {
   if (n == 0) return VC_OK;
   const bool rans = v.coder == 1;
   Params P;
@@ -337,7 +343,10 @@ vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32
   P.fgws = nullptr;
   P.ws_item0 = 0;
   // coarse levels of detail are written by the reconstruction kernel itself
-  if (mode == VC_MODE_PIPELINED && lod == 0) return launch_pipelined(v, P, n, stream);
+  if (mode == VC_MODE_PIPELINED && lod == 0) {
+    if (ws_ext) return VC_ERR_ARG;  // the pipelined schedule allocates its own workspaces
+    return launch_pipelined(v, P, n, stream);
+  }
   if (mode == VC_MODE_PIPELINED) mode = VC_MODE_GRID;
   const bool batched = mode == VC_MODE_BATCHED;
   const uint32_t nt = v.sched.threads;
@@ -345,8 +354,12 @@ vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32
   if (!k) return VC_ERR_UNSUPPORTED;
   const uint32_t smem = v.dv.sm.total;
   if (!set_smem(k, smem)) return VC_ERR_CUDA;
-  uint8_t* ws = nullptr;
-  if (rans) {
+  uint8_t* ws = nullptr;      // allocated here (freed at the end)
+  if (rans && ws_ext) {       // caller-provided workspace: nothing is allocated or freed
+    if ((size_t)n * v.dv.sm.ws_stride > ws_cap) return VC_ERR_ARG;
+    P.ws = ws_ext;
+    if (!set_smem(reinterpret_cast<void*>(&rans_symbols_kernel), v.dv.sm.a_smem)) return VC_ERR_CUDA;
+  } else if (rans) {
     if (cudaMallocAsync(reinterpret_cast<void**>(&ws), (size_t)n * v.dv.sm.ws_stride, stream) != cudaSuccess) {
       cudaGetLastError();
       return VC_ERR_OOM;
@@ -367,7 +380,7 @@ vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32
   auto mark = [&](int i) { return !ev || cudaEventRecord(ev[i], stream) == cudaSuccess; };
   auto run_symbols = [&](uint32_t base, uint32_t count) -> bool {
     if (!rans) return true;
-    if (!launch_symbols(P, ws, base, count, v.dv.sm.a_smem, stream)) return false;
+    if (!launch_symbols(P, const_cast<uint8_t*>(P.ws), base, count, v.dv.sm.a_smem, stream)) return false;
     ++v.launches;
     return true;
   };

@@ -101,5 +101,10 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
                          SmemLayout* out);
 vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
                         uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream);
+// Same, with the rANS symbol workspace supplied by the caller (ws_ext, ws_cap bytes, 16-byte
+// aligned) instead of allocated: VC_ERR_ARG if n items need more than ws_cap or mode is pipelined.
+vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
+                           uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream, uint8_t* ws_ext,
+                           size_t ws_cap);
 
 }  // namespace vc
