@@ -198,6 +198,111 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def orbit_camera(vc, i: int, frame: int, dims, width: int, height: int, fov: float = 0.8):
+    """Camera i of the serving workload at a frame: an orbit of radius 1.2-3 volume diagonals
+    around the volume centre, on a seeded random axis and phase, 1 degree per frame."""
+    import math
+    rng = np.random.default_rng(1000 + i)
+    axis = rng.normal(size=3)
+    axis /= np.linalg.norm(axis)
+    a = np.cross(axis, rng.normal(size=3))
+    a /= np.linalg.norm(a)
+    b = np.cross(axis, a)
+    radius = float(np.linalg.norm(dims)) * rng.uniform(1.2, 3.0)
+    phase = rng.uniform(0, 2 * math.pi) + math.radians(frame)
+    centre = np.asarray(dims, np.float64) / 2
+    pos = centre + radius * (math.cos(phase) * a + math.sin(phase) * b)
+    return vc.make_camera(pos, centre - pos, axis, fov, width, height)
+
+
+def serving_leg(args, local: int):
+    """Camera-driven serving on the 4096^3 recipe scaled to n^3 (n = --serve-size): 64 orbiting
+    cameras at 1920x1080 request their visible bricks every frame (request stage on the GPU), the
+    server admits, batches and decodes them into a 2 GiB cache; versus plain per-request decoding
+    (one launch per brick, one request after the other, no cache)."""
+    import torch
+    import synth
+    import paper_2609_36898_gb300 as vc
+    n = args.serve_size
+    spec = synth.c4_scaled(n)
+    t = time.time()
+    V = synth.fill(spec)
+    enc = vc.vc_encode_volume(V, B_LOG2, op_mask=0x7F, coder=CODER_RANS)
+    del V
+    prep = time.time() - t
+    stream = torch.cuda.current_stream(local)
+    vol = vc.vc_load_compressed(enc, local, stream.cuda_stream)
+    srv = vc.vc_server_create(2 << 30, local)
+    vi = vc.vc_server_add_volume(srv, vol)
+    dims = (n, n, n)
+    ncam, W, H, max_lod = args.serve_cameras, 1920, 1080, 3
+    lat, rstage, frame_ms = [], [], []
+    prev = []
+    vox = 0
+    t_all = time.perf_counter()
+    for f in range(args.serve_frames):
+        cams = [orbit_camera(vc, i, f, dims, W, H) for i in range(ncam)]
+        t0 = time.perf_counter()
+        rids = vc.vc_request_bricks(srv, vi, cams, max_lod)
+        t1 = time.perf_counter()
+        for r in rids:
+            if vc.vc_wait(srv, r, 120000) != vc.VC_REQ_DONE:
+                raise RuntimeError("serving request failed")
+        t2 = time.perf_counter()
+        for r in prev:
+            vc.vc_request_release(srv, r)
+        for r in rids:
+            info = vc.vc_request_info_get(srv, r)
+            lat.append((info.t_done_ns - info.t_submit_ns) / 1e6)
+        prev = rids
+        rstage.append(1000 * (t1 - t0))
+        frame_ms.append(1000 * (t2 - t0))
+    wall = time.perf_counter() - t_all
+    st = vc.vc_server_stats_get(srv)
+    for r in prev:
+        vc.vc_request_release(srv, r)
+    vox = st.voxels_decoded
+    vc.vc_release(srv)
+    lists = vc.vc_camera_bricks(vol, [orbit_camera(vc, i, 0, dims, W, H) for i in range(ncam)], max_lod)
+    edge = 1 << B_LOG2
+
+    # plain: each camera's request of frame 0, one launch per brick, one request after the other
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(ncam + 1)]
+    status = torch.zeros(vc.VC_STATUS_WORDS, dtype=torch.int32, device="cuda")
+    maxn = max(len(i) for i, _ in lists)
+    cache = torch.empty(maxn * edge ** 3, dtype=torch.int32, device="cuda")
+    slots = torch.arange(maxn, dtype=torch.int32, device="cuda")
+    plain_vox = 0
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    for c, (ids, lods) in enumerate(lists):
+        for lod in np.unique(lods):
+            sel = ids[lods == lod]
+            ids_t = torch.from_numpy(sel.view(np.int32)).cuda()
+            vc.vc_decode_bricks(vol, ids_t.data_ptr(), sel.size, slots.data_ptr(), cache.data_ptr(), int(lod),
+                                vc.VC_MODE_PLAIN, status.data_ptr(), stream.cuda_stream)
+            plain_vox += sel.size * (edge >> int(lod)) ** 3
+        e[c + 1].record(stream)
+    torch.cuda.synchronize()
+    plain_lat = [e[0].elapsed_time(e[c + 1]) for c in range(ncam)]
+    plain_s = plain_lat[-1] / 1000.0
+    vc.vc_release(vol)
+    pct = lambda a, q: float(np.percentile(np.asarray(a), q)) if len(a) else None  # noqa: E731
+    return {
+        "workload": f"{n}^3 Voronoi (4096^3 recipe: one seed per 16^3 cell, 10% background), 32^3 bricks, rANS; "
+                    f"{ncam} orbiting cameras at {W}x{H}, {args.serve_frames} frames, 2 GiB cache, lod <= {max_lod}",
+        "served": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "requests": len(lat),
+                   "gvoxel_s": vox / wall / 1e9, "request_stage_ms_median": pct(rstage, 50),
+                   "frame_ms_median": pct(frame_ms, 50), "bricks_decoded": int(st.bricks_decoded),
+                   "bricks_hit": int(st.bricks_hit), "batches": int(st.batches), "evictions": int(st.evictions)},
+        "plain": {"p50_ms": pct(plain_lat, 50), "p99_ms": pct(plain_lat, 99), "requests": ncam,
+                  "gvoxel_s": plain_vox / plain_s / 1e9 if plain_s > 0 else None,
+                  "note": "frame 0's requests, all submitted at once, decoded one after the other with one launch per brick"},
+        "status": int(status[0]),
+        "prep_s": prep,
+    }
+
+
 def run_ours(args):
     import torch
     import paper_2609_36898_gb300 as vc
@@ -310,6 +415,10 @@ def run_ours(args):
     e2e_val = world * vox_per_step * e2e_steps / e2e_s / 1e9
     assert np.array_equal(labels_np[: e ** 3].reshape(e, e, e), V[:e, :e, :e])
 
+    serving = None
+    if args.serve_frames > 0:
+        serving = serving_leg(args, local)
+
     out = None
     if rank == 0:
         cpu = None
@@ -339,6 +448,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "schedules_gvoxel_s": modes,
+            "serving": serving,
             "wall_s_timed_region": wall,
             "prep_s": {"generate": t_gen, "encode": t_enc},
         }
@@ -357,6 +467,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="batched", choices=["grid", "batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-frames", type=int, default=8, help="frames of the serving leg (0 = skip it)")
+    ap.add_argument("--serve-size", type=int, default=1024, help="edge of the serving volume")
+    ap.add_argument("--serve-cameras", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -181,6 +181,132 @@ vc_status vc_decode_bricks(vc_volume* vol, const uint32_t* brick_ids, uint32_t n
 vc_status vc_decode_bricks_host(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, uint32_t lod,
                                 uint32_t mode, uint32_t* labels_out, int32_t* status_out, void* cuda_stream);
 
+/* ---- serving: device brick cache, admission, continuous batching ----
+ * Paper (Methods, "GPU rendering pipeline"; Results, "GPU-based rendering pipeline"): bricks are
+ * requested, cache space is freed from bricks no longer needed and assigned to new bricks, and
+ * all new bricks are decoded in parallel, every frame. A vc_server runs that loop for many
+ * clients at once on one device: it owns one device cache buffer, admits requests in arrival
+ * order when their missing bricks fit into free plus evictable (unpinned, least recently used
+ * first) cache memory, and decodes the missing bricks of all admitted requests in shared batches
+ * (one batched-schedule launch per volume and level of detail), up to max_inflight batches on the
+ * GPU at a time. Requests that arrive while batches run join the next batch.
+ *
+ * Cache layout: an 8-ary buddy allocator over the buffer. A block of class c is 4 * 8^c bytes, a
+ * (2^c)^3 brick of u32 labels; a brick of edge e = b >> lod takes a block of class
+ * max(log2 e, min_class) and its labels (x fastest) start at the block's byte offset, which is a
+ * multiple of the block size. A request's bricks stay pinned (never evicted or moved) from its
+ * admission until vc_request_release. All calls are thread-safe. */
+
+#define VC_REQ_WAITING 0   /* submitted, not yet admitted (not enough cache memory yet) */
+#define VC_REQ_ADMITTED 1  /* cache space assigned, decode pending or running */
+#define VC_REQ_DONE 2      /* every brick resident; offsets valid until vc_request_release */
+#define VC_REQ_FAILED 3    /* a decode error (status holds its code) or a fatal CUDA error */
+
+typedef struct vc_server vc_server;
+
+typedef struct vc_server_config {
+  uint64_t cache_bytes;      /* device cache size (rounded down to whole top-class blocks) */
+  int32_t device;            /* CUDA device of the server and of every volume added to it */
+  uint32_t max_batch_items;  /* bricks per decode batch (0 = 65536) */
+  uint32_t max_inflight;     /* batches on the GPU at once, 1..8 (0 = 2) */
+  uint32_t min_class;        /* smallest block class (0 = 2, i.e. 256 bytes) */
+  uint32_t max_class;        /* largest block class = log2 of the largest brick edge (0 = 6) */
+  uint32_t reserved[3];
+} vc_server_config;
+
+typedef struct vc_request_info {
+  int32_t state, status;
+  uint32_t volume_index, n_bricks, hits; /* hits: bricks already cached or being decoded */
+  uint32_t reserved;
+  uint64_t bytes;                        /* cache bytes the request pins */
+  uint64_t t_submit_ns, t_admit_ns, t_done_ns;  /* host steady clock */
+} vc_request_info;
+
+typedef struct vc_server_stats {
+  uint64_t cache_bytes, cache_free_bytes, cache_evictable_bytes, cache_entries, evictions;
+  uint64_t requests_submitted, requests_admitted, requests_done, requests_failed, requests_waiting;
+  uint64_t bricks_hit, bricks_missed, bricks_decoded, batches, batches_inflight, batch_errors;
+  uint64_t voxels_decoded;  /* sum of (b >> lod)^3 over decoded bricks */
+} vc_server_stats;
+
+/* Creates a server (allocates the cache, batch buffers and streams; starts its thread).
+ * VC_ERR_ARG for an invalid configuration, VC_ERR_OOM if the cache does not fit. */
+vc_status vc_server_create(const vc_server_config* cfg, vc_server** out);
+/* Makes a loaded volume servable under *volume_index. The server does not own the volume: keep
+ * it loaded until the server is released. VC_ERR_ARG if it lives on another device,
+ * VC_ERR_UNSUPPORTED if its bricks exceed max_class. */
+vc_status vc_server_add_volume(vc_server* srv, vc_volume* vol, uint32_t* volume_index);
+/* Enqueues a request for n bricks (host arrays: ids, and levels of detail or NULL for all 0);
+ * returns at once with its id. VC_ERR_ARG for an id or lod out of range, VC_ERR_BUSY if the
+ * request needs more bytes than the whole cache (it could never be admitted). */
+vc_status vc_submit_bricks(vc_server* srv, uint32_t volume_index, const uint32_t* brick_ids, const uint32_t* lods,
+                           uint32_t n, uint64_t* request_id);
+/* Reads a request's state; once VC_REQ_DONE, offsets_out (host, n x u64, may be NULL) receives
+ * each brick's byte offset in the cache buffer. Returns the request's error code if it failed. */
+vc_status vc_poll(vc_server* srv, uint64_t request_id, int32_t* state, uint64_t* offsets_out);
+/* Blocks until the request is done or failed, or timeout_ms passed (VC_ERR_TIMEOUT). */
+vc_status vc_wait(vc_server* srv, uint64_t request_id, uint32_t timeout_ms, int32_t* state);
+vc_status vc_request_info_get(vc_server* srv, uint64_t request_id, vc_request_info* info);
+/* Unpins a done or failed request's bricks (they become evictable) and forgets the request.
+ * VC_ERR_BUSY while it is still waiting or admitted. */
+vc_status vc_request_release(vc_server* srv, uint64_t request_id);
+/* The cache buffer (device) and its size; read decoded bricks at the offsets vc_poll gives. */
+vc_status vc_server_cache(vc_server* srv, void** cache_dev, uint64_t* cache_bytes);
+vc_status vc_server_stats_get(vc_server* srv, vc_server_stats* out);
+
+/* ---- camera request stage ----
+ * Paper, Methods "GPU rendering pipeline" and Results "Ray marching": rays mark the bricks they
+ * pass as visible, bricks with no visible label are skipped, and the level of detail of a brick
+ * depends only on its centre, so that one of its voxels covers about one pixel. This library's
+ * reading at brick granularity: pixel (px, py) of a W x H pinhole camera shoots the ray
+ * pos + t (f + sx r + sy u), f = dir / |dir|, r = f x up / |f x up|, u = r x f,
+ * sx = ((px + 1/2) 2/W - 1) tan(fov_y/2) W/H, sy = (1 - (py + 1/2) 2/H) tan(fov_y/2); it walks the
+ * brick grid cell by cell (DDA with an integer brick index and a sub-brick position in [0, 1]);
+ * every brick whose palette holds a label other than 0 is requested, and the ray ends after the
+ * first brick whose palette has no label 0. Level of detail of a requested brick = the largest
+ * k <= max_lod with 4^k <= |centre - pos|^2 (2 tan(fov_y/2) / H)^2. Coordinates are voxel units
+ * (voxel (x, y, z) spans [x, x+1) x ...). The frame is computed in double precision and rounded to
+ * float; every per-ray step is one correctly rounded float operation in a fixed order. */
+typedef struct vc_camera {
+  float pos[3], dir[3], up[3];
+  float fov_y;             /* vertical field of view, radians */
+  uint32_t width, height;  /* pixels (width * height < 2^32) */
+} vc_camera;
+
+/* Runs the request stage for ncams cameras on `cuda_stream` and waits for it: counts[i] (host)
+ * receives the number of bricks camera i requests; brick_ids / lods (host, ncams x cap u32;
+ * camera i at i * cap) receive the first min(counts[i], cap) of them in ascending id order with
+ * their levels of detail. Device scratch comes from the stream-ordered allocator. */
+vc_status vc_camera_bricks(vc_volume* vol, const vc_camera* cams, uint32_t ncams, uint32_t max_lod, uint32_t cap,
+                           uint32_t* counts, uint32_t* brick_ids, uint32_t* lods, void* cuda_stream);
+
+/* Serving form of the same: runs the request stage for ncams cameras (on the server's own
+ * stream; concurrent callers take turns), then submits one request per camera with its bricks
+ * and levels of detail, exactly as vc_submit_bricks would; request_ids_out (host, ncams) receives
+ * their ids. Returns once the requests are queued (not decoded). */
+vc_status vc_request_bricks(vc_server* srv, uint32_t volume_index, const vc_camera* cams, uint32_t ncams,
+                            uint32_t max_lod, uint64_t* request_ids_out);
+
+/* Host-only view of the server's cache bookkeeping (no device memory, no CUDA calls): the same
+ * buddy allocator, LRU eviction and all-or-nothing admission that a vc_server runs, over an
+ * abstract buffer of `bytes` bytes. Keys are opaque 64-bit values; classes as above. */
+typedef struct vc_brick_cache vc_brick_cache;
+typedef struct vc_brick_cache_stats {
+  uint64_t capacity_bytes, free_bytes, evictable_bytes, entries, evictions, hits, misses;
+} vc_brick_cache_stats;
+/* VC_ERR_ARG unless min_class <= max_class <= 9, bytes holds one max_class block and the number of
+ * min_class blocks is at most 2^31. */
+vc_status vc_brick_cache_create(uint64_t bytes, uint32_t min_class, uint32_t max_class, vc_brick_cache** out);
+/* Pins an entry per key (allocating, evicting least recently used unpinned entries as needed);
+ * all or nothing: VC_ERR_BUSY and no pin taken if the keys do not fit. hits_out[i] = 1 if the key
+ * was present. Each pin is dropped by one vc_brick_cache_unpin of its entry. */
+vc_status vc_brick_cache_acquire(vc_brick_cache* c, const uint64_t* keys, const uint32_t* classes, uint32_t n,
+                                 uint32_t* entries_out, uint64_t* offsets_out, uint8_t* hits_out);
+vc_status vc_brick_cache_unpin(vc_brick_cache* c, const uint32_t* entries, uint32_t n);
+/* Marks an entry invalid (a failed decode): never a hit again, freed with its last pin. */
+vc_status vc_brick_cache_invalidate(vc_brick_cache* c, uint32_t entry);
+vc_status vc_brick_cache_stats_get(vc_brick_cache* c, vc_brick_cache_stats* out);
+
 /* ---- decode without allocation (the paper has no counterpart) ----
  * For callers that must not allocate device memory while decoding: code that runs inside CUDA
  * stream capture, real-time loops that cannot wait for the allocator, processes whose device
@@ -225,8 +351,10 @@ vc_status vc_volume_set_profiling(vc_volume* vol, int enable);
  * reset != 0 zeroes the counters and frees the event sets for reuse afterwards. */
 vc_status vc_volume_kernel_stats(vc_volume* vol, int reset, vc_kernel_stats* out);
 
-/* Releases a handle returned by this library (a vc_volume); NULL is a no-op. Synchronises the
- * device before freeing device memory. */
+/* Releases a handle returned by this library (a vc_volume, vc_server or vc_brick_cache); NULL is
+ * a no-op.
+ * A volume: synchronises the device before freeing device memory. A server: stops its thread,
+ * waits for its batches on the GPU and frees its cache (pending requests are dropped). */
 vc_status vc_release(void* handle);
 
 /* ---- encoder (CPU, multi-threaded; the paper compresses on the CPU with OpenMP, Methods

@@ -1,4 +1,5 @@
-"""CSGV oracle: plain single-threaded CPU encoder / decoder (ctypes over ``csgv_oracle.c``).
+"""CSGV oracle: plain single-threaded CPU encoder / decoder (ctypes over ``csgv_oracle.c``) and the
+camera request stage (``camera_oracle.c``).
 
 TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU-baseline leg are
 the only callers. The GPU library never imports this package and shares no code with it.
@@ -12,7 +13,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "csgv_oracle.c")
+_SRCS = [os.path.join(_HERE, "csgv_oracle.c"), os.path.join(_HERE, "camera_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -33,10 +34,11 @@ class OracleError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so next to its source (gcc, plain C11)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile liboracle.so next to its sources (gcc, plain C11, no floating-point contraction)."""
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(s) for s in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-fPIC", "-shared", _SRC, "-o", tmp])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fPIC", "-shared"] + _SRCS
+                              + ["-lm", "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -60,6 +62,8 @@ def _load():
                                            ctypes.POINTER(SZ)]
         lib.oracle_pack_bricks.restype = ctypes.c_int
         lib.oracle_free.argtypes = [P]
+        lib.oracle_camera_bricks.argtypes = [P, SZ, P, P, P, ctypes.c_float, U32, U32, U32, P, P, U32, P]
+        lib.oracle_camera_bricks.restype = ctypes.c_int
         for f in ("oracle_encode_volume", "oracle_decode_brick", "oracle_decode_volume", "oracle_brick_nodes",
                   "oracle_brick_symbols", "oracle_delta_nibbles", "oracle_rans_quantize", "oracle_pack_single_brick"):
             getattr(lib, f).restype = ctypes.c_int
@@ -211,3 +215,25 @@ def pack_bricks(log2b: int, streams, op_mask: int = OP_ALL, coder: int = CODER_P
     if rc:
         raise OracleError(rc, "pack_bricks")
     return _take(ptr, size.value)
+
+
+def camera_bricks(vol: np.ndarray, pos, dir, up, fov_y: float, width: int, height: int, max_lod: int = 31):
+    """Bricks that a pinhole camera's pixel rays request (ascending ids) and their levels of detail."""
+    vol = np.ascontiguousarray(vol, dtype=np.uint8)
+    f3 = lambda v: np.ascontiguousarray(np.asarray(v, dtype=np.float32).reshape(3))  # noqa: E731
+    p, d, u = f3(pos), f3(dir), f3(up)
+    n_out = ctypes.c_uint32()
+    lib = _load()
+    rc = lib.oracle_camera_bricks(vol.ctypes.data, vol.size, p.ctypes.data, d.ctypes.data, u.ctypes.data,
+                                  ctypes.c_float(fov_y), width, height, max_lod, None, None, 0, ctypes.byref(n_out))
+    if rc not in (0, -7):
+        raise OracleError(rc, "camera bricks")
+    n = n_out.value
+    ids = np.zeros(max(n, 1), dtype=np.uint32)
+    lods = np.zeros(max(n, 1), dtype=np.uint32)
+    rc = lib.oracle_camera_bricks(vol.ctypes.data, vol.size, p.ctypes.data, d.ctypes.data, u.ctypes.data,
+                                  ctypes.c_float(fov_y), width, height, max_lod, ids.ctypes.data, lods.ctypes.data, n,
+                                  ctypes.byref(n_out))
+    if rc:
+        raise OracleError(rc, "camera bricks")
+    return ids[:n], lods[:n]

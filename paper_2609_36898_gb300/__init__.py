@@ -65,6 +65,45 @@ class vc_kernel_stats(ctypes.Structure):
                 ("symbol_ms", ctypes.c_double), ("reconstruct_ms", ctypes.c_double)]
 
 
+class vc_server_config(ctypes.Structure):
+    _fields_ = [("cache_bytes", ctypes.c_uint64), ("device", ctypes.c_int32), ("max_batch_items", ctypes.c_uint32),
+                ("max_inflight", ctypes.c_uint32), ("min_class", ctypes.c_uint32), ("max_class", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 3)]
+
+
+class vc_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("volume_index", ctypes.c_uint32),
+                ("n_bricks", ctypes.c_uint32), ("hits", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("bytes", ctypes.c_uint64), ("t_submit_ns", ctypes.c_uint64), ("t_admit_ns", ctypes.c_uint64),
+                ("t_done_ns", ctypes.c_uint64)]
+
+
+class vc_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "cache_bytes", "cache_free_bytes", "cache_evictable_bytes", "cache_entries", "evictions",
+        "requests_submitted", "requests_admitted", "requests_done", "requests_failed", "requests_waiting",
+        "bricks_hit", "bricks_missed", "bricks_decoded", "batches", "batches_inflight", "batch_errors",
+        "voxels_decoded")]
+
+
+class vc_brick_cache_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "capacity_bytes", "free_bytes", "evictable_bytes", "entries", "evictions", "hits", "misses")]
+
+
+class vc_camera(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_float * 3), ("dir", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
+                ("fov_y", ctypes.c_float), ("width", ctypes.c_uint32), ("height", ctypes.c_uint32)]
+
+
+def make_camera(pos, dir, up, fov_y: float, width: int, height: int) -> vc_camera:
+    f3 = ctypes.c_float * 3
+    return vc_camera(f3(*[float(x) for x in pos]), f3(*[float(x) for x in dir]), f3(*[float(x) for x in up]),
+                     float(fov_y), int(width), int(height))
+
+
+VC_REQ_WAITING, VC_REQ_ADMITTED, VC_REQ_DONE, VC_REQ_FAILED = 0, 1, 2, 3
+
 _lib = None
 
 
@@ -87,6 +126,30 @@ def _lib_handle():
         lib.vc_volume_set_profiling.argtypes = [P, ctypes.c_int]
         lib.vc_volume_kernel_stats.argtypes = [P, ctypes.c_int, ctypes.POINTER(vc_kernel_stats)]
         lib.vc_encode_volume.argtypes = [P, P, U32, U32, U32, U32, U32, ctypes.POINTER(P), ctypes.POINTER(SZ)]
+        PU64 = ctypes.POINTER(ctypes.c_uint64)
+        lib.vc_server_create.argtypes = [ctypes.POINTER(vc_server_config), ctypes.POINTER(P)]
+        lib.vc_server_add_volume.argtypes = [P, P, ctypes.POINTER(U32)]
+        lib.vc_submit_bricks.argtypes = [P, U32, P, P, U32, PU64]
+        lib.vc_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(I32), P]
+        lib.vc_wait.argtypes = [P, ctypes.c_uint64, U32, ctypes.POINTER(I32)]
+        lib.vc_request_info_get.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(vc_request_info)]
+        lib.vc_request_release.argtypes = [P, ctypes.c_uint64]
+        lib.vc_server_cache.argtypes = [P, ctypes.POINTER(P), PU64]
+        lib.vc_server_stats_get.argtypes = [P, ctypes.POINTER(vc_server_stats)]
+        lib.vc_camera_bricks.argtypes = [P, P, U32, U32, U32, P, P, P, P]
+        lib.vc_request_bricks.argtypes = [P, U32, P, U32, U32, P]
+        lib.vc_camera_bricks.restype = I32
+        lib.vc_request_bricks.restype = I32
+        lib.vc_brick_cache_create.argtypes = [ctypes.c_uint64, U32, U32, ctypes.POINTER(P)]
+        lib.vc_brick_cache_acquire.argtypes = [P, P, P, U32, P, P, P]
+        lib.vc_brick_cache_unpin.argtypes = [P, P, U32]
+        lib.vc_brick_cache_invalidate.argtypes = [P, U32]
+        lib.vc_brick_cache_stats_get.argtypes = [P, ctypes.POINTER(vc_brick_cache_stats)]
+        for f in ("vc_server_create", "vc_server_add_volume", "vc_submit_bricks", "vc_poll", "vc_wait",
+                  "vc_request_info_get", "vc_request_release", "vc_server_cache", "vc_server_stats_get",
+                  "vc_brick_cache_create", "vc_brick_cache_acquire", "vc_brick_cache_unpin",
+                  "vc_brick_cache_invalidate", "vc_brick_cache_stats_get"):
+            getattr(lib, f).restype = I32
         lib.vc_free_bytes.argtypes = [P]
         lib.vc_free_bytes.restype = None
         lib.vc_status_string.argtypes = [I32]
@@ -182,6 +245,135 @@ def vc_encode_volume(V: np.ndarray, log2b: int, op_mask: int = 0x7F, coder: int 
     out = np.frombuffer(ctypes.string_at(ptr, size.value), dtype=np.uint8).copy()
     lib.vc_free_bytes(ptr)
     return out
+
+
+# ---- serving
+
+def vc_server_create(cache_bytes: int, device: int = 0, max_batch_items: int = 0, max_inflight: int = 0,
+                     min_class: int = 0, max_class: int = 0) -> ctypes.c_void_p:
+    cfg = vc_server_config(cache_bytes, device, max_batch_items, max_inflight, min_class, max_class)
+    out = ctypes.c_void_p()
+    _check(_lib_handle().vc_server_create(ctypes.byref(cfg), ctypes.byref(out)), "vc_server_create")
+    return out
+
+
+def vc_server_add_volume(srv, vol) -> int:
+    idx = ctypes.c_uint32()
+    _check(_lib_handle().vc_server_add_volume(srv, vol, ctypes.byref(idx)), "vc_server_add_volume")
+    return idx.value
+
+
+def vc_submit_bricks(srv, volume_index: int, brick_ids, lods=None) -> int:
+    ids = np.ascontiguousarray(brick_ids, dtype=np.uint32)
+    lp = None
+    if lods is not None:
+        lods = np.ascontiguousarray(np.broadcast_to(np.asarray(lods, dtype=np.uint32), ids.shape))
+        lp = lods.ctypes.data
+    rid = ctypes.c_uint64()
+    _check(_lib_handle().vc_submit_bricks(srv, volume_index, ids.ctypes.data if ids.size else None, lp, ids.size,
+                                          ctypes.byref(rid)), "vc_submit_bricks")
+    return rid.value
+
+
+def vc_poll(srv, request_id: int, n: int = 0):
+    """Returns (state, offsets or None); raises VCError if the request failed."""
+    st = ctypes.c_int32()
+    offs = np.zeros(n, dtype=np.uint64) if n else None
+    _check(_lib_handle().vc_poll(srv, request_id, ctypes.byref(st), offs.ctypes.data if n else None), "vc_poll")
+    return st.value, (offs if st.value == VC_REQ_DONE else None)
+
+
+def vc_wait(srv, request_id: int, timeout_ms: int = 60000) -> int:
+    st = ctypes.c_int32()
+    _check(_lib_handle().vc_wait(srv, request_id, timeout_ms, ctypes.byref(st)), "vc_wait")
+    return st.value
+
+
+def vc_request_info_get(srv, request_id: int) -> vc_request_info:
+    info = vc_request_info()
+    _check(_lib_handle().vc_request_info_get(srv, request_id, ctypes.byref(info)), "vc_request_info_get")
+    return info
+
+
+def vc_request_release(srv, request_id: int) -> None:
+    _check(_lib_handle().vc_request_release(srv, request_id), "vc_request_release")
+
+
+def vc_server_cache(srv):
+    p, nb = ctypes.c_void_p(), ctypes.c_uint64()
+    _check(_lib_handle().vc_server_cache(srv, ctypes.byref(p), ctypes.byref(nb)), "vc_server_cache")
+    return p.value, nb.value
+
+
+def vc_server_stats_get(srv) -> vc_server_stats:
+    st = vc_server_stats()
+    _check(_lib_handle().vc_server_stats_get(srv, ctypes.byref(st)), "vc_server_stats_get")
+    return st
+
+
+def vc_camera_bricks(vol, cams, max_lod: int = 31, cap: int | None = None, stream: int = 0):
+    """Returns per camera (ids, lods) of the requested bricks (ascending ids)."""
+    cams = list(cams)
+    arr = (vc_camera * len(cams))(*cams)
+    lib = _lib_handle()
+    counts = np.zeros(len(cams), dtype=np.uint32)
+    if cap is None:
+        _check(lib.vc_camera_bricks(vol, ctypes.byref(arr), len(cams), max_lod, 0, counts.ctypes.data, None, None,
+                                    ctypes.c_void_p(stream)), "vc_camera_bricks")
+        cap = int(counts.max()) if len(cams) else 0
+    ids = np.zeros(max(1, len(cams) * cap), dtype=np.uint32)
+    lods = np.zeros(max(1, len(cams) * cap), dtype=np.uint32)
+    _check(lib.vc_camera_bricks(vol, ctypes.byref(arr), len(cams), max_lod, cap, counts.ctypes.data, ids.ctypes.data,
+                                lods.ctypes.data, ctypes.c_void_p(stream)), "vc_camera_bricks")
+    return [(ids[i * cap: i * cap + min(int(counts[i]), cap)].copy(), lods[i * cap: i * cap + min(int(counts[i]), cap)].copy())
+            for i in range(len(cams))]
+
+
+def vc_request_bricks(srv, volume_index: int, cams, max_lod: int = 31) -> list:
+    cams = list(cams)
+    arr = (vc_camera * len(cams))(*cams)
+    out = np.zeros(len(cams), dtype=np.uint64)
+    _check(_lib_handle().vc_request_bricks(srv, volume_index, ctypes.byref(arr), len(cams), max_lod, out.ctypes.data),
+           "vc_request_bricks")
+    return [int(x) for x in out]
+
+
+def vc_brick_cache_create(nbytes: int, min_class: int, max_class: int) -> ctypes.c_void_p:
+    out = ctypes.c_void_p()
+    _check(_lib_handle().vc_brick_cache_create(nbytes, min_class, max_class, ctypes.byref(out)),
+           "vc_brick_cache_create")
+    return out
+
+
+def vc_brick_cache_acquire(cache, keys, classes):
+    """Returns (entries, offsets, hits) or None if the keys do not fit (VC_ERR_BUSY)."""
+    k = np.ascontiguousarray(keys, dtype=np.uint64)
+    c = np.ascontiguousarray(np.broadcast_to(np.asarray(classes, dtype=np.uint32), k.shape))
+    n = k.size
+    ent = np.zeros(n, dtype=np.uint32)
+    off = np.zeros(n, dtype=np.uint64)
+    hit = np.zeros(n, dtype=np.uint8)
+    rc = _lib_handle().vc_brick_cache_acquire(cache, k.ctypes.data, c.ctypes.data, n, ent.ctypes.data,
+                                              off.ctypes.data, hit.ctypes.data)
+    if rc == VC_ERR_BUSY:
+        return None
+    _check(rc, "vc_brick_cache_acquire")
+    return ent, off, hit.astype(bool)
+
+
+def vc_brick_cache_unpin(cache, entries) -> None:
+    e = np.ascontiguousarray(entries, dtype=np.uint32)
+    _check(_lib_handle().vc_brick_cache_unpin(cache, e.ctypes.data, e.size), "vc_brick_cache_unpin")
+
+
+def vc_brick_cache_invalidate(cache, entry: int) -> None:
+    _check(_lib_handle().vc_brick_cache_invalidate(cache, entry), "vc_brick_cache_invalidate")
+
+
+def vc_brick_cache_stats_get(cache) -> vc_brick_cache_stats:
+    st = vc_brick_cache_stats()
+    _check(_lib_handle().vc_brick_cache_stats_get(cache, ctypes.byref(st)), "vc_brick_cache_stats_get")
+    return st
 
 
 # ------------------------------------------------------------------ convenience wrapper (torch)

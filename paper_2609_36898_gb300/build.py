@@ -17,8 +17,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (source, object name, extra flags): the reconstruction kernels are compiled once per thread count
 SOURCES = [("decode.cu", "decode", []), ("decode_nt.cu", "decode_nt256", ["-DVC_NT=256"]),
            ("decode_nt.cu", "decode_nt512", ["-DVC_NT=512"]), ("decode_nt.cu", "decode_nt1024", ["-DVC_NT=1024"]),
-           ("vc_api.cu", "vc_api", []), ("decode_noalloc.cu", "decode_noalloc", []), ("encode.cpp", "encode", [])]
-HEADERS = ["vc_internal.h", "decode_kernels.cuh"]
+           ("vc_api.cu", "vc_api", []), ("decode_noalloc.cu", "decode_noalloc", []), ("encode.cpp", "encode", []),
+           ("cache.cpp", "cache", []), ("server.cpp", "server", []),
+           ("request.cu", "request", ["-Xcompiler", "-ffp-contract=off", "--fmad=false"])]
+HEADERS = ["vc_internal.h", "decode_kernels.cuh", "cache.h"]
 
 
 def _nvcc() -> str:

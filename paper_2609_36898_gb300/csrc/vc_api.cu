@@ -74,6 +74,7 @@ void free_volume(Volume* v) {
   }
   cudaFree(v->d_file);
   cudaFree(v->d_tables);
+  cudaFree(v->d_flags);
   cudaFree(v->d_host_ids);
   cudaFree(v->d_host_slots);
   cudaFree(v->d_host_cache);
@@ -138,6 +139,7 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   const uint8_t* st = p + kHeaderBytes;
   const uint8_t* rec = p + rec_off;
   uint32_t max_pal = 0, max_sym = 0, max_delta = 0, max_words = 0, max_stage = 0;
+  std::vector<uint8_t> bflags(n_bricks, 0);
   uint32_t prev = le32(st);
   if (prev != 0) return VC_ERR_FORMAT;
   for (uint32_t i = 0; i < n_bricks; ++i) {
@@ -161,6 +163,8 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
                                       : (uint32_t)(((16 + 4 * ns + 4 * (uint64_t)n_pal) + 15) & ~15ull) +
                                             (((S + 1) / 2 + 15) & ~15u);
     max_stage = std::max(max_stage, stage);
+    const uint8_t* pal = r + 16 + 4 * ns;
+    for (uint32_t k = 0; k < n_pal; ++k) bflags[i] |= le32(pal + 4 * (size_t)k) == 0 ? 1u : 2u;
   }
   if (le32(st + 4 * (size_t)n_bricks) != records_words) return VC_ERR_FORMAT;
   if (max_pal > hdr_max_pal || max_sym > hdr_max_sym) return VC_ERR_FORMAT;
@@ -202,7 +206,12 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
     free_volume(v);
     return VC_ERR_OOM;
   }
-  v->device_bytes = file_bytes + 64 + 4 * kRansM;
+  if (cudaMalloc(&v->d_flags, n_bricks) != cudaSuccess) {
+    cudaGetLastError();
+    free_volume(v);
+    return VC_ERR_OOM;
+  }
+  v->device_bytes = file_bytes + 64 + 4 * kRansM + n_bricks;
   // rANS table: per slot, freq[symbol] | (slot - cum[symbol]) << 13 | symbol << 25
   std::vector<uint32_t> tab(kRansM, 0);
   if (coder == 1) {
@@ -215,6 +224,7 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   bool ok = cudaMemsetAsync(v->d_file + file_bytes, 0, 64, stream) == cudaSuccess &&
             cudaMemcpyAsync(v->d_file, p, file_bytes, cudaMemcpyHostToDevice, stream) == cudaSuccess &&
             cudaMemcpyAsync(v->d_tables, tab.data(), 4 * kRansM, cudaMemcpyHostToDevice, stream) == cudaSuccess &&
+            cudaMemcpyAsync(v->d_flags, bflags.data(), n_bricks, cudaMemcpyHostToDevice, stream) == cudaSuccess &&
             cudaStreamSynchronize(stream) == cudaSuccess;
   if (!ok) { free_volume(v); return VC_ERR_CUDA; }
   v->dv.records = reinterpret_cast<const uint32_t*>(v->d_file + rec_off);
@@ -392,6 +402,8 @@ vc_status vc_release(void* handle) {
     free_volume(static_cast<Volume*>(handle));
     return VC_OK;
   }
+  if (release_server(handle)) return VC_OK;
+  if (release_cache(handle)) return VC_OK;
   return VC_ERR_ARG;
 }
 

@@ -18,6 +18,8 @@ constexpr uint32_t kMaxIdx8 = 0xFCu;      // palette indices below this fit 8-bi
 constexpr uint32_t kMaxIdx16 = 0xFFF0u;   // same for 16-bit grids
 constexpr uint32_t kFlagNoStop = 1u;
 constexpr uint32_t kHandleVolume = 0x564F4C31u;  // "VOL1"
+constexpr uint32_t kHandleServer = 0x53525631u;  // "SRV1"
+constexpr uint32_t kHandleCache = 0x43484331u;   // "CHC1"
 constexpr uint32_t kRansWarps = 16u;      // bricks (warps) per block of the rANS symbol kernel
 constexpr uint32_t kRing = 3u;            // pipelined schedule: workspace slots (chunks in flight)
 
@@ -77,6 +79,7 @@ struct Volume {
   cudaEvent_t ev_fork, ev_join[3], ev_a[kRing], ev_f[kRing], ev_o[kRing];
   uint8_t* d_file;       // device copy of the whole file (+ slack)
   uint8_t* d_tables;     // rANS table
+  uint8_t* d_flags;      // per brick: bit 0 = palette holds label 0, bit 1 = holds another label
   DevVolume dv;
   // staging for vc_decode_bricks_host
   uint32_t* d_host_ids;
@@ -94,6 +97,18 @@ struct Volume {
 };
 
 constexpr uint32_t kProfCalls = 256;
+
+// server.cpp: releases a vc_server (false if the handle is not one)
+bool release_server(void* handle);
+// cache.cpp: releases a vc_brick_cache (false if the handle is not one)
+bool release_cache(void* handle);
+
+// request.cu: the camera request stage (rays -> visible bricks and their levels of detail)
+size_t camera_scratch_bytes(const Volume& v, uint32_t ncams);
+constexpr size_t kCamDevBytes = 76;  // per camera, pinned host staging
+vc_status launch_camera_requests(const Volume& v, const vc_camera* cams, uint32_t ncams, uint32_t max_lod,
+                                 uint32_t cap, uint8_t* d_scratch, void* h_cams_pinned, uint32_t* d_counts,
+                                 uint32_t* d_ids, uint32_t* d_lods, cudaStream_t stream);
 
 // decode.cu
 bool schedule_supported(uint32_t L, uint32_t threads);

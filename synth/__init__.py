@@ -150,6 +150,11 @@ def c4() -> VolumeSpec:
     return VolumeSpec(dims=(4096, 4096, 4096), grid=16, seed=4, lam=1.0, bg=0.1, brick=32, name="c4_4096cube_b32")
 
 
+def c4_scaled(n: int = 1024) -> VolumeSpec:
+    """The 4096^3 recipe (one seed per 16^3 grid cell on average, 10% background) on an n^3 box."""
+    return VolumeSpec(dims=(n, n, n), grid=16, seed=4, lam=1.0, bg=0.1, brick=32, name=f"c4_{n}cube_b32")
+
+
 def c5() -> list:
     """The 8 resident volumes of the mixed serving workload: (dims, brick, cell diameter, background)."""
     rows = [(256, 16, 8, 0.0), (256, 32, 16, 0.1), (512, 32, 24, 0.2), (512, 64, 32, 0.4),
