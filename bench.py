@@ -39,6 +39,23 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over all ranks (the job is as slow as its slowest rank); x itself at N = 1."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank_step: int, steps: int, slowest_s: float) -> float:
+    """Whole-job throughput (weak scaling: every rank decodes its own full workload): units of all
+    ranks over the slowest rank's time, in G units per second."""
+    return world * units_per_rank_step * steps / slowest_s / 1e9
+
+
 def make_workload():
     import synth
     import paper_2609_36898_gb300 as vc
@@ -235,10 +252,13 @@ def serving_leg(args, local: int):
     srv = vc.vc_server_create(2 << 30, local)
     vi = vc.vc_server_add_volume(srv, vol)
     dims = (n, n, n)
-    ncam, W, H, max_lod = args.serve_cameras, 1920, 1080, 3
+    # 1920 x 1080 on the 4096^3 volume; scaled with the volume edge so that a voxel covers the same
+    # share of the image (the level-of-detail rule sees the same voxel-to-pixel ratios)
+    ncam, max_lod = args.serve_cameras, 3
+    W, H = max(16, 1920 * n // 4096), max(9, 1080 * n // 4096)
     lat, rstage, frame_ms = [], [], []
     prev = []
-    vox = 0
+    delivered = 0
     t_all = time.perf_counter()
     for f in range(args.serve_frames):
         cams = [orbit_camera(vc, i, f, dims, W, H) for i in range(ncam)]
@@ -254,6 +274,7 @@ def serving_leg(args, local: int):
         for r in rids:
             info = vc.vc_request_info_get(srv, r)
             lat.append((info.t_done_ns - info.t_submit_ns) / 1e6)
+            delivered += info.bytes // 4
         prev = rids
         rstage.append(1000 * (t1 - t0))
         frame_ms.append(1000 * (t2 - t0))
@@ -266,8 +287,10 @@ def serving_leg(args, local: int):
     lists = vc.vc_camera_bricks(vol, [orbit_camera(vc, i, 0, dims, W, H) for i in range(ncam)], max_lod)
     edge = 1 << B_LOG2
 
-    # plain: each camera's request of frame 0, one launch per brick, one request after the other
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(ncam + 1)]
+    # plain: the first cameras' requests of frame 0, one launch per brick, one request after the
+    # other (bounded: a full frame would take minutes)
+    lists = lists[:args.serve_plain_cameras]
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(len(lists) + 1)]
     status = torch.zeros(vc.VC_STATUS_WORDS, dtype=torch.int32, device="cuda")
     maxn = max(len(i) for i, _ in lists)
     cache = torch.empty(maxn * edge ** 3, dtype=torch.int32, device="cuda")
@@ -284,20 +307,25 @@ def serving_leg(args, local: int):
             plain_vox += sel.size * (edge >> int(lod)) ** 3
         e[c + 1].record(stream)
     torch.cuda.synchronize()
-    plain_lat = [e[0].elapsed_time(e[c + 1]) for c in range(ncam)]
+    plain_lat = [e[0].elapsed_time(e[c + 1]) for c in range(len(lists))]
     plain_s = plain_lat[-1] / 1000.0
     vc.vc_release(vol)
     pct = lambda a, q: float(np.percentile(np.asarray(a), q)) if len(a) else None  # noqa: E731
     return {
         "workload": f"{n}^3 Voronoi (4096^3 recipe: one seed per 16^3 cell, 10% background), 32^3 bricks, rANS; "
-                    f"{ncam} orbiting cameras at {W}x{H}, {args.serve_frames} frames, 2 GiB cache, lod <= {max_lod}",
+                    f"{ncam} orbiting cameras at {W}x{H} (1920x1080 scaled by {n}/4096), {args.serve_frames} frames, "
+                    f"2 GiB cache, lod <= {max_lod}",
         "served": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "requests": len(lat),
-                   "gvoxel_s": vox / wall / 1e9, "request_stage_ms_median": pct(rstage, 50),
+                   "gvoxel_s": delivered / wall / 1e9, "decoded_gvoxel_s": vox / wall / 1e9,
+                   "request_stage_ms_median": pct(rstage, 50),
                    "frame_ms_median": pct(frame_ms, 50), "bricks_decoded": int(st.bricks_decoded),
                    "bricks_hit": int(st.bricks_hit), "batches": int(st.batches), "evictions": int(st.evictions)},
-        "plain": {"p50_ms": pct(plain_lat, 50), "p99_ms": pct(plain_lat, 99), "requests": ncam,
+        "plain": {"p50_ms": pct(plain_lat, 50), "p99_ms": pct(plain_lat, 99), "requests": len(lists),
                   "gvoxel_s": plain_vox / plain_s / 1e9 if plain_s > 0 else None,
-                  "note": "frame 0's requests, all submitted at once, decoded one after the other with one launch per brick"},
+                  "note": f"frame 0's requests of the first {len(lists)} cameras, all submitted at once, decoded one "
+                          "after the other with one launch per brick, no cache"},
+        "metrics": "gvoxel_s = voxels delivered to requests (hits and decodes) per second of the frame loop; "
+                   "decoded_gvoxel_s = voxels the server decoded per second; latency = submit to resident",
         "status": int(status[0]),
         "prep_s": prep,
     }
@@ -359,15 +387,11 @@ def run_ours(args):
     kst = vc.vc_volume_kernel_stats(vol.handle, reset=True)
     vc.vc_volume_set_profiling(vol.handle, False)
     step_ms = [s.elapsed_time(t) for s, t in zip(starts, ends)]
-    dev_s = sum(step_ms) / 1000.0
-    if world > 1:
-        t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_s = float(t.item())
+    dev_s = max_over_ranks(sum(step_ms) / 1000.0, dev)
     if int(status[0]) != 0:
         raise RuntimeError(f"decode status {status.tolist()}")
     vox_per_step = n * e ** 3
-    value = world * vox_per_step * args.steps / dev_s / 1e9
+    value = job_rate(world, vox_per_step, args.steps, dev_s)
     algo = algorithmic_bytes(enc, n, e)
     # the dominant kernel is the reconstruction kernel: its average launch duration comes from the
     # library's timing events on the launching stream (one launch per step)
@@ -470,6 +494,7 @@ def main():
     ap.add_argument("--serve-frames", type=int, default=8, help="frames of the serving leg (0 = skip it)")
     ap.add_argument("--serve-size", type=int, default=1024, help="edge of the serving volume")
     ap.add_argument("--serve-cameras", type=int, default=64)
+    ap.add_argument("--serve-plain-cameras", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -153,6 +153,16 @@ typedef struct vc_schedule {
 vc_status vc_volume_set_schedule(vc_volume* vol, const vc_schedule* sched);
 vc_status vc_volume_get_schedule(const vc_volume* vol, vc_schedule* sched);
 
+/* Autotuner: times every schedule this build supports for the volume (threads per brick 256 /
+ * 512 / 1024, staging depth 1 / 2, persistent blocks per SM all / 1 / 2, grid and batched) by
+ * decoding the given sample (same arguments as vc_decode_bricks; the cache is overwritten) once
+ * untimed and `reps` times timed (0 = 3) with CUDA events on `cuda_stream`, then keeps the fastest
+ * schedule on the volume. *best and *best_mode receive it, *best_ms (may be NULL) its mean time.
+ * Synchronises the stream. Status words accumulate errors of all runs. */
+vc_status vc_volume_autotune(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, const uint32_t* cache_slots,
+                             uint32_t* cache, uint32_t lod, int32_t* status_dev, void* cuda_stream, uint32_t reps,
+                             vc_schedule* best, uint32_t* best_mode, float* best_ms);
+
 /* Decodes n bricks on `cuda_stream` (the Decompress stage: all requested bricks in parallel,
  * Results "GPU-based rendering pipeline"; Methods "GPU rendering pipeline").
  *   brick_ids   device, n x u32: brick ids (< n_bricks); duplicates allowed
@@ -343,7 +353,7 @@ typedef struct vc_kernel_stats {
 } vc_kernel_stats;
 
 /* enable != 0: later grid and batched decode calls on this volume record CUDA timing events on
- * their stream around the symbol kernel and the reconstruction kernel (up to 256 calls between
+ * their stream around the symbol kernel and the reconstruction kernel (up to 4096 calls between
  * resets; the events are the library's). Host only; allocates the events on first use. */
 vc_status vc_volume_set_profiling(vc_volume* vol, int enable);
 

@@ -136,6 +136,9 @@ def _lib_handle():
         lib.vc_request_release.argtypes = [P, ctypes.c_uint64]
         lib.vc_server_cache.argtypes = [P, ctypes.POINTER(P), PU64]
         lib.vc_server_stats_get.argtypes = [P, ctypes.POINTER(vc_server_stats)]
+        lib.vc_volume_autotune.argtypes = [P, P, U32, P, P, U32, P, P, U32, ctypes.POINTER(vc_schedule),
+                                           ctypes.POINTER(U32), ctypes.POINTER(ctypes.c_float)]
+        lib.vc_volume_autotune.restype = I32
         lib.vc_camera_bricks.argtypes = [P, P, U32, U32, U32, P, P, P, P]
         lib.vc_request_bricks.argtypes = [P, U32, P, U32, U32, P]
         lib.vc_camera_bricks.restype = I32
@@ -199,6 +202,17 @@ def vc_decode_bricks(vol, brick_ids_ptr: int, n: int, cache_slots_ptr: int, cach
     _check(_lib_handle().vc_decode_bricks(vol, ctypes.c_void_p(brick_ids_ptr), n, ctypes.c_void_p(cache_slots_ptr),
                                           ctypes.c_void_p(cache_ptr), lod, mode, ctypes.c_void_p(status_ptr),
                                           ctypes.c_void_p(stream)), "vc_decode_bricks")
+
+
+def vc_volume_autotune(vol, brick_ids_ptr: int, n: int, cache_slots_ptr: int, cache_ptr: int, lod: int,
+                       status_ptr: int, stream: int = 0, reps: int = 3):
+    """Returns ((threads, stage_depth, blocks_per_sm, chunk), mode, mean ms) of the fastest schedule."""
+    s, m, ms = vc_schedule(), ctypes.c_uint32(), ctypes.c_float()
+    _check(_lib_handle().vc_volume_autotune(vol, ctypes.c_void_p(brick_ids_ptr), n, ctypes.c_void_p(cache_slots_ptr),
+                                            ctypes.c_void_p(cache_ptr), lod, ctypes.c_void_p(status_ptr),
+                                            ctypes.c_void_p(stream), reps, ctypes.byref(s), ctypes.byref(m),
+                                            ctypes.byref(ms)), "vc_volume_autotune")
+    return (s.threads, s.stage_depth, s.blocks_per_sm, s.chunk), m.value, ms.value
 
 
 def vc_decode_bricks_noalloc(vol, brick_ids_ptr: int, n: int, cache_slots_ptr: int, cache_ptr: int, lod: int,

@@ -19,7 +19,8 @@ SOURCES = [("decode.cu", "decode", []), ("decode_nt.cu", "decode_nt256", ["-DVC_
            ("decode_nt.cu", "decode_nt512", ["-DVC_NT=512"]), ("decode_nt.cu", "decode_nt1024", ["-DVC_NT=1024"]),
            ("vc_api.cu", "vc_api", []), ("decode_noalloc.cu", "decode_noalloc", []), ("encode.cpp", "encode", []),
            ("cache.cpp", "cache", []), ("server.cpp", "server", []),
-           ("request.cu", "request", ["-Xcompiler", "-ffp-contract=off", "--fmad=false"])]
+           ("request.cu", "request", ["-Xcompiler", "-ffp-contract=off", "--fmad=false"]),
+           ("autotune.cpp", "autotune", [])]
 HEADERS = ["vc_internal.h", "decode_kernels.cuh", "cache.h"]
 
 

@@ -2,7 +2,6 @@
 #include "cache.h"
 
 #include <algorithm>
-#include <unordered_set>
 
 namespace vc {
 
@@ -98,8 +97,7 @@ void BrickCache::lru_remove(uint32_t e) {
 
 void BrickCache::remove_entry(uint32_t e) {
   Entry& E = entries_[e];
-  auto it = map_.find(E.key);
-  if (it != map_.end() && it->second == e) map_.erase(it);
+  if (map_.find(E.key) == e) map_.erase(E.key);
   release_block(E.cls, E.block);
   free_bytes_ += block_bytes(E.cls);
   E = Entry();
@@ -119,18 +117,17 @@ bool BrickCache::acquire(const uint64_t* keys, const uint32_t* cls, uint32_t n, 
   // admission: the missing keys' bytes must fit in free + evictable bytes, not counting the
   // evictable entries this call will pin as hits
   uint64_t need = 0, hit_evictable = 0;
-  {
-    std::unordered_set<uint64_t> seen;
-    for (uint32_t i = 0; i < n; ++i) {
-      if (!seen.insert(keys[i]).second) continue;
-      const uint32_t c = std::max(cls[i], min_cls_);
-      if (c > max_cls_) return false;
-      auto it = map_.find(keys[i]);
-      if (it != map_.end() && entries_[it->second].valid) {
-        if (entries_[it->second].pins == 0) hit_evictable += block_bytes(entries_[it->second].cls);
-      } else {
-        need += block_bytes(c);
-      }
+  seen_.clear();
+  for (uint32_t i = 0; i < n; ++i) {
+    if (seen_.find(keys[i]) != FlatMap::kMissing) continue;
+    seen_.put(keys[i], 0);
+    const uint32_t c = std::max(cls[i], min_cls_);
+    if (c > max_cls_) return false;
+    const uint32_t e = map_.find(keys[i]);
+    if (e != FlatMap::kMissing) {
+      if (entries_[e].pins == 0) hit_evictable += block_bytes(entries_[e].cls);
+    } else {
+      need += block_bytes(c);
     }
   }
   if (need > free_bytes_ + evictable_bytes_ - hit_evictable) return false;
@@ -139,14 +136,10 @@ bool BrickCache::acquire(const uint64_t* keys, const uint32_t* cls, uint32_t n, 
   uint32_t done = 0;
   std::vector<uint32_t> order;
   order.reserve(n);
-  for (uint32_t i = 0; i < n; ++i) {
-    auto it = map_.find(keys[i]);
-    if (it != map_.end() && entries_[it->second].valid) order.push_back(i);
-  }
-  for (uint32_t i = 0; i < n; ++i) {
-    auto it = map_.find(keys[i]);
-    if (!(it != map_.end() && entries_[it->second].valid)) order.push_back(i);
-  }
+  for (uint32_t i = 0; i < n; ++i)
+    if (map_.find(keys[i]) != FlatMap::kMissing) order.push_back(i);
+  for (uint32_t i = 0; i < n; ++i)
+    if (map_.find(keys[i]) == FlatMap::kMissing) order.push_back(i);
   std::vector<Ref> tmp(n);
   std::vector<uint8_t> tmp_created(n, 0);
   auto undo = [&]() {
@@ -162,9 +155,9 @@ bool BrickCache::acquire(const uint64_t* keys, const uint32_t* cls, uint32_t n, 
   for (; done < n; ++done) {
     const uint32_t i = order[done];
     const uint32_t c = std::max(cls[i], min_cls_);
-    auto it = map_.find(keys[i]);
-    if (it != map_.end() && entries_[it->second].valid) {
-      const uint32_t e = it->second;
+    const uint32_t hit_e = map_.find(keys[i]);
+    if (hit_e != FlatMap::kMissing) {
+      const uint32_t e = hit_e;
       Entry& E = entries_[e];
       if (E.pins++ == 0) lru_remove(e);
       tmp[done] = Ref{e, (uint64_t)E.block * block_bytes(E.cls), true};
@@ -193,7 +186,7 @@ bool BrickCache::acquire(const uint64_t* keys, const uint32_t* cls, uint32_t n, 
     E.block = blk;
     E.pins = 1;
     E.ready_seq = ~0ull;  // not decoded yet
-    map_[keys[i]] = e;    // replaces an invalid entry's mapping, if any
+    map_.put(keys[i], e);
     tmp[done] = Ref{e, (uint64_t)blk * block_bytes(c), false};
     tmp_created[done] = 1;
   }
@@ -216,8 +209,7 @@ void BrickCache::unpin(uint32_t e) {
 void BrickCache::invalidate(uint32_t e) {
   Entry& E = entries_[e];
   E.valid = false;
-  auto it = map_.find(E.key);
-  if (it != map_.end() && it->second == e) map_.erase(it);
+  if (map_.find(E.key) == e) map_.erase(E.key);
   if (E.pins == 0) {
     lru_remove(e);
     // removed from the map already: release the block and the entry

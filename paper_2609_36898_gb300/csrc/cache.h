@@ -13,10 +13,81 @@
 
 #include <stdint.h>
 
-#include <unordered_map>
+#include <algorithm>
 #include <vector>
 
 namespace vc {
+
+// Open-addressing hash map from 64-bit keys (never ~0) to 32-bit values: linear probing,
+// backward-shift deletion, power-of-two capacity kept at most half full.
+class FlatMap {
+ public:
+  static constexpr uint64_t kEmpty = ~0ull;
+  static constexpr uint32_t kMissing = 0xFFFFFFFFu;
+  FlatMap() { rehash(64); }
+  uint32_t find(uint64_t k) const {
+    for (uint64_t i = home(k);; i = (i + 1) & mask_) {
+      if (keys_[i] == k) return vals_[i];
+      if (keys_[i] == kEmpty) return kMissing;
+    }
+  }
+  void put(uint64_t k, uint32_t v) {
+    if (2 * (size_ + 1) > keys_.size()) rehash(2 * keys_.size());
+    uint64_t i = home(k);
+    while (keys_[i] != kEmpty && keys_[i] != k) i = (i + 1) & mask_;
+    if (keys_[i] == kEmpty) ++size_;
+    keys_[i] = k;
+    vals_[i] = v;
+  }
+  bool erase(uint64_t k) {
+    uint64_t i = home(k);
+    while (keys_[i] != k) {
+      if (keys_[i] == kEmpty) return false;
+      i = (i + 1) & mask_;
+    }
+    for (uint64_t j = i;;) {  // pull later members of the probe run back into the hole
+      j = (j + 1) & mask_;
+      if (keys_[j] == kEmpty) break;
+      const uint64_t h = home(keys_[j]);
+      const bool movable = i <= j ? (h <= i || h > j) : (h <= i && h > j);
+      if (movable) {
+        keys_[i] = keys_[j];
+        vals_[i] = vals_[j];
+        i = j;
+      }
+    }
+    keys_[i] = kEmpty;
+    --size_;
+    return true;
+  }
+  void clear() {
+    std::fill(keys_.begin(), keys_.end(), kEmpty);
+    size_ = 0;
+  }
+  size_t size() const { return size_; }
+
+ private:
+  uint64_t home(uint64_t k) const { return (k * 0x9E3779B97F4A7C15ull) >> shift_; }
+  void rehash(size_t cap) {
+    std::vector<uint64_t> ok;
+    std::vector<uint32_t> ov;
+    ok.swap(keys_);
+    ov.swap(vals_);
+    keys_.assign(cap, kEmpty);
+    vals_.assign(cap, 0);
+    mask_ = cap - 1;
+    shift_ = 64;
+    for (size_t c = cap; c > 1; c >>= 1) --shift_;
+    size_ = 0;
+    for (size_t i = 0; i < ok.size(); ++i)
+      if (ok[i] != kEmpty) put(ok[i], ov[i]);
+  }
+  std::vector<uint64_t> keys_;
+  std::vector<uint32_t> vals_;
+  uint64_t mask_ = 0;
+  uint32_t shift_ = 64;
+  size_t size_ = 0;
+};
 
 class BrickCache {
  public:
@@ -90,7 +161,8 @@ class BrickCache {
   std::vector<Level> levels_;
   std::vector<Entry> entries_;
   std::vector<uint32_t> free_entries_;
-  std::unordered_map<uint64_t, uint32_t> map_;
+  FlatMap map_;
+  FlatMap seen_;  // scratch of acquire()
   int32_t lru_head_ = -1, lru_tail_ = -1;
 };
 

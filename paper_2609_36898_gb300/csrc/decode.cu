@@ -48,35 +48,20 @@ using namespace dev;
 // ------------------------------------------------------------------------------------------
 // rANS symbols: one warp per request item. Table entry per slot: freq | (slot - cum) << 13 |
 // symbol << 25. Full steps of 32 symbols run without bounds checks; the last step is guarded.
-// Returns true if the stream was consumed exactly and every state ended at 2^16.
-template <bool SMEM>
+// Returns true if the stream was consumed exactly and every state ended at 2^16. The coded words
+// flow through a register window: lane l holds words wb + l, wb + 32 + l (in use) and the next two
+// runs of 32 (loads in flight), so the global-memory latency stays off the state chain.
 __device__ __forceinline__ bool rans_steps(const uint32_t* tab, const uint16_t* words, uint32_t nw, uint32_t S,
                                            uint32_t x, uint32_t ns, uint8_t* out, uint32_t lane) {
   const uint32_t lt = lanemask_lt();
   const uint32_t full = S & ~31u;
   uint8_t* o = out + (lane >> 1);
   const bool even = !(lane & 1u);
-  uint32_t ptr = 0;
+  auto ld = [&](uint32_t i) -> uint32_t { return i < nw ? (uint32_t)__ldg(words + i) : 0u; };
+  uint32_t wb = 0, w0 = ld(lane), w1 = ld(32u + lane), w2 = ld(64u + lane), w3 = ld(96u + lane);
+  uint32_t ptr = 0;  // words consumed; ptr - wb < 32 between steps
   bool bad = false;
-  for (uint32_t base = 0; base < full; base += 32u) {
-    const uint32_t e = tab[x & (kRansM - 1u)];
-    const uint32_t s = e >> 25;
-    x = (e & 0x1FFFu) * (x >> 12) + ((e >> 13) & 0xFFFu);
-    const bool need = x < (1u << 16);
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
-    if (need) {
-      const uint32_t at = ptr + __popc(m & lt);
-      bad |= at >= nw;
-      x = (x << 16) | (uint32_t)words[at < nw ? at : 0u];
-    }
-    ptr += __popc(m);
-    const uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, s, 1);
-    if (even) o[base >> 1] = (uint8_t)(s | (hi << 4));
-  }
-  if (full < S) {
-    const uint32_t i = full + lane;
-    const bool active = i < S;
-    uint32_t s = 0;
+  auto step = [&](bool active, uint32_t& s) {
     if (active) {
       const uint32_t e = tab[x & (kRansM - 1u)];
       s = e >> 25;
@@ -84,12 +69,32 @@ __device__ __forceinline__ bool rans_steps(const uint32_t* tab, const uint16_t* 
     }
     const bool need = active && x < (1u << 16);
     const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
+    const uint32_t r = ptr - wb + __popc(m & lt);  // < 63
+    const uint32_t v0 = __shfl_sync(0xFFFFFFFFu, w0, r & 31u), v1 = __shfl_sync(0xFFFFFFFFu, w1, r & 31u);
     if (need) {
-      const uint32_t at = ptr + __popc(m & lt);
-      bad |= at >= nw;
-      x = (x << 16) | (uint32_t)words[at < nw ? at : 0u];
+      bad |= ptr + __popc(m & lt) >= nw;
+      x = (x << 16) | (r < 32u ? v0 : v1);
     }
     ptr += __popc(m);
+    if (ptr - wb >= 32u) {  // slide the window by one run of 32 words
+      wb += 32u;
+      w0 = w1;
+      w1 = w2;
+      w2 = w3;
+      w3 = ld(wb + 96u + lane);
+    }
+  };
+  for (uint32_t base = 0; base < full; base += 32u) {
+    uint32_t s = 0;
+    step(true, s);
+    const uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, s, 1);
+    if (even) o[base >> 1] = (uint8_t)(s | (hi << 4));
+  }
+  if (full < S) {
+    const uint32_t i = full + lane;
+    const bool active = i < S;
+    uint32_t s = 0;
+    step(active, s);
     const uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, s, 1);
     if (active && even) o[full >> 1] = (uint8_t)(s | (i + 1 < S ? hi << 4 : 0u));
   }
@@ -117,21 +122,9 @@ __global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_kernel(const __g
   const uint32_t x0 = lane < ns ? rec[4 + lane] : (1u << 16);
   const bool bad_state = __any_sync(0xFFFFFFFFu, lane < ns && x0 < (1u << 16));
   uint8_t* out = ws + (size_t)(item - P.ws_item0) * SL.ws_stride;
-  // the coded bytes (a 16-byte aligned span) go to this warp's shared buffer when they fit
   const uint32_t cofs = 16u + 4u * ns + 4u * np;
-  const uint32_t a0 = cofs & ~15u, a1 = (cofs + cb + 15u) & ~15u;
-  bool ok;
-  if (a1 - a0 <= SL.a_buf) {
-    unsigned char* buf = sm + 4u * kRansM + warp * SL.a_buf;
-    const uint4* src = reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(rec) + a0);
-    uint4* dst = reinterpret_cast<uint4*>(buf);
-    for (uint32_t i = lane; i < (a1 - a0) / 16u; i += 32u) dst[i] = src[i];
-    __syncwarp();
-    ok = rans_steps<true>(tab, reinterpret_cast<const uint16_t*>(buf + (cofs - a0)), nw, S, x0, ns, out, lane);
-  } else {
-    ok = rans_steps<false>(tab, reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(rec) + cofs),
-                           nw, S, x0, ns, out, lane);
-  }
+  const bool ok = rans_steps(tab, reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(rec) + cofs),
+                             nw, S, x0, ns, out, lane);
   if ((!ok || bad_state) && lane == 0) report(P.status, VC_ERR_CORRUPT, item);
 }
 
@@ -181,17 +174,14 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   const uint32_t b = 1u << L;
   const uint32_t ncells = ((1u << (3 * L)) - 1u) / 7u;  // levels 0..L-1
   const uint32_t stream_words = (v.max_sym + 7u) / 8u;
-  const uint32_t psum_bytes = v.max_delta ? 4u * (9u * threads + 64u) : 0u;  // general parse path
   uint32_t o = 0;
-  s.misc_off = o; o += 512;
-  s.lut_off = o; o += 1024;
+  s.misc_off = o; o += 1024;
   s.nwords = (v.max_sym + 31u) / 32u + 2u;
   s.mask_off = o; o += align16(4 * 4 * s.nwords);
   s.nodes_words = stream_words + 4u;
   s.nodes_off = o; o += v.max_delta ? align16(4 * s.nodes_words) : 0u;
   s.dlist_cap = v.max_delta;
   s.dlist_off = o; o += align16(4 * (v.max_delta ? v.max_delta : 1u));
-  const uint32_t levels_off = o;
   s.g_off = o; o += align16(s.gt_bytes * (ncells + 7u));  // level 1 starts at cell 8 (alignment)
   // per level l >= 1 below L, one byte per level-(l-1) cell: its children's stop-0 bits
   const uint32_t ns_bytes = ((1u << (3 * (L - 1))) - 1u) / 7u;
@@ -202,17 +192,12 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   s.list0_cap = (cap[0] + 7u) & ~7u;
   s.list_off = o; o += align16(2u * (s.list0_cap + cap[1]));
   if (split) {
-    // no finest grid here (it goes to a workspace); the parse summaries borrow the level arrays,
-    // which are not in use yet, extended if they are too small
+    // no finest grid here (it goes to a workspace)
     s.fg_off = 0;
-    s.psum_off = levels_off;
-    if (o - levels_off < psum_bytes) o = levels_off + align16(psum_bytes);
     s.pal_cap = 0;
     s.pal_off = o;
   } else {
-    // the finest grid also hosts the general parse path's summaries
-    s.fg_off = o; o += align16(std::max<uint32_t>(s.gt_bytes * b * b * b, psum_bytes));
-    s.psum_off = s.fg_off;
+    s.fg_off = o; o += align16(s.gt_bytes * b * b * b);
     // private palette copy (frees the stage early); 256 entries for byte grids
     s.pal_cap = s.gt_bytes == 1 ? 256u : (v.max_pal <= 1024u ? v.max_pal : 0u);
     s.pal_off = o; o += align16(4u * s.pal_cap);
@@ -228,9 +213,8 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   if (s.total > (uint32_t)optin) return VC_ERR_UNSUPPORTED;
   // rANS symbol kernel: table + one coded-word buffer per warp
   s.ws_stride = align16((v.max_sym + 1u) / 2u) + 16u;
-  s.a_buf = align16(4u * v.max_rec_words);
-  if (4u * kRansM + kRansWarps * s.a_buf > (uint32_t)optin) s.a_buf = 0;
-  s.a_smem = 4u * kRansM + kRansWarps * s.a_buf;
+  s.a_buf = 0;
+  s.a_smem = 4u * kRansM;  // the slot table only: many blocks per SM hide the step latency
   *out = s;
   return VC_OK;
 }

@@ -139,31 +139,10 @@ __device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t& pa
 }
 
 // ------------------------------------------------------------------------------------------
-// Parse table, one u32 per byte value: for start state s in {0, 1} (1 = a delta entry is
-// expected), bits [16 s, 16 s + 13) hold the end state (bit 0), which nibbles are operations
-// (bits 1-2), which are delta operations (bits 3-4) and the operation nibbles themselves,
-// compacted (bits 5-12).
-__device__ __forceinline__ uint32_t parse_entry(uint32_t byte) {
-  uint32_t out = 0;
-#pragma unroll
-  for (uint32_t s = 0; s < 2; ++s) {
-    uint32_t st = s, opm = 0, delm = 0;
-#pragma unroll
-    for (uint32_t h = 0; h < 2; ++h) {
-      const uint32_t v = (byte >> (4 * h)) & 15u;
-      if (st == 0) {
-        opm |= 1u << h;
-        if ((v & 7u) == OP_DELTA) { delm |= 1u << h; st = 1; }
-      } else {
-        st = (v >> 3) & 1u;  // another entry follows
-      }
-    }
-    const uint32_t val = opm == 3u ? byte : (opm == 1u ? (byte & 15u) : (opm == 2u ? (byte >> 4) : 0u));
-    out |= (st | (opm << 1) | (delm << 3) | (val << 5)) << (16 * s);
-  }
-  return out;
-}
-__device__ __forceinline__ uint32_t parse_pick(uint32_t e, uint32_t st) { return (st ? e >> 16 : e) & 0x1FFFu; }
+// Parse of the symbol stream: which nibbles are operations and which are delta entries. It is a
+// 2-state automaton (state 1 = "a delta entry comes next"): from state 0 a nibble is an operation
+// and the state becomes 1 iff it is a delta operation (low 3 bits = 6); from state 1 the nibble is
+// an entry and the state stays 1 iff its bit 3 ("another entry follows") is set.
 
 // delta from the entries at nibble i..; 0 when invalid (runs past S or needs an eighth entry)
 __device__ __forceinline__ uint32_t read_delta(const uint32_t* sw, uint32_t i, uint32_t S) {
@@ -183,225 +162,163 @@ struct ParseOut {
   uint32_t n_delta;
 };
 
-// The table entry of byte k of stream word x; bytes past the end of the stream (S nibbles) are
-// masked: a lone low nibble keeps only its own half.
-__device__ __forceinline__ uint32_t parse_byte(const uint32_t* lut, uint32_t x, uint32_t k, uint32_t nib_left) {
-  const uint32_t byte = (x >> (8u * k)) & 0xFFu;
-  uint32_t e = lut[byte];
-  if (nib_left < 2u * k + 2u) {
-    // only the low nibble is part of the stream: recompute for one nibble (rare: last byte)
-    const uint32_t v = byte & 15u;
-    uint32_t out = 0;
+// For the 8 nibbles of stream word x: D = nibbles whose low 3 bits are 6 (delta operations if they
+// are operations); A / B = bit i holds the state after nibble i when the word is entered in state
+// 0 / 1. The per-nibble transitions are composed by prefix doubling on 8-bit masks.
+__device__ __forceinline__ void word_states(uint32_t x, uint32_t& D, uint32_t& A, uint32_t& B) {
+  D = nib_eq8(x, OP_DELTA);
+  uint32_t a = D, e = gather_nib_bits((x >> 3) & 0x11111111u);  // after nibble i from 0 / from 1
 #pragma unroll
-    for (uint32_t s = 0; s < 2; ++s) {
-      uint32_t st = s, opm = 0, delm = 0;
-      if (st == 0) {
-        opm = 1u;
-        if ((v & 7u) == OP_DELTA) { delm = 1u; st = 1; }
-      } else {
-        st = (v >> 3) & 1u;
-      }
-      out |= (st | (opm << 1) | (delm << 3) | ((opm ? v : 0u) << 5)) << (16 * s);
-    }
-    e = out;
+  for (uint32_t k = 1; k < 8; k <<= 1) {
+    const uint32_t ha = a << k, hb = (e << k) | ((1u << k) - 1u);  // identity below bit k
+    const uint32_t na = (ha & e) | (~ha & a), nb = (hb & e) | (~hb & a);
+    a = na & 0xFFu;
+    e = nb & 0xFFu;
   }
-  return e;
+  A = a;
+  B = e;
 }
 
-// State of the parse automaton before symbol p0 (0 = an operation is expected), found by looking
-// back to the nearest self-synchronising symbol: after any symbol v in {0..5, 7} the next one is an
-// operation whatever came before (an operation that is not a delta, or a last delta entry), and
-// after 14 a delta entry follows either way. -1 if none lies within 64 symbols.
-__device__ __forceinline__ int lookback_state(const uint32_t* sw, uint32_t p0) {
-  if (p0 == 0) return 0;
-  const uint32_t lim = p0 > 64u ? p0 - 64u : 0u;
-  uint32_t q = p0;
-  int st = -1;
-  while (q > lim) {
-    --q;
-    const uint32_t v = nib_at(sw, q);
-    if (v < 8u && v != 6u) { st = 0; ++q; break; }
-    if (v == 14u) { st = 1; ++q; break; }
-  }
-  if (st < 0) {
-    if (q != 0) return -1;
-    st = 0;  // reached the start of the stream
-  }
-  for (; q < p0; ++q) {
-    const uint32_t v = nib_at(sw, q);
-    st = st == 0 ? (int)((v & 7u) == OP_DELTA) : (int)(v >> 3);
-  }
-  return st;
+// Operation nibbles of a word entered in state st (nv valid nibbles); *end = the state after it.
+__device__ __forceinline__ uint32_t word_ops(uint32_t A, uint32_t B, uint32_t st, uint32_t nv, uint32_t* end) {
+  const uint32_t F = st ? B : A;
+  *end = (F >> (nv - 1u)) & 1u;
+  const uint32_t entering = ((F << 1) | st) & 0xFFu;
+  return ~entering & ((1u << nv) - 1u);
 }
 
-// Pass B of the parse: from start state st at word w0, writes this thread's node symbols from node
-// index j (8 per u32 through a 64-bit accumulator) and its delta values from index d.
-__device__ __forceinline__ void parse_emit(const uint32_t* sw, uint32_t S, uint32_t w0, uint32_t w1, uint32_t st,
-                                           uint32_t jstart, uint32_t d, uint32_t* nodes, uint32_t nodes_words,
-                                           uint32_t* dlist, uint32_t dcap, const uint32_t* lut) {
-  uint32_t j = jstart;
-  uint64_t acc = 0;
-  auto flush = [&](uint32_t wi) {
-    if (wi < nodes_words) {
-      if (wi == (jstart >> 3) && (jstart & 7u)) atomicOr(&nodes[wi], (uint32_t)acc);
-      else nodes[wi] = (uint32_t)acc;
-    }
-    acc >>= 32;
-  };
-  for (uint32_t w = w0; w < w1; ++w) {
-    const uint32_t x = sw[w];
-    const uint32_t left = S - 8u * w;
-    if (st == 0 && left >= 8u && nib_eq8(x, OP_DELTA) == 0) {
-      // from an operation, 8 symbols none of which can start or continue a delta: 8 operations
-      acc |= (uint64_t)x << (4u * (j & 7u));
-      j += 8;
-      flush((j - 8u) >> 3);
-      continue;
-    }
-    const uint32_t nb = left >= 8u ? 4u : (left + 1u) >> 1;
+// The nibbles of x selected by m, packed from nibble 0 upwards.
+__device__ __forceinline__ uint32_t pack_nibbles(uint32_t x, uint32_t m) {
+  if (m == 0xFFu) return x;
+  uint32_t out = 0, pos = 0;
 #pragma unroll
-    for (uint32_t k = 0; k < 4; ++k) {
-      if (k < nb) {
-        const uint32_t f = parse_pick(parse_byte(lut, x, k, left), st);
-        const uint32_t opm = (f >> 1) & 3u, cnt = __popc(opm);
-        const uint32_t p = j & 7u;
-        acc |= (uint64_t)(f >> 5) << (4u * p);
-        j += cnt;
-        if (p + cnt >= 8u) flush((j - cnt) >> 3);  // a word of 8 node symbols is complete
-        const uint32_t delm = (f >> 3) & 3u;
-        if (delm) {
-#pragma unroll
-          for (uint32_t h = 0; h < 2; ++h)
-            if (delm & (1u << h)) {
-              if (d < dcap) dlist[d] = 8u * w + 2u * k + h + 1u;  // first entry; resolved after the parse
-              ++d;
-            }
-        }
-        st = f & 1u;
-      }
-    }
+  for (uint32_t i = 0; i < 8; ++i) {
+    const uint32_t take = (m >> i) & 1u;
+    out |= (take ? (x >> (4u * i)) & 15u : 0u) << pos;
+    pos += 4u * take;
   }
-  if ((j & 7u) && (j >> 3) < nodes_words) atomicOr(&nodes[j >> 3], (uint32_t)acc);
+  return out;
 }
 
-// Builds nodes[] (8 operation symbols per u32, zero-padded) and dlist[] from the symbol stream.
-// scratch: 8 NT + 2 words, used only when some chunk has no self-synchronising symbol nearby.
+// A chunk summary for both entering states: bit s of e = the state after the chunk entered in
+// state s; nd_s = nodes | delta operations << 16 counted from entering state s.
+struct Fn2 {
+  uint32_t e, nd0, nd1;
+};
+__device__ __forceinline__ Fn2 fn_then(const Fn2& p, const Fn2& c) {  // p, then c
+  const uint32_t p0 = p.e & 1u, p1 = (p.e >> 1) & 1u;
+  const uint32_t c0 = c.e & 1u, c1 = (c.e >> 1) & 1u;
+  Fn2 r;
+  r.nd0 = p.nd0 + (p0 ? c.nd1 : c.nd0);
+  r.nd1 = p.nd1 + (p1 ? c.nd1 : c.nd0);
+  r.e = (p0 ? c1 : c0) | ((p1 ? c1 : c0) << 1);
+  return r;
+}
+__device__ __forceinline__ Fn2 fn_shfl_up(const Fn2& f, uint32_t d) {
+  return Fn2{__shfl_up_sync(0xFFFFFFFFu, f.e, d), __shfl_up_sync(0xFFFFFFFFu, f.nd0, d),
+             __shfl_up_sync(0xFFFFFFFFu, f.nd1, d)};
+}
+
+// Builds nodes[] (8 operation symbols per u32) and dlist[] (first-entry nibble index of each delta
+// operation) from the symbol stream. Each thread takes a contiguous run of stream words: it
+// summarises the run for both entering states, a block-wide scan of the summaries gives every run
+// its entering state and its node and delta bases, and the runs then write their operation
+// nibbles. scan_tmp: 3 (NT / 32) + 3 words. Node counts must stay below 2^16 (b <= 32).
 template <int NT>
 __device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes, uint32_t nodes_words,
-                                 uint32_t* dlist, uint32_t dcap, const uint32_t* lut, uint32_t* scan_tmp,
-                                 uint32_t* sum, int* s_err) {
+                                 uint32_t* dlist, uint32_t dcap, uint32_t* scan_tmp, int* s_err) {
+  constexpr uint32_t NW = NT / 32;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t T = (S + 7u) >> 3;  // stream words
   const uint32_t WP = (T + NT - 1) / NT;
   const uint32_t w0 = min(tid * WP, T), w1 = min(w0 + WP, T);
-  for (uint32_t w = tid; w < nodes_words; w += NT) nodes[w] = 0u;
-  const int st0 = w0 < w1 ? lookback_state(sw, 8u * w0) : 0;
-  ParseOut out;
-  if (!__syncthreads_or(st0 < 0)) {
-    // fast path: every chunk knows its start state; count, scan, emit
-    uint32_t st = (uint32_t)st0, n = 0, d = 0;
+  // 1. this run's summary for entering state 0 and 1
+  Fn2 f{2u, 0u, 0u};  // identity
+  {
+    uint32_t s0 = 0, s1 = 1;
     for (uint32_t w = w0; w < w1; ++w) {
       const uint32_t x = sw[w];
-      const uint32_t left = S - 8u * w;
-      if (st == 0 && left >= 8u && nib_eq8(x, OP_DELTA) == 0) {
-        n += 8;
-        continue;
-      }
-      const uint32_t nb = left >= 8u ? 4u : (left + 1u) >> 1;
-#pragma unroll
-      for (uint32_t k = 0; k < 4; ++k) {
-        if (k < nb) {
-          const uint32_t f = parse_pick(parse_byte(lut, x, k, left), st);
-          n += __popc((f >> 1) & 3u); d += __popc((f >> 3) & 3u); st = f & 1u;
-        }
-      }
+      const uint32_t nv = min(8u, S - 8u * w);
+      uint32_t D, A, B, e0, e1;
+      word_states(x, D, A, B);
+      const uint32_t m0 = word_ops(A, B, s0, nv, &e0), m1 = word_ops(A, B, s1, nv, &e1);
+      f.nd0 += __popc(m0) | (__popc(m0 & D) << 16);
+      f.nd1 += __popc(m1) | (__popc(m1 & D) << 16);
+      s0 = e0;
+      s1 = e1;
     }
-    if (w0 < w1 && w1 == T && st != 0) set_err(s_err, VC_ERR_CORRUPT);  // ends inside a delta chain
-    uint32_t jb, db, tn, td;
-    block_scan2<NT>(n, d, jb, db, tn, td, scan_tmp);
-    parse_emit(sw, S, w0, w1, (uint32_t)st0, jb, db, nodes, nodes_words, dlist, dcap, lut);
-    out.n_nodes = tn;
-    out.n_delta = td;
-    __syncthreads();
-    return out;
+    f.e = s0 | (s1 << 1);
   }
-  // general path: summaries for both start states composed by a warp scan
-  uint32_t s0 = 0, s1 = 1, n0 = 0, n1 = 0, d0 = 0, d1 = 0;
-  bool merged = false;
-  for (uint32_t w = w0; w < w1; ++w) {
-    const uint32_t x = sw[w];
-    const uint32_t left = S - 8u * w;
-    const uint32_t nb = left >= 8u ? 4u : (left + 1u) >> 1;
+  // 2. exclusive scan of the summaries over the block (warp shuffles, then the warp totals)
+  Fn2 inc = f;
 #pragma unroll
-    for (uint32_t k = 0; k < 4; ++k) {
-      if (k < nb) {
-        const uint32_t e = parse_byte(lut, x, k, left);
-        const uint32_t f0 = parse_pick(e, s0);
-        n0 += __popc((f0 >> 1) & 3u); d0 += __popc((f0 >> 3) & 3u); s0 = f0 & 1u;
-        if (!merged) {
-          const uint32_t f1 = parse_pick(e, s1);
-          n1 += __popc((f1 >> 1) & 3u); d1 += __popc((f1 >> 3) & 3u); s1 = f1 & 1u;
-          if (s1 == s0) { merged = true; n1 -= n0; d1 -= d0; }  // keep the offsets from here on
-        }
-      }
-    }
+  for (uint32_t d = 1; d < 32; d <<= 1) {
+    const Fn2 p = fn_shfl_up(inc, d);
+    if (lane >= d) inc = fn_then(p, inc);
   }
-  if (merged) { n1 += n0; d1 += d0; s1 = s0; }
-  // sum layout (padded by one word per 32 against bank conflicts): end states, n0, n1, d0, d1,
-  // then start state / node base / delta base
-  auto at = [](uint32_t t) { return t + (t >> 5); };
-  constexpr uint32_t SP = NT + NT / 32;
-  sum[at(tid)] = s0 | (s1 << 1);
-  sum[SP + at(tid)] = n0;
-  sum[2 * SP + at(tid)] = n1;
-  sum[3 * SP + at(tid)] = d0;
-  sum[4 * SP + at(tid)] = d1;
+  if (lane == 31) { scan_tmp[3 * warp] = inc.e; scan_tmp[3 * warp + 1] = inc.nd0; scan_tmp[3 * warp + 2] = inc.nd1; }
   __syncthreads();
   if (warp == 0) {
-    constexpr uint32_t PER = NT / 32;
-    uint32_t E0 = 0, E1 = 1, N0 = 0, N1 = 0, D0 = 0, D1 = 0;  // identity
-    for (uint32_t t = lane * PER; t < lane * PER + PER; ++t) {
-      const uint32_t te = sum[at(t)];
-      const uint32_t a0 = E0 ? sum[2 * SP + at(t)] : sum[SP + at(t)], b0 = E0 ? sum[4 * SP + at(t)] : sum[3 * SP + at(t)];
-      const uint32_t a1 = E1 ? sum[2 * SP + at(t)] : sum[SP + at(t)], b1 = E1 ? sum[4 * SP + at(t)] : sum[3 * SP + at(t)];
-      N0 += a0; D0 += b0; E0 = (te >> E0) & 1u;
-      N1 += a1; D1 += b1; E1 = (te >> E1) & 1u;
-    }
+    Fn2 v = lane < NW ? Fn2{scan_tmp[3 * lane], scan_tmp[3 * lane + 1], scan_tmp[3 * lane + 2]} : Fn2{2u, 0u, 0u};
+    Fn2 vi = v;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint32_t pE0 = __shfl_up_sync(0xFFFFFFFFu, E0, off), pE1 = __shfl_up_sync(0xFFFFFFFFu, E1, off);
-      const uint32_t pN0 = __shfl_up_sync(0xFFFFFFFFu, N0, off), pN1 = __shfl_up_sync(0xFFFFFFFFu, N1, off);
-      const uint32_t pD0 = __shfl_up_sync(0xFFFFFFFFu, D0, off), pD1 = __shfl_up_sync(0xFFFFFFFFu, D1, off);
-      if (lane >= (uint32_t)off) {
-        // prefix p, then this lane's function c from p's end state
-        const uint32_t cE0 = E0, cE1 = E1, cN0 = N0, cN1 = N1, cD0 = D0, cD1 = D1;
-        N0 = pN0 + (pE0 ? cN1 : cN0); D0 = pD0 + (pE0 ? cD1 : cD0); E0 = pE0 ? cE1 : cE0;
-        N1 = pN1 + (pE1 ? cN1 : cN0); D1 = pD1 + (pE1 ? cD1 : cD0); E1 = pE1 ? cE1 : cE0;
-      }
+    for (uint32_t d = 1; d < NW; d <<= 1) {
+      const Fn2 p = fn_shfl_up(vi, d);
+      if (lane >= d) vi = fn_then(p, vi);
     }
-    uint32_t xs = __shfl_up_sync(0xFFFFFFFFu, E0, 1), xn = __shfl_up_sync(0xFFFFFFFFu, N0, 1),
-             xd = __shfl_up_sync(0xFFFFFFFFu, D0, 1);
-    if (lane == 0) { xs = 0; xn = 0; xd = 0; }
-    for (uint32_t t = lane * PER; t < lane * PER + PER; ++t) {
-      const uint32_t te = sum[at(t)];
-      const uint32_t tn = xs ? sum[2 * SP + at(t)] : sum[SP + at(t)];
-      const uint32_t td = xs ? sum[4 * SP + at(t)] : sum[3 * SP + at(t)];
-      sum[5 * SP + at(t)] = xs;
-      sum[6 * SP + at(t)] = xn;
-      sum[7 * SP + at(t)] = xd;
-      xn += tn; xd += td; xs = (te >> xs) & 1u;
-    }
-    if (lane == 31) {
-      sum[8 * SP] = xn;
-      sum[8 * SP + 1] = xd;
-      if (xs != 0) set_err(s_err, VC_ERR_CORRUPT);  // the stream ends inside a delta entry chain
-    }
+    Fn2 ex = fn_shfl_up(vi, 1);
+    if (lane == 0) ex = Fn2{2u, 0u, 0u};
+    __syncwarp();
+    if (lane < NW) { scan_tmp[3 * lane] = ex.e; scan_tmp[3 * lane + 1] = ex.nd0; scan_tmp[3 * lane + 2] = ex.nd1; }
+    if (lane == NW - 1) { scan_tmp[3 * NW] = vi.e; scan_tmp[3 * NW + 1] = vi.nd0; }
   }
   __syncthreads();
-  parse_emit(sw, S, w0, w1, sum[5 * SP + at(tid)], sum[6 * SP + at(tid)], sum[7 * SP + at(tid)], nodes, nodes_words,
-             dlist, dcap, lut);
-  out.n_nodes = sum[8 * SP];
-  out.n_delta = sum[8 * SP + 1];
+  Fn2 pre = fn_shfl_up(inc, 1);
+  if (lane == 0) pre = Fn2{2u, 0u, 0u};
+  pre = fn_then(Fn2{scan_tmp[3 * warp], scan_tmp[3 * warp + 1], scan_tmp[3 * warp + 2]}, pre);
+  uint32_t st = pre.e & 1u;  // the stream starts in state 0
+  uint32_t j = pre.nd0 & 0xFFFFu, d = pre.nd0 >> 16;
+  const uint32_t total_e = scan_tmp[3 * NW] & 1u, total_nd = scan_tmp[3 * NW + 1];
+  // the node words this run shares with its neighbours start at zero
+  const uint32_t jend = j + ((st ? f.nd1 : f.nd0) & 0xFFFFu);
+  if ((j >> 3) < nodes_words) nodes[j >> 3] = 0u;
+  if ((jend >> 3) < nodes_words) nodes[jend >> 3] = 0u;
+  __syncthreads();
+  // 3. write this run's operation nibbles and delta positions
+  const uint32_t jstart = j;
+  uint64_t acc = 0;
+  for (uint32_t w = w0; w < w1; ++w) {
+    const uint32_t x = sw[w];
+    const uint32_t nv = min(8u, S - 8u * w);
+    uint32_t D, A, B, end;
+    word_states(x, D, A, B);
+    const uint32_t m = word_ops(A, B, st, nv, &end);
+    st = end;
+    const uint32_t cnt = __popc(m);
+    const uint32_t p = j & 7u;
+    acc |= (uint64_t)pack_nibbles(x, m) << (4u * p);
+    j += cnt;
+    if (p + cnt >= 8u) {  // node word (j - cnt) / 8 is complete
+      const uint32_t wi = (j - cnt) >> 3;
+      if (wi < nodes_words) {
+        if (wi == (jstart >> 3)) atomicOr(&nodes[wi], (uint32_t)acc);
+        else nodes[wi] = (uint32_t)acc;
+      }
+      acc >>= 32;
+    }
+    uint32_t dm = m & D;
+    while (dm) {
+      const uint32_t b = __ffs(dm) - 1u;
+      dm &= dm - 1u;
+      if (d < dcap) dlist[d] = 8u * w + b + 1u;  // first entry; resolved after the parse
+      ++d;
+    }
+  }
+  if ((j & 7u) && (j >> 3) < nodes_words) atomicOr(&nodes[j >> 3], (uint32_t)acc);
+  if (tid == 0 && total_e != 0) set_err(s_err, VC_ERR_CORRUPT);  // the stream ends inside a delta entry chain
+  ParseOut out;
+  out.n_nodes = total_nd & 0xFFFFu;
+  out.n_delta = total_nd >> 16;
   __syncthreads();
   return out;
 }
@@ -481,7 +398,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   uint32_t* misc = reinterpret_cast<uint32_t*>(sm + SL.misc_off);
   uint32_t* wtot = misc + 16;      // NW warp totals (words 16..47)
-  uint32_t* scan_tmp = misc + 48;  // 2 NW + 2 words (48..113)
+  uint32_t* scan_tmp = misc + 48;  // 3 NW + 3 words (48..255)
 
   const uint32_t n_pal = head[0], S = head[1], nd = head[3];
   const uint32_t ns = RANS ? (S < 32u ? S : 32u) : 0u;
@@ -509,9 +426,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   } else {
     uint32_t* nodes = reinterpret_cast<uint32_t*>(sm + SL.nodes_off);
     // the general parse path borrows the finest grid (not in use yet) for its summaries
-    const ParseOut po = parse_stream<NT>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap,
-                                         reinterpret_cast<const uint32_t*>(sm + SL.lut_off), scan_tmp,
-                                         reinterpret_cast<uint32_t*>(sm + SL.psum_off), s_err);
+    const ParseOut po = parse_stream<NT>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap, scan_tmp, s_err);
     c.nodes = nodes;
     c.n_nodes = po.n_nodes;
     if (po.n_delta != nd) set_err(s_err, VC_ERR_CORRUPT);
@@ -894,11 +809,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
-template <int NT>
-__device__ __forceinline__ void init_parse_lut(unsigned char* sm, const SmemLayout& SL) {
-  uint32_t* lut = reinterpret_cast<uint32_t*>(sm + SL.lut_off);
-  for (uint32_t i = threadIdx.x; i < 256u; i += NT) lut[i] = parse_entry(i);
-}
 
 // Where one request item's data lives: the record, and the bytes to stage in shared memory.
 struct ItemSrc {
@@ -941,7 +851,6 @@ __global__ void __launch_bounds__(NT) decode_grid_kernel(const __grid_constant__
     return;
   }
   if (threadIdx.x == 0) *s_err = 0;
-  init_parse_lut<NT>(sm, SL);
   const ItemSrc src = item_src<RANS>(P, item, brick);
   const uint32_t* head = src.rec;
   const uint32_t* sw = src.stream;
@@ -1009,7 +918,6 @@ __global__ void __launch_bounds__(NT) decode_batched_kernel(const __grid_constan
     mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
-  init_parse_lut<NT>(sm, SL);
   __syncthreads();
   // stage depth 2: the next item is claimed (and its copy started) while this one is decoded;
   // depth 1: claimed once this one is done

@@ -25,8 +25,7 @@ constexpr uint32_t kRing = 3u;            // pipelined schedule: workspace slots
 
 // Byte offsets of the reconstruction kernel's shared-memory regions (one brick per block).
 struct SmemLayout {
-  uint32_t misc_off;     // error flag, items, counters, mbarriers, warp totals, scan scratch
-  uint32_t lut_off;      // parse table: 2 states x 256 byte values (u16)
+  uint32_t misc_off;     // error flag, items, counters, mbarriers, warp totals, scan scratch (1 KiB)
   uint32_t stage_off;    // staged record (plain) or record head + decoded symbols (rANS)
   uint32_t stage_bytes;  // per buffer; 0 = read from global memory
   uint32_t nstage;       // 1 or 2 buffers (2 = prefetch the next brick in the batched kernel)
@@ -39,7 +38,6 @@ struct SmemLayout {
   uint32_t g_off;        // palette index per cell of levels 0..L-1 (gt_bytes each)
   uint32_t ns_off;       // per level, one byte per parent cell: which children have stop bit 0
   uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each)
-  uint32_t psum_off;     // summaries of the general parse path (aliases idle regions)
   uint32_t fg_stride;    // split schedule: bytes per item of the finest-grid workspace
   uint32_t list_off;     // stop-0 cells by rank (u16), two buffers: even / odd levels
   uint32_t list0_cap;    // entries of the even-level buffer
@@ -96,7 +94,7 @@ struct Volume {
   uint32_t prof_dropped;   // calls not recorded (ring full)
 };
 
-constexpr uint32_t kProfCalls = 256;
+constexpr uint32_t kProfCalls = 4096;
 
 // server.cpp: releases a vc_server (false if the handle is not one)
 bool release_server(void* handle);
