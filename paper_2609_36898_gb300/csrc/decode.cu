@@ -71,10 +71,7 @@ __device__ __forceinline__ bool rans_steps(const uint32_t* tab, const uint16_t* 
     const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
     const uint32_t r = ptr - wb + __popc(m & lt);  // < 63
     const uint32_t v0 = __shfl_sync(0xFFFFFFFFu, w0, r & 31u), v1 = __shfl_sync(0xFFFFFFFFu, w1, r & 31u);
-    if (need) {
-      bad |= ptr + __popc(m & lt) >= nw;
-      x = (x << 16) | (r < 32u ? v0 : v1);
-    }
+    if (need) x = (x << 16) | (r < 32u ? v0 : v1);  // words past the end read as 0; caught by ptr != nw
     ptr += __popc(m);
     if (ptr - wb >= 32u) {  // slide the window by one run of 32 words
       wb += 32u;
@@ -84,6 +81,7 @@ __device__ __forceinline__ bool rans_steps(const uint32_t* tab, const uint16_t* 
       w3 = ld(wb + 96u + lane);
     }
   };
+#pragma unroll 2
   for (uint32_t base = 0; base < full; base += 32u) {
     uint32_t s = 0;
     step(true, s);
@@ -173,12 +171,11 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   s.gt_bytes = v.max_pal < kMaxIdx8 ? 1u : 2u;
   const uint32_t b = 1u << L;
   const uint32_t ncells = ((1u << (3 * L)) - 1u) / 7u;  // levels 0..L-1
-  const uint32_t stream_words = (v.max_sym + 7u) / 8u;
   uint32_t o = 0;
   s.misc_off = o; o += 1024;
-  s.nwords = (v.max_sym + 31u) / 32u + 2u;
-  s.mask_off = o; o += align16(4 * 4 * s.nwords);
-  s.nodes_words = stream_words + 4u;
+  s.nwords = (v.max_nodes + 31u) / 32u + 2u;
+  s.mask_off = o; o += align16(12 * s.nwords);  // 2 u32 masks + 2 u16 prefixes per word
+  s.nodes_words = (v.max_nodes + 7u) / 8u + 4u;
   s.nodes_off = o; o += v.max_delta ? align16(4 * s.nodes_words) : 0u;
   s.dlist_cap = v.max_delta;
   s.dlist_off = o; o += align16(4 * (v.max_delta ? v.max_delta : 1u));
@@ -186,10 +183,13 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   // per level l >= 1 below L, one byte per level-(l-1) cell: its children's stop-0 bits
   const uint32_t ns_bytes = ((1u << (3 * (L - 1))) - 1u) / 7u;
   s.ns_off = o; o += align16(ns_bytes ? ns_bytes : 1u);
-  // the stop-0 cells of each level by rank, two buffers (even / odd levels)
+  // the stop-0 cells of each level by rank, two buffers (even / odd levels); a level's stop-0 cells
+  // have 8 emitted children each, so there are at most max_nodes / 8 of them
   uint32_t cap[2] = {1u, 1u};
-  for (uint32_t l = 0; l + 1 <= L; ++l) cap[l & 1u] = std::max(cap[l & 1u], 1u << (3 * l));
+  for (uint32_t l = 0; l + 1 <= L; ++l)
+    cap[l & 1u] = std::max(cap[l & 1u], std::min(1u << (3 * l), v.max_nodes / 8u + 1u));
   s.list0_cap = (cap[0] + 7u) & ~7u;
+  s.list1_cap = cap[1];
   s.list_off = o; o += align16(2u * (s.list0_cap + cap[1]));
   if (split) {
     // no finest grid here (it goes to a workspace)
@@ -197,7 +197,10 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
     s.pal_cap = 0;
     s.pal_off = o;
   } else {
-    s.fg_off = o; o += align16(s.gt_bytes * b * b * b);
+    // the finest index grid holds one z half at a time for b = 32 (plus the last plane of the first)
+    const uint32_t nh = L >= 5 ? 2u : 1u;
+    s.fg_off = o; o += align16(s.gt_bytes * b * b * b / nh);
+    s.plane_off = o; o += nh == 2 ? align16(s.gt_bytes * b * b) : 0u;
     // private palette copy (frees the stage early); 256 entries for byte grids
     s.pal_cap = s.gt_bytes == 1 ? 256u : (v.max_pal <= 1024u ? v.max_pal : 0u);
     s.pal_off = o; o += align16(4u * s.pal_cap);

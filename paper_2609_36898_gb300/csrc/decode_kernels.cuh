@@ -330,8 +330,8 @@ struct BrickCtx {
   uint32_t n_nodes;
   const uint32_t* adv_mask;
   const uint32_t* del_mask;
-  const uint32_t* adv_pre;
-  const uint32_t* del_pre;
+  const uint16_t* adv_pre;  // palette advances before node 32 w (< 2^16: n_pal < 65520)
+  const uint16_t* del_pre;  // delta operations before node 32 w (< 2^16 for b <= 32)
   const uint32_t* dlist;
   uint32_t dlist_cap;
   uint32_t op_mask;
@@ -438,8 +438,8 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   // 2. palette-cursor masks and prefix counts (32 nodes per word)
   uint32_t* adv_mask = reinterpret_cast<uint32_t*>(sm + SL.mask_off);
   uint32_t* del_mask = adv_mask + SL.nwords;
-  uint32_t* adv_pre = adv_mask + 2 * SL.nwords;
-  uint32_t* del_pre = adv_mask + 3 * SL.nwords;
+  uint16_t* adv_pre = reinterpret_cast<uint16_t*>(adv_mask + 2 * SL.nwords);
+  uint16_t* del_pre = adv_pre + SL.nwords;
   c.adv_mask = adv_mask; c.del_mask = del_mask; c.adv_pre = adv_pre; c.del_pre = del_pre;
   {
     const uint32_t nw32 = (c.n_nodes + 31u) >> 5;
@@ -463,7 +463,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     uint32_t pa, pd, ta, td;
     block_scan2<NT>(sa, sd, pa, pd, ta, td, scan_tmp);
     for (uint32_t w = a0; w < a1; ++w) {
-      adv_pre[w] = pa; del_pre[w] = pd;
+      adv_pre[w] = (uint16_t)pa; del_pre[w] = (uint16_t)pd;
       pa += __popc(adv_mask[w]); pd += __popc(del_mask[w]);
     }
     if (tid == 0 && (ta != n_pal || td != nd)) set_err(s_err, VC_ERR_CORRUPT);
@@ -622,14 +622,18 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
       if (w < warp) base += t;
       total += t;
     }
-    // list this level's stop-0 cells by rank; resolve the neighbour marks among the children
+    // list this level's stop-0 cells by rank (a corrupt stream may claim more than the buffer
+    // holds: flagged, and the list is cut); resolve the neighbour marks among the children
+    const uint32_t lcap = (l & 1u) ? SL.list1_cap : SL.list0_cap;
     for (uint32_t r = r0; r < r1; ++r) {
       const uint32_t p = list_prev[r];
       uint32_t open8 = NSl[p];
       while (open8) {
         const uint32_t o = __ffs(open8) - 1u;
         open8 &= open8 - 1u;
-        list_cur[base++] = (uint16_t)(8u * p + o);
+        if (base < lcap) list_cur[base] = (uint16_t)(8u * p + o);
+        else set_err(s_err, VC_ERR_CORRUPT);
+        ++base;
       }
 #pragma unroll
       for (uint32_t o = 0; o < 8; ++o) {
@@ -640,7 +644,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     }
     __syncthreads();
     off += 8u * npar;
-    npar = total;
+    npar = min(total, lcap);
     gofs_prev = gofs;
     gofs += 1u << (3u * l);
     nsofs_prev = nsofs;
@@ -649,104 +653,133 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
 
   if (finest) {
     // 4. finest level: constant blocks of stopped level-(L-1) cells, then the 8 operations of each
-    // stop-0 cell (from the rank list)
+    // stop-0 cell (from the rank list), the neighbour marks, the output. For b = 32 the index grid
+    // holds one z half at a time (levels are in Morton order, whose top bit is z's, so the first
+    // half of the level-(L-1) cells and of the rank list covers z < b / 2); the last plane of the
+    // first half is kept for the -z neighbours of the second.
     if (tid == 0 && off + 8u * npar != c.n_nodes) set_err(s_err, VC_ERR_CORRUPT);
     const GT* Gp = G + gofs_prev;
     constexpr uint32_t pcells = 1u << (3 * (L - 1));
-    constexpr uint32_t PC = (pcells + NT - 1) / NT;
-    const uint32_t ftid = flin<L>(tid & (NT - 1u) & (pcells - 1u));
-#pragma unroll
-    for (uint32_t k = 0; k < PC; ++k) {
-      const uint32_t p = tid + k * NT;  // with NT a power of two, p's bits are tid's plus k * NT's
-      if (p < pcells && !open_cell(L - 1u, p, nsofs_prev)) {
-        const uint32_t g = Gp[p];
-        const uint32_t f0 = pcells > NT ? ftid + flin<L>(k * NT) : flin<L>(p);
-        store_pair<GT>(fg, f0, g, g);
-        store_pair<GT>(fg, f0 + b, g, g);
-        store_pair<GT>(fg, f0 + b * b, g, g);
-        store_pair<GT>(fg, f0 + b * b + b, g, g);
-      }
-    }
+    constexpr uint32_t NH = (!SPLIT && L >= 5) ? 2u : 1u;  // z halves
+    constexpr uint32_t hcells = pcells / NH;                 // level-(L-1) cells per half
+    constexpr uint32_t hvox = b * b * b / NH;                // voxels per half
+    constexpr uint32_t PC = (hcells + NT - 1) / NT;
+    const uint32_t ftid = flin<L>(tid & (NT - 1u) & (hcells - 1u));
     const uint16_t* plist = lists[(L - 1u) & 1u];
-    for (uint32_t r = tid; r < npar; r += NT) {
-      const uint32_t p = plist[r];
-      uint32_t v[8];
-      decode8(off + 8u * r, Gp[p], compact3(p), compact3(p >> 1), compact3(p >> 2), true, v);
-      const uint32_t f0 = flin<L>(p);
-      store_pair<GT>(fg, f0, v[0], v[1]);
-      store_pair<GT>(fg, f0 + b, v[2], v[3]);
-      store_pair<GT>(fg, f0 + b * b, v[4], v[5]);
-      store_pair<GT>(fg, f0 + b * b + b, v[6], v[7]);
+    GT* plane = reinterpret_cast<GT*>(sm + SL.plane_off);  // z = b/2 - 1, resolved (NH == 2)
+    // ranks of the first half: open cells are listed in increasing Morton order
+    uint32_t rsplit = npar;
+    if (NH == 2) {
+      uint32_t lo = 0, hi = npar;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (plist[mid] < hcells) lo = mid + 1; else hi = mid;
+      }
+      rsplit = lo;
     }
-    __syncthreads();
-    // neighbour marks of the finest level, resolved per decoded block (at most three hops each), so
-    // that the output pass is a plain gather
-    for (uint32_t r = tid; r < npar; r += NT) {
-      const uint32_t f0 = flin<L>(plist[r]);
-      const uint32_t rows[4] = {f0, f0 + b, f0 + b * b, f0 + b * b + b};
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-#pragma unroll
-        for (uint32_t i = 0; i < 2; ++i) {
-          const uint32_t pos = rows[h] + i;
-          uint32_t g = fg[pos];
-          if (g >= MARK) {
-            uint32_t q = pos;
 #pragma unroll 1
-            for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
-              const uint32_t a = g - MARK;
-              q -= a == 0 ? 1u : (a == 1 ? b : b * b);
-              g = fg[q];
+    for (uint32_t h = 0; h < NH; ++h) {
+      const uint32_t rb = h ? rsplit : 0u, re = (h + 1 < NH) ? rsplit : npar;
+#pragma unroll
+      for (uint32_t k = 0; k < PC; ++k) {
+        const uint32_t pl = tid + k * NT;  // with NT a power of two, pl's bits are tid's plus k * NT's
+        const uint32_t p = h * hcells + pl;
+        if (pl < hcells && !open_cell(L - 1u, p, nsofs_prev)) {
+          const uint32_t g = Gp[p];
+          const uint32_t f0 = hcells > NT ? ftid + flin<L>(k * NT) : flin<L>(pl);
+          store_pair<GT>(fg, f0, g, g);
+          store_pair<GT>(fg, f0 + b, g, g);
+          store_pair<GT>(fg, f0 + b * b, g, g);
+          store_pair<GT>(fg, f0 + b * b + b, g, g);
+        }
+      }
+      for (uint32_t r = rb + tid; r < re; r += NT) {
+        const uint32_t p = plist[r];
+        uint32_t v[8];
+        decode8(off + 8u * r, Gp[p], compact3(p), compact3(p >> 1), compact3(p >> 2), true, v);
+        const uint32_t f0 = flin<L>(p) - h * hvox;
+        store_pair<GT>(fg, f0, v[0], v[1]);
+        store_pair<GT>(fg, f0 + b, v[2], v[3]);
+        store_pair<GT>(fg, f0 + b * b, v[4], v[5]);
+        store_pair<GT>(fg, f0 + b * b + b, v[6], v[7]);
+      }
+      __syncthreads();
+      // neighbour marks of this half, resolved per decoded block (at most three hops each; a -z
+      // hop out of the second half lands on the kept plane, whose values are final)
+      for (uint32_t r = rb + tid; r < re; r += NT) {
+        const uint32_t f0 = flin<L>(plist[r]) - h * hvox;
+        const uint32_t rows[4] = {f0, f0 + b, f0 + b * b, f0 + b * b + b};
+#pragma unroll
+        for (int hh = 0; hh < 4; ++hh) {
+#pragma unroll
+          for (uint32_t i = 0; i < 2; ++i) {
+            const uint32_t pos = rows[hh] + i;
+            uint32_t g = fg[pos];
+            if (g >= MARK) {
+              int32_t q = (int32_t)pos;
+#pragma unroll 1
+              for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
+                const uint32_t a = g - MARK;
+                q -= a == 0 ? 1 : (a == 1 ? (int32_t)b : (int32_t)(b * b));
+                g = q >= 0 ? (uint32_t)fg[q] : (NH == 2 ? (uint32_t)plane[q + (int32_t)(b * b)] : MARK + 3u);
+              }
+              if (g >= MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
+              fg[pos] = (GT)g;
             }
-            if (g >= MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
-            fg[pos] = (GT)g;
           }
         }
       }
-    }
-    __syncthreads();
-    if (SPLIT) {
-      on_stage_free();
-      return;
-    }
-    if (pal_copied) on_stage_free();
-    constexpr uint32_t quads = b * b * b / 4u;
-    // resolves the neighbour marks of voxel pos (at most three hops)
-    auto resolve_fg = [&](uint32_t pos, uint32_t g) -> uint32_t {
-#pragma unroll 1
-      for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
-        const uint32_t a = g - MARK;
-        pos -= a == 0 ? 1u : (a == 1 ? b : b * b);
-        g = fg[pos];
+      __syncthreads();
+      if (SPLIT) {
+        on_stage_free();
+        return;
       }
-      if (g >= MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
-      return g;
-    };
-    if constexpr (sizeof(GT) == 1) {
-      if (pal_copied) {
-        // byte grid and a 256-entry palette copy: every index is in bounds, marks are rare
-        const uint32_t* fg32 = reinterpret_cast<const uint32_t*>(fg);
+      if (pal_copied && h + 1 == NH) on_stage_free();
+      constexpr uint32_t quads = hvox / 4u;
+      uint32_t* outh = out + h * hvox;
+      // resolves the neighbour marks of voxel pos (at most three hops)
+      auto resolve_fg = [&](uint32_t pos, uint32_t g) -> uint32_t {
+        int32_t q = (int32_t)pos;
+#pragma unroll 1
+        for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
+          const uint32_t a = g - MARK;
+          q -= a == 0 ? 1 : (a == 1 ? (int32_t)b : (int32_t)(b * b));
+          g = q >= 0 ? (uint32_t)fg[q] : (NH == 2 ? (uint32_t)plane[q + (int32_t)(b * b)] : MARK + 3u);
+        }
+        if (g >= MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
+        return g;
+      };
+      if constexpr (sizeof(GT) == 1) {
+        if (pal_copied) {
+          // byte grid and a 256-entry palette copy: every index is in bounds, marks are resolved
+          const uint32_t* fg32 = reinterpret_cast<const uint32_t*>(fg);
 #pragma unroll 4
-        for (uint32_t q = tid; q < quads; q += NT) {
-          const uint32_t x = fg32[q];  // marks were resolved above
-          store16(out + 4u * q, c.pal[x & 0xFFu], c.pal[(x >> 8) & 0xFFu], c.pal[(x >> 16) & 0xFFu], c.pal[x >> 24]);
+          for (uint32_t q = tid; q < quads; q += NT) {
+            const uint32_t x = fg32[q];
+            store16(outh + 4u * q, c.pal[x & 0xFFu], c.pal[(x >> 8) & 0xFFu], c.pal[(x >> 16) & 0xFFu], c.pal[x >> 24]);
+          }
+        } else {
+          const uint32_t* fg32 = reinterpret_cast<const uint32_t*>(fg);
+          for (uint32_t q = tid; q < quads; q += NT) {
+            const uint32_t x = fg32[q];
+            uint32_t idx[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) idx[i] = resolve_fg(4u * q + (uint32_t)i, (x >> (8 * i)) & 0xFFu);
+            store16(outh + 4u * q, label_of(c, idx[0]), label_of(c, idx[1]), label_of(c, idx[2]), label_of(c, idx[3]));
+          }
         }
       } else {
-        const uint32_t* fg32 = reinterpret_cast<const uint32_t*>(fg);
         for (uint32_t q = tid; q < quads; q += NT) {
-          const uint32_t x = fg32[q];
-          uint32_t idx[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) idx[i] = resolve_fg(4u * q + (uint32_t)i, (x >> (8 * i)) & 0xFFu);
-          store16(out + 4u * q, label_of(c, idx[0]), label_of(c, idx[1]), label_of(c, idx[2]), label_of(c, idx[3]));
+          const uint2 x = reinterpret_cast<const uint2*>(fg)[q];
+          const uint32_t idx[4] = {resolve_fg(4u * q, x.x & 0xFFFFu), resolve_fg(4u * q + 1u, x.x >> 16),
+                                   resolve_fg(4u * q + 2u, x.y & 0xFFFFu), resolve_fg(4u * q + 3u, x.y >> 16)};
+          store16(outh + 4u * q, label_of(c, idx[0]), label_of(c, idx[1]), label_of(c, idx[2]), label_of(c, idx[3]));
         }
       }
-    } else {
-      for (uint32_t q = tid; q < quads; q += NT) {
-        const uint2 x = reinterpret_cast<const uint2*>(fg)[q];
-        const uint32_t idx[4] = {resolve_fg(4u * q, x.x & 0xFFFFu), resolve_fg(4u * q + 1u, x.x >> 16),
-                                 resolve_fg(4u * q + 2u, x.y & 0xFFFFu), resolve_fg(4u * q + 3u, x.y >> 16)};
-        store16(out + 4u * q, label_of(c, idx[0]), label_of(c, idx[1]), label_of(c, idx[2]), label_of(c, idx[3]));
+      if (h + 1 < NH) {
+        // keep the last plane of this half, then the grid takes the next half
+        for (uint32_t i = tid; i < b * b; i += NT) plane[i] = fg[hvox - b * b + i];
+        __syncthreads();
       }
     }
   } else {

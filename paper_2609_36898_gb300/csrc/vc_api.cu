@@ -138,7 +138,7 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   // Brick Starts and every record's sizes
   const uint8_t* st = p + kHeaderBytes;
   const uint8_t* rec = p + rec_off;
-  uint32_t max_pal = 0, max_sym = 0, max_delta = 0, max_words = 0, max_stage = 0;
+  uint32_t max_pal = 0, max_sym = 0, max_delta = 0, max_words = 0, max_stage = 0, max_nodes = 0;
   std::vector<uint8_t> bflags(n_bricks, 0);
   uint32_t prev = le32(st);
   if (prev != 0) return VC_ERR_FORMAT;
@@ -157,6 +157,7 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
     max_pal = std::max(max_pal, n_pal);
     max_sym = std::max(max_sym, S);
     max_delta = std::max(max_delta, nd);
+    max_nodes = std::max(max_nodes, S - nd);
     max_words = std::max(max_words, e - a);
     // bytes the reconstruction kernel stages: the record (plain), or its head and decoded symbols (rANS)
     const uint32_t stage = coder == 0 ? 4 * (e - a)
@@ -181,6 +182,7 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   v->L = L; v->op_mask = op_mask; v->coder = coder; v->flags = flags; v->n_bricks = n_bricks;
   v->max_pal = max_pal; v->max_sym = max_sym; v->max_delta = max_delta; v->max_rec_words = max_words;
   v->max_stage = max_stage;
+  v->max_nodes = max_nodes;
   v->encoded_bytes = nbytes;
   v->sched.threads = 256;
   v->sched.stage_depth = 1;

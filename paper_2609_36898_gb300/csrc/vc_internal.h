@@ -31,16 +31,18 @@ struct SmemLayout {
   uint32_t nstage;       // 1 or 2 buffers (2 = prefetch the next brick in the batched kernel)
   uint32_t nodes_off;    // node-indexed operation symbols, 8 per u32 (delta bricks only)
   uint32_t nodes_words;
-  uint32_t mask_off;     // adv_mask, del_mask, adv_pre, del_pre: 4 x nwords u32
+  uint32_t mask_off;     // adv_mask, del_mask (nwords u32 each), adv_pre, del_pre (nwords u16 each)
   uint32_t nwords;
   uint32_t dlist_off;    // delta values of the brick's delta operations
   uint32_t dlist_cap;
   uint32_t g_off;        // palette index per cell of levels 0..L-1 (gt_bytes each)
   uint32_t ns_off;       // per level, one byte per parent cell: which children have stop bit 0
-  uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each)
+  uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each; one z half for b = 32)
+  uint32_t plane_off;    // b = 32: the last z plane of the first half (for -z neighbours of the second)
   uint32_t fg_stride;    // split schedule: bytes per item of the finest-grid workspace
   uint32_t list_off;     // stop-0 cells by rank (u16), two buffers: even / odd levels
   uint32_t list0_cap;    // entries of the even-level buffer
+  uint32_t list1_cap;    // entries of the odd-level buffer
   uint32_t pal_off;      // private copy of the brick's palette
   uint32_t pal_cap;      // entries it can hold (0 = palettes are read from the stage)
   uint32_t gt_bytes;     // 1 (max_pal < 252) or 2
@@ -70,6 +72,7 @@ struct Volume {
   uint32_t dims[3];
   uint32_t L, op_mask, coder, flags, n_bricks, nb[3];
   uint32_t max_pal, max_sym, max_delta, max_rec_words, max_stage;
+  uint32_t max_nodes;    // max over bricks of S - n_delta (every delta operation has an entry): bounds nodes
   uint64_t encoded_bytes, device_bytes;
   vc_schedule sched;     // threads per block, staging depth, persistent blocks per SM, chunk
   SmemLayout sm_split;   // layout of the split reconstruction kernel (pipelined schedule)
