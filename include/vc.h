@@ -214,6 +214,9 @@ vc_status vc_decode_bricks_host(vc_volume* vol, const uint32_t* brick_ids, uint3
 
 typedef struct vc_server vc_server;
 
+#define VC_SERVER_GRAPHS 1u  /* launch each batch as one CUDA graph (captured once per batch slot and
+                                shape, then updated in place with the next batch's parameters) */
+
 typedef struct vc_server_config {
   uint64_t cache_bytes;      /* device cache size (rounded down to whole top-class blocks) */
   int32_t device;            /* CUDA device of the server and of every volume added to it */
@@ -221,7 +224,8 @@ typedef struct vc_server_config {
   uint32_t max_inflight;     /* batches on the GPU at once, 1..8 (0 = 2) */
   uint32_t min_class;        /* smallest block class (0 = 2, i.e. 256 bytes) */
   uint32_t max_class;        /* largest block class = log2 of the largest brick edge (0 = 6) */
-  uint32_t reserved[3];
+  uint32_t flags;            /* VC_SERVER_GRAPHS */
+  uint32_t reserved[2];
 } vc_server_config;
 
 typedef struct vc_request_info {
@@ -237,6 +241,8 @@ typedef struct vc_server_stats {
   uint64_t requests_submitted, requests_admitted, requests_done, requests_failed, requests_waiting;
   uint64_t bricks_hit, bricks_missed, bricks_decoded, batches, batches_inflight, batch_errors;
   uint64_t voxels_decoded;  /* sum of (b >> lod)^3 over decoded bricks */
+  uint64_t graph_launches, graph_instantiations;  /* VC_SERVER_GRAPHS: batches launched as graphs,
+                                                     graphs instantiated (the rest were updated) */
 } vc_server_stats;
 
 /* Creates a server (allocates the cache, batch buffers and streams; starts its thread).

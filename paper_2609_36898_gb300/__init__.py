@@ -68,7 +68,7 @@ class vc_kernel_stats(ctypes.Structure):
 class vc_server_config(ctypes.Structure):
     _fields_ = [("cache_bytes", ctypes.c_uint64), ("device", ctypes.c_int32), ("max_batch_items", ctypes.c_uint32),
                 ("max_inflight", ctypes.c_uint32), ("min_class", ctypes.c_uint32), ("max_class", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 3)]
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
 
 
 class vc_request_info(ctypes.Structure):
@@ -83,7 +83,7 @@ class vc_server_stats(ctypes.Structure):
         "cache_bytes", "cache_free_bytes", "cache_evictable_bytes", "cache_entries", "evictions",
         "requests_submitted", "requests_admitted", "requests_done", "requests_failed", "requests_waiting",
         "bricks_hit", "bricks_missed", "bricks_decoded", "batches", "batches_inflight", "batch_errors",
-        "voxels_decoded")]
+        "voxels_decoded", "graph_launches", "graph_instantiations")]
 
 
 class vc_brick_cache_stats(ctypes.Structure):
@@ -263,9 +263,12 @@ def vc_encode_volume(V: np.ndarray, log2b: int, op_mask: int = 0x7F, coder: int 
 
 # ---- serving
 
+VC_SERVER_GRAPHS = 1
+
+
 def vc_server_create(cache_bytes: int, device: int = 0, max_batch_items: int = 0, max_inflight: int = 0,
-                     min_class: int = 0, max_class: int = 0) -> ctypes.c_void_p:
-    cfg = vc_server_config(cache_bytes, device, max_batch_items, max_inflight, min_class, max_class)
+                     min_class: int = 0, max_class: int = 0, flags: int = 0) -> ctypes.c_void_p:
+    cfg = vc_server_config(cache_bytes, device, max_batch_items, max_inflight, min_class, max_class, flags)
     out = ctypes.c_void_p()
     _check(_lib_handle().vc_server_create(ctypes.byref(cfg), ctypes.byref(out)), "vc_server_create")
     return out

@@ -75,6 +75,11 @@ struct BatchSlot {
   cudaEvent_t done = nullptr;
   uint32_t *h_ids = nullptr, *h_slots = nullptr, *d_ids = nullptr, *d_slots = nullptr;
   int32_t *h_status = nullptr, *d_status = nullptr;
+  // CUDA-graph launches (VC_SERVER_GRAPHS): the rANS symbol workspace is the slot's own, so the
+  // captured work allocates nothing and a later batch of the same shape updates the graph in place
+  uint8_t* d_ws = nullptr;
+  size_t ws_cap = 0;
+  cudaGraphExec_t exec = nullptr;
 };
 
 struct Group {
@@ -144,6 +149,8 @@ void free_server(Server* s) {
     if (b.stream) cudaStreamSynchronize(b.stream);
     if (b.stream) cudaStreamDestroy(b.stream);
     if (b.done) cudaEventDestroy(b.done);
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+    cudaFree(b.d_ws);
     cudaFreeHost(b.h_ids);
     cudaFreeHost(b.h_slots);
     cudaFreeHost(b.h_status);
@@ -254,19 +261,67 @@ bool launch_batch(Server* s) {
   s->pos_launched += taken.size();
   batch.pos_end = s->pos_launched;
   const size_t ng = batch.groups.size();
-  bool ok = cudaMemcpyAsync(B.d_ids, B.h_ids, 4ull * at, cudaMemcpyHostToDevice, B.stream) == cudaSuccess &&
-            cudaMemcpyAsync(B.d_slots, B.h_slots, 4ull * at, cudaMemcpyHostToDevice, B.stream) == cudaSuccess &&
-            cudaMemsetAsync(B.d_status, 0, 4ull * VC_STATUS_WORDS * ng, B.stream) == cudaSuccess;
+  const bool graphs = (s->cfg.flags & VC_SERVER_GRAPHS) != 0;
+  // workspace offsets of the groups (graph launches only)
+  std::vector<size_t> ws_off(ng, 0);
+  bool ok = true;
+  if (graphs) {
+    size_t need = 0;
+    for (size_t g = 0; g < ng; ++g) {
+      ws_off[g] = need;
+      const Volume& v = *s->volumes[batch.groups[g].vol];
+      if (v.coder == 1) need += ((size_t)batch.groups[g].count * v.dv.sm.ws_stride + 255) & ~size_t(255);
+    }
+    if (need > B.ws_cap) {  // grow outside any capture
+      cudaStreamSynchronize(B.stream);
+      cudaFree(B.d_ws);
+      B.d_ws = nullptr;
+      B.ws_cap = 0;
+      if (cudaMalloc(reinterpret_cast<void**>(&B.d_ws), need) != cudaSuccess) {
+        cudaGetLastError();
+        ok = false;
+      } else {
+        B.ws_cap = need;
+      }
+    }
+    ok = ok && cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  }
+  ok = ok && cudaMemcpyAsync(B.d_ids, B.h_ids, 4ull * at, cudaMemcpyHostToDevice, B.stream) == cudaSuccess &&
+       cudaMemcpyAsync(B.d_slots, B.h_slots, 4ull * at, cudaMemcpyHostToDevice, B.stream) == cudaSuccess &&
+       cudaMemsetAsync(B.d_status, 0, 4ull * VC_STATUS_WORDS * ng, B.stream) == cudaSuccess;
   for (size_t g = 0; ok && g < ng; ++g) {
     const Group& G = batch.groups[g];
-    ok = launch_decode(*s->volumes[G.vol], B.d_ids + G.first, G.count, B.d_slots + G.first,
-                       reinterpret_cast<uint32_t*>(s->d_cache), G.lod, VC_MODE_BATCHED,
-                       B.d_status + VC_STATUS_WORDS * g, B.stream) == VC_OK;
+    Volume& v = *s->volumes[G.vol];
+    if (graphs && v.coder == 1)
+      ok = launch_decode_ws(v, B.d_ids + G.first, G.count, B.d_slots + G.first, reinterpret_cast<uint32_t*>(s->d_cache),
+                            G.lod, VC_MODE_BATCHED, B.d_status + VC_STATUS_WORDS * g, B.stream, B.d_ws + ws_off[g],
+                            B.ws_cap - ws_off[g]) == VC_OK;
+    else
+      ok = launch_decode(v, B.d_ids + G.first, G.count, B.d_slots + G.first, reinterpret_cast<uint32_t*>(s->d_cache),
+                         G.lod, VC_MODE_BATCHED, B.d_status + VC_STATUS_WORDS * g, B.stream) == VC_OK;
   }
   ok = ok &&
        cudaMemcpyAsync(B.h_status, B.d_status, 4ull * VC_STATUS_WORDS * ng, cudaMemcpyDeviceToHost, B.stream) ==
-           cudaSuccess &&
-       cudaEventRecord(B.done, B.stream) == cudaSuccess;
+           cudaSuccess;
+  if (graphs) {
+    cudaGraph_t graph = nullptr;
+    const bool captured = cudaStreamEndCapture(B.stream, &graph) == cudaSuccess && graph;
+    ok = ok && captured;
+    if (ok) {
+      cudaGraphExecUpdateResultInfo info;
+      if (!B.exec || cudaGraphExecUpdate(B.exec, graph, &info) != cudaSuccess) {
+        cudaGetLastError();
+        if (B.exec) cudaGraphExecDestroy(B.exec);
+        B.exec = nullptr;
+        ok = cudaGraphInstantiate(&B.exec, graph, 0) == cudaSuccess;
+        if (ok) ++s->stats.graph_instantiations;
+      }
+      ok = ok && cudaGraphLaunch(B.exec, B.stream) == cudaSuccess;
+      if (ok) ++s->stats.graph_launches;
+    }
+    if (graph) cudaGraphDestroy(graph);
+  }
+  ok = ok && cudaEventRecord(B.done, B.stream) == cudaSuccess;
   if (!ok) {
     s->fatal = VC_ERR_CUDA;
     return false;
@@ -388,7 +443,8 @@ vc_status vc_server_create(const vc_server_config* cfg, vc_server** out) {
   if (!c.max_inflight) c.max_inflight = 2;
   if (!c.max_class) c.max_class = 6;
   if (!c.min_class) c.min_class = 2;
-  if (c.min_class > c.max_class || c.max_class > 9 || c.max_inflight > 8 || c.cache_bytes < BrickCache::block_bytes(c.max_class))
+  if (c.min_class > c.max_class || c.max_class > 9 || c.max_inflight > 8 ||
+      c.cache_bytes < BrickCache::block_bytes(c.max_class) || (c.flags & ~VC_SERVER_GRAPHS))
     return VC_ERR_ARG;
   Server* s = new (std::nothrow) Server();
   if (!s) return VC_ERR_OOM;

@@ -236,3 +236,27 @@ def test_corrupt_brick_fails_its_request(volumes):
         vc.vc_request_release(srv, ok)
     finally:
         close_server(srv, vols)
+
+
+def test_graph_launched_batches_match_the_oracle(volumes):
+    """With VC_SERVER_GRAPHS every batch is one CUDA graph; batches of a repeated shape update the
+    graph in place. Results are the same bricks as without graphs."""
+    srv, vols = make_server(volumes, 64 * MiB, max_batch_items=32, flags=vc.VC_SERVER_GRAPHS)
+    try:
+        rng = np.random.default_rng(9)
+        for k in range(10):
+            vi = k % len(volumes)
+            V, enc, log2b = volumes[vi]
+            nb = oracle.header(enc)["n_bricks"]
+            bricks = rng.choice(nb, size=min(nb, 20), replace=False).astype(np.uint32)
+            lods = np.zeros(bricks.size, dtype=np.uint32)
+            rid, got = run_request(srv, vi, bricks, lods, log2b)
+            for g, b in zip(got[:5], bricks[:5]):
+                assert np.array_equal(g, expected(volumes, vi, b, 0))
+            vc.vc_request_release(srv, rid)
+        st = vc.vc_server_stats_get(srv)
+        assert st.graph_launches == st.batches and st.batches >= 10
+        assert st.graph_instantiations < st.graph_launches  # later batches updated an existing graph
+        assert st.requests_failed == 0
+    finally:
+        close_server(srv, vols)
