@@ -199,7 +199,9 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   } else {
     // the finest index grid holds one z half at a time for b = 32 (plus the last plane of the first)
     const uint32_t nh = L >= 5 ? 2u : 1u;
-    s.fg_off = o; o += align16(s.gt_bytes * b * b * b / nh);
+    s.fg_off = o;
+    s.fg_bytes = align16(s.gt_bytes * b * b * b / nh);
+    o += s.fg_bytes;
     s.plane_off = o; o += nh == 2 ? align16(s.gt_bytes * b * b) : 0u;
     // private palette copy (frees the stage early); 256 entries for byte grids
     s.pal_cap = s.gt_bytes == 1 ? 256u : (v.max_pal <= 1024u ? v.max_pal : 0u);

@@ -223,10 +223,12 @@ __device__ __forceinline__ Fn2 fn_shfl_up(const Fn2& f, uint32_t d) {
 // operation) from the symbol stream. Each thread takes a contiguous run of stream words: it
 // summarises the run for both entering states, a block-wide scan of the summaries gives every run
 // its entering state and its node and delta bases, and the runs then write their operation
-// nibbles. scan_tmp: 3 (NT / 32) + 3 words. Node counts must stay below 2^16 (b <= 32).
+// nibbles. scan_tmp: 3 (NT / 32) + 3 words. wst (may be NULL): one word per stream word, where the
+// first pass leaves each word's automaton masks for the second. Node counts must stay below 2^16
+// (b <= 32).
 template <int NT>
 __device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes, uint32_t nodes_words,
-                                 uint32_t* dlist, uint32_t dcap, uint32_t* scan_tmp, int* s_err) {
+                                 uint32_t* dlist, uint32_t dcap, uint32_t* scan_tmp, uint32_t* wst, int* s_err) {
   constexpr uint32_t NW = NT / 32;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t T = (S + 7u) >> 3;  // stream words
@@ -241,6 +243,7 @@ __device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes
       const uint32_t nv = min(8u, S - 8u * w);
       uint32_t D, A, B, e0, e1;
       word_states(x, D, A, B);
+      if (wst) wst[w] = D | (A << 8) | (B << 16);
       const uint32_t m0 = word_ops(A, B, s0, nv, &e0), m1 = word_ops(A, B, s1, nv, &e1);
       f.nd0 += __popc(m0) | (__popc(m0 & D) << 16);
       f.nd1 += __popc(m1) | (__popc(m1 & D) << 16);
@@ -291,7 +294,14 @@ __device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes
     const uint32_t x = sw[w];
     const uint32_t nv = min(8u, S - 8u * w);
     uint32_t D, A, B, end;
-    word_states(x, D, A, B);
+    if (wst) {
+      const uint32_t v = wst[w];
+      D = v & 0xFFu;
+      A = (v >> 8) & 0xFFu;
+      B = v >> 16;
+    } else {
+      word_states(x, D, A, B);
+    }
     const uint32_t m = word_ops(A, B, st, nv, &end);
     st = end;
     const uint32_t cnt = __popc(m);
@@ -426,7 +436,9 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   } else {
     uint32_t* nodes = reinterpret_cast<uint32_t*>(sm + SL.nodes_off);
     // the general parse path borrows the finest grid (not in use yet) for its summaries
-    const ParseOut po = parse_stream<NT>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap, scan_tmp, s_err);
+    // the finest grid is idle during the parse: it keeps the per-word automaton masks
+    uint32_t* wst = (!SPLIT && ((S + 7u) >> 3) * 4u <= SL.fg_bytes) ? reinterpret_cast<uint32_t*>(sm + SL.fg_off) : nullptr;
+    const ParseOut po = parse_stream<NT>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap, scan_tmp, wst, s_err);
     c.nodes = nodes;
     c.n_nodes = po.n_nodes;
     if (po.n_delta != nd) set_err(s_err, VC_ERR_CORRUPT);
@@ -635,12 +647,12 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
         else set_err(s_err, VC_ERR_CORRUPT);
         ++base;
       }
-#pragma unroll
-      for (uint32_t o = 0; o < 8; ++o) {
-        const uint32_t m = 8u * p + o;
-        const uint32_t g = Gl[m];
-        if (g >= MARK) Gl[m] = (GT)resolve_morton<GT>(Gl, m, g, s_err);
-      }
+    }
+    // one child per thread: the chains are short, dependent loads, so spread them out
+    for (uint32_t cc = tid; cc < 8u * npar; cc += NT) {
+      const uint32_t m = 8u * list_prev[cc >> 3] + (cc & 7u);
+      const uint32_t g = Gl[m];
+      if (g >= MARK) Gl[m] = (GT)resolve_morton<GT>(Gl, m, g, s_err);
     }
     __syncthreads();
     off += 8u * npar;
@@ -706,26 +718,25 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
       __syncthreads();
       // neighbour marks of this half, resolved per decoded block (at most three hops each; a -z
       // hop out of the second half lands on the kept plane, whose values are final)
-      for (uint32_t r = rb + tid; r < re; r += NT) {
-        const uint32_t f0 = flin<L>(plist[r]) - h * hvox;
-        const uint32_t rows[4] = {f0, f0 + b, f0 + b * b, f0 + b * b + b};
+      // (one row of 2 voxels per thread, 4 threads per block: the chains are short, dependent
+      // loads, so spread them out)
+      for (uint32_t cc = tid; cc < 4u * (re - rb); cc += NT) {
+        const uint32_t row = cc & 3u;
+        const uint32_t pos0 = flin<L>(plist[rb + (cc >> 2)]) - h * hvox + (row & 1u) * b + (row >> 1) * (b * b);
 #pragma unroll
-        for (int hh = 0; hh < 4; ++hh) {
-#pragma unroll
-          for (uint32_t i = 0; i < 2; ++i) {
-            const uint32_t pos = rows[hh] + i;
-            uint32_t g = fg[pos];
-            if (g >= MARK) {
-              int32_t q = (int32_t)pos;
+        for (uint32_t i = 0; i < 2; ++i) {
+          const uint32_t pos = pos0 + i;
+          uint32_t g = fg[pos];
+          if (g >= MARK) {
+            int32_t q = (int32_t)pos;
 #pragma unroll 1
-              for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
-                const uint32_t a = g - MARK;
-                q -= a == 0 ? 1 : (a == 1 ? (int32_t)b : (int32_t)(b * b));
-                g = q >= 0 ? (uint32_t)fg[q] : (NH == 2 ? (uint32_t)plane[q + (int32_t)(b * b)] : MARK + 3u);
-              }
-              if (g >= MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
-              fg[pos] = (GT)g;
+            for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
+              const uint32_t a = g - MARK;
+              q -= a == 0 ? 1 : (a == 1 ? (int32_t)b : (int32_t)(b * b));
+              g = q >= 0 ? (uint32_t)fg[q] : (NH == 2 ? (uint32_t)plane[q + (int32_t)(b * b)] : MARK + 3u);
             }
+            if (g >= MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
+            fg[pos] = (GT)g;
           }
         }
       }

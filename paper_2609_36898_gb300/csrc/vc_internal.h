@@ -39,6 +39,7 @@ struct SmemLayout {
   uint32_t ns_off;       // per level, one byte per parent cell: which children have stop bit 0
   uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each; one z half for b = 32)
   uint32_t plane_off;    // b = 32: the last z plane of the first half (for -z neighbours of the second)
+  uint32_t fg_bytes;     // bytes of the finest grid region (0 in the split schedule)
   uint32_t fg_stride;    // split schedule: bytes per item of the finest-grid workspace
   uint32_t list_off;     // stop-0 cells by rank (u16), two buffers: even / odd levels
   uint32_t list0_cap;    // entries of the even-level buffer
