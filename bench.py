@@ -423,6 +423,31 @@ def run_ours(args):
             tot += ev0.elapsed_time(ev1)
         modes[mname] = nsub * e ** 3 * reps / (tot / 1000.0) / 1e9
 
+    # cache paletting (packed palette indices instead of u32 labels), same bricks, batched schedule
+    pw, pbits, pper = vc.vc_volume_slot_words(vol.handle, 0, True)
+    pcache = torch.empty(n * pw, dtype=torch.int32, device=dev)
+    pm = vc.MODES[args.mode] | vc.VC_MODE_PALETTED
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    vc.vc_decode_bricks(vol.handle, ids.data_ptr(), n, ids.data_ptr(), pcache.data_ptr(), 0, pm, status.data_ptr(),
+                        stream.cuda_stream)
+    ptot = 0.0
+    for _ in range(5):
+        flush.fill_(5)
+        ev0.record(stream)
+        vc.vc_decode_bricks(vol.handle, ids.data_ptr(), n, ids.data_ptr(), pcache.data_ptr(), 0, pm,
+                            status.data_ptr(), stream.cuda_stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ptot += ev0.elapsed_time(ev1)
+    p_s = ptot / 5 / 1000.0
+    p_algo = algo - 4 * n * e ** 3 + 4 * n * pw
+    paletted = {"gvoxel_s": vox_per_step / p_s / 1e9, "bits_per_index": pbits, "indices_per_word": pper,
+                "bytes_per_voxel_written": 4.0 * pw / e ** 3, "step_ms": 1000 * p_s,
+                "algorithmic_bytes_per_step": p_algo, "step_frac_of_peak": p_algo / p_s / 1e9 / peak}
+    del pcache
+    if int(status[0]) != 0:
+        raise RuntimeError(f"paletted decode status {status.tolist()}")
+
     # end to end through the host entry point: ids host->device, decode, labels device->host (pinned)
     ids_h = torch.arange(n, dtype=torch.int32).numpy().view(np.uint32)
     labels_h = torch.empty(n * e ** 3, dtype=torch.int32, pin_memory=True)
@@ -472,6 +497,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "schedules_gvoxel_s": modes,
+            "paletted": paletted,
             "serving": serving,
             "wall_s_timed_region": wall,
             "prep_s": {"generate": t_gen, "encode": t_enc},

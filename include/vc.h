@@ -106,6 +106,10 @@ typedef int32_t vc_status;
                                rANS symbols, reconstruction (finest index grids to a workspace), and
                                output expansion; the caller's stream waits for all of them */
 
+#define VC_MODE_PALETTED 0x100 /* OR'ed into a mode: cache paletting (Methods, "Cache paletting"): each
+                                  slot holds packed palette indices instead of u32 labels, see
+                                  vc_volume_slot_words; not with VC_MODE_PIPELINED */
+
 typedef struct vc_volume vc_volume;
 
 typedef struct vc_volume_info {
@@ -163,15 +167,25 @@ vc_status vc_volume_autotune(vc_volume* vol, const uint32_t* brick_ids, uint32_t
                              uint32_t* cache, uint32_t lod, int32_t* status_dev, void* cuda_stream, uint32_t reps,
                              vc_schedule* best, uint32_t* best_mode, float* best_ms);
 
+/* Size of one cache slot at level of detail lod: *words u32 words. Labels: (b >> lod)^3 words
+ * (*bits = 32, *per_word = 1). Paletted (paletted != 0): I = ceil(log2 max_pal) bits per voxel
+ * (at least 1), E = floor(32 / I) indices per word, none straddling a word; voxel v (x fastest)
+ * is bits [I (v mod E), I (v mod E) + I) of word v / E; its label is the brick's palette entry
+ * at that index (the palette stays in the encoding). Host only. */
+vc_status vc_volume_slot_words(const vc_volume* vol, uint32_t lod, uint32_t paletted, uint32_t* words,
+                               uint32_t* bits, uint32_t* per_word);
+
 /* Decodes n bricks on `cuda_stream` (the Decompress stage: all requested bricks in parallel,
  * Results "GPU-based rendering pipeline"; Methods "GPU rendering pipeline").
  *   brick_ids   device, n x u32: brick ids (< n_bricks); duplicates allowed
  *   cache_slots device, n x u32: destination slot of each brick
- *   cache       device, u32 labels; brick i is written to cache + cache_slots[i] * (b >> lod)^3 as
- *               (b >> lod)^3 labels, x fastest; must be 16-byte aligned; caller-owned
+ *   cache       device, u32 words; brick i is written to cache + cache_slots[i] * W as W words, W =
+ *               (b >> lod)^3 labels x fastest, or with VC_MODE_PALETTED the packed indices of
+ *               vc_volume_slot_words; must be 16-byte aligned; caller-owned
  *   lod         level of detail: 0 = finest (b^3 labels), k = level L - k of the brick's hierarchy
  *               (each node the mode of its 2^3 children); 0 <= lod <= L
  *   mode        VC_MODE_PLAIN, VC_MODE_GRID, VC_MODE_BATCHED or VC_MODE_PIPELINED (same output,
+ *               optionally | VC_MODE_PALETTED except with the pipelined schedule;
  *               different schedule); the pipelined schedule uses the volume's own streams, so calls
  *               on one volume must not be enqueued from several host threads at once
  *   status_dev  device, VC_STATUS_WORDS int32 (see Conventions); the caller zeroes words 0..1 before

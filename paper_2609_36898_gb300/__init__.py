@@ -25,6 +25,7 @@ VC_ERR_BUSY = -7
 VC_ERR_UNSUPPORTED = -8
 VC_STATUS_WORDS = 4
 VC_MODE_PLAIN, VC_MODE_GRID, VC_MODE_BATCHED, VC_MODE_PIPELINED = 0, 1, 2, 3
+VC_MODE_PALETTED = 0x100
 MODES = {"plain": VC_MODE_PLAIN, "grid": VC_MODE_GRID, "batched": VC_MODE_BATCHED, "pipelined": VC_MODE_PIPELINED}
 
 
@@ -139,6 +140,8 @@ def _lib_handle():
         lib.vc_volume_autotune.argtypes = [P, P, U32, P, P, U32, P, P, U32, ctypes.POINTER(vc_schedule),
                                            ctypes.POINTER(U32), ctypes.POINTER(ctypes.c_float)]
         lib.vc_volume_autotune.restype = I32
+        lib.vc_volume_slot_words.argtypes = [P, U32, U32, ctypes.POINTER(U32), ctypes.POINTER(U32), ctypes.POINTER(U32)]
+        lib.vc_volume_slot_words.restype = I32
         lib.vc_camera_bricks.argtypes = [P, P, U32, U32, U32, P, P, P, P]
         lib.vc_request_bricks.argtypes = [P, U32, P, U32, U32, P]
         lib.vc_camera_bricks.restype = I32
@@ -202,6 +205,14 @@ def vc_decode_bricks(vol, brick_ids_ptr: int, n: int, cache_slots_ptr: int, cach
     _check(_lib_handle().vc_decode_bricks(vol, ctypes.c_void_p(brick_ids_ptr), n, ctypes.c_void_p(cache_slots_ptr),
                                           ctypes.c_void_p(cache_ptr), lod, mode, ctypes.c_void_p(status_ptr),
                                           ctypes.c_void_p(stream)), "vc_decode_bricks")
+
+
+def vc_volume_slot_words(vol, lod: int = 0, paletted: bool = False):
+    """(words per slot, bits per index, indices per word)."""
+    w, b, e = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(_lib_handle().vc_volume_slot_words(vol, lod, int(bool(paletted)), ctypes.byref(w), ctypes.byref(b),
+                                              ctypes.byref(e)), "vc_volume_slot_words")
+    return w.value, b.value, e.value
 
 
 def vc_volume_autotune(vol, brick_ids_ptr: int, n: int, cache_slots_ptr: int, cache_ptr: int, lod: int,

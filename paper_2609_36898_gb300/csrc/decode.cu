@@ -154,6 +154,13 @@ uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
 }  // namespace
 
+void palette_packing(uint32_t max_pal, uint32_t* bits, uint32_t* per_word) {
+  uint32_t I = 1;
+  while ((1u << I) < max_pal) ++I;  // ceil(log2 max_pal), at least 1
+  *bits = I;
+  *per_word = 32u / I;
+}
+
 bool schedule_supported(uint32_t L, uint32_t threads) {
   if (L < 1 || L > 5) return false;
   if (threads == 256) return true;
@@ -331,6 +338,15 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   P.ws = nullptr;
   P.fgws = nullptr;
   P.ws_item0 = 0;
+  const uint32_t edge = (1u << v.L) >> lod;
+  P.out_words = edge * edge * edge;
+  P.pal_bits = P.pal_per = 0;
+  if (mode & VC_MODE_PALETTED) {
+    mode &= ~VC_MODE_PALETTED;
+    if (mode == VC_MODE_PIPELINED) return VC_ERR_UNSUPPORTED;
+    palette_packing(v.max_pal, &P.pal_bits, &P.pal_per);
+    P.out_words = (edge * edge * edge + P.pal_per - 1u) / P.pal_per;
+  }
   // coarse levels of detail are written by the reconstruction kernel itself
   if (mode == VC_MODE_PIPELINED && lod == 0) {
     if (ws_ext) return VC_ERR_ARG;  // the pipelined schedule allocates its own workspaces

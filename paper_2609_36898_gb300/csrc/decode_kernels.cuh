@@ -26,6 +26,9 @@ struct Params {
   const uint8_t* ws;  // decoded rANS symbols, ws_stride bytes per item (nullptr for plain volumes)
   uint8_t* fgws;      // split schedule: finest index grids, fg_stride bytes per item
   uint32_t ws_item0;  // the workspaces hold items ws_item0 .. (a chunk of the request)
+  uint32_t out_words; // u32 words per cache slot
+  uint32_t pal_bits;  // 0: labels; else cache paletting: pal_bits-bit palette indices,
+  uint32_t pal_per;   //   pal_per of them per u32 word (none straddles a word)
 };
 
 template <typename GT>
@@ -760,7 +763,37 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
         if (g >= MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
         return g;
       };
-      if constexpr (sizeof(GT) == 1) {
+      if (P.pal_bits) {
+        // cache paletting (Methods, "Cache paletting"): pal_per indices of pal_bits bits in each
+        // u32 word, voxels in x-fastest order. A word that straddles the two halves is written
+        // with the second, which reads the first half's last voxels from the kept plane.
+        const uint32_t E = P.pal_per, I = P.pal_bits;
+        const uint32_t wlo = h ? hvox / E : 0u;
+        const uint32_t whi = h + 1 < NH ? hvox / E : (b * b * b + E - 1u) / E;
+        for (uint32_t w = wlo + tid; w < whi; w += NT) {
+          const uint32_t v0 = w * E;
+          uint32_t word = 0;
+          if (sizeof(GT) == 1 && E <= 8u && v0 >= h * hvox && v0 + 8u <= (h + 1u) * hvox) {
+            // byte grid, 8 indices at hand from two or three aligned words
+            const uint32_t lv = v0 - h * hvox;
+            const uint32_t* g32 = reinterpret_cast<const uint32_t*>(fg) + (lv >> 2);
+            const uint32_t sh = (lv & 3u) * 8u;
+            const uint32_t lo = __funnelshift_r(g32[0], g32[1], sh);
+            const uint32_t hi = sh ? __funnelshift_r(g32[1], g32[2], sh) : g32[1];
+#pragma unroll
+            for (uint32_t i = 0; i < 8; ++i)
+              if (i < E) word |= (((i < 4 ? lo : hi) >> (8u * (i & 3u))) & 0xFFu) << (I * i);
+          } else {
+            for (uint32_t i = 0; i < E; ++i) {
+              const uint32_t v = v0 + i;
+              if (v >= b * b * b) break;
+              const uint32_t g = v >= h * hvox ? (uint32_t)fg[v - h * hvox] : (uint32_t)plane[v + b * b - hvox];
+              word |= g << (I * i);
+            }
+          }
+          out[w] = word;
+        }
+      } else if constexpr (sizeof(GT) == 1) {
         if (pal_copied) {
           // byte grid and a 256-entry palette copy: every index is in bounds, marks are resolved
           const uint32_t* fg32 = reinterpret_cast<const uint32_t*>(fg);
@@ -798,7 +831,18 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     const GT* Gl = G + gofs_prev;
     const uint32_t n = 1u << Lout;
     const uint32_t total = n * n * n;
-    if (total >= 4u) {
+    auto cell = [&](uint32_t t) -> uint32_t {
+      const uint32_t x = t & (n - 1u), y = (t >> Lout) & (n - 1u), z = t >> (2 * Lout);
+      return Gl[spread3(x) | (spread3(y) << 1) | (spread3(z) << 2)];
+    };
+    if (P.pal_bits) {  // cache paletting, as at the finest level
+      const uint32_t E = P.pal_per, I = P.pal_bits;
+      for (uint32_t w = tid; w * E < total; w += NT) {
+        uint32_t word = 0;
+        for (uint32_t i = 0; i < E && w * E + i < total; ++i) word |= cell(w * E + i) << (I * i);
+        out[w] = word;
+      }
+    } else if (total >= 4u) {
       for (uint32_t q = tid; q < total / 4u; q += NT) {
         const uint32_t li = q << 2;
         uint32_t v[4];
@@ -912,7 +956,7 @@ __global__ void __launch_bounds__(NT) decode_grid_kernel(const __grid_constant__
   }
   __syncthreads();
   const uint32_t edge = (1u << L) >> P.lod;
-  uint32_t* out = P.cache + (size_t)P.slots[item] * edge * edge * edge;
+  uint32_t* out = P.cache + (size_t)P.slots[item] * P.out_words;
   GT* fgg = SPLIT ? reinterpret_cast<GT*>(P.fgws + (size_t)(item - P.ws_item0) * SL.fg_stride) : nullptr;
   decode_brick<L, GT, RANS, NT, SPLIT>(P, head, sw, out, sm, s_err, [] {}, fgg);
   __syncthreads();
@@ -1000,7 +1044,7 @@ __global__ void __launch_bounds__(NT) decode_batched_kernel(const __grid_constan
                                    : (RANS ? reinterpret_cast<const uint32_t*>(stage[buf] + src.head_bytes)
                                            : head + 4u + head[0]);
       const uint32_t edge = (1u << L) >> P.lod;
-      uint32_t* out = P.cache + (size_t)P.slots[item] * edge * edge * edge;
+      uint32_t* out = P.cache + (size_t)P.slots[item] * P.out_words;
       // depth 1: the next item's copy starts as soon as this brick's stage is free
       GT* fgg = SPLIT ? reinterpret_cast<GT*>(P.fgws + (size_t)(item - P.ws_item0) * SL.fg_stride) : nullptr;
       decode_brick<L, GT, RANS, NT, SPLIT>(P, head, sw, out, sm, s_err, [&] {

@@ -59,7 +59,8 @@ extern "C" vc_status vc_decode_bricks_noalloc(vc_volume* vol, const uint32_t* br
   if (!v || v->kind != vc::kHandleVolume) return VC_ERR_ARG;
   if (n == 0) return VC_OK;
   if (!brick_ids || !cache_slots || !cache || !status_dev) return VC_ERR_ARG;
-  if (lod > v->L || (mode != VC_MODE_GRID && mode != VC_MODE_BATCHED)) return VC_ERR_ARG;
+  const uint32_t base_mode = mode & ~VC_MODE_PALETTED;
+  if (lod > v->L || (base_mode != VC_MODE_GRID && base_mode != VC_MODE_BATCHED)) return VC_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(cache) & 15u) return VC_ERR_ARG;
   if (v->coder == 1 && (size_t)n * v->dv.sm.ws_stride > kNoAllocWsBytes) return VC_ERR_ARG;
   DeviceGuard g(v->device);

@@ -292,7 +292,7 @@ vc_status vc_decode_bricks(vc_volume* vol, const uint32_t* brick_ids, uint32_t n
   if (!v || v->kind != kHandleVolume) return VC_ERR_ARG;
   if (n == 0) return VC_OK;
   if (!brick_ids || !cache_slots || !cache || !status_dev) return VC_ERR_ARG;
-  if (lod > v->L || mode > VC_MODE_PIPELINED) return VC_ERR_ARG;
+  if (lod > v->L || (mode & ~VC_MODE_PALETTED) > VC_MODE_PIPELINED) return VC_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(cache) & 15u) return VC_ERR_ARG;
   DeviceGuard g(v->device);
   return launch_decode(*v, brick_ids, n, cache_slots, cache, lod, mode, status_dev,
@@ -348,6 +348,19 @@ vc_status vc_decode_bricks_host(vc_volume* vol, const uint32_t* brick_ids, uint3
   if (cudaMemcpyAsync(&st, v->d_host_status, 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess) return VC_ERR_CUDA;
   if (cudaStreamSynchronize(stream) != cudaSuccess) return VC_ERR_CUDA;
   *status_out = st;
+  return VC_OK;
+}
+
+vc_status vc_volume_slot_words(const vc_volume* vol, uint32_t lod, uint32_t paletted, uint32_t* words,
+                               uint32_t* bits, uint32_t* per_word) {
+  const Volume* v = reinterpret_cast<const Volume*>(vol);
+  if (!v || v->kind != kHandleVolume || !words || lod > v->L) return VC_ERR_ARG;
+  const uint32_t edge = (1u << v->L) >> lod;
+  uint32_t I = 32, E = 1;
+  if (paletted) palette_packing(v->max_pal, &I, &E);
+  *words = (edge * edge * edge + E - 1u) / E;
+  if (bits) *bits = I;
+  if (per_word) *per_word = E;
   return VC_OK;
 }
 

@@ -113,6 +113,8 @@ vc_status launch_camera_requests(const Volume& v, const vc_camera* cams, uint32_
                                  uint32_t* d_ids, uint32_t* d_lods, cudaStream_t stream);
 
 // decode.cu
+// cache paletting: bits per palette index (ceil(log2 max_pal), >= 1) and indices per u32 word
+void palette_packing(uint32_t max_pal, uint32_t* bits, uint32_t* per_word);
 bool schedule_supported(uint32_t L, uint32_t threads);
 vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, bool split,
                          SmemLayout* out);
