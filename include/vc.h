@@ -102,9 +102,10 @@ typedef int32_t vc_status;
 #define VC_MODE_GRID 1    /* one launch, one thread block per brick */
 #define VC_MODE_BATCHED 2 /* one persistent launch: thread blocks pull bricks from a work counter and
                              prefetch the next brick's record with a bulk copy while decoding */
-#define VC_MODE_PIPELINED 3 /* chunks of bricks flow through three kernels on three library streams:
-                               rANS symbols, reconstruction (finest index grids to a workspace), and
-                               output expansion; the caller's stream waits for all of them */
+#define VC_MODE_PIPELINED 3 /* chunks of bricks (vc_schedule.chunk) flow through the rANS symbol kernel
+                               and the reconstruction kernel on two library streams, so that one
+                               chunk's symbols decode while the previous chunk is reconstructed;
+                               the caller's stream waits for both (plain volumes: one launch) */
 
 #define VC_MODE_PALETTED 0x100 /* OR'ed into a mode: cache paletting (Methods, "Cache paletting"): each
                                   slot holds packed palette indices instead of u32 labels, see

@@ -13,33 +13,36 @@
 //  B. reconstruct kernels: one thread block per brick (grid) or persistent blocks pulling bricks
 //     from a work counter with a bulk-copy prefetch of the next brick's record (batched):
 //       1. parse: the symbol stream alternates between operations and the delta entries that
-//          follow a delta operation (Methods, "Compressed segmentation volumes"). Threads
-//          summarise byte-sized chunks with a 2-state table for both start states, a warp scan
-//          composes the summaries, and a second pass writes the node-indexed operations (8 per
-//          u32) and the delta values. Bricks without delta operations skip this: their symbols
-//          are the node operations.
+//          follow a delta operation (Methods, "Compressed segmentation volumes"), a 2-state
+//          automaton. Per 32-bit word of 8 symbols, SWAR prefix doubling on 8-bit masks gives the
+//          state after every symbol for both entering states at once; each thread summarises a
+//          run of words, a block scan composes the runs, and a second pass writes the operations
+//          (8 per u32, node-indexed) and the delta positions. Bricks without delta operations
+//          skip this: their symbols are the node operations.
 //       2. palette cursor: per 32 nodes, SWAR masks of advance / delta operations and exclusive
 //          prefix counts, so that any node's cursor k_j is one popc away (Supplementary Fig.
 //          "CSGV ablation" caption: advance reads the next entry, last re-reads it, delta re-reads
 //          the entry delta back).
-//       3. coarse levels 0..L-1: a dense Morton-indexed grid per level of palette indices G and of
-//          ranks R among the level's stop-0 nodes (level l+1 emits the 8 children of each, in rank
-//          order; Results, "CSGV results"). Neighbour copies are written as marks and resolved by
-//          walking at most three hops (each hop turns an even coordinate odd, and a copy needs an
-//          even one), so no extra rounds or barriers are needed.
-//       4. finest level: one pass over the level-(L-1) cells writes each 2^3 block of the
-//          finest grid (a byte or u16 palette index per voxel): constant blocks in four stores,
-//          emitted blocks from their 8 operations at once. A second pass reads four voxels,
-//          resolves any neighbour marks, maps indices to labels and writes 16 bytes per thread.
+//       3. coarse levels 1..L-1, parent-major: the stop-0 cells of a level are listed by rank, and
+//          rank r's 8 children are the nodes at offset + 8 r (Results, "CSGV results"). Each
+//          thread decodes 8 children at once (SWAR classes of the 8 operation nibbles); neighbour
+//          copies are written as marks and then resolved, one child per thread, by walking at
+//          most three hops (each hop turns an even coordinate odd, and a copy needs an even one).
+//       4. finest level, in two z halves for b = 32: stopped cells fill their 2^3 blocks of the
+//          index grid (two cells per store row), stop-0 cells decode their 8 operations, marks are
+//          resolved, and the output pass maps indices to labels (16-byte stores) or packs palette
+//          indices (cache paletting).
+//     The pipelined schedule runs A and B on two library streams chunk by chunk, so that the
+//     symbols of one chunk decode while the previous chunk is reconstructed.
 // Every rule of the format is checked on the way; the first error of a request goes to the
 // caller's status buffer (no traps).
 #include "decode_kernels.cuh"
 
 namespace vc {
 
-void* pick_kernel_nt256(uint32_t L, bool gt16, bool rans, bool batched, bool split);
-void* pick_kernel_nt512(uint32_t L, bool gt16, bool rans, bool batched, bool split);
-void* pick_kernel_nt1024(uint32_t L, bool gt16, bool rans, bool batched, bool split);
+void* pick_kernel_nt256(uint32_t L, bool gt16, bool rans, bool batched);
+void* pick_kernel_nt512(uint32_t L, bool gt16, bool rans, bool batched);
+void* pick_kernel_nt1024(uint32_t L, bool gt16, bool rans, bool batched);
 
 namespace {
 
@@ -127,27 +130,13 @@ __global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_kernel(const __g
 }
 
 // ------------------------------------------------------------------------------------------
-void* pick_kernel(uint32_t L, uint32_t threads, bool gt16, bool rans, bool batched, bool split) {
+void* pick_kernel(uint32_t L, uint32_t threads, bool gt16, bool rans, bool batched) {
   switch (threads) {
-    case 256: return pick_kernel_nt256(L, gt16, rans, batched, split);
-    case 512: return pick_kernel_nt512(L, gt16, rans, batched, split);
-    case 1024: return pick_kernel_nt1024(L, gt16, rans, batched, split);
+    case 256: return pick_kernel_nt256(L, gt16, rans, batched);
+    case 512: return pick_kernel_nt512(L, gt16, rans, batched);
+    case 1024: return pick_kernel_nt1024(L, gt16, rans, batched);
     default: return nullptr;
   }
-}
-
-void* pick_output_kernel(uint32_t L, bool gt16) {
-#define VC_OUT(LL) \
-  case LL: return gt16 ? reinterpret_cast<void*>(&output_kernel<LL, uint16_t>) : reinterpret_cast<void*>(&output_kernel<LL, uint8_t>);
-  switch (L) {
-    VC_OUT(1)
-    VC_OUT(2)
-    VC_OUT(3)
-    VC_OUT(4)
-    VC_OUT(5)
-    default: return nullptr;
-  }
-#undef VC_OUT
 }
 
 uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -167,8 +156,7 @@ bool schedule_supported(uint32_t L, uint32_t threads) {
   return (threads == 512 || threads == 1024) && L >= 4;
 }
 
-vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, bool split,
-                         SmemLayout* out) {
+vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, SmemLayout* out) {
   const uint32_t L = v.L;
   if (!schedule_supported(L, threads) || nstage < 1 || nstage > 2) return VC_ERR_UNSUPPORTED;
   int optin = 0;
@@ -198,23 +186,15 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   s.list0_cap = (cap[0] + 7u) & ~7u;
   s.list1_cap = cap[1];
   s.list_off = o; o += align16(2u * (s.list0_cap + cap[1]));
-  if (split) {
-    // no finest grid here (it goes to a workspace)
-    s.fg_off = 0;
-    s.pal_cap = 0;
-    s.pal_off = o;
-  } else {
-    // the finest index grid holds one z half at a time for b = 32 (plus the last plane of the first)
-    const uint32_t nh = L >= 5 ? 2u : 1u;
-    s.fg_off = o;
-    s.fg_bytes = align16(s.gt_bytes * b * b * b / nh);
-    o += s.fg_bytes;
-    s.plane_off = o; o += nh == 2 ? align16(s.gt_bytes * b * b) : 0u;
-    // private palette copy (frees the stage early); 256 entries for byte grids
-    s.pal_cap = s.gt_bytes == 1 ? 256u : (v.max_pal <= 1024u ? v.max_pal : 0u);
-    s.pal_off = o; o += align16(4u * s.pal_cap);
-  }
-  s.fg_stride = align16(s.gt_bytes * b * b * b) + 16u;
+  // the finest index grid holds one z half at a time for b = 32 (plus the last plane of the first)
+  const uint32_t nh = L >= 5 ? 2u : 1u;
+  s.fg_off = o;
+  s.fg_bytes = align16(s.gt_bytes * b * b * b / nh);
+  o += s.fg_bytes;
+  s.plane_off = o; o += nh == 2 ? align16(s.gt_bytes * b * b) : 0u;
+  // private palette copy (frees the stage early); 256 entries for byte grids
+  s.pal_cap = s.gt_bytes == 1 ? 256u : (v.max_pal <= 1024u ? v.max_pal : 0u);
+  s.pal_off = o; o += align16(4u * s.pal_cap);
   const uint32_t fixed = o;
   uint32_t stage = align16(v.max_stage) + 16u;  // slack for 8-nibble windows at the end
   if (fixed + nstage * stage > (uint32_t)optin) stage = 0;
@@ -247,30 +227,33 @@ bool launch_symbols(const Params& P, uint8_t* ws, uint32_t base, uint32_t count,
                           smem, s) == cudaSuccess;
 }
 
-// The pipelined schedule: chunks of request items flow through the rANS symbol kernel (stream 0),
-// the split reconstruction kernel (stream 1) and the output kernel (stream 2); a ring of
-// workspace slots is reused once the chunk that last used it has moved on.
+// The pipelined schedule: chunks of request items flow through the rANS symbol kernel (stream 0)
+// and the reconstruction kernel (stream 1, one block per brick), so that the symbols of chunk k+1
+// decode while chunk k is reconstructed; a ring of symbol workspaces is reused once the chunk that
+// last used it is done. Plain-coded volumes have no symbol stage: one reconstruction launch.
 vc_status launch_pipelined(Volume& v, Params P, uint32_t n, cudaStream_t stream) {
   const bool rans = v.coder == 1;
   const uint32_t nt = v.sched.threads;
-  const SmemLayout& SL = v.sm_split;
-  P.v.sm = SL;
-  void* kf = pick_kernel(v.L, nt, SL.gt_bytes == 2, rans, false, true);
-  void* ko = pick_output_kernel(v.L, SL.gt_bytes == 2);
-  if (!kf || !ko) return VC_ERR_UNSUPPORTED;
+  const SmemLayout& SL = v.dv.sm;
+  void* kf = pick_kernel(v.L, nt, SL.gt_bytes == 2, rans, false);
+  if (!kf) return VC_ERR_UNSUPPORTED;
   if (!set_smem(kf, SL.total)) return VC_ERR_CUDA;
-  if (rans && !set_smem(reinterpret_cast<void*>(&rans_symbols_kernel), SL.a_smem)) return VC_ERR_CUDA;
+  if (!rans) {
+    void* args[] = {&P};
+    if (cudaLaunchKernel(kf, dim3(n), dim3(nt), args, SL.total, stream) != cudaSuccess) return VC_ERR_CUDA;
+    ++v.launches;
+    return VC_OK;
+  }
+  if (!set_smem(reinterpret_cast<void*>(&rans_symbols_kernel), SL.a_smem)) return VC_ERR_CUDA;
   const uint32_t chunk = std::max<uint32_t>(1u, v.sched.chunk ? v.sched.chunk : 512u);
   const uint32_t nchunks = (n + chunk - 1) / chunk;
   const uint32_t ring = std::min<uint32_t>(kRing, nchunks);
-  uint8_t *ws = nullptr, *fgws = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&fgws), (size_t)ring * chunk * SL.fg_stride, stream) != cudaSuccess ||
-      (rans && cudaMallocAsync(reinterpret_cast<void**>(&ws), (size_t)ring * chunk * SL.ws_stride, stream) != cudaSuccess)) {
+  uint8_t* ws = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), (size_t)ring * chunk * SL.ws_stride, stream) != cudaSuccess) {
     cudaGetLastError();
-    if (fgws) cudaFreeAsync(fgws, stream);
     return VC_ERR_OOM;
   }
-  const cudaStream_t sA = v.aux[0], sF = v.aux[1], sO = v.aux[2];
+  const cudaStream_t sA = v.aux[0], sF = v.aux[1];
   vc_status rc = VC_OK;
   auto ok = [&](cudaError_t e) {
     if (e != cudaSuccess && rc == VC_OK) rc = VC_ERR_CUDA;
@@ -279,38 +262,27 @@ vc_status launch_pipelined(Volume& v, Params P, uint32_t n, cudaStream_t stream)
   ok(cudaEventRecord(v.ev_fork, stream));
   ok(cudaStreamWaitEvent(sA, v.ev_fork, 0));
   ok(cudaStreamWaitEvent(sF, v.ev_fork, 0));
-  ok(cudaStreamWaitEvent(sO, v.ev_fork, 0));
   for (uint32_t k = 0; k < nchunks && rc == VC_OK; ++k) {
     const uint32_t base = k * chunk, cnt = std::min(chunk, n - base), slot = k % ring;
     Params Q = P;
     Q.item_base = base;
     Q.n = base + cnt;
     Q.ws_item0 = base;
-    Q.ws = ws ? ws + (size_t)slot * chunk * SL.ws_stride : nullptr;
-    Q.fgws = fgws + (size_t)slot * chunk * SL.fg_stride;
-    if (rans) {
-      if (k >= ring) ok(cudaStreamWaitEvent(sA, v.ev_f[slot], 0));  // symbols slot read by F(k - ring)
-      ok(launch_symbols(Q, const_cast<uint8_t*>(Q.ws), base, cnt, SL.a_smem, sA) ? cudaSuccess : cudaErrorLaunchFailure);
-      ok(cudaEventRecord(v.ev_a[slot], sA));
-      ok(cudaStreamWaitEvent(sF, v.ev_a[slot], 0));
-    }
-    if (k >= ring) ok(cudaStreamWaitEvent(sF, v.ev_o[slot], 0));  // grid slot read by O(k - ring)
+    Q.ws = ws + (size_t)slot * chunk * SL.ws_stride;
+    if (k >= ring) ok(cudaStreamWaitEvent(sA, v.ev_f[slot], 0));  // slot read by chunk k - ring
+    ok(launch_symbols(Q, const_cast<uint8_t*>(Q.ws), base, cnt, SL.a_smem, sA) ? cudaSuccess : cudaErrorLaunchFailure);
+    ok(cudaEventRecord(v.ev_a[slot], sA));
+    ok(cudaStreamWaitEvent(sF, v.ev_a[slot], 0));
     void* argsF[] = {&Q};
     ok(cudaLaunchKernel(kf, dim3(cnt), dim3(nt), argsF, SL.total, sF));
     ok(cudaEventRecord(v.ev_f[slot], sF));
-    ok(cudaStreamWaitEvent(sO, v.ev_f[slot], 0));
-    void* argsO[] = {&Q};
-    ok(cudaLaunchKernel(ko, dim3(cnt), dim3(256), argsO, 0, sO));
-    ok(cudaEventRecord(v.ev_o[slot], sO));
-    v.launches += rans ? 3 : 2;
+    v.launches += 2;
   }
-  // join: the caller's stream waits for all three
+  // join: the caller's stream waits for both
   ok(cudaEventRecord(v.ev_join[0], sA));
   ok(cudaEventRecord(v.ev_join[1], sF));
-  ok(cudaEventRecord(v.ev_join[2], sO));
-  for (int i = 0; i < 3; ++i) ok(cudaStreamWaitEvent(stream, v.ev_join[i], 0));
-  cudaFreeAsync(fgws, stream);
-  if (ws) cudaFreeAsync(ws, stream);
+  for (int i = 0; i < 2; ++i) ok(cudaStreamWaitEvent(stream, v.ev_join[i], 0));
+  cudaFreeAsync(ws, stream);
   return rc;
 }
 
@@ -336,7 +308,6 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   P.status = status;
   P.item_base = 0;
   P.ws = nullptr;
-  P.fgws = nullptr;
   P.ws_item0 = 0;
   const uint32_t edge = (1u << v.L) >> lod;
   P.out_words = edge * edge * edge;
@@ -355,7 +326,7 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   if (mode == VC_MODE_PIPELINED) mode = VC_MODE_GRID;
   const bool batched = mode == VC_MODE_BATCHED;
   const uint32_t nt = v.sched.threads;
-  void* k = pick_kernel(v.L, nt, v.dv.sm.gt_bytes == 2, rans, batched, false);
+  void* k = pick_kernel(v.L, nt, v.dv.sm.gt_bytes == 2, rans, batched);
   if (!k) return VC_ERR_UNSUPPORTED;
   const uint32_t smem = v.dv.sm.total;
   if (!set_smem(k, smem)) return VC_ERR_CUDA;

@@ -24,7 +24,6 @@ struct Params {
   int32_t* status;
   uint32_t item_base;
   const uint8_t* ws;  // decoded rANS symbols, ws_stride bytes per item (nullptr for plain volumes)
-  uint8_t* fgws;      // split schedule: finest index grids, fg_stride bytes per item
   uint32_t ws_item0;  // the workspaces hold items ws_item0 .. (a chunk of the request)
   uint32_t out_words; // u32 words per cache slot
   uint32_t pal_bits;  // 0: labels; else cache paletting: pal_bits-bit palette indices,
@@ -400,11 +399,9 @@ __device__ __forceinline__ void store_pair(GT* fg, uint32_t pos, uint32_t lo, ui
 // sw: its symbols as packed nibbles (u32 aligned); out: destination of (b >> lod)^3 labels.
 // on_stage_free() is called by every thread exactly once, as soon as the staged record is no longer
 // read: right after the finest grid is filled when the palette fits its shared copy, else at the end.
-// SPLIT: the finest index grid goes to fg_global (global memory) and the output pass is left to
-// output_kernel; otherwise the grid lives in shared memory and labels are written here.
-template <int L, typename GT, bool RANS, int NT, bool SPLIT, typename Hook>
+template <int L, typename GT, bool RANS, int NT, typename Hook>
 __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32_t* sw, uint32_t* out,
-                             unsigned char* sm, int* s_err, Hook&& on_stage_free, GT* fg_global) {
+                             unsigned char* sm, int* s_err, Hook&& on_stage_free) {
   constexpr uint32_t NW = NT / 32;
   constexpr uint32_t MARK = GridT<GT>::MARK;
   const SmemLayout& SL = P.v.sm;
@@ -419,7 +416,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   BrickCtx c;
   c.pal = head + 4 + ns;
   c.n_pal = n_pal;
-  const bool pal_copied = !SPLIT && n_pal <= SL.pal_cap;
+  const bool pal_copied = n_pal <= SL.pal_cap;
   if (pal_copied) {  // a private copy of the palette frees the stage before the output pass; byte
                      // grids get 256 entries (zero padded) so that any byte index stays in bounds
     uint32_t* pc = reinterpret_cast<uint32_t*>(sm + SL.pal_off);
@@ -440,7 +437,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     uint32_t* nodes = reinterpret_cast<uint32_t*>(sm + SL.nodes_off);
     // the general parse path borrows the finest grid (not in use yet) for its summaries
     // the finest grid is idle during the parse: it keeps the per-word automaton masks
-    uint32_t* wst = (!SPLIT && ((S + 7u) >> 3) * 4u <= SL.fg_bytes) ? reinterpret_cast<uint32_t*>(sm + SL.fg_off) : nullptr;
+    uint32_t* wst = ((S + 7u) >> 3) * 4u <= SL.fg_bytes ? reinterpret_cast<uint32_t*>(sm + SL.fg_off) : nullptr;
     const ParseOut po = parse_stream<NT>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap, scan_tmp, wst, s_err);
     c.nodes = nodes;
     c.n_nodes = po.n_nodes;
@@ -498,7 +495,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   const bool no_stop = (P.v.flags & kFlagNoStop) != 0;
   constexpr uint32_t b = 1u << L;
   const bool finest = Lout == (uint32_t)L;
-  GT* fg = SPLIT ? fg_global : reinterpret_cast<GT*>(sm + SL.fg_off);
+  GT* fg = reinterpret_cast<GT*>(sm + SL.fg_off);
 
   // the 8 children (nodes j0 .. j0+7) of a stop-0 cell with index gp at coordinates (px, py, pz):
   // palette indices or neighbour marks into v, returns the children emitted with stop bit 0
@@ -675,7 +672,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     if (tid == 0 && off + 8u * npar != c.n_nodes) set_err(s_err, VC_ERR_CORRUPT);
     const GT* Gp = G + gofs_prev;
     constexpr uint32_t pcells = 1u << (3 * (L - 1));
-    constexpr uint32_t NH = (!SPLIT && L >= 5) ? 2u : 1u;  // z halves
+    constexpr uint32_t NH = L >= 5 ? 2u : 1u;  // z halves
     constexpr uint32_t hcells = pcells / NH;                 // level-(L-1) cells per half
     constexpr uint32_t hvox = b * b * b / NH;                // voxels per half
     constexpr uint32_t PC = (hcells + NT - 1) / NT;
@@ -744,10 +741,6 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
         }
       }
       __syncthreads();
-      if (SPLIT) {
-        on_stage_free();
-        return;
-      }
       if (pal_copied && h + 1 == NH) on_stage_free();
       constexpr uint32_t quads = hvox / 4u;
       uint32_t* outh = out + h * hvox;
@@ -926,7 +919,7 @@ __device__ __forceinline__ ItemSrc item_src(const Params& P, uint32_t item, uint
 }
 
 // One thread block per request item (grid and per-brick schedules).
-template <int L, typename GT, bool RANS, int NT, bool SPLIT>
+template <int L, typename GT, bool RANS, int NT>
 __global__ void __launch_bounds__(NT) decode_grid_kernel(const __grid_constant__ Params P) {
   extern __shared__ __align__(128) unsigned char sm[];
   const SmemLayout& SL = P.v.sm;
@@ -955,10 +948,8 @@ __global__ void __launch_bounds__(NT) decode_grid_kernel(const __grid_constant__
                                            (RANS ? src.head_bytes : 16u + 4u * src.rec[0]));
   }
   __syncthreads();
-  const uint32_t edge = (1u << L) >> P.lod;
   uint32_t* out = P.cache + (size_t)P.slots[item] * P.out_words;
-  GT* fgg = SPLIT ? reinterpret_cast<GT*>(P.fgws + (size_t)(item - P.ws_item0) * SL.fg_stride) : nullptr;
-  decode_brick<L, GT, RANS, NT, SPLIT>(P, head, sw, out, sm, s_err, [] {}, fgg);
+  decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, s_err, [] {});
   __syncthreads();
   if (threadIdx.x == 0 && *s_err) report(P.status, *s_err, item);
 }
@@ -966,7 +957,7 @@ __global__ void __launch_bounds__(NT) decode_grid_kernel(const __grid_constant__
 // Persistent thread blocks pull items from the work counter in status[2]; while one brick is
 // decoded, the next brick's record (and symbols) are already being copied into the other stage
 // buffer by the TMA engine.
-template <int L, typename GT, bool RANS, int NT, bool SPLIT>
+template <int L, typename GT, bool RANS, int NT>
 __global__ void __launch_bounds__(NT) decode_batched_kernel(const __grid_constant__ Params P) {
   extern __shared__ __align__(128) unsigned char sm[];
   const SmemLayout& SL = P.v.sm;
@@ -1043,14 +1034,12 @@ __global__ void __launch_bounds__(NT) decode_batched_kernel(const __grid_constan
       const uint32_t* sw = !staged ? src.stream
                                    : (RANS ? reinterpret_cast<const uint32_t*>(stage[buf] + src.head_bytes)
                                            : head + 4u + head[0]);
-      const uint32_t edge = (1u << L) >> P.lod;
       uint32_t* out = P.cache + (size_t)P.slots[item] * P.out_words;
       // depth 1: the next item's copy starts as soon as this brick's stage is free
-      GT* fgg = SPLIT ? reinterpret_cast<GT*>(P.fgws + (size_t)(item - P.ws_item0) * SL.fg_stride) : nullptr;
-      decode_brick<L, GT, RANS, NT, SPLIT>(P, head, sw, out, sm, s_err, [&] {
+      decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, s_err, [&] {
         if (!prefetch && tid == 0) claim_and_issue(0);
         released = true;
-      }, fgg);
+      });
       __syncthreads();
       if (tid == 0 && *s_err) report(P.status, *s_err, item);
     }
@@ -1063,70 +1052,6 @@ __global__ void __launch_bounds__(NT) decode_batched_kernel(const __grid_constan
   }
 }
 
-
-// ------------------------------------------------------------------------------------------
-// Output expansion for the split schedule: one block per request item turns the finest index
-// grid (written by the split reconstruction kernel) into labels, 16 bytes per store. Neighbour
-// marks (rare) are resolved by walking at most three hops in the grid.
-template <int L, typename GT>
-__global__ void __launch_bounds__(256) output_kernel(const __grid_constant__ Params P) {
-  constexpr uint32_t b = 1u << L;
-  constexpr uint32_t MARK = GridT<GT>::MARK;
-  constexpr uint32_t PAL_SMEM = 2048;
-  __shared__ uint32_t pal_s[PAL_SMEM];
-  const uint32_t item = P.item_base + blockIdx.x;
-  if (item >= P.n) return;
-  const uint32_t brick = P.ids[item];
-  if (brick >= P.v.n_bricks) return;  // reported by the reconstruction kernel
-  const uint32_t* rec = P.v.records + P.v.starts[brick];
-  const uint32_t n_pal = rec[0], S = rec[1];
-  const uint32_t ns = P.v.coder == 1 ? (S < 32u ? S : 32u) : 0u;
-  const uint32_t* pal_g = rec + 4 + ns;
-  const bool in_smem = n_pal <= PAL_SMEM;
-  if (in_smem) {
-    const uint32_t lim = sizeof(GT) == 1 ? 256u : n_pal;  // byte grids: pad so any index is in bounds
-    for (uint32_t i = threadIdx.x; i < lim; i += 256u) pal_s[i] = i < n_pal ? pal_g[i] : 0u;
-  }
-  __syncthreads();
-  const GT* fg = reinterpret_cast<const GT*>(P.fgws + (size_t)(item - P.ws_item0) * P.v.sm.fg_stride);
-  uint32_t* out = P.cache + (size_t)P.slots[item] * b * b * b;
-  auto resolve = [&](uint32_t pos, uint32_t g) -> uint32_t {
-#pragma unroll 1
-    for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
-      const uint32_t a = g - MARK;
-      pos -= a == 0 ? 1u : (a == 1 ? b : b * b);
-      g = fg[pos];
-    }
-    return g >= MARK ? 0u : g;  // a mark chain longer than three hops was reported as corrupt
-  };
-  auto label = [&](uint32_t idx) -> uint32_t {
-    if (sizeof(GT) == 1 && in_smem) return pal_s[idx];
-    return idx < n_pal ? (in_smem ? pal_s[idx] : pal_g[idx]) : 0u;
-  };
-  constexpr uint32_t quads = b * b * b / 4u;
-  if constexpr (sizeof(GT) == 1) {
-    const uint32_t* fg32 = reinterpret_cast<const uint32_t*>(fg);
-#pragma unroll 4
-    for (uint32_t q = threadIdx.x; q < quads; q += 256u) {
-      uint32_t x = fg32[q];
-      if (__vcmpgeu4(x, 0xFDFDFDFDu)) {
-        uint32_t y = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) y |= resolve(4u * q + (uint32_t)i, (x >> (8 * i)) & 0xFFu) << (8 * i);
-        x = y;
-      }
-      store16(out + 4u * q, label(x & 0xFFu), label((x >> 8) & 0xFFu), label((x >> 16) & 0xFFu), label(x >> 24));
-    }
-  } else {
-    const uint2* fg64 = reinterpret_cast<const uint2*>(fg);
-#pragma unroll 2
-    for (uint32_t q = threadIdx.x; q < quads; q += 256u) {
-      const uint2 x = fg64[q];
-      store16(out + 4u * q, label(resolve(4u * q, x.x & 0xFFFFu)), label(resolve(4u * q + 1u, x.x >> 16)),
-              label(resolve(4u * q + 2u, x.y & 0xFFFFu)), label(resolve(4u * q + 3u, x.y >> 16)));
-    }
-  }
-}
 }  // namespace
 }  // namespace dev
 }  // namespace vc

@@ -9,23 +9,20 @@ namespace vc {
 namespace {
 
 template <int L, typename GT, bool RANS>
-void* kernel_for(bool batched, bool split) {
-  if (split)
-    return batched ? reinterpret_cast<void*>(&dev::decode_batched_kernel<L, GT, RANS, VC_NT, true>)
-                   : reinterpret_cast<void*>(&dev::decode_grid_kernel<L, GT, RANS, VC_NT, true>);
-  return batched ? reinterpret_cast<void*>(&dev::decode_batched_kernel<L, GT, RANS, VC_NT, false>)
-                 : reinterpret_cast<void*>(&dev::decode_grid_kernel<L, GT, RANS, VC_NT, false>);
+void* kernel_for(bool batched) {
+  return batched ? reinterpret_cast<void*>(&dev::decode_batched_kernel<L, GT, RANS, VC_NT>)
+                 : reinterpret_cast<void*>(&dev::decode_grid_kernel<L, GT, RANS, VC_NT>);
 }
 
 }  // namespace
 
 #define VC_CAT2(a, b) a##b
 #define VC_CAT(a, b) VC_CAT2(a, b)
-void* VC_CAT(pick_kernel_nt, VC_NT)(uint32_t L, bool gt16, bool rans, bool batched, bool split) {
+void* VC_CAT(pick_kernel_nt, VC_NT)(uint32_t L, bool gt16, bool rans, bool batched) {
 #define VC_PICK(LL)                                                                          \
   case LL:                                                                                   \
-    if (gt16) return rans ? kernel_for<LL, uint16_t, true>(batched, split) : kernel_for<LL, uint16_t, false>(batched, split); \
-    return rans ? kernel_for<LL, uint8_t, true>(batched, split) : kernel_for<LL, uint8_t, false>(batched, split);
+    if (gt16) return rans ? kernel_for<LL, uint16_t, true>(batched) : kernel_for<LL, uint16_t, false>(batched); \
+    return rans ? kernel_for<LL, uint8_t, true>(batched) : kernel_for<LL, uint8_t, false>(batched);
   switch (L) {
 #if VC_NT == 256
     VC_PICK(1)

@@ -247,7 +247,12 @@ bool launch_batch(Server* s) {
   }
   uint32_t at = 0;
   for (const auto& key : order) {
-    const auto& idx = by_group[key];
+    auto& idx = by_group[key];
+    // longest records first: the persistent blocks take items in order, so the big bricks start
+    // early and the short ones fill the tail
+    const uint32_t* rw = s->volumes[key.first]->h_rec_words;
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](uint32_t a, uint32_t b) { return rw[taken[a].brick] > rw[taken[b].brick]; });
     batch.groups.push_back(Group{key.first, key.second, at, (uint32_t)idx.size()});
     const uint64_t edge = (1u << s->volumes[key.first]->L) >> key.second;
     s->stats.voxels_decoded += edge * edge * edge * idx.size();

@@ -29,7 +29,7 @@ struct DeviceGuard {
 };
 
 void destroy_pipeline(Volume* v) {
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 2; ++i) {
     if (v->aux[i]) cudaStreamDestroy(v->aux[i]);
     if (v->ev_join[i]) cudaEventDestroy(v->ev_join[i]);
   }
@@ -37,13 +37,12 @@ void destroy_pipeline(Volume* v) {
   for (uint32_t i = 0; i < kRing; ++i) {
     if (v->ev_a[i]) cudaEventDestroy(v->ev_a[i]);
     if (v->ev_f[i]) cudaEventDestroy(v->ev_f[i]);
-    if (v->ev_o[i]) cudaEventDestroy(v->ev_o[i]);
   }
 }
 
 bool create_pipeline(Volume* v) {
   bool ok = true;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 2; ++i) {
     ok = ok && cudaStreamCreateWithFlags(&v->aux[i], cudaStreamNonBlocking) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&v->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
   }
@@ -51,16 +50,10 @@ bool create_pipeline(Volume* v) {
   for (uint32_t i = 0; i < kRing; ++i) {
     ok = ok && cudaEventCreateWithFlags(&v->ev_a[i], cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&v->ev_f[i], cudaEventDisableTiming) == cudaSuccess;
-    ok = ok && cudaEventCreateWithFlags(&v->ev_o[i], cudaEventDisableTiming) == cudaSuccess;
   }
   return ok;
 }
 
-vc_status layouts_for(Volume* v, const vc_schedule& sc, SmemLayout* fused, SmemLayout* split) {
-  vc_status rc = compute_layout(*v, v->device, sc.threads, sc.stage_depth, false, fused);
-  if (rc == VC_OK) rc = compute_layout(*v, v->device, sc.threads, 1, true, split);
-  return rc;
-}
 
 void free_volume(Volume* v) {
   if (!v) return;
@@ -79,6 +72,7 @@ void free_volume(Volume* v) {
   cudaFree(v->d_host_slots);
   cudaFree(v->d_host_cache);
   cudaFree(v->d_host_status);
+  std::free(v->h_rec_words);
   v->kind = 0;
   delete v;
 }
@@ -183,18 +177,25 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   v->max_pal = max_pal; v->max_sym = max_sym; v->max_delta = max_delta; v->max_rec_words = max_words;
   v->max_stage = max_stage;
   v->max_nodes = max_nodes;
+  v->h_rec_words = static_cast<uint32_t*>(std::malloc(4 * (size_t)n_bricks + 4));
+  if (!v->h_rec_words) { delete v; return VC_ERR_OOM; }
+  for (uint32_t i = 0; i < n_bricks; ++i) v->h_rec_words[i] = le32(st + 4 * ((size_t)i + 1)) - le32(st + 4 * (size_t)i);
   v->encoded_bytes = nbytes;
   v->sched.threads = 256;
   v->sched.stage_depth = 1;
   v->sched.blocks_per_sm = 0;
   v->sched.chunk = 512;
-  SmemLayout sl, sls;
-  vc_status rc = layouts_for(v, v->sched, &sl, &sls);
-  if (rc != VC_OK) { delete v; return rc; }
-  v->sm_split = sls;
+  SmemLayout sl;
+  vc_status rc = compute_layout(*v, device, v->sched.threads, v->sched.stage_depth, &sl);
+  if (rc != VC_OK) {
+    std::free(v->h_rec_words);
+    delete v;
+    return rc;
+  }
   if (!create_pipeline(v)) {
     cudaGetLastError();
     destroy_pipeline(v);
+    std::free(v->h_rec_words);
     delete v;
     return VC_ERR_CUDA;
   }
@@ -269,13 +270,12 @@ vc_status vc_volume_set_schedule(vc_volume* vol, const vc_schedule* sched) {
   if (sched->stage_depth < 1 || sched->stage_depth > 2) return VC_ERR_ARG;
   if (!schedule_supported(v->L, sched->threads)) return VC_ERR_UNSUPPORTED;
   DeviceGuard g(v->device);
-  SmemLayout sl, sls;
-  const vc_status rc = layouts_for(v, *sched, &sl, &sls);
+  SmemLayout sl;
+  const vc_status rc = compute_layout(*v, v->device, sched->threads, sched->stage_depth, &sl);
   if (rc != VC_OK) return rc;
   v->sched = *sched;
   if (!v->sched.chunk) v->sched.chunk = 512;
   v->dv.sm = sl;
-  v->sm_split = sls;
   return VC_OK;
 }
 

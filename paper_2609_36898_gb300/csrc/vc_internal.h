@@ -39,8 +39,7 @@ struct SmemLayout {
   uint32_t ns_off;       // per level, one byte per parent cell: which children have stop bit 0
   uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each; one z half for b = 32)
   uint32_t plane_off;    // b = 32: the last z plane of the first half (for -z neighbours of the second)
-  uint32_t fg_bytes;     // bytes of the finest grid region (0 in the split schedule)
-  uint32_t fg_stride;    // split schedule: bytes per item of the finest-grid workspace
+  uint32_t fg_bytes;     // bytes of the finest grid region
   uint32_t list_off;     // stop-0 cells by rank (u16), two buffers: even / odd levels
   uint32_t list0_cap;    // entries of the even-level buffer
   uint32_t list1_cap;    // entries of the odd-level buffer
@@ -76,9 +75,8 @@ struct Volume {
   uint32_t max_nodes;    // max over bricks of S - n_delta (every delta operation has an entry): bounds nodes
   uint64_t encoded_bytes, device_bytes;
   vc_schedule sched;     // threads per block, staging depth, persistent blocks per SM, chunk
-  SmemLayout sm_split;   // layout of the split reconstruction kernel (pipelined schedule)
-  cudaStream_t aux[3];   // pipelined schedule: symbol, reconstruction and output streams
-  cudaEvent_t ev_fork, ev_join[3], ev_a[kRing], ev_f[kRing], ev_o[kRing];
+  cudaStream_t aux[2];   // pipelined schedule: symbol and reconstruction streams
+  cudaEvent_t ev_fork, ev_join[2], ev_a[kRing], ev_f[kRing];
   uint8_t* d_file;       // device copy of the whole file (+ slack)
   uint8_t* d_tables;     // rANS table
   uint8_t* d_flags;      // per brick: bit 0 = palette holds label 0, bit 1 = holds another label
@@ -88,6 +86,7 @@ struct Volume {
   uint32_t* d_host_slots;
   uint32_t* d_host_cache;
   int32_t* d_host_status;
+  uint32_t* h_rec_words;  // host copy: record size of each brick in 32-bit words (work ordering)
   size_t host_cap_items, host_cap_words;
   // kernel accounting: launches are always counted; with prof set, each grid / batched decode call
   // records three timing events (before the symbol kernel, between, after the reconstruction)
@@ -116,8 +115,7 @@ vc_status launch_camera_requests(const Volume& v, const vc_camera* cams, uint32_
 // cache paletting: bits per palette index (ceil(log2 max_pal), >= 1) and indices per u32 word
 void palette_packing(uint32_t max_pal, uint32_t* bits, uint32_t* per_word);
 bool schedule_supported(uint32_t L, uint32_t threads);
-vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, bool split,
-                         SmemLayout* out);
+vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, SmemLayout* out);
 vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
                         uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream);
 // Same, with the rANS symbol workspace supplied by the caller (ws_ext, ws_cap bytes, 16-byte

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 
 import paper_2609_36898_gb300 as vc  # noqa: E402
 
-MODES = ["plain", "grid", "batched"]
+MODES = ["plain", "grid", "batched", "pipelined"]
 
 
 @pytest.fixture(scope="module", autouse=True)
