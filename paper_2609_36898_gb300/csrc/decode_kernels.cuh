@@ -245,8 +245,8 @@ __device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes
       const uint32_t nv = min(8u, S - 8u * w);
       uint32_t D, A, B, e0, e1;
       word_states(x, D, A, B);
-      if (wst) wst[w] = D | (A << 8) | (B << 16);
       const uint32_t m0 = word_ops(A, B, s0, nv, &e0), m1 = word_ops(A, B, s1, nv, &e1);
+      if (wst) wst[w] = m0 | (m1 << 8) | (D << 16);  // this word's operations on both paths
       f.nd0 += __popc(m0) | (__popc(m0 & D) << 16);
       f.nd1 += __popc(m1) | (__popc(m1 & D) << 16);
       s0 = e0;
@@ -282,6 +282,7 @@ __device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes
   if (lane == 0) pre = Fn2{2u, 0u, 0u};
   pre = fn_then(Fn2{scan_tmp[3 * warp], scan_tmp[3 * warp + 1], scan_tmp[3 * warp + 2]}, pre);
   uint32_t st = pre.e & 1u;  // the stream starts in state 0
+  const uint32_t path = st;  // which of the two paths of the first pass this run takes
   uint32_t j = pre.nd0 & 0xFFFFu, d = pre.nd0 >> 16;
   const uint32_t total_e = scan_tmp[3 * NW] & 1u, total_nd = scan_tmp[3 * NW + 1];
   // the node words this run shares with its neighbours start at zero
@@ -295,17 +296,17 @@ __device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes
   for (uint32_t w = w0; w < w1; ++w) {
     const uint32_t x = sw[w];
     const uint32_t nv = min(8u, S - 8u * w);
-    uint32_t D, A, B, end;
+    uint32_t D, m;
     if (wst) {
       const uint32_t v = wst[w];
-      D = v & 0xFFu;
-      A = (v >> 8) & 0xFFu;
-      B = v >> 16;
+      m = (v >> (8u * path)) & 0xFFu;
+      D = v >> 16;
     } else {
+      uint32_t A, B, end;
       word_states(x, D, A, B);
+      m = word_ops(A, B, st, nv, &end);
+      st = end;
     }
-    const uint32_t m = word_ops(A, B, st, nv, &end);
-    st = end;
     const uint32_t cnt = __popc(m);
     const uint32_t p = j & 7u;
     acc |= (uint64_t)pack_nibbles(x, m) << (4u * p);
