@@ -284,7 +284,11 @@ def serving_leg(args, local: int):
         vc.vc_request_release(srv, r)
     vox = st.voxels_decoded
     vc.vc_release(srv)
-    lists = vc.vc_camera_bricks(vol, [orbit_camera(vc, i, 0, dims, W, H) for i in range(ncam)], max_lod)
+    cams0 = [orbit_camera(vc, i, 0, dims, W, H) for i in range(ncam)]
+    vc.vc_camera_bricks(vol, cams0[:1], max_lod)  # warm-up
+    t0 = time.perf_counter()
+    lists = vc.vc_camera_bricks(vol, cams0, max_lod, cap=int(vc.vc_volume_info_get(vol).n_bricks))
+    camera_stage_ms = 1000 * (time.perf_counter() - t0)
     edge = 1 << B_LOG2
 
     # plain: the first cameras' requests of frame 0, one launch per brick, one request after the
@@ -318,6 +322,8 @@ def serving_leg(args, local: int):
         "served": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "requests": len(lat),
                    "gvoxel_s": delivered / wall / 1e9, "decoded_gvoxel_s": vox / wall / 1e9,
                    "request_stage_ms_median": pct(rstage, 50),
+                   "camera_stage_alone_ms": camera_stage_ms,
+                   "bricks_requested_per_camera": float(np.mean([len(i) for i, _ in lists])),
                    "frame_ms_median": pct(frame_ms, 50), "bricks_decoded": int(st.bricks_decoded),
                    "bricks_hit": int(st.bricks_hit), "batches": int(st.batches), "evictions": int(st.evictions)},
         "plain": {"p50_ms": pct(plain_lat, 50), "p99_ms": pct(plain_lat, 99), "requests": len(lists),

@@ -397,7 +397,8 @@ __device__ __forceinline__ void store_pair(GT* fg, uint32_t pos, uint32_t lo, ui
 
 // ------------------------------------------------------------------------------------------
 // Decode one brick. head: the record (header, [states], palette) in shared or global memory;
-// sw: its symbols as packed nibbles (u32 aligned); out: destination of (b >> lod)^3 labels.
+// sw: its symbols as packed nibbles (u32 aligned); out: the slot, (b >> lod)^3 labels or packed
+// palette indices (P.pal_bits).
 // on_stage_free() is called by every thread exactly once, as soon as the staged record is no longer
 // read: right after the finest grid is filled when the palette fits its shared copy, else at the end.
 template <int L, typename GT, bool RANS, int NT, typename Hook>
