@@ -276,3 +276,42 @@ def test_rans_corrupt_words_flagged():
     _, st = gpu_decode(bad, [0], 0, "batched")
     assert st[0] == vc.VC_ERR_CORRUPT
     assert rec["n_sym"] == len(sym)
+
+
+def _many_label_volume(n_labels_per_brick_edge: int, edge: int, seed: int) -> np.ndarray:
+    """A volume whose bricks hold many distinct labels: small cubes of side n with unique ids."""
+    rng = np.random.default_rng(seed)
+    s = n_labels_per_brick_edge
+    cells = rng.permutation(np.arange(1, (edge // s) ** 3 + 1, dtype=np.uint32) * 2654435761 % 4294967291 + 1)
+    grid = cells.reshape(edge // s, edge // s, edge // s).astype(np.uint32)
+    return np.repeat(np.repeat(np.repeat(grid, s, 0), s, 1), s, 2)
+
+
+@pytest.mark.parametrize("coder", [0, 1])
+def test_parity_16bit_index_grids(coder):
+    """Bricks with more than 251 labels take the 16-bit index grids: 2^3 cubes of distinct labels
+    give 4096 labels per 32^3 brick; every brick, every level of detail, every schedule."""
+    V = _many_label_volume(2, 64, 3)
+    V[:, :, :8] = 7  # a few repeated labels and a constant slab too
+    enc = vc.vc_encode_volume(V, 5, op_mask=0x7F, coder=coder)
+    assert oracle.header(enc)["max_pal"] >= 252
+    ids = np.arange(oracle.header(enc)["n_bricks"])
+    for lod in (0, 1, 3, 5):
+        ref = oracle_bricks(enc, ids, lod)
+        for mode in MODES:
+            out, st = gpu_decode(enc, ids, lod, mode)
+            assert st[0] == 0, (mode, lod, st)
+            assert np.array_equal(out, ref), (mode, lod)
+
+
+@pytest.mark.parametrize("log2b", [3, 4])
+def test_parity_all_distinct_worst_case(log2b):
+    """Every voxel its own label: the largest palettes and streams a brick of this size can have."""
+    b = 1 << log2b
+    V = _many_label_volume(1, 2 * b, 11)
+    for coder in (0, 1):
+        enc = vc.vc_encode_volume(V, log2b, op_mask=0x7F, coder=coder)
+        ids = np.arange(oracle.header(enc)["n_bricks"])
+        out, st = gpu_decode(enc, ids, 0, "grid")
+        assert st[0] == 0
+        assert np.array_equal(out, oracle_bricks(enc, ids, 0))
