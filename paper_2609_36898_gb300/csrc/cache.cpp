@@ -114,19 +114,36 @@ bool BrickCache::evict_one() {
 }
 
 bool BrickCache::acquire(const uint64_t* keys, const uint32_t* cls, uint32_t n, Ref* out) {
+  // one lookup per key: the entries already present (hits) are remembered for the passes below
+  found_.resize(n);
+  if (++epoch_ == 0) {  // after 2^32 calls: old marks could match again
+    std::fill(mark_.begin(), mark_.end(), 0u);
+    epoch_ = 1;
+  }
+  if (mark_.size() < entries_.size()) mark_.resize(entries_.size(), 0);
   // admission: the missing keys' bytes must fit in free + evictable bytes, not counting the
-  // evictable entries this call will pin as hits
+  // evictable entries this call will pin as hits (each distinct key counted once)
   uint64_t need = 0, hit_evictable = 0;
-  seen_.clear();
+  uint32_t n_hits = 0;
+  bool seen_used = false;
   for (uint32_t i = 0; i < n; ++i) {
-    if (seen_.find(keys[i]) != FlatMap::kMissing) continue;
-    seen_.put(keys[i], 0);
     const uint32_t c = std::max(cls[i], min_cls_);
     if (c > max_cls_) return false;
     const uint32_t e = map_.find(keys[i]);
+    found_[i] = e;
     if (e != FlatMap::kMissing) {
-      if (entries_[e].pins == 0) hit_evictable += block_bytes(entries_[e].cls);
+      ++n_hits;
+      if (mark_[e] != epoch_) {
+        mark_[e] = epoch_;
+        if (entries_[e].pins == 0) hit_evictable += block_bytes(entries_[e].cls);
+      }
     } else {
+      if (!seen_used) {
+        seen_.clear();
+        seen_used = true;
+      }
+      if (seen_.find(keys[i]) != FlatMap::kMissing) continue;
+      seen_.put(keys[i], 0);
       need += block_bytes(c);
     }
   }
@@ -134,33 +151,33 @@ bool BrickCache::acquire(const uint64_t* keys, const uint32_t* cls, uint32_t n, 
 
   // hits first, so that the evictions below cannot take them
   uint32_t done = 0;
-  std::vector<uint32_t> order;
-  order.reserve(n);
-  for (uint32_t i = 0; i < n; ++i)
-    if (map_.find(keys[i]) != FlatMap::kMissing) order.push_back(i);
-  for (uint32_t i = 0; i < n; ++i)
-    if (map_.find(keys[i]) == FlatMap::kMissing) order.push_back(i);
-  std::vector<Ref> tmp(n);
-  std::vector<uint8_t> tmp_created(n, 0);
+  order_.resize(n);
+  {
+    uint32_t h = 0, m = n_hits;
+    for (uint32_t i = 0; i < n; ++i) order_[found_[i] != FlatMap::kMissing ? h++ : m++] = i;
+  }
+  tmp_.resize(n);
+  tmp_created_.assign(n, 0);
   auto undo = [&]() {
     for (uint32_t j = done; j-- > 0;) {
-      const uint32_t e = tmp[j].entry;
+      const uint32_t e = tmp_[j].entry;
       Entry& E = entries_[e];
       if (--E.pins == 0) {
-        if (tmp_created[j] || !E.valid) remove_entry(e);
+        if (tmp_created_[j] || !E.valid) remove_entry(e);
         else lru_push_front(e);
       }
     }
   };
   for (; done < n; ++done) {
-    const uint32_t i = order[done];
+    const uint32_t i = order_[done];
     const uint32_t c = std::max(cls[i], min_cls_);
-    const uint32_t hit_e = map_.find(keys[i]);
+    // a hit from the first pass, or a key created earlier in this pass (a duplicate miss)
+    const uint32_t hit_e = done < n_hits ? found_[i] : map_.find(keys[i]);
     if (hit_e != FlatMap::kMissing) {
       const uint32_t e = hit_e;
       Entry& E = entries_[e];
       if (E.pins++ == 0) lru_remove(e);
-      tmp[done] = Ref{e, (uint64_t)E.block * block_bytes(E.cls), true};
+      tmp_[done] = Ref{e, (uint64_t)E.block * block_bytes(E.cls), true};
       continue;
     }
     uint32_t blk;
@@ -187,12 +204,12 @@ bool BrickCache::acquire(const uint64_t* keys, const uint32_t* cls, uint32_t n, 
     E.pins = 1;
     E.ready_seq = ~0ull;  // not decoded yet
     map_.put(keys[i], e);
-    tmp[done] = Ref{e, (uint64_t)blk * block_bytes(c), false};
-    tmp_created[done] = 1;
+    tmp_[done] = Ref{e, (uint64_t)blk * block_bytes(c), false};
+    tmp_created_[done] = 1;
   }
   for (uint32_t j = 0; j < n; ++j) {
-    out[order[j]] = tmp[j];
-    if (tmp[j].hit) ++hits_; else ++misses_;
+    out[order_[j]] = tmp_[j];
+    if (tmp_[j].hit) ++hits_; else ++misses_;
   }
   return true;
 }

@@ -162,7 +162,12 @@ class BrickCache {
   std::vector<Entry> entries_;
   std::vector<uint32_t> free_entries_;
   FlatMap map_;
-  FlatMap seen_;  // scratch of acquire()
+  // scratch of acquire(): duplicate misses, per-key lookups, per-entry marks, pass order
+  FlatMap seen_;
+  std::vector<uint32_t> found_, mark_, order_;
+  std::vector<Ref> tmp_;
+  std::vector<uint8_t> tmp_created_;
+  uint32_t epoch_ = 0;
   int32_t lru_head_ = -1, lru_tail_ = -1;
 };
 
