@@ -351,24 +351,6 @@ struct BrickCtx {
   int* s_err;
 };
 
-// Palette index of node j with operation o in {ADV, LAST, DELTA}.
-__device__ __forceinline__ uint32_t pal_index(const BrickCtx& c, uint32_t j, uint32_t o) {
-  const uint32_t w = j >> 5, lt = (1u << (j & 31u)) - 1u;
-  const uint32_t k = c.adv_pre[w] + __popc(c.adv_mask[w] & lt);
-  if (o == OP_ADV) {
-    if (k >= c.n_pal) { set_err(c.s_err, VC_ERR_CORRUPT); return 0; }
-    return k;
-  }
-  if (o == OP_LAST) {
-    if (k == 0) { set_err(c.s_err, VC_ERR_CORRUPT); return 0; }
-    return k - 1;
-  }
-  const uint32_t d = c.del_pre[w] + __popc(c.del_mask[w] & lt);
-  const uint32_t delta = d < c.dlist_cap ? c.dlist[d] : 0u;
-  if (delta == 0 || delta > k) { set_err(c.s_err, VC_ERR_CORRUPT); return 0; }
-  return k - delta;
-}
-
 __device__ __forceinline__ uint32_t label_of(const BrickCtx& c, uint32_t idx) {
   return idx < c.n_pal ? c.pal[idx] : 0u;
 }
