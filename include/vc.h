@@ -123,7 +123,7 @@ typedef struct vc_volume_info {
   uint32_t max_pal, max_sym, max_delta;
   uint64_t encoded_bytes;  /* bytes passed to vc_load_compressed */
   uint64_t device_bytes;   /* device memory owned by the volume */
-  uint32_t smem_bytes;     /* dynamic shared memory per thread block of the decoder */
+  uint32_t smem_bytes;     /* dynamic shared memory per thread block of the decoder (0 for b = 64) */
   uint32_t device;
 } vc_volume_info;
 
@@ -132,7 +132,9 @@ typedef struct vc_volume_info {
  * builds the decoder's per-volume tables (rANS slot table). The copy is enqueued on `cuda_stream`;
  * the call synchronises that stream before returning, so the caller may free `host_bytes` at once.
  * Errors: VC_ERR_ARG (NULL pointer), VC_ERR_FORMAT (invalid bytes), VC_ERR_UNSUPPORTED (a brick
- * needs more shared memory than a thread block has), VC_ERR_OOM, VC_ERR_CUDA. On error *out is
+ * of b <= 32 needs more shared memory than a thread block has, or a palette of 65520 entries or
+ * more), VC_ERR_OOM, VC_ERR_CUDA. Bricks of b = 64 are decoded with their working set in global
+ * scratch memory (about a megabyte per persistent thread block, allocated per decode call). On error *out is
  * NULL and nothing is leaked. (Paper: the compressed volume is uploaded to GPU memory once and
  * decoded on demand, Methods "Volcanite rendering".) */
 vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, void* cuda_stream,
@@ -154,7 +156,9 @@ typedef struct vc_schedule {
 /* Sets the schedule used by later decode calls on this volume (host only; not while a decode of
  * this volume is being enqueued from another thread). VC_ERR_UNSUPPORTED if the combination
  * is not built or its shared memory does not fit; the previous schedule then stays. The default
- * after loading is {256, 1, 0, 512}. */
+ * after loading is {256, 1, 0, 512} ({512, 1, 0, 512} for b = 64). For b = 64 every schedule runs
+ * one persistent kernel (blocks_per_sm, 0 = 2, blocks per SM, each with its own global scratch
+ * slice); stage_depth and chunk have no effect there. */
 vc_status vc_volume_set_schedule(vc_volume* vol, const vc_schedule* sched);
 vc_status vc_volume_get_schedule(const vc_volume* vol, vc_schedule* sched);
 
@@ -188,7 +192,8 @@ vc_status vc_volume_slot_words(const vc_volume* vol, uint32_t lod, uint32_t pale
  *   mode        VC_MODE_PLAIN, VC_MODE_GRID, VC_MODE_BATCHED or VC_MODE_PIPELINED (same output,
  *               optionally | VC_MODE_PALETTED except with the pipelined schedule;
  *               different schedule); the pipelined schedule uses the volume's own streams, so calls
- *               on one volume must not be enqueued from several host threads at once
+ *               on one volume must not be enqueued from several host threads at once; for b = 64
+ *               grid and pipelined run the batched schedule
  *   status_dev  device, VC_STATUS_WORDS int32 (see Conventions); the caller zeroes words 0..1 before
  *               the first call and reads them after synchronising; errors accumulate across calls
  * Returns VC_ERR_ARG for bad host-side arguments and VC_ERR_CUDA if a launch fails; stream-side
@@ -347,9 +352,11 @@ vc_status vc_brick_cache_stats_get(vc_brick_cache* c, vc_brick_cache_stats* out)
  * no library that allocates).
  *   Same arguments, output and status reporting as vc_decode_bricks, with mode VC_MODE_GRID or
  *   VC_MODE_BATCHED only (VC_ERR_ARG otherwise).
- *   Size limit: for rANS volumes, n x (16 * ceil(ceil(max_sym / 2) / 16) + 16) bytes must fit in
- *   VC_NOALLOC_WS_BYTES, else VC_ERR_ARG and nothing is enqueued; plain-coded volumes use no
- *   workspace and have no limit.
+ *   Size limit: for rANS volumes, n x (16 * ceil(ceil(max_sym / 2) / 16) + 16) bytes (rounded up
+ *   to 256) must fit in VC_NOALLOC_WS_BYTES, else VC_ERR_ARG and nothing is enqueued; plain-coded
+ *   volumes of b <= 32 use no workspace and have no limit. For b = 64 the rest of the array must
+ *   also hold at least one scratch slice of the decoder (VC_ERR_ARG otherwise); the persistent
+ *   grid is cut to the slices that fit.
  *   Zeroing: the workspace needs none; as for vc_decode_bricks, the caller zeroes status words
  *   0..1 before the first call.
  *   Set-up: the first call on a device (with that device current) looks up the array's device

@@ -151,7 +151,7 @@ void palette_packing(uint32_t max_pal, uint32_t* bits, uint32_t* per_word) {
 }
 
 bool schedule_supported(uint32_t L, uint32_t threads) {
-  if (L < 1 || L > 5) return false;
+  if (L < 1 || L > 6) return false;
   if (threads == 256) return true;
   return (threads == 512 || threads == 1024) && L >= 4;
 }
@@ -168,8 +168,10 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   const uint32_t ncells = ((1u << (3 * L)) - 1u) / 7u;  // levels 0..L-1
   uint32_t o = 0;
   s.misc_off = o; o += 1024;
+  // b = 64 bricks keep their regions in global scratch (see SmemLayout::gscratch)
+  const bool global = L >= 6;
   s.nwords = (v.max_nodes + 31u) / 32u + 2u;
-  s.mask_off = o; o += align16(12 * s.nwords);  // 2 u32 masks + 2 u16 prefixes per word
+  s.mask_off = o; o += align16((global ? 16 : 12) * s.nwords);  // 2 u32 masks + 2 prefixes per word
   s.nodes_words = (v.max_nodes + 7u) / 8u + 4u;
   s.nodes_off = o; o += v.max_delta ? align16(4 * s.nodes_words) : 0u;
   s.dlist_cap = v.max_delta;
@@ -187,7 +189,7 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   s.list1_cap = cap[1];
   s.list_off = o; o += align16(2u * (s.list0_cap + cap[1]));
   // the finest index grid holds one z half at a time for b = 32 (plus the last plane of the first)
-  const uint32_t nh = L >= 5 ? 2u : 1u;
+  const uint32_t nh = L == 5 ? 2u : 1u;
   s.fg_off = o;
   s.fg_bytes = align16(s.gt_bytes * b * b * b / nh);
   o += s.fg_bytes;
@@ -195,6 +197,18 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   // private palette copy (frees the stage early); 256 entries for byte grids
   s.pal_cap = s.gt_bytes == 1 ? 256u : (v.max_pal <= 1024u ? v.max_pal : 0u);
   s.pal_off = o; o += align16(4u * s.pal_cap);
+  if (global) {  // nothing staged: the record and symbols are read where they are
+    s.stage_bytes = 0;
+    s.nstage = nstage;
+    s.stage_off = o;
+    s.total = o;
+    s.gscratch = (o + 255u) & ~255u;
+    s.ws_stride = align16((v.max_sym + 1u) / 2u) + 16u;
+    s.a_buf = 0;
+    s.a_smem = 4u * kRansM;
+    *out = s;
+    return VC_OK;
+  }
   const uint32_t fixed = o;
   uint32_t stage = align16(v.max_stage) + 16u;  // slack for 8-nibble windows at the end
   if (fixed + nstage * stage > (uint32_t)optin) stage = 0;
@@ -286,7 +300,20 @@ vc_status launch_pipelined(Volume& v, Params P, uint32_t n, cudaStream_t stream)
   return rc;
 }
 
+// b = 64: persistent blocks of the scratch kernel, before the occupancy limit (blocks_per_sm, else
+// 2 per SM: each holds a scratch slice of about a megabyte)
+uint32_t scratch_grid(const Volume& v, uint32_t n) {
+  const uint32_t per_sm = v.sched.blocks_per_sm ? v.sched.blocks_per_sm : 2u;
+  return std::min(n, std::max(1u, v.sms) * per_sm);
+}
+
 }  // namespace
+
+size_t decode_ws_bytes(const Volume& v, uint32_t n) {
+  const SmemLayout& SL = v.dv.sm;
+  const size_t sym = v.coder == 1 ? ((size_t)n * SL.ws_stride + 255u) & ~size_t(255) : 0u;
+  return sym + (SL.gscratch ? (size_t)scratch_grid(v, n) * SL.gscratch : 0u);
+}
 
 vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
                         uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream) {
@@ -318,34 +345,47 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
     palette_packing(v.max_pal, &P.pal_bits, &P.pal_per);
     P.out_words = (edge * edge * edge + P.pal_per - 1u) / P.pal_per;
   }
+  const SmemLayout& SL = v.dv.sm;
+  const bool scratch = SL.gscratch != 0;
+  if (mode == VC_MODE_PIPELINED && ws_ext) return VC_ERR_ARG;  // it allocates its own workspaces
   // coarse levels of detail are written by the reconstruction kernel itself
-  if (mode == VC_MODE_PIPELINED && lod == 0) {
-    if (ws_ext) return VC_ERR_ARG;  // the pipelined schedule allocates its own workspaces
-    return launch_pipelined(v, P, n, stream);
-  }
-  if (mode == VC_MODE_PIPELINED) mode = VC_MODE_GRID;
+  if (mode == VC_MODE_PIPELINED && lod == 0 && !scratch) return launch_pipelined(v, P, n, stream);
+  // b = 64: one persistent kernel serves the grid, batched and pipelined schedules
+  if (mode == VC_MODE_PIPELINED || (scratch && mode == VC_MODE_GRID)) mode = scratch ? VC_MODE_BATCHED : VC_MODE_GRID;
   const bool batched = mode == VC_MODE_BATCHED;
   const uint32_t nt = v.sched.threads;
-  void* k = pick_kernel(v.L, nt, v.dv.sm.gt_bytes == 2, rans, batched);
+  void* k = pick_kernel(v.L, nt, SL.gt_bytes == 2, rans, batched);
   if (!k) return VC_ERR_UNSUPPORTED;
-  const uint32_t smem = v.dv.sm.total;
+  const uint32_t smem = scratch ? 0u : SL.total;
   if (!set_smem(k, smem)) return VC_ERR_CUDA;
-  uint8_t* ws = nullptr;      // allocated here (freed at the end)
-  if (rans && ws_ext) {       // caller-provided workspace: nothing is allocated or freed
-    if ((size_t)n * v.dv.sm.ws_stride > ws_cap) return VC_ERR_ARG;
-    P.ws = ws_ext;
-    if (!set_smem(reinterpret_cast<void*>(&rans_symbols_kernel), v.dv.sm.a_smem)) return VC_ERR_CUDA;
-  } else if (rans) {
-    if (cudaMallocAsync(reinterpret_cast<void**>(&ws), (size_t)n * v.dv.sm.ws_stride, stream) != cudaSuccess) {
+  if (rans && !set_smem(reinterpret_cast<void*>(&rans_symbols_kernel), SL.a_smem)) return VC_ERR_CUDA;
+  // workspace: the rANS symbols of the n items, then (b = 64) one scratch slice per block
+  const size_t sym_bytes = rans ? ((size_t)n * SL.ws_stride + 255u) & ~size_t(255) : 0u;
+  uint32_t sgrid = 0;
+  if (scratch) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)nt, 0) != cudaSuccess) return VC_ERR_CUDA;
+    if (per_sm < 1) return VC_ERR_UNSUPPORTED;
+    sgrid = std::min(scratch_grid(v, n), std::max(1u, v.sms) * (uint32_t)per_sm);
+    if (ws_ext) {
+      if (ws_cap < sym_bytes + SL.gscratch) return VC_ERR_ARG;
+      sgrid = (uint32_t)std::min<size_t>(sgrid, (ws_cap - sym_bytes) / SL.gscratch);
+    }
+  } else if (rans && ws_ext && (size_t)n * SL.ws_stride > ws_cap) {
+    return VC_ERR_ARG;
+  }
+  uint8_t* ws = nullptr;  // allocated here (freed at the end); none with a caller-provided workspace
+  uint8_t* wsb = ws_ext;
+  const size_t need = sym_bytes + (size_t)sgrid * SL.gscratch;
+  if (!ws_ext && need) {
+    if (cudaMallocAsync(reinterpret_cast<void**>(&ws), need, stream) != cudaSuccess) {
       cudaGetLastError();
       return VC_ERR_OOM;
     }
-    P.ws = ws;
-    if (!set_smem(reinterpret_cast<void*>(&rans_symbols_kernel), v.dv.sm.a_smem)) {
-      cudaFreeAsync(ws, stream);
-      return VC_ERR_CUDA;
-    }
+    wsb = ws;
   }
+  if (rans) P.ws = wsb;
+  uint8_t* scr = scratch ? wsb + sym_bytes : nullptr;
   vc_status rc = VC_OK;
   // timing events of this call (grid and batched schedules), if profiling is on and a set is free
   cudaEvent_t* ev = nullptr;
@@ -362,11 +402,25 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   };
   auto run = [&](dim3 grid) -> bool {
     void* args[] = {&P};
-    if (cudaLaunchKernel(k, grid, dim3(nt), args, smem, stream) != cudaSuccess) return false;
+    void* args_scratch[] = {&P, &scr};
+    if (cudaLaunchKernel(k, grid, dim3(nt), scratch ? args_scratch : args, smem, stream) != cudaSuccess) return false;
     ++v.launches;
     return true;
   };
-  if (mode == VC_MODE_PLAIN) {
+  auto reset_counter = [&]() {
+    return cudaMemsetAsync(reinterpret_cast<uint32_t*>(status) + 2, 0, sizeof(uint32_t), stream) == cudaSuccess;
+  };
+  if (scratch && mode == VC_MODE_PLAIN) {
+    for (uint32_t i = 0; i < n && rc == VC_OK; ++i) {
+      P.item_base = i;
+      P.n = i + 1u;
+      if (!run_symbols(i, 1) || !reset_counter() || !run(dim3(1))) rc = VC_ERR_CUDA;
+    }
+    P.n = n;
+  } else if (scratch) {
+    if (!mark(0) || !run_symbols(0, n) || !reset_counter() || !mark(1) || !run(dim3(sgrid)) || !mark(2))
+      rc = VC_ERR_CUDA;
+  } else if (mode == VC_MODE_PLAIN) {
     for (uint32_t i = 0; i < n && rc == VC_OK; ++i) {
       P.item_base = i;
       if (!run_symbols(i, 1) || !run(dim3(1))) rc = VC_ERR_CUDA;
@@ -383,9 +437,7 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
     } else {
       if (v.sched.blocks_per_sm) per_sm = std::min<int>(per_sm, (int)v.sched.blocks_per_sm);
       const uint32_t grid = std::min<uint32_t>(n, (uint32_t)(sms * per_sm));
-      if (!mark(0) || !run_symbols(0, n) ||
-          cudaMemsetAsync(reinterpret_cast<uint32_t*>(status) + 2, 0, sizeof(uint32_t), stream) != cudaSuccess ||
-          !mark(1) || !run(dim3(grid)) || !mark(2))
+      if (!mark(0) || !run_symbols(0, n) || !reset_counter() || !mark(1) || !run(dim3(grid)) || !mark(2))
         rc = VC_ERR_CUDA;
     }
   }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "vc_internal.h"
 
@@ -203,41 +204,56 @@ __device__ __forceinline__ uint32_t pack_nibbles(uint32_t x, uint32_t m) {
 }
 
 // A chunk summary for both entering states: bit s of e = the state after the chunk entered in
-// state s; nd_s = nodes | delta operations << 16 counted from entering state s.
+// state s; nd_s = nodes | delta operations << K counted from entering state s. ND is uint32_t with
+// K = 16 while node counts stay below 2^16 (b <= 32) and uint64_t with K = 32 beyond.
+template <typename ND>
 struct Fn2 {
-  uint32_t e, nd0, nd1;
+  uint32_t e;
+  ND nd0, nd1;
 };
-__device__ __forceinline__ Fn2 fn_then(const Fn2& p, const Fn2& c) {  // p, then c
+template <typename ND>
+__device__ __forceinline__ Fn2<ND> fn_id() {
+  return Fn2<ND>{2u, 0, 0};
+}
+template <typename ND>
+__device__ __forceinline__ Fn2<ND> fn_then(const Fn2<ND>& p, const Fn2<ND>& c) {  // p, then c
   const uint32_t p0 = p.e & 1u, p1 = (p.e >> 1) & 1u;
   const uint32_t c0 = c.e & 1u, c1 = (c.e >> 1) & 1u;
-  Fn2 r;
+  Fn2<ND> r;
   r.nd0 = p.nd0 + (p0 ? c.nd1 : c.nd0);
   r.nd1 = p.nd1 + (p1 ? c.nd1 : c.nd0);
   r.e = (p0 ? c1 : c0) | ((p1 ? c1 : c0) << 1);
   return r;
 }
-__device__ __forceinline__ Fn2 fn_shfl_up(const Fn2& f, uint32_t d) {
-  return Fn2{__shfl_up_sync(0xFFFFFFFFu, f.e, d), __shfl_up_sync(0xFFFFFFFFu, f.nd0, d),
-             __shfl_up_sync(0xFFFFFFFFu, f.nd1, d)};
+template <typename ND>
+__device__ __forceinline__ Fn2<ND> fn_shfl_up(const Fn2<ND>& f, uint32_t d) {
+  return Fn2<ND>{__shfl_up_sync(0xFFFFFFFFu, f.e, d), __shfl_up_sync(0xFFFFFFFFu, f.nd0, d),
+                 __shfl_up_sync(0xFFFFFFFFu, f.nd1, d)};
 }
 
 // Builds nodes[] (8 operation symbols per u32) and dlist[] (first-entry nibble index of each delta
 // operation) from the symbol stream. Each thread takes a contiguous run of stream words: it
 // summarises the run for both entering states, a block-wide scan of the summaries gives every run
 // its entering state and its node and delta bases, and the runs then write their operation
-// nibbles. scan_tmp: 3 (NT / 32) + 3 words. wst (may be NULL): one word per stream word, where the
-// first pass leaves each word's automaton masks for the second. Node counts must stay below 2^16
-// (b <= 32).
-template <int NT>
+// nibbles. scan_tmp: 5 (NT / 32) + 5 words (8-byte aligned). wst (may be NULL): one word per
+// stream word, where the first pass leaves each word's automaton masks for the second. WIDE counts
+// nodes in 32 bits (needed from 2^16 nodes on, b = 64), otherwise in 16.
+template <int NT, bool WIDE>
 __device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes, uint32_t nodes_words,
                                  uint32_t* dlist, uint32_t dcap, uint32_t* scan_tmp, uint32_t* wst, int* s_err) {
+  using ND = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+  using F = Fn2<ND>;
+  constexpr uint32_t K = WIDE ? 32u : 16u;
+  constexpr ND NMASK = WIDE ? (ND)0xFFFFFFFFu : (ND)0xFFFFu;
   constexpr uint32_t NW = NT / 32;
+  ND* tnd = reinterpret_cast<ND*>(scan_tmp);  // [2 (NW + 1)] node / delta counts
+  uint32_t* te = scan_tmp + 2 * (NW + 1) * (sizeof(ND) / 4);  // [NW + 1] exit states
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t T = (S + 7u) >> 3;  // stream words
   const uint32_t WP = (T + NT - 1) / NT;
   const uint32_t w0 = min(tid * WP, T), w1 = min(w0 + WP, T);
   // 1. this run's summary for entering state 0 and 1
-  Fn2 f{2u, 0u, 0u};  // identity
+  F f = fn_id<ND>();
   {
     uint32_t s0 = 0, s1 = 1;
     for (uint32_t w = w0; w < w1; ++w) {
@@ -247,46 +263,47 @@ __device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes
       word_states(x, D, A, B);
       const uint32_t m0 = word_ops(A, B, s0, nv, &e0), m1 = word_ops(A, B, s1, nv, &e1);
       if (wst) wst[w] = m0 | (m1 << 8) | (D << 16);  // this word's operations on both paths
-      f.nd0 += __popc(m0) | (__popc(m0 & D) << 16);
-      f.nd1 += __popc(m1) | (__popc(m1 & D) << 16);
+      f.nd0 += (ND)__popc(m0) | ((ND)__popc(m0 & D) << K);
+      f.nd1 += (ND)__popc(m1) | ((ND)__popc(m1 & D) << K);
       s0 = e0;
       s1 = e1;
     }
     f.e = s0 | (s1 << 1);
   }
   // 2. exclusive scan of the summaries over the block (warp shuffles, then the warp totals)
-  Fn2 inc = f;
+  F inc = f;
 #pragma unroll
   for (uint32_t d = 1; d < 32; d <<= 1) {
-    const Fn2 p = fn_shfl_up(inc, d);
+    const F p = fn_shfl_up(inc, d);
     if (lane >= d) inc = fn_then(p, inc);
   }
-  if (lane == 31) { scan_tmp[3 * warp] = inc.e; scan_tmp[3 * warp + 1] = inc.nd0; scan_tmp[3 * warp + 2] = inc.nd1; }
+  if (lane == 31) { te[warp] = inc.e; tnd[2 * warp] = inc.nd0; tnd[2 * warp + 1] = inc.nd1; }
   __syncthreads();
   if (warp == 0) {
-    Fn2 v = lane < NW ? Fn2{scan_tmp[3 * lane], scan_tmp[3 * lane + 1], scan_tmp[3 * lane + 2]} : Fn2{2u, 0u, 0u};
-    Fn2 vi = v;
+    F v = lane < NW ? F{te[lane], tnd[2 * lane], tnd[2 * lane + 1]} : fn_id<ND>();
+    F vi = v;
 #pragma unroll
     for (uint32_t d = 1; d < NW; d <<= 1) {
-      const Fn2 p = fn_shfl_up(vi, d);
+      const F p = fn_shfl_up(vi, d);
       if (lane >= d) vi = fn_then(p, vi);
     }
-    Fn2 ex = fn_shfl_up(vi, 1);
-    if (lane == 0) ex = Fn2{2u, 0u, 0u};
+    F ex = fn_shfl_up(vi, 1);
+    if (lane == 0) ex = fn_id<ND>();
     __syncwarp();
-    if (lane < NW) { scan_tmp[3 * lane] = ex.e; scan_tmp[3 * lane + 1] = ex.nd0; scan_tmp[3 * lane + 2] = ex.nd1; }
-    if (lane == NW - 1) { scan_tmp[3 * NW] = vi.e; scan_tmp[3 * NW + 1] = vi.nd0; }
+    if (lane < NW) { te[lane] = ex.e; tnd[2 * lane] = ex.nd0; tnd[2 * lane + 1] = ex.nd1; }
+    if (lane == NW - 1) { te[NW] = vi.e; tnd[2 * NW] = vi.nd0; }
   }
   __syncthreads();
-  Fn2 pre = fn_shfl_up(inc, 1);
-  if (lane == 0) pre = Fn2{2u, 0u, 0u};
-  pre = fn_then(Fn2{scan_tmp[3 * warp], scan_tmp[3 * warp + 1], scan_tmp[3 * warp + 2]}, pre);
+  F pre = fn_shfl_up(inc, 1);
+  if (lane == 0) pre = fn_id<ND>();
+  pre = fn_then(F{te[warp], tnd[2 * warp], tnd[2 * warp + 1]}, pre);
   uint32_t st = pre.e & 1u;  // the stream starts in state 0
   const uint32_t path = st;  // which of the two paths of the first pass this run takes
-  uint32_t j = pre.nd0 & 0xFFFFu, d = pre.nd0 >> 16;
-  const uint32_t total_e = scan_tmp[3 * NW] & 1u, total_nd = scan_tmp[3 * NW + 1];
+  uint32_t j = (uint32_t)(pre.nd0 & NMASK), d = (uint32_t)(pre.nd0 >> K);
+  const uint32_t total_e = te[NW] & 1u;
+  const ND total_nd = tnd[2 * NW];
   // the node words this run shares with its neighbours start at zero
-  const uint32_t jend = j + ((st ? f.nd1 : f.nd0) & 0xFFFFu);
+  const uint32_t jend = j + (uint32_t)((st ? f.nd1 : f.nd0) & NMASK);
   if ((j >> 3) < nodes_words) nodes[j >> 3] = 0u;
   if ((jend >> 3) < nodes_words) nodes[jend >> 3] = 0u;
   __syncthreads();
@@ -330,8 +347,8 @@ __device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes
   if ((j & 7u) && (j >> 3) < nodes_words) atomicOr(&nodes[j >> 3], (uint32_t)acc);
   if (tid == 0 && total_e != 0) set_err(s_err, VC_ERR_CORRUPT);  // the stream ends inside a delta entry chain
   ParseOut out;
-  out.n_nodes = total_nd & 0xFFFFu;
-  out.n_delta = total_nd >> 16;
+  out.n_nodes = (uint32_t)(total_nd & NMASK);
+  out.n_delta = (uint32_t)(total_nd >> K);
   __syncthreads();
   return out;
 }
@@ -343,8 +360,6 @@ struct BrickCtx {
   uint32_t n_nodes;
   const uint32_t* adv_mask;
   const uint32_t* del_mask;
-  const uint16_t* adv_pre;  // palette advances before node 32 w (< 2^16: n_pal < 65520)
-  const uint16_t* del_pre;  // delta operations before node 32 w (< 2^16 for b <= 32)
   const uint32_t* dlist;
   uint32_t dlist_cap;
   uint32_t op_mask;
@@ -392,7 +407,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   uint32_t* misc = reinterpret_cast<uint32_t*>(sm + SL.misc_off);
   uint32_t* wtot = misc + 16;      // NW warp totals (words 16..47)
-  uint32_t* scan_tmp = misc + 48;  // 3 NW + 3 words (48..255)
+  uint32_t* scan_tmp = misc + 48;  // 5 NW + 5 words (48..255), 8-byte aligned
 
   const uint32_t n_pal = head[0], S = head[1], nd = head[3];
   const uint32_t ns = RANS ? (S < 32u ? S : 32u) : 0u;
@@ -422,7 +437,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     // the general parse path borrows the finest grid (not in use yet) for its summaries
     // the finest grid is idle during the parse: it keeps the per-word automaton masks
     uint32_t* wst = ((S + 7u) >> 3) * 4u <= SL.fg_bytes ? reinterpret_cast<uint32_t*>(sm + SL.fg_off) : nullptr;
-    const ParseOut po = parse_stream<NT>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap, scan_tmp, wst, s_err);
+    const ParseOut po = parse_stream<NT, (L >= 6)>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap, scan_tmp, wst, s_err);
     c.nodes = nodes;
     c.n_nodes = po.n_nodes;
     if (po.n_delta != nd) set_err(s_err, VC_ERR_CORRUPT);
@@ -434,9 +449,11 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   // 2. palette-cursor masks and prefix counts (32 nodes per word)
   uint32_t* adv_mask = reinterpret_cast<uint32_t*>(sm + SL.mask_off);
   uint32_t* del_mask = adv_mask + SL.nwords;
-  uint16_t* adv_pre = reinterpret_cast<uint16_t*>(adv_mask + 2 * SL.nwords);
-  uint16_t* del_pre = adv_pre + SL.nwords;
-  c.adv_mask = adv_mask; c.del_mask = del_mask; c.adv_pre = adv_pre; c.del_pre = del_pre;
+  // prefix counts: 16 bits while a brick has fewer than 2^16 nodes (b <= 32), 32 bits beyond
+  using Pre = typename std::conditional<(L >= 6), uint32_t, uint16_t>::type;
+  Pre* adv_pre = reinterpret_cast<Pre*>(adv_mask + 2 * SL.nwords);
+  Pre* del_pre = adv_pre + SL.nwords;
+  c.adv_mask = adv_mask; c.del_mask = del_mask;
   {
     const uint32_t nw32 = (c.n_nodes + 31u) >> 5;
     const uint32_t per = (nw32 + NT - 1) / NT;
@@ -459,7 +476,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     uint32_t pa, pd, ta, td;
     block_scan2<NT>(sa, sd, pa, pd, ta, td, scan_tmp);
     for (uint32_t w = a0; w < a1; ++w) {
-      adv_pre[w] = (uint16_t)pa; del_pre[w] = (uint16_t)pd;
+      adv_pre[w] = (Pre)pa; del_pre[w] = (Pre)pd;
       pa += __popc(adv_mask[w]); pd += __popc(del_mask[w]);
     }
     if (tid == 0 && (ta != n_pal || td != nd)) set_err(s_err, VC_ERR_CORRUPT);
@@ -656,7 +673,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     if (tid == 0 && off + 8u * npar != c.n_nodes) set_err(s_err, VC_ERR_CORRUPT);
     const GT* Gp = G + gofs_prev;
     constexpr uint32_t pcells = 1u << (3 * (L - 1));
-    constexpr uint32_t NH = L >= 5 ? 2u : 1u;  // z halves
+    constexpr uint32_t NH = L == 5 ? 2u : 1u;  // z halves (b = 64 works in global scratch: one)
     constexpr uint32_t hcells = pcells / NH;                 // level-(L-1) cells per half
     constexpr uint32_t hvox = b * b * b / NH;                // voxels per half
     constexpr uint32_t PC = (hcells + NT - 1) / NT;
@@ -676,7 +693,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
 #pragma unroll 1
     for (uint32_t h = 0; h < NH; ++h) {
       const uint32_t rb = h ? rsplit : 0u, re = (h + 1 < NH) ? rsplit : npar;
-#pragma unroll
+#pragma unroll(PC <= 16u ? PC : 8u)
       for (uint32_t k = 0; k < PC; ++k) {
         const uint32_t pl = tid + k * NT;  // with NT a power of two, pl's bits are tid's plus k * NT's
         const uint32_t p = h * hcells + pl;
@@ -1033,6 +1050,38 @@ __global__ void __launch_bounds__(NT) decode_batched_kernel(const __grid_constan
       __syncthreads();  // every thread is done with stage[0] before it is refilled
       if (tid == 0) claim_and_issue(0);
     }
+  }
+}
+
+// b = 64: the working set of one brick (about a megabyte: nodes, masks, grids) is beyond shared
+// memory, so each persistent block keeps its regions in its own slice (P.v.sm.gscratch bytes) of
+// a global-memory scratch buffer, largely L2-resident, and reads the record and symbols where they
+// are. Blocks pull items from the work counter in status[2] (items item_base + counter).
+template <int L, typename GT, bool RANS, int NT>
+__global__ void __launch_bounds__(NT) decode_scratch_kernel(const __grid_constant__ Params P, uint8_t* scratch) {
+  __shared__ int s_err;
+  __shared__ uint32_t s_item;
+  unsigned char* sm = scratch + (size_t)blockIdx.x * P.v.sm.gscratch;
+  uint32_t* counter = reinterpret_cast<uint32_t*>(P.status) + 2;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_item = P.item_base + atomicAdd(counter, 1u);
+      s_err = 0;
+    }
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= P.n) break;
+    const uint32_t brick = P.ids[item];
+    if (brick >= P.v.n_bricks) {
+      if (threadIdx.x == 0) report(P.status, VC_ERR_ARG, item);
+    } else {
+      const ItemSrc src = item_src<RANS>(P, item, brick);
+      uint32_t* out = P.cache + (size_t)P.slots[item] * P.out_words;
+      decode_brick<L, GT, RANS, NT>(P, src.rec, src.stream, out, sm, &s_err, [] {});
+      __syncthreads();
+      if (threadIdx.x == 0 && s_err) report(P.status, s_err, item);
+    }
+    __syncthreads();  // s_item and s_err are taken over by the next item
   }
 }
 

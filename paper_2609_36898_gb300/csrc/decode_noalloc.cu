@@ -62,7 +62,7 @@ extern "C" vc_status vc_decode_bricks_noalloc(vc_volume* vol, const uint32_t* br
   const uint32_t base_mode = mode & ~VC_MODE_PALETTED;
   if (lod > v->L || (base_mode != VC_MODE_GRID && base_mode != VC_MODE_BATCHED)) return VC_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(cache) & 15u) return VC_ERR_ARG;
-  if (v->coder == 1 && (size_t)n * v->dv.sm.ws_stride > kNoAllocWsBytes) return VC_ERR_ARG;
+  if (v->coder == 1 && (size_t)n * v->dv.sm.ws_stride > kNoAllocWsBytes) return VC_ERR_ARG;  // more checks in the launch
   DeviceGuard g(v->device);
   uint8_t* ws = nullptr;
   const vc_status rc = workspace_for(v->device, &ws);

@@ -10,8 +10,13 @@ namespace {
 
 template <int L, typename GT, bool RANS>
 void* kernel_for(bool batched) {
-  return batched ? reinterpret_cast<void*>(&dev::decode_batched_kernel<L, GT, RANS, VC_NT>)
-                 : reinterpret_cast<void*>(&dev::decode_grid_kernel<L, GT, RANS, VC_NT>);
+  if constexpr (L >= 6) {
+    (void)batched;  // one kernel for every schedule
+    return reinterpret_cast<void*>(&dev::decode_scratch_kernel<L, GT, RANS, VC_NT>);
+  } else {
+    return batched ? reinterpret_cast<void*>(&dev::decode_batched_kernel<L, GT, RANS, VC_NT>)
+                   : reinterpret_cast<void*>(&dev::decode_grid_kernel<L, GT, RANS, VC_NT>);
+  }
 }
 
 }  // namespace
@@ -31,6 +36,7 @@ void* VC_CAT(pick_kernel_nt, VC_NT)(uint32_t L, bool gt16, bool rans, bool batch
 #endif
     VC_PICK(4)
     VC_PICK(5)
+    VC_PICK(6)
     default:
       return nullptr;
   }

@@ -275,7 +275,7 @@ bool launch_batch(Server* s) {
     for (size_t g = 0; g < ng; ++g) {
       ws_off[g] = need;
       const Volume& v = *s->volumes[batch.groups[g].vol];
-      if (v.coder == 1) need += ((size_t)batch.groups[g].count * v.dv.sm.ws_stride + 255) & ~size_t(255);
+      need += (decode_ws_bytes(v, batch.groups[g].count) + 255) & ~size_t(255);
     }
     if (need > B.ws_cap) {  // grow outside any capture
       cudaStreamSynchronize(B.stream);
@@ -297,7 +297,7 @@ bool launch_batch(Server* s) {
   for (size_t g = 0; ok && g < ng; ++g) {
     const Group& G = batch.groups[g];
     Volume& v = *s->volumes[G.vol];
-    if (graphs && v.coder == 1)
+    if (graphs && decode_ws_bytes(v, G.count) != 0)  // rANS symbols or b = 64 scratch
       ok = launch_decode_ws(v, B.d_ids + G.first, G.count, B.d_slots + G.first, reinterpret_cast<uint32_t*>(s->d_cache),
                             G.lod, VC_MODE_BATCHED, B.d_status + VC_STATUS_WORDS * g, B.stream, B.d_ws + ws_off[g],
                             B.ws_cap - ws_off[g]) == VC_OK;

@@ -181,7 +181,14 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   if (!v->h_rec_words) { delete v; return VC_ERR_OOM; }
   for (uint32_t i = 0; i < n_bricks; ++i) v->h_rec_words[i] = le32(st + 4 * ((size_t)i + 1)) - le32(st + 4 * (size_t)i);
   v->encoded_bytes = nbytes;
-  v->sched.threads = 256;
+  v->sched.threads = L >= 6 ? 512 : 256;  // b = 64: more threads per (much larger) brick
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    std::free(v->h_rec_words);
+    delete v;
+    return VC_ERR_CUDA;
+  }
+  v->sms = (uint32_t)sms;
   v->sched.stage_depth = 1;
   v->sched.blocks_per_sm = 0;
   v->sched.chunk = 512;
@@ -259,7 +266,7 @@ vc_status vc_volume_info_get(const vc_volume* vol, vc_volume_info* info) {
   info->max_delta = v->max_delta;
   info->encoded_bytes = v->encoded_bytes;
   info->device_bytes = v->device_bytes;
-  info->smem_bytes = v->dv.sm.total;
+  info->smem_bytes = v->dv.sm.gscratch ? 0u : v->dv.sm.total;
   info->device = (uint32_t)v->device;
   return VC_OK;
 }

@@ -31,7 +31,7 @@ struct SmemLayout {
   uint32_t nstage;       // 1 or 2 buffers (2 = prefetch the next brick in the batched kernel)
   uint32_t nodes_off;    // node-indexed operation symbols, 8 per u32 (delta bricks only)
   uint32_t nodes_words;
-  uint32_t mask_off;     // adv_mask, del_mask (nwords u32 each), adv_pre, del_pre (nwords u16 each)
+  uint32_t mask_off;     // adv_mask, del_mask (nwords u32 each), adv_pre, del_pre (nwords u16 each; u32 for b = 64)
   uint32_t nwords;
   uint32_t dlist_off;    // delta values of the brick's delta operations
   uint32_t dlist_cap;
@@ -47,6 +47,8 @@ struct SmemLayout {
   uint32_t pal_cap;      // entries it can hold (0 = palettes are read from the stage)
   uint32_t gt_bytes;     // 1 (max_pal < 252) or 2
   uint32_t total;
+  uint32_t gscratch;     // 0: the regions are in shared memory; else b = 64: they are in a global
+                         // scratch slice of this many bytes per thread block (no shared memory)
   // rANS symbol kernel
   uint32_t ws_stride;    // bytes of decoded symbols per request item (workspace)
   uint32_t a_buf;        // per-warp coded-word buffer bytes
@@ -71,6 +73,7 @@ struct Volume {
   int device;
   uint32_t dims[3];
   uint32_t L, op_mask, coder, flags, n_bricks, nb[3];
+  uint32_t sms;          // multiprocessors of the device
   uint32_t max_pal, max_sym, max_delta, max_rec_words, max_stage;
   uint32_t max_nodes;    // max over bricks of S - n_delta (every delta operation has an entry): bounds nodes
   uint64_t encoded_bytes, device_bytes;
@@ -118,8 +121,12 @@ bool schedule_supported(uint32_t L, uint32_t threads);
 vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, SmemLayout* out);
 vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
                         uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream);
-// Same, with the rANS symbol workspace supplied by the caller (ws_ext, ws_cap bytes, 16-byte
-// aligned) instead of allocated: VC_ERR_ARG if n items need more than ws_cap or mode is pipelined.
+// Workspace bytes a decode of n items may use (rANS symbols, then b = 64 scratch slices); 0 if none.
+size_t decode_ws_bytes(const Volume& v, uint32_t n);
+// Same as launch_decode, with the workspace supplied by the caller (ws_ext, ws_cap bytes, 256-byte
+// aligned) instead of allocated: VC_ERR_ARG if the rANS symbols of n items (plus one scratch slice
+// for b = 64) need more than ws_cap or mode is pipelined. For b = 64 the persistent grid shrinks to
+// the scratch slices that fit.
 vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
                            uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream, uint8_t* ws_ext,
                            size_t ws_cap);

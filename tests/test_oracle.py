@@ -42,7 +42,7 @@ def small_volume():
 
 # ---------------------------------------------------------------- round trip (lossless)
 
-@pytest.mark.parametrize("log2b", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("log2b", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("coder", [oracle.CODER_PLAIN, oracle.CODER_RANS])
 def test_roundtrip_lossless(small_volume, log2b, coder):
     enc = oracle.encode_volume(small_volume, log2b, coder=coder)
@@ -163,7 +163,7 @@ def test_emitted_node_labels_are_the_mode_pyramid(small_volume):
 
 @pytest.mark.parametrize("coder", [oracle.CODER_PLAIN, oracle.CODER_RANS])
 def test_coarse_lod_is_mode_pyramid(small_volume, coder):
-    for log2b in (2, 3, 4, 5):
+    for log2b in (2, 3, 4, 5, 6):
         b = 1 << log2b
         enc = oracle.encode_volume(small_volume, log2b, coder=coder)
         for bid in range(oracle.header(enc)["n_bricks"]):
