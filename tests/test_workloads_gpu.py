@@ -79,10 +79,10 @@ def test_uneven_power_diagram_volume_full_size_subset():
 
 
 def test_mixed_volumes_poisson_serving():
-    # the 8 volumes of the mixed workload at 128^3 (64^3 bricks are beyond this build: 32^3 instead)
+    # the 8 volumes of the mixed workload at 128^3 (brick sizes 16, 32 and 64)
     specs = []
     for sp in synth.c5():
-        b = min(sp.brick, 32)
+        b = sp.brick
         specs.append((synth.VolumeSpec(dims=(128, 128, 128), grid=sp.grid, seed=sp.seed, lam=sp.lam, bg=sp.bg, brick=b,
                                        name=sp.name + "_128"), b))
     vols, encs = [], []
