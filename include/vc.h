@@ -125,8 +125,6 @@ typedef struct vc_volume_info {
   uint64_t device_bytes;   /* device memory owned by the volume */
   uint32_t smem_bytes;     /* dynamic shared memory per thread block of the decoder (0 for b = 64) */
   uint32_t device;
-  uint32_t ws_bytes_per_item; /* rANS: decode workspace per request item (the symbol kernel's split
-                                 stream: operations and delta values); 0 for plain volumes */
 } vc_volume_info;
 
 /* Parses and validates `nbytes` host bytes of a VCZ1 volume (header, Brick Starts, every record's
@@ -354,8 +352,8 @@ vc_status vc_brick_cache_stats_get(vc_brick_cache* c, vc_brick_cache_stats* out)
  * no library that allocates).
  *   Same arguments, output and status reporting as vc_decode_bricks, with mode VC_MODE_GRID or
  *   VC_MODE_BATCHED only (VC_ERR_ARG otherwise).
- *   Size limit: for rANS volumes, n x vc_volume_info.ws_bytes_per_item bytes (rounded up to 256)
- *   must fit in VC_NOALLOC_WS_BYTES, else VC_ERR_ARG and nothing is enqueued; plain-coded
+ *   Size limit: for rANS volumes, n x (16 * ceil(ceil(max_sym / 2) / 16) + 16) bytes (rounded up
+ *   to 256) must fit in VC_NOALLOC_WS_BYTES, else VC_ERR_ARG and nothing is enqueued; plain-coded
  *   volumes of b <= 32 use no workspace and have no limit. For b = 64 the rest of the array must
  *   also hold at least one scratch slice of the decoder (VC_ERR_ARG otherwise); the persistent
  *   grid is cut to the slices that fit.

@@ -53,7 +53,6 @@ class vc_volume_info(ctypes.Structure):
         ("device_bytes", ctypes.c_uint64),
         ("smem_bytes", ctypes.c_uint32),
         ("device", ctypes.c_uint32),
-        ("ws_bytes_per_item", ctypes.c_uint32),
     ]
 
 

@@ -49,104 +49,17 @@ namespace {
 using namespace dev;
 
 // ------------------------------------------------------------------------------------------
-// Four bytes, each < 16, to four nibbles.
-__device__ __forceinline__ uint32_t bytes_to_nibbles(uint32_t x) {
-  x = (x | (x >> 4)) & 0x00FF00FFu;
-  return (x | (x >> 8)) & 0x0000FFFFu;
-}
-
-// Splits the symbols into node operations and delta values as the coder emits them, 32 per step
-// in lane order. The stream alternates between operations and the entries of the delta
-// operations (Methods, "Compressed segmentation volumes"): after a delta operation, entries
-// follow while their bit 3 (continuation) is set; a delta is the entries' low 3 bits, most
-// significant first, at most 7 entries (more is invalid, value 0). Operations are packed 8 per
-// u32 through a 64-byte ring per warp in shared memory; delta values are written as they close.
-struct OpSink {
-  uint32_t* ops;       // operation words, capacity ops_words
-  uint32_t ops_words;
-  uint32_t* dvals;     // delta values, capacity nd
-  uint32_t nd;
-  uint8_t* ring;
-  uint32_t nn = 0;     // operations so far
-  uint32_t dcnt = 0;   // delta values so far
-  uint32_t chain = 0;  // 1 while inside a delta's entries
-  uint32_t pv = 0, pn = 0;  // the open delta's value and entry count
-
-  __device__ __forceinline__ void step(uint32_t s, bool active, uint32_t lane) {
-    const uint32_t Am = __ballot_sync(0xFFFFFFFFu, active);
-    const uint32_t Dm = __ballot_sync(0xFFFFFFFFu, active && (s & 7u) == 6u);  // delta operation if an op
-    const uint32_t Em = __ballot_sync(0xFFFFFFFFu, active && !(s & 8u));       // ends an entry chain
-    uint32_t entries = 0, pos = 0;
-#pragma unroll 1
-    while (pos < 32u) {  // pos: the first lane not yet classified (uniform)
-      if (chain) {
-        const uint32_t endm = Em & (0xFFFFFFFFu << pos);
-        const uint32_t q = endm ? (uint32_t)__ffs(endm) - 1u : 32u;  // the closing entry
-        const uint32_t last = q < 32u ? q : 31u;
-#pragma unroll 1
-        for (uint32_t l = pos; l <= last; ++l) {
-          const uint32_t v = __shfl_sync(0xFFFFFFFFu, s, l);
-          if (!((Am >> l) & 1u)) break;
-          entries |= 1u << l;
-          pv = (pv << 3) | (v & 7u);
-          ++pn;
-        }
-        if (q >= 32u) break;  // continues in the next step (or runs past the stream: corrupt)
-        if (lane == 0 && dcnt < nd) dvals[dcnt] = pn <= 7u ? pv : 0u;
-        ++dcnt;
-        chain = 0;
-        pos = q + 1u;
-        continue;
-      }
-      const uint32_t cand = Dm & (0xFFFFFFFFu << pos);
-      if (!cand) break;
-      pos = (uint32_t)__ffs(cand);  // the delta operation's lane + 1: its entries start here
-      chain = 1;
-      pv = 0;
-      pn = 0;
-    }
-    const uint32_t om = Am & ~entries;
-    if ((om >> lane) & 1u) ring[(nn + __popc(om & lanemask_lt())) & 63u] = (uint8_t)s;
-    const uint32_t nn2 = nn + __popc(om);
-    __syncwarp();
-    const uint32_t w = (nn >> 3) + lane;  // operation words completed by this step (at most 4)
-    if (w < (nn2 >> 3) && w < ops_words) {
-      const uint2 b = *reinterpret_cast<const uint2*>(ring + ((8u * w) & 63u));
-      ops[w] = bytes_to_nibbles(b.x) | (bytes_to_nibbles(b.y) << 16);
-    }
-    __syncwarp();
-    nn = nn2;
-  }
-
-  // Flushes the last partial word and writes the item header; true if the stream ended outside
-  // an entry chain with exactly nd delta operations.
-  __device__ __forceinline__ bool finish(uint32_t lane, uint32_t* hdr) {
-    const uint32_t w = nn >> 3;
-    if ((nn & 7u) && lane == 0 && w < ops_words) {
-      const uint2 b = *reinterpret_cast<const uint2*>(ring + ((8u * w) & 63u));
-      const uint32_t x = bytes_to_nibbles(b.x) | (bytes_to_nibbles(b.y) << 16);
-      ops[w] = x & ((1u << (4u * (nn & 7u))) - 1u);
-    }
-    const uint32_t nodes = nn < 8u * ops_words ? nn : 8u * ops_words;
-    if (lane == 0) {
-      hdr[0] = nodes;
-      hdr[1] = dcnt;
-      hdr[2] = 0u;
-      hdr[3] = 0u;
-    }
-    return chain == 0 && dcnt == nd && nn <= 8u * ops_words;
-  }
-};
-
 // rANS symbols: one warp per request item. Table entry per slot: freq | (slot - cum) << 13 |
 // symbol << 25. Full steps of 32 symbols run without bounds checks; the last step is guarded.
 // Returns true if the stream was consumed exactly and every state ended at 2^16. The coded words
 // flow through a register window: lane l holds words wb + l, wb + 32 + l (in use) and the next two
 // runs of 32 (loads in flight), so the global-memory latency stays off the state chain.
 __device__ __forceinline__ bool rans_steps(const uint32_t* tab, const uint16_t* words, uint32_t nw, uint32_t S,
-                                           uint32_t x, uint32_t ns, OpSink& sink, uint32_t lane) {
+                                           uint32_t x, uint32_t ns, uint8_t* out, uint32_t lane) {
   const uint32_t lt = lanemask_lt();
   const uint32_t full = S & ~31u;
+  uint8_t* o = out + (lane >> 1);
+  const bool even = !(lane & 1u);
   auto ld = [&](uint32_t i) -> uint32_t { return i < nw ? (uint32_t)__ldg(words + i) : 0u; };
   uint32_t wb = 0, w0 = ld(lane), w1 = ld(32u + lane), w2 = ld(64u + lane), w3 = ld(96u + lane);
   uint32_t ptr = 0;  // words consumed; ptr - wb < 32 between steps
@@ -175,13 +88,16 @@ __device__ __forceinline__ bool rans_steps(const uint32_t* tab, const uint16_t* 
   for (uint32_t base = 0; base < full; base += 32u) {
     uint32_t s = 0;
     step(true, s);
-    sink.step(s, true, lane);
+    const uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, s, 1);
+    if (even) o[base >> 1] = (uint8_t)(s | (hi << 4));
   }
   if (full < S) {
-    const bool active = full + lane < S;
+    const uint32_t i = full + lane;
+    const bool active = i < S;
     uint32_t s = 0;
     step(active, s);
-    sink.step(s, active, lane);
+    const uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, s, 1);
+    if (active && even) o[full >> 1] = (uint8_t)(s | (i + 1 < S ? hi << 4 : 0u));
   }
   bad |= ptr != nw;
   bad |= lane < ns && x != (1u << 16);
@@ -201,23 +117,16 @@ __global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_kernel(const __g
   const uint32_t brick = P.ids[item];
   if (brick >= P.v.n_bricks) return;  // reported by the reconstruction kernel
   const uint32_t* rec = P.v.records + P.v.starts[brick];
-  const uint32_t np = rec[0], S = rec[1], cb = rec[2], nd = rec[3];
+  const uint32_t np = rec[0], S = rec[1], cb = rec[2];
   const uint32_t ns = S < 32u ? S : 32u;
   const uint32_t nw = cb >> 1;
   const uint32_t x0 = lane < ns ? rec[4 + lane] : (1u << 16);
   const bool bad_state = __any_sync(0xFFFFFFFFu, lane < ns && x0 < (1u << 16));
-  uint32_t* hdr = reinterpret_cast<uint32_t*>(ws + (size_t)(item - P.ws_item0) * SL.ws_stride);
-  OpSink sink;
-  sink.ops = hdr + 4;
-  sink.ops_words = ops_cap_words(S, nd);
-  sink.dvals = sink.ops + sink.ops_words;
-  sink.nd = nd;
-  sink.ring = sm + 4u * kRansM + 64u * warp;
+  uint8_t* out = ws + (size_t)(item - P.ws_item0) * SL.ws_stride;
   const uint32_t cofs = 16u + 4u * ns + 4u * np;
   const bool ok = rans_steps(tab, reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(rec) + cofs),
-                             nw, S, x0, ns, sink, lane);
-  const bool split_ok = sink.finish(lane, hdr);
-  if ((!ok || bad_state || !split_ok) && lane == 0) report(P.status, VC_ERR_CORRUPT, item);
+                             nw, S, x0, ns, out, lane);
+  if ((!ok || bad_state) && lane == 0) report(P.status, VC_ERR_CORRUPT, item);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -263,13 +172,10 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   const bool global = L >= 6;
   s.nwords = (v.max_nodes + 31u) / 32u + 2u;
   s.mask_off = o; o += align16((global ? 16 : 12) * s.nwords);  // 2 u32 masks + 2 prefixes per word
-  // the in-kernel parse (plain volumes; rANS volumes arrive split by the symbol kernel): node
-  // operations and delta values
-  const bool parse = v.coder == 0 && v.max_delta != 0;
   s.nodes_words = (v.max_nodes + 7u) / 8u + 4u;
-  s.nodes_off = o; o += parse ? align16(4 * s.nodes_words) : 0u;
-  s.dlist_cap = parse ? v.max_delta : 0u;
-  s.dlist_off = o; o += align16(4 * (parse ? v.max_delta : 1u));
+  s.nodes_off = o; o += v.max_delta ? align16(4 * s.nodes_words) : 0u;
+  s.dlist_cap = v.max_delta;
+  s.dlist_off = o; o += align16(4 * (v.max_delta ? v.max_delta : 1u));
   s.g_off = o; o += align16(s.gt_bytes * (ncells + 7u));  // level 1 starts at cell 8 (alignment)
   // per level l >= 1 below L, one byte per level-(l-1) cell: its children's stop-0 bits
   const uint32_t ns_bytes = ((1u << (3 * (L - 1))) - 1u) / 7u;
@@ -297,9 +203,9 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
     s.stage_off = o;
     s.total = o;
     s.gscratch = (o + 255u) & ~255u;
-    s.ws_stride = align16(v.max_ws_item) + 16u;
+    s.ws_stride = align16((v.max_sym + 1u) / 2u) + 16u;
     s.a_buf = 0;
-    s.a_smem = 4u * kRansM + 64u * kRansWarps;
+    s.a_smem = 4u * kRansM;
     *out = s;
     return VC_OK;
   }
@@ -311,11 +217,10 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   s.stage_off = o; o += nstage * stage;
   s.total = o;
   if (s.total > (uint32_t)optin) return VC_ERR_UNSUPPORTED;
-  // rANS symbol kernel: the slot table and a 64-byte operation ring per warp (many blocks per SM
-  // hide the step latency); per item, operations and delta values (16 bytes of slack after them)
-  s.ws_stride = align16(v.max_ws_item) + 16u;
+  // rANS symbol kernel: table + one coded-word buffer per warp
+  s.ws_stride = align16((v.max_sym + 1u) / 2u) + 16u;
   s.a_buf = 0;
-  s.a_smem = 4u * kRansM + 64u * kRansWarps;
+  s.a_smem = 4u * kRansM;  // the slot table only: many blocks per SM hide the step latency
   *out = s;
   return VC_OK;
 }

@@ -24,7 +24,7 @@ struct Params {
   uint32_t lod;
   int32_t* status;
   uint32_t item_base;
-  const uint8_t* ws;  // rANS: operations and delta values per item, ws_stride bytes each (else nullptr)
+  const uint8_t* ws;  // decoded rANS symbols, ws_stride bytes per item (nullptr for plain volumes)
   uint32_t ws_item0;  // the workspaces hold items ws_item0 .. (a chunk of the request)
   uint32_t out_words; // u32 words per cache slot
   uint32_t pal_bits;  // 0: labels; else cache paletting: pal_bits-bit palette indices,
@@ -394,9 +394,8 @@ __device__ __forceinline__ void store_pair(GT* fg, uint32_t pos, uint32_t lo, ui
 
 // ------------------------------------------------------------------------------------------
 // Decode one brick. head: the record (header, [states], palette) in shared or global memory;
-// sw: plain volumes: its symbols as packed nibbles (u32 aligned); rANS: the split stream the
-// symbol kernel left (see ops_cap_words); out: the slot, (b >> lod)^3 labels or packed palette
-// indices (P.pal_bits).
+// sw: its symbols as packed nibbles (u32 aligned); out: the slot, (b >> lod)^3 labels or packed
+// palette indices (P.pal_bits).
 // on_stage_free() is called by every thread exactly once, as soon as the staged record is no longer
 // read: right after the finest grid is filled when the palette fits its shared copy, else at the end.
 template <int L, typename GT, bool RANS, int NT, typename Hook>
@@ -430,14 +429,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   c.dlist_cap = nd < SL.dlist_cap ? nd : SL.dlist_cap;
 
   // 1. operations per node
-  if (RANS) {
-    // the symbol kernel has split the stream: [n_nodes, n_delta, 0, 0], the operations, the
-    // delta values (its checks went to the status buffer)
-    c.n_nodes = sw[0];
-    c.nodes = sw + 4;
-    c.dlist = sw + 4 + ops_cap_words(S, nd);
-    c.dlist_cap = nd;
-  } else if (nd == 0) {
+  if (nd == 0) {
     c.nodes = sw;
     c.n_nodes = S;
   } else {
@@ -554,7 +546,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
             v[o] = k - 1u;
           } else {
             const uint32_t di = dd0 + __popc(del8 & below);
-            const uint32_t delta = di < c.dlist_cap ? c.dlist[di] : 0u;
+            const uint32_t delta = di < c.dlist_cap ? dlist[di] : 0u;
             bad |= delta == 0u || delta > k;
             v[o] = k - delta;
           }
@@ -903,9 +895,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // Where one request item's data lives: the record, and the bytes to stage in shared memory.
 struct ItemSrc {
   const uint32_t* rec;     // record in global memory
-  const uint32_t* stream;  // symbols (plain: in the record) or the split stream (rANS: workspace)
+  const uint32_t* stream;  // symbols in global memory (record for plain, workspace for rANS)
   uint32_t head_bytes;     // staged head (whole record for plain)
-  uint32_t stream_bytes;   // staged operations and delta values after the head (rANS only)
+  uint32_t stream_bytes;   // staged symbols after the head (rANS only)
 };
 
 template <bool RANS>
@@ -914,11 +906,11 @@ __device__ __forceinline__ ItemSrc item_src(const Params& P, uint32_t item, uint
   const uint32_t a = P.v.starts[brick], e = P.v.starts[brick + 1];
   s.rec = P.v.records + a;
   if (RANS) {
-    const uint32_t np = s.rec[0], S = s.rec[1], nd = s.rec[3];
+    const uint32_t np = s.rec[0], S = s.rec[1];
     const uint32_t ns = S < 32u ? S : 32u;
     s.head_bytes = (16u + 4u * ns + 4u * np + 15u) & ~15u;
     s.stream = reinterpret_cast<const uint32_t*>(P.ws + (size_t)(item - P.ws_item0) * P.v.sm.ws_stride);
-    s.stream_bytes = item_ws_bytes(S, nd);
+    s.stream_bytes = (((S + 1u) >> 1) + 15u) & ~15u;
   } else {
     s.head_bytes = (e - a) * 4u;
     s.stream = s.rec + 4u + s.rec[0];

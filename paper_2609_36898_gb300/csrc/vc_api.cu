@@ -132,7 +132,7 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   // Brick Starts and every record's sizes
   const uint8_t* st = p + kHeaderBytes;
   const uint8_t* rec = p + rec_off;
-  uint32_t max_pal = 0, max_sym = 0, max_delta = 0, max_words = 0, max_stage = 0, max_nodes = 0, max_ws_item = 0;
+  uint32_t max_pal = 0, max_sym = 0, max_delta = 0, max_words = 0, max_stage = 0, max_nodes = 0;
   std::vector<uint8_t> bflags(n_bricks, 0);
   uint32_t prev = le32(st);
   if (prev != 0) return VC_ERR_FORMAT;
@@ -153,13 +153,11 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
     max_delta = std::max(max_delta, nd);
     max_nodes = std::max(max_nodes, S - nd);
     max_words = std::max(max_words, e - a);
-    // bytes the reconstruction kernel stages: the record (plain), or its head and the operations
-    // and delta values the symbol kernel left (rANS)
+    // bytes the reconstruction kernel stages: the record (plain), or its head and decoded symbols (rANS)
     const uint32_t stage = coder == 0 ? 4 * (e - a)
                                       : (uint32_t)(((16 + 4 * ns + 4 * (uint64_t)n_pal) + 15) & ~15ull) +
-                                            item_ws_bytes(S, nd);
+                                            (((S + 1) / 2 + 15) & ~15u);
     max_stage = std::max(max_stage, stage);
-    if (coder == 1) max_ws_item = std::max(max_ws_item, item_ws_bytes(S, nd));
     const uint8_t* pal = r + 16 + 4 * ns;
     for (uint32_t k = 0; k < n_pal; ++k) bflags[i] |= le32(pal + 4 * (size_t)k) == 0 ? 1u : 2u;
   }
@@ -179,7 +177,6 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   v->max_pal = max_pal; v->max_sym = max_sym; v->max_delta = max_delta; v->max_rec_words = max_words;
   v->max_stage = max_stage;
   v->max_nodes = max_nodes;
-  v->max_ws_item = max_ws_item;
   v->h_rec_words = static_cast<uint32_t*>(std::malloc(4 * (size_t)n_bricks + 4));
   if (!v->h_rec_words) { delete v; return VC_ERR_OOM; }
   for (uint32_t i = 0; i < n_bricks; ++i) v->h_rec_words[i] = le32(st + 4 * ((size_t)i + 1)) - le32(st + 4 * (size_t)i);
@@ -271,7 +268,6 @@ vc_status vc_volume_info_get(const vc_volume* vol, vc_volume_info* info) {
   info->device_bytes = v->device_bytes;
   info->smem_bytes = v->dv.sm.gscratch ? 0u : v->dv.sm.total;
   info->device = (uint32_t)v->device;
-  info->ws_bytes_per_item = v->coder == 1 ? v->dv.sm.ws_stride : 0u;
   return VC_OK;
 }
 

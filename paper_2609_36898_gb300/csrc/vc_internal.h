@@ -23,17 +23,6 @@ constexpr uint32_t kHandleCache = 0x43484331u;   // "CHC1"
 constexpr uint32_t kRansWarps = 16u;      // bricks (warps) per block of the rANS symbol kernel
 constexpr uint32_t kRing = 3u;            // pipelined schedule: workspace slots (chunks in flight)
 
-// rANS volumes: the symbol kernel leaves each request item's symbols already split into node
-// operations and delta values, in its workspace slot: u32 [n_nodes, n_delta, 0, 0], then the
-// operations (8 per u32) in ops_cap_words(S, nd) words (S - nd bounds the node count: every delta
-// operation has at least one entry), then nd delta values (u32, 0 = invalid).
-__host__ __device__ inline uint32_t ops_cap_words(uint32_t S, uint32_t nd) {
-  return (((S - nd + 7u) >> 3) + 3u) & ~3u;
-}
-__host__ __device__ inline uint32_t item_ws_bytes(uint32_t S, uint32_t nd) {
-  return 16u + 4u * ops_cap_words(S, nd) + ((4u * nd + 15u) & ~15u);
-}
-
 // Byte offsets of the reconstruction kernel's shared-memory regions (one brick per block).
 struct SmemLayout {
   uint32_t misc_off;     // error flag, items, counters, mbarriers, warp totals, scan scratch (1 KiB)
@@ -61,7 +50,7 @@ struct SmemLayout {
   uint32_t gscratch;     // 0: the regions are in shared memory; else b = 64: they are in a global
                          // scratch slice of this many bytes per thread block (no shared memory)
   // rANS symbol kernel
-  uint32_t ws_stride;    // workspace bytes per request item (rANS: operations and delta values)
+  uint32_t ws_stride;    // bytes of decoded symbols per request item (workspace)
   uint32_t a_buf;        // per-warp coded-word buffer bytes
   uint32_t a_smem;       // dynamic shared memory per block
 };
@@ -87,7 +76,6 @@ struct Volume {
   uint32_t sms;          // multiprocessors of the device
   uint32_t max_pal, max_sym, max_delta, max_rec_words, max_stage;
   uint32_t max_nodes;    // max over bricks of S - n_delta (every delta operation has an entry): bounds nodes
-  uint32_t max_ws_item;  // rANS: max over bricks of item_ws_bytes
   uint64_t encoded_bytes, device_bytes;
   vc_schedule sched;     // threads per block, staging depth, persistent blocks per SM, chunk
   cudaStream_t aux[2];   // pipelined schedule: symbol and reconstruction streams

@@ -21,6 +21,10 @@ def torch():
     return t
 
 
+def _ws_stride(max_sym: int) -> int:
+    return 16 * (((max_sym + 1) // 2 + 15) // 16) + 16
+
+
 @pytest.mark.parametrize("coder", [1, 0])
 @pytest.mark.parametrize("mode", ["grid", "batched"])
 def test_noalloc_matches_decode_bricks_twice_in_a_row(torch, coder, mode):
@@ -63,8 +67,7 @@ def test_noalloc_rejects_requests_beyond_its_workspace(torch):
     enc = vc.vc_encode_volume(V, 5, op_mask=0x7F, coder=1)
     vol = vc.Volume(enc)
     info = vc.vc_volume_info_get(vol.handle)
-    stride = int(info.ws_bytes_per_item)
-    assert stride > 0
+    stride = _ws_stride(int(info.max_sym))
     n_max = VC_NOALLOC_WS_BYTES // stride
     ids = torch.zeros(n_max + 1, dtype=torch.int32, device="cuda")
     cache = torch.zeros((n_max + 1) * vol.b ** 3, dtype=torch.int32, device="cuda")
