@@ -167,13 +167,19 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   const uint32_t b = 1u << L;
   const uint32_t ncells = ((1u << (3 * L)) - 1u) / 7u;  // levels 0..L-1
   uint32_t o = 0;
-  s.misc_off = o; o += 1024;
+  // misc: words 0..15 (flags, items, mbarriers), 16..47 warp totals, then 5 (NT / 32) + 5 words of
+  // scan scratch
+  s.misc_off = o; o += align16(4u * (48u + 5u * (threads / 32u) + 5u));
   // b = 64 bricks keep their regions in global scratch (see SmemLayout::gscratch)
   const bool global = L >= 6;
   s.nwords = (v.max_nodes + 31u) / 32u + 2u;
   s.mask_off = o; o += align16((global ? 16 : 12) * s.nwords);  // 2 u32 masks + 2 prefixes per word
+  // node operations: written by the parse; bricks without delta operations use their staged
+  // symbols directly, or a copy here when the stage lies in the finest grid's region
+  const bool pal_always_copied = s.gt_bytes == 1 || v.max_pal <= 1024u;
+  const bool stage_in_fg = nstage == 1 && pal_always_copied && !global;
   s.nodes_words = (v.max_nodes + 7u) / 8u + 4u;
-  s.nodes_off = o; o += v.max_delta ? align16(4 * s.nodes_words) : 0u;
+  s.nodes_off = o; o += (v.max_delta || stage_in_fg) ? align16(4 * s.nodes_words) : 0u;
   s.dlist_cap = v.max_delta;
   s.dlist_off = o; o += align16(4 * (v.max_delta ? v.max_delta : 1u));
   s.g_off = o; o += align16(s.gt_bytes * (ncells + 7u));  // level 1 starts at cell 8 (alignment)
@@ -194,10 +200,16 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   s.fg_bytes = align16(s.gt_bytes * b * b * b / nh);
   o += s.fg_bytes;
   s.plane_off = o; o += nh == 2 ? align16(s.gt_bytes * b * b) : 0u;
-  // private palette copy (frees the stage early); 256 entries for byte grids
-  s.pal_cap = s.gt_bytes == 1 ? 256u : (v.max_pal <= 1024u ? v.max_pal : 0u);
+  // private palette copy (frees the stage early); byte grids: a power of two >= max_pal (indices
+  // are masked with pal_cap - 1, so any byte stays in bounds)
+  uint32_t p2 = 16u;
+  while (p2 < v.max_pal) p2 <<= 1;
+  s.pal_cap = s.gt_bytes == 1 ? p2 : (v.max_pal <= 1024u ? v.max_pal : 0u);
   s.pal_off = o; o += align16(4u * s.pal_cap);
   if (global) {  // nothing staged: the record and symbols are read where they are
+    s.stage_in_fg = 0;
+    s.wst_off = s.fg_off;
+    s.wst_bytes = s.fg_bytes;
     s.stage_bytes = 0;
     s.nstage = nstage;
     s.stage_off = o;
@@ -211,10 +223,22 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   }
   const uint32_t fixed = o;
   uint32_t stage = align16(v.max_stage) + 16u;  // slack for 8-nibble windows at the end
-  if (fixed + nstage * stage > (uint32_t)optin) stage = 0;
-  s.stage_bytes = stage;
+  s.wst_off = s.fg_off;
+  s.wst_bytes = s.fg_bytes;
   s.nstage = nstage;
-  s.stage_off = o; o += nstage * stage;
+  if (stage_in_fg && stage <= s.fg_bytes) {
+    // one stage at the start of the finest grid's region, the parse's masks after it
+    s.stage_in_fg = 1;
+    s.stage_bytes = stage;
+    s.stage_off = s.fg_off;
+    s.wst_off = s.fg_off + stage;
+    s.wst_bytes = s.fg_bytes - stage;
+  } else {
+    if (fixed + nstage * stage > (uint32_t)optin) stage = 0;
+    s.stage_in_fg = 0;
+    s.stage_bytes = stage;
+    s.stage_off = o; o += nstage * stage;
+  }
   s.total = o;
   if (s.total > (uint32_t)optin) return VC_ERR_UNSUPPORTED;
   // rANS symbol kernel: table + one coded-word buffer per warp

@@ -429,14 +429,21 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   c.dlist_cap = nd < SL.dlist_cap ? nd : SL.dlist_cap;
 
   // 1. operations per node
-  if (nd == 0) {
+  if (nd == 0 && SL.stage_in_fg) {
+    // the symbols are the operations; copied out of the stage, which the finest grid overwrites
+    uint32_t* nodes = reinterpret_cast<uint32_t*>(sm + SL.nodes_off);
+    const uint32_t nw = min((S + 7u) / 8u + 2u, SL.nodes_words);
+    for (uint32_t i = tid; i < nw; i += NT) nodes[i] = sw[i];
+    c.nodes = nodes;
+    c.n_nodes = S;
+    __syncthreads();
+  } else if (nd == 0) {
     c.nodes = sw;
     c.n_nodes = S;
   } else {
     uint32_t* nodes = reinterpret_cast<uint32_t*>(sm + SL.nodes_off);
-    // the general parse path borrows the finest grid (not in use yet) for its summaries
-    // the finest grid is idle during the parse: it keeps the per-word automaton masks
-    uint32_t* wst = ((S + 7u) >> 3) * 4u <= SL.fg_bytes ? reinterpret_cast<uint32_t*>(sm + SL.fg_off) : nullptr;
+    // the finest grid's region is idle during the parse: it keeps the per-word automaton masks
+    uint32_t* wst = ((S + 7u) >> 3) * 4u <= SL.wst_bytes ? reinterpret_cast<uint32_t*>(sm + SL.wst_off) : nullptr;
     const ParseOut po = parse_stream<NT, (L >= 6)>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap, scan_tmp, wst, s_err);
     c.nodes = nodes;
     c.n_nodes = po.n_nodes;
@@ -742,7 +749,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
         }
       }
       __syncthreads();
-      if (pal_copied && h + 1 == NH) on_stage_free();
+      if (pal_copied && !SL.stage_in_fg && h + 1 == NH) on_stage_free();
       constexpr uint32_t quads = hvox / 4u;
       uint32_t* outh = out + h * hvox;
       // resolves the neighbour marks of voxel pos (at most three hops)
@@ -789,12 +796,14 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
         }
       } else if constexpr (sizeof(GT) == 1) {
         if (pal_copied) {
-          // byte grid and a 256-entry palette copy: every index is in bounds, marks are resolved
+          // byte grid and a zero-padded power-of-two palette copy: masked indices stay in bounds,
+          // marks are resolved
           const uint32_t* fg32 = reinterpret_cast<const uint32_t*>(fg);
+          const uint32_t pm = SL.pal_cap - 1u;
 #pragma unroll 4
           for (uint32_t q = tid; q < quads; q += NT) {
             const uint32_t x = fg32[q];
-            store16(outh + 4u * q, c.pal[x & 0xFFu], c.pal[(x >> 8) & 0xFFu], c.pal[(x >> 16) & 0xFFu], c.pal[x >> 24]);
+            store16(outh + 4u * q, c.pal[x & pm], c.pal[(x >> 8) & pm], c.pal[(x >> 16) & pm], c.pal[(x >> 24) & pm]);
           }
         } else {
           const uint32_t* fg32 = reinterpret_cast<const uint32_t*>(fg);
@@ -852,7 +861,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
       out[0] = label_of(c, Gl[0]);
     }
   }
-  if (!finest || !pal_copied) {
+  if (!finest || !pal_copied || SL.stage_in_fg) {
     __syncthreads();
     on_stage_free();
   }
@@ -920,8 +929,11 @@ __device__ __forceinline__ ItemSrc item_src(const Params& P, uint32_t item, uint
 }
 
 // One thread block per request item (grid and per-brick schedules).
+// 256-thread blocks are held to 48 registers so that five fit an SM (40 warps)
+constexpr int min_blocks(int NT) { return NT == 256 ? 5 : 1; }
+
 template <int L, typename GT, bool RANS, int NT>
-__global__ void __launch_bounds__(NT) decode_grid_kernel(const __grid_constant__ Params P) {
+__global__ void __launch_bounds__(NT, min_blocks(NT)) decode_grid_kernel(const __grid_constant__ Params P) {
   extern __shared__ __align__(128) unsigned char sm[];
   const SmemLayout& SL = P.v.sm;
   int* s_err = reinterpret_cast<int*>(sm + SL.misc_off);
@@ -959,7 +971,7 @@ __global__ void __launch_bounds__(NT) decode_grid_kernel(const __grid_constant__
 // decoded, the next brick's record (and symbols) are already being copied into the other stage
 // buffer by the TMA engine.
 template <int L, typename GT, bool RANS, int NT>
-__global__ void __launch_bounds__(NT) decode_batched_kernel(const __grid_constant__ Params P) {
+__global__ void __launch_bounds__(NT, min_blocks(NT)) decode_batched_kernel(const __grid_constant__ Params P) {
   extern __shared__ __align__(128) unsigned char sm[];
   const SmemLayout& SL = P.v.sm;
   uint32_t* misc = reinterpret_cast<uint32_t*>(sm + SL.misc_off);

@@ -25,8 +25,10 @@ constexpr uint32_t kRing = 3u;            // pipelined schedule: workspace slots
 
 // Byte offsets of the reconstruction kernel's shared-memory regions (one brick per block).
 struct SmemLayout {
-  uint32_t misc_off;     // error flag, items, counters, mbarriers, warp totals, scan scratch (1 KiB)
+  uint32_t misc_off;     // error flag, items, counters, mbarriers, warp totals, scan scratch
   uint32_t stage_off;    // staged record (plain) or record head + decoded symbols (rANS)
+  uint32_t stage_in_fg;  // 1: the (single) stage lies inside the finest grid's region, which is idle
+                         // until the stream has been parsed; the stage is then free only at the end
   uint32_t stage_bytes;  // per buffer; 0 = read from global memory
   uint32_t nstage;       // 1 or 2 buffers (2 = prefetch the next brick in the batched kernel)
   uint32_t nodes_off;    // node-indexed operation symbols, 8 per u32 (delta bricks only)
@@ -40,11 +42,14 @@ struct SmemLayout {
   uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each; one z half for b = 32)
   uint32_t plane_off;    // b = 32: the last z plane of the first half (for -z neighbours of the second)
   uint32_t fg_bytes;     // bytes of the finest grid region
+  uint32_t wst_off;      // the parse's per-word automaton masks (inside the finest grid's region)
+  uint32_t wst_bytes;
   uint32_t list_off;     // stop-0 cells by rank (u16), two buffers: even / odd levels
   uint32_t list0_cap;    // entries of the even-level buffer
   uint32_t list1_cap;    // entries of the odd-level buffer
   uint32_t pal_off;      // private copy of the brick's palette
-  uint32_t pal_cap;      // entries it can hold (0 = palettes are read from the stage)
+  uint32_t pal_cap;      // entries it can hold (0 = palettes are read from the stage); byte grids: a
+                         // power of two >= max_pal, zero padded (indices are masked with pal_cap - 1)
   uint32_t gt_bytes;     // 1 (max_pal < 252) or 2
   uint32_t total;
   uint32_t gscratch;     // 0: the regions are in shared memory; else b = 64: they are in a global
