@@ -172,16 +172,18 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   s.misc_off = o; o += align16(4u * (48u + 5u * (threads / 32u) + 5u));
   // b = 64 bricks keep their regions in global scratch (see SmemLayout::gscratch)
   const bool global = L >= 6;
-  s.nwords = (v.max_nodes + 31u) / 32u + 2u;
-  s.mask_off = o; o += align16((global ? 16 : 12) * s.nwords);  // 2 u32 masks + 2 prefixes per word
-  // node operations: written by the parse; bricks without delta operations use their staged
-  // symbols directly, or a copy here when the stage lies in the finest grid's region
+  // a single stage may alias the regions a brick fills only after its parse (see stage_alias)
   const bool pal_always_copied = s.gt_bytes == 1 || v.max_pal <= 1024u;
-  const bool stage_in_fg = nstage == 1 && pal_always_copied && !global;
+  const bool may_alias = nstage == 1 && pal_always_copied && !global;
+  // node operations: written by the parse; bricks without delta operations use their staged
+  // symbols directly, or a copy here when the stage is aliased
   s.nodes_words = (v.max_nodes + 7u) / 8u + 4u;
-  s.nodes_off = o; o += (v.max_delta || stage_in_fg) ? align16(4 * s.nodes_words) : 0u;
+  s.nodes_off = o; o += (v.max_delta || may_alias) ? align16(4 * s.nodes_words) : 0u;
   s.dlist_cap = v.max_delta;
   s.dlist_off = o; o += align16(4 * (v.max_delta ? v.max_delta : 1u));
+  // cursor masks, level grids, stop bytes and rank lists: one contiguous span
+  s.nwords = (v.max_nodes + 31u) / 32u + 2u;
+  s.mask_off = o; o += align16((global ? 16 : 12) * s.nwords);  // 2 u32 masks + 2 prefixes per word
   s.g_off = o; o += align16(s.gt_bytes * (ncells + 7u));  // level 1 starts at cell 8 (alignment)
   // per level l >= 1 below L, one byte per level-(l-1) cell: its children's stop-0 bits
   const uint32_t ns_bytes = ((1u << (3 * (L - 1))) - 1u) / 7u;
@@ -194,6 +196,7 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   s.list0_cap = (cap[0] + 7u) & ~7u;
   s.list1_cap = cap[1];
   s.list_off = o; o += align16(2u * (s.list0_cap + cap[1]));
+  const uint32_t span_bytes = o - s.mask_off;
   // the finest index grid holds one z half at a time for b = 32 (plus the last plane of the first)
   const uint32_t nh = L == 5 ? 2u : 1u;
   s.fg_off = o;
@@ -207,7 +210,7 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   s.pal_cap = s.gt_bytes == 1 ? p2 : (v.max_pal <= 1024u ? v.max_pal : 0u);
   s.pal_off = o; o += align16(4u * s.pal_cap);
   if (global) {  // nothing staged: the record and symbols are read where they are
-    s.stage_in_fg = 0;
+    s.stage_alias = 0;
     s.wst_off = s.fg_off;
     s.wst_bytes = s.fg_bytes;
     s.stage_bytes = 0;
@@ -226,16 +229,14 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   s.wst_off = s.fg_off;
   s.wst_bytes = s.fg_bytes;
   s.nstage = nstage;
-  if (stage_in_fg && stage <= s.fg_bytes) {
-    // one stage at the start of the finest grid's region, the parse's masks after it
-    s.stage_in_fg = 1;
+  if (may_alias && stage <= span_bytes) {
+    // one stage over the masks .. rank lists span
+    s.stage_alias = 1;
     s.stage_bytes = stage;
-    s.stage_off = s.fg_off;
-    s.wst_off = s.fg_off + stage;
-    s.wst_bytes = s.fg_bytes - stage;
+    s.stage_off = s.mask_off;
   } else {
     if (fixed + nstage * stage > (uint32_t)optin) stage = 0;
-    s.stage_in_fg = 0;
+    s.stage_alias = 0;
     s.stage_bytes = stage;
     s.stage_off = o; o += nstage * stage;
   }

@@ -429,8 +429,8 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   c.dlist_cap = nd < SL.dlist_cap ? nd : SL.dlist_cap;
 
   // 1. operations per node
-  if (nd == 0 && SL.stage_in_fg) {
-    // the symbols are the operations; copied out of the stage, which the finest grid overwrites
+  if (nd == 0 && SL.stage_alias) {
+    // the symbols are the operations; copied out of the stage, which step 2 overwrites
     uint32_t* nodes = reinterpret_cast<uint32_t*>(sm + SL.nodes_off);
     const uint32_t nw = min((S + 7u) / 8u + 2u, SL.nodes_words);
     for (uint32_t i = tid; i < nw; i += NT) nodes[i] = sw[i];
@@ -451,6 +451,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     // delta values from their entries, one delta operation per thread (visible after the barriers
     // of step 2)
     for (uint32_t d = tid; d < c.dlist_cap; d += NT) dlist[d] = read_delta(sw, dlist[d], S);
+    if (SL.stage_alias) __syncthreads();  // the stage is read up to here; step 2 overwrites it
   }
 
   // 2. palette-cursor masks and prefix counts (32 nodes per word)
@@ -749,7 +750,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
         }
       }
       __syncthreads();
-      if (pal_copied && !SL.stage_in_fg && h + 1 == NH) on_stage_free();
+      if (pal_copied && h + 1 == NH) on_stage_free();
       constexpr uint32_t quads = hvox / 4u;
       uint32_t* outh = out + h * hvox;
       // resolves the neighbour marks of voxel pos (at most three hops)
@@ -861,7 +862,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
       out[0] = label_of(c, Gl[0]);
     }
   }
-  if (!finest || !pal_copied || SL.stage_in_fg) {
+  if (!finest || !pal_copied) {
     __syncthreads();
     on_stage_free();
   }

@@ -27,8 +27,9 @@ constexpr uint32_t kRing = 3u;            // pipelined schedule: workspace slots
 struct SmemLayout {
   uint32_t misc_off;     // error flag, items, counters, mbarriers, warp totals, scan scratch
   uint32_t stage_off;    // staged record (plain) or record head + decoded symbols (rANS)
-  uint32_t stage_in_fg;  // 1: the (single) stage lies inside the finest grid's region, which is idle
-                         // until the stream has been parsed; the stage is then free only at the end
+  uint32_t stage_alias;  // 1: the (single) stage lies over the masks .. rank lists span, which a
+                         // brick fills only after its parse and no longer reads once its finest
+                         // level is decoded (the next brick's copy then lands there)
   uint32_t stage_bytes;  // per buffer; 0 = read from global memory
   uint32_t nstage;       // 1 or 2 buffers (2 = prefetch the next brick in the batched kernel)
   uint32_t nodes_off;    // node-indexed operation symbols, 8 per u32 (delta bricks only)
@@ -42,7 +43,7 @@ struct SmemLayout {
   uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each; one z half for b = 32)
   uint32_t plane_off;    // b = 32: the last z plane of the first half (for -z neighbours of the second)
   uint32_t fg_bytes;     // bytes of the finest grid region
-  uint32_t wst_off;      // the parse's per-word automaton masks (inside the finest grid's region)
+  uint32_t wst_off;      // the parse's per-word automaton masks (the finest grid's region)
   uint32_t wst_bytes;
   uint32_t list_off;     // stop-0 cells by rank (u16), two buffers: even / odd levels
   uint32_t list0_cap;    // entries of the even-level buffer
