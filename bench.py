@@ -30,8 +30,9 @@ B_LOG2 = 5
 CODER_RANS = 1
 METRIC = "decoded Gvoxel/s"
 UNIT = "Gvoxel/s"
-KERNEL_NAME = {"grid": "decode_grid_kernel<L=5,u8 grid,rANS,256 threads>",
-               "batched": "decode_batched_kernel<L=5,u8 grid,rANS,256 threads>"}
+def kernel_name(mode: str, threads: int) -> str:
+    return f"decode_{mode}_kernel<L=5,u8 grid,rANS,{threads} threads>"
+
 WORKLOAD = "512^3 uint32 Voronoi volume (~20k cells, 10% background), 32^3 bricks (4096), rANS, all operations"
 
 
@@ -138,12 +139,13 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel_src_hash: str):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "decode_batched_512cube_b32_rans.json")
+def ncu_traffic(kernel_src_hash: str, mode: str, threads: int):
+    """DRAM bytes per launch from the committed ncu summary of this schedule's kernel, if taken on
+    the current kernel source."""
+    p = os.path.join(ROOT, "profiles", f"decode_{mode}_512cube_b32_rans.json")
     try:
         d = json.load(open(p))
-        if d.get("kernel_source_sha256") == kernel_src_hash:
+        if d.get("kernel_source_sha256") == kernel_src_hash and d.get("kernel") == kernel_name(mode, threads):
             return d.get("dram_bytes_per_launch_full_workload")
     except Exception:
         pass
@@ -466,7 +468,18 @@ def run_ours(args):
     status = torch.zeros(vc.VC_STATUS_WORDS, dtype=torch.int32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    mode = vc.MODES[args.mode]
+    if args.mode == "auto":
+        # the library's autotuner picks the schedule (grid or batched, threads per brick, staging
+        # depth, blocks per SM) on this very request, before the warm-up
+        sched, mode, _ = vc.vc_volume_autotune(vol.handle, ids.data_ptr(), n, ids.data_ptr(), cache.data_ptr(), 0,
+                                               status.data_ptr(), stream.cuda_stream, reps=3)
+        torch.cuda.synchronize()
+        status.zero_()
+        mode_name = next(k for k in ("grid", "batched") if vc.MODES[k] == mode)
+    else:
+        mode_name = args.mode
+        mode = vc.MODES[mode_name]
+    sched = vc.vc_volume_get_schedule(vol.handle)
 
     def step():
         vc.vc_decode_bricks(vol.handle, ids.data_ptr(), n, ids.data_ptr(), cache.data_ptr(), 0, mode,
@@ -519,7 +532,7 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
     achieved = algo / recon_s / 1e9
     step_achieved = algo / (dev_s / args.steps) / 1e9
-    traffic = ncu_traffic(kernel_hash())
+    traffic = ncu_traffic(kernel_hash(), mode_name, sched[0])
 
     # other schedules on the same data (context): plain = one launch per brick, grid = one launch
     # (the one-launch-per-brick schedule runs on the first 512 bricks only, to bound launch counts)
@@ -543,7 +556,7 @@ def run_ours(args):
     # cache paletting (packed palette indices instead of u32 labels), same bricks, batched schedule
     pw, pbits, pper = vc.vc_volume_slot_words(vol.handle, 0, True)
     pcache = torch.empty(n * pw, dtype=torch.int32, device=dev)
-    pm = vc.MODES[args.mode] | vc.VC_MODE_PALETTED
+    pm = mode | vc.VC_MODE_PALETTED
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     vc.vc_decode_bricks(vol.handle, ids.data_ptr(), n, ids.data_ptr(), pcache.data_ptr(), 0, pm, status.data_ptr(),
                         stream.cuda_stream)
@@ -603,12 +616,14 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1000.0 * dev_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "bricks_per_step": n, "voxels_per_step": vox_per_step,
-                       "schedule": args.mode, "encoded_bytes": int(enc.size),
+                       "schedule": mode_name, "autotuned": args.mode == "auto",
+                       "threads_per_brick": sched[0], "stage_depth": sched[1], "blocks_per_sm": sched[2],
+                       "encoded_bytes": int(enc.size),
                        "bits_per_voxel": 8.0 * enc.size / V.size, "l2": "flushed before every step (256 MiB write)",
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_launch": algo, "kernel": KERNEL_NAME[args.mode],
+                         "algorithmic_bytes_per_launch": algo, "kernel": kernel_name(mode_name, sched[0]),
                          "kernel_ms": 1000.0 * recon_s, "symbol_kernel_ms": 1000.0 * symbol_s,
                          "step_achieved": step_achieved, "step_frac": step_achieved / peak},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
@@ -636,7 +651,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="batched", choices=["grid", "batched"])
+    ap.add_argument("--mode", default="auto", choices=["auto", "grid", "batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-frames", type=int, default=8, help="frames of the serving leg (0 = skip it)")
     ap.add_argument("--serve-size", type=int, default=1024, help="edge of the serving volume")
