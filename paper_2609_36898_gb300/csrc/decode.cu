@@ -112,8 +112,9 @@ __global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_kernel(const __g
   for (uint32_t i = threadIdx.x; i < kRansM; i += 32u * kRansWarps) tab[i] = P.v.rans_tab[i];
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint32_t item = P.item_base + blockIdx.x * kRansWarps + warp;
-  if (item >= P.n) return;
+  const uint32_t k = P.item_base + blockIdx.x * kRansWarps + warp;
+  if (k >= P.n) return;
+  const uint32_t item = scheduled_item(P, k);
   const uint32_t brick = P.ids[item];
   if (brick >= P.v.n_bricks) return;  // reported by the reconstruction kernel
   const uint32_t* rec = P.v.records + P.v.starts[brick];
@@ -127,6 +128,47 @@ __global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_kernel(const __g
   const bool ok = rans_steps(tab, reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(rec) + cofs),
                              nw, S, x0, ns, out, lane);
   if ((!ok || bad_state) && lane == 0) report(P.status, VC_ERR_CORRUPT, item);
+}
+
+// ------------------------------------------------------------------------------------------
+// Size-aware order: the request's items sorted longest record first (a counting sort into 256
+// buckets of record size, one block), so that the longest bricks do not start last and stretch
+// the tail of the launch. order[k] = the item scheduled k-th; ties keep no particular order.
+constexpr uint32_t kOrderBuckets = 256u;
+constexpr uint32_t kOrderThreads = 1024u;
+constexpr uint32_t kOrderMin = 1024u;  // smaller requests keep their own order
+
+__global__ void __launch_bounds__(kOrderThreads) order_kernel(const __grid_constant__ Params P, uint32_t max_words,
+                                                               uint32_t* order) {
+  __shared__ uint32_t cnt[kOrderBuckets];
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t i = tid; i < kOrderBuckets; i += kOrderThreads) cnt[i] = 0u;
+  __syncthreads();
+  auto bucket = [&](uint32_t item) -> uint32_t {  // 0 = longest
+    const uint32_t brick = P.ids[item];
+    if (brick >= P.v.n_bricks) return kOrderBuckets - 1u;  // reported by the decode kernels
+    const uint32_t w = min(P.v.starts[brick + 1] - P.v.starts[brick], max_words);
+    return (uint32_t)(((uint64_t)(max_words - w) * (kOrderBuckets - 1u)) / max_words);
+  };
+  for (uint32_t i = tid; i < P.n; i += kOrderThreads) atomicAdd(&cnt[bucket(i)], 1u);
+  __syncthreads();
+  if (tid < 32u) {  // exclusive scan of the counts, 8 buckets per lane
+    constexpr uint32_t per = kOrderBuckets / 32u;
+    uint32_t v[per], sum = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < per; ++j) { v[j] = cnt[tid * per + j]; sum += v[j]; }
+    uint32_t inc = sum;
+#pragma unroll
+    for (uint32_t d = 1; d < 32u; d <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+      if (tid >= d) inc += t;
+    }
+    uint32_t base = inc - sum;
+#pragma unroll
+    for (uint32_t j = 0; j < per; ++j) { cnt[tid * per + j] = base; base += v[j]; }
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < P.n; i += kOrderThreads) order[atomicAdd(&cnt[bucket(i)], 1u)] = i;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -341,13 +383,13 @@ size_t decode_ws_bytes(const Volume& v, uint32_t n) {
 }
 
 vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
-                        uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream) {
-  return launch_decode_ws(v, ids, n, slots, cache, lod, mode, status, stream, nullptr, 0);
+                        uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream, bool presorted) {
+  return launch_decode_ws(v, ids, n, slots, cache, lod, mode, status, stream, nullptr, 0, presorted);
 }
 
 vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
                            uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream, uint8_t* ws_ext,
-                           size_t ws_cap) {
+                           size_t ws_cap, bool presorted) {
   if (n == 0) return VC_OK;
   const bool rans = v.coder == 1;
   Params P;
@@ -361,6 +403,7 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   P.item_base = 0;
   P.ws = nullptr;
   P.ws_item0 = 0;
+  P.order = nullptr;
   const uint32_t edge = (1u << v.L) >> lod;
   P.out_words = edge * edge * edge;
   P.pal_bits = P.pal_per = 0;
@@ -399,9 +442,13 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   } else if (rans && ws_ext && (size_t)n * SL.ws_stride > ws_cap) {
     return VC_ERR_ARG;
   }
+  // size-aware order (one-launch schedules of large requests): 4 n bytes after the rest
+  const size_t base_need = sym_bytes + (size_t)sgrid * SL.gscratch;
+  const bool want_order = !presorted && n >= kOrderMin && mode != VC_MODE_PLAIN &&
+                          (!ws_ext || base_need + 4ull * n <= ws_cap);
   uint8_t* ws = nullptr;  // allocated here (freed at the end); none with a caller-provided workspace
   uint8_t* wsb = ws_ext;
-  const size_t need = sym_bytes + (size_t)sgrid * SL.gscratch;
+  const size_t need = base_need + (want_order ? 4ull * n : 0ull);
   if (!ws_ext && need) {
     if (cudaMallocAsync(reinterpret_cast<void**>(&ws), need, stream) != cudaSuccess) {
       cudaGetLastError();
@@ -412,6 +459,17 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   if (rans) P.ws = wsb;
   uint8_t* scr = scratch ? wsb + sym_bytes : nullptr;
   vc_status rc = VC_OK;
+  if (want_order) {
+    uint32_t* order = reinterpret_cast<uint32_t*>(wsb + base_need);
+    void* args[] = {&P, &v.max_rec_words, &order};
+    if (cudaLaunchKernel(reinterpret_cast<void*>(&order_kernel), dim3(1), dim3(kOrderThreads), args, 0, stream) !=
+        cudaSuccess) {
+      if (ws) cudaFreeAsync(ws, stream);
+      return VC_ERR_CUDA;
+    }
+    ++v.launches;
+    P.order = order;
+  }
   // timing events of this call (grid and batched schedules), if profiling is on and a set is free
   cudaEvent_t* ev = nullptr;
   if (v.prof && mode != VC_MODE_PLAIN) {

@@ -29,7 +29,11 @@ struct Params {
   uint32_t out_words; // u32 words per cache slot
   uint32_t pal_bits;  // 0: labels; else cache paletting: pal_bits-bit palette indices,
   uint32_t pal_per;   //   pal_per of them per u32 word (none straddles a word)
+  const uint32_t* order;  // size-aware order: the k-th scheduled item is order[k] (nullptr: k)
 };
+
+// The item scheduled k-th (k < P.n).
+__device__ __forceinline__ uint32_t scheduled_item(const Params& P, uint32_t k) { return P.order ? P.order[k] : k; }
 
 template <typename GT>
 struct GridT {
@@ -938,8 +942,9 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) decode_grid_kernel(const _
   extern __shared__ __align__(128) unsigned char sm[];
   const SmemLayout& SL = P.v.sm;
   int* s_err = reinterpret_cast<int*>(sm + SL.misc_off);
-  const uint32_t item = P.item_base + blockIdx.x;
-  if (item >= P.n) return;
+  const uint32_t k = P.item_base + blockIdx.x;
+  if (k >= P.n) return;
+  const uint32_t item = scheduled_item(P, k);
   const uint32_t brick = P.ids[item];
   if (brick >= P.v.n_bricks) {
     if (threadIdx.x == 0) report(P.status, VC_ERR_ARG, item);
@@ -984,7 +989,8 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) decode_batched_kernel(cons
 
   // thread 0: claims the next item and, if it fits, starts copying its data into stage[buf]
   auto claim_and_issue = [&](uint32_t buf) {
-    const uint32_t item = atomicAdd(counter, 1u);
+    const uint32_t k = atomicAdd(counter, 1u);
+    const uint32_t item = k < P.n ? scheduled_item(P, k) : k;  // >= P.n: no more items
     misc[1 + buf] = item;
     uint32_t bytes = 0;
     ItemSrc src{};
@@ -1078,7 +1084,8 @@ __global__ void __launch_bounds__(NT) decode_scratch_kernel(const __grid_constan
   uint32_t* counter = reinterpret_cast<uint32_t*>(P.status) + 2;
   for (;;) {
     if (threadIdx.x == 0) {
-      s_item = P.item_base + atomicAdd(counter, 1u);
+      const uint32_t k = P.item_base + atomicAdd(counter, 1u);
+      s_item = k < P.n ? scheduled_item(P, k) : k;  // >= P.n: no more items
       s_err = 0;
     }
     __syncthreads();

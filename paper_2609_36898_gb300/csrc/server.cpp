@@ -300,10 +300,10 @@ bool launch_batch(Server* s) {
     if (graphs && decode_ws_bytes(v, G.count) != 0)  // rANS symbols or b = 64 scratch
       ok = launch_decode_ws(v, B.d_ids + G.first, G.count, B.d_slots + G.first, reinterpret_cast<uint32_t*>(s->d_cache),
                             G.lod, VC_MODE_BATCHED, B.d_status + VC_STATUS_WORDS * g, B.stream, B.d_ws + ws_off[g],
-                            B.ws_cap - ws_off[g]) == VC_OK;
+                            B.ws_cap - ws_off[g], /*presorted=*/true) == VC_OK;
     else
       ok = launch_decode(v, B.d_ids + G.first, G.count, B.d_slots + G.first, reinterpret_cast<uint32_t*>(s->d_cache),
-                         G.lod, VC_MODE_BATCHED, B.d_status + VC_STATUS_WORDS * g, B.stream) == VC_OK;
+                         G.lod, VC_MODE_BATCHED, B.d_status + VC_STATUS_WORDS * g, B.stream, /*presorted=*/true) == VC_OK;
   }
   ok = ok &&
        cudaMemcpyAsync(B.h_status, B.d_status, 4ull * VC_STATUS_WORDS * ng, cudaMemcpyDeviceToHost, B.stream) ==

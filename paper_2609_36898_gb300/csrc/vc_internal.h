@@ -125,8 +125,10 @@ vc_status launch_camera_requests(const Volume& v, const vc_camera* cams, uint32_
 void palette_packing(uint32_t max_pal, uint32_t* bits, uint32_t* per_word);
 bool schedule_supported(uint32_t L, uint32_t threads);
 vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, SmemLayout* out);
+// presorted: the items are already in the order they should run (else requests of 1024 items or
+// more in the grid / batched schedules run longest record first)
 vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
-                        uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream);
+                        uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream, bool presorted = false);
 // Workspace bytes a decode of n items may use (rANS symbols, then b = 64 scratch slices); 0 if none.
 size_t decode_ws_bytes(const Volume& v, uint32_t n);
 // Same as launch_decode, with the workspace supplied by the caller (ws_ext, ws_cap bytes, 256-byte
@@ -135,6 +137,6 @@ size_t decode_ws_bytes(const Volume& v, uint32_t n);
 // the scratch slices that fit.
 vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
                            uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream, uint8_t* ws_ext,
-                           size_t ws_cap);
+                           size_t ws_cap, bool presorted = false);
 
 }  // namespace vc

@@ -136,6 +136,27 @@ def test_random_order_duplicates_and_scattered_slots(small_volume):
             assert np.array_equal(out[s], oracle.decode_brick(enc, int(i)))
 
 
+@pytest.mark.parametrize("coder", [0, 1])
+def test_large_request_runs_longest_first_with_the_same_result(coder):
+    """Requests of 1024 items or more run in size-aware order (longest record first) in the grid
+    and batched schedules: duplicates, scattered slots and an out-of-range id (reported with its
+    own item index) give the same result as in request order."""
+    V = synth.fill(synth.small(dims=(128, 128, 96), seed=21, grid=16, diameter=12.0, bg=0.2))
+    enc = vc.vc_encode_volume(V, 4, op_mask=0x7F, coder=coder)
+    n = oracle.header(enc)["n_bricks"]  # 384 bricks of 16^3, of varied record sizes
+    rng = np.random.default_rng(5)
+    ids = rng.integers(0, n, size=1500)
+    ids[777] = n + 3
+    slots = rng.permutation(2000)[:1500]
+    ref = oracle_bricks(enc, np.arange(n), 0)
+    for mode in ("grid", "batched", "plain"):
+        out, st = gpu_decode(enc, ids, 0, mode, slots=slots)
+        assert st[0] == vc.VC_ERR_ARG and st[1] == 777, (mode, st)
+        for k in range(0, 1500, 7):
+            if k != 777:
+                assert np.array_equal(out[slots[k]], ref[ids[k]]), (mode, k)
+
+
 def test_empty_request_is_noop(small_volume):
     enc = oracle.encode_volume(small_volume, 3)
     vol = vc.Volume(enc)
