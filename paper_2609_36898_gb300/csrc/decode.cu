@@ -209,9 +209,9 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   const uint32_t b = 1u << L;
   const uint32_t ncells = ((1u << (3 * L)) - 1u) / 7u;  // levels 0..L-1
   uint32_t o = 0;
-  // misc: words 0..15 (flags, items, mbarriers), 16..47 warp totals, then the scan scratch:
-  // 5 (NT / 32) + 5 words, and at least 52 (the finest level's part tables)
-  s.misc_off = o; o += align16(4u * (48u + std::max(5u * (threads / 32u) + 5u, 52u)));
+  // misc: words 0..15 (flags, items, mbarriers), 16..47 warp totals, then 5 (NT / 32) + 5 words of
+  // scan scratch
+  s.misc_off = o; o += align16(4u * (48u + 5u * (threads / 32u) + 5u));
   // b = 64 bricks keep their regions in global scratch (see SmemLayout::gscratch)
   const bool global = L >= 6;
   // a single stage may alias the regions a brick fills only after its parse (see stage_alias)

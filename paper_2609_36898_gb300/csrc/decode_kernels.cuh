@@ -411,7 +411,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   uint32_t* misc = reinterpret_cast<uint32_t*>(sm + SL.misc_off);
   uint32_t* wtot = misc + 16;      // NW warp totals (words 16..47)
-  uint32_t* scan_tmp = misc + 48;  // max(5 NW + 5, 52) words, 8-byte aligned
+  uint32_t* scan_tmp = misc + 48;  // 5 NW + 5 words (48..255), 8-byte aligned
 
   const uint32_t n_pal = head[0], S = head[1], nd = head[3];
   const uint32_t ns = RANS ? (S < 32u ? S : 32u) : 0u;
@@ -679,10 +679,9 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   if (finest) {
     // 4. finest level: constant blocks of stopped level-(L-1) cells, then the 8 operations of each
     // stop-0 cell (from the rank list), the neighbour marks, the output. For b = 32 the index grid
-    // holds one z quarter (b / 4 planes) at a time, the last plane of the previous quarter kept
-    // for the -z neighbours. Level-(L-1) cells are in Morton order, whose top bits are z, y, x, z:
-    // a quarter is 4 runs of the order (one per top y, x bit), and so are its open cells in the
-    // rank list.
+    // holds one z quarter at a time (levels are in Morton order, whose top bits are z's, so each
+    // quarter of the level-(L-1) cells and a run of the rank list cover b / 4 planes); the last
+    // plane of each quarter is kept for the -z neighbours of the next.
     if (tid == 0 && off + 8u * npar != c.n_nodes) set_err(s_err, VC_ERR_CORRUPT);
     const GT* Gp = G + gofs_prev;
     constexpr uint32_t pcells = 1u << (3 * (L - 1));
@@ -690,86 +689,40 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     constexpr uint32_t hcells = pcells / NH;                 // level-(L-1) cells per part
     constexpr uint32_t hvox = b * b * b / NH;                // voxels per part
     constexpr uint32_t PC = (hcells + NT - 1) / NT;
-    constexpr uint32_t CB = 3 * (L - 1);                     // Morton bits of a level-(L-1) cell
-    constexpr uint32_t RB = NH > 1 ? CB - 4 : CB;            // log2 of a run's cells
-    constexpr uint32_t RUN = 1u << RB;
-    const uint32_t tl = tid & (NT - 1u);
-    const uint32_t ftid = flin<L>(tl & (RUN - 1u) & (hcells - 1u));
+    const uint32_t ftid = flin<L>(tid & (NT - 1u) & (hcells - 1u));
     const uint16_t* plist = lists[(L - 1u) & 1u];
     GT* plane = reinterpret_cast<GT*>(sm + SL.plane_off);  // the previous part's last plane, resolved
-    // part tables (scan scratch, free by now): bnd[R] = first rank of run R (R = 0 .. 16); per
-    // part h at 20 + 8 h: d_j = first rank of its run j minus the part-local index where run j
-    // starts (j = 0 .. 3), then the part-local starts of runs 1 .. 3, then the part's open cells
-    uint32_t* bnd = scan_tmp;
+    // first rank of each part after the first: open cells are listed in increasing Morton order
+    // (one binary search per boundary, misc words 9 ..)
     if (NH > 1) {
-      if (tid <= 16u) {
+      if (tid + 1u < NH) {
+        const uint32_t cell = (tid + 1u) * hcells;
         uint32_t lo = 0, hi = npar;
-        const uint32_t cell = tid * RUN;
         while (lo < hi) {
           const uint32_t mid = (lo + hi) >> 1;
           if (plist[mid] < cell) lo = mid + 1; else hi = mid;
         }
-        bnd[tid] = tid == 16u ? npar : lo;
-      }
-      __syncthreads();
-      if (tid < NH) {
-        uint32_t* t = bnd + 20u + 8u * tid;
-        uint32_t acc = 0;
-        for (uint32_t j = 0; j < 4u; ++j) {
-          const uint32_t R = ((tid >> 1) << 3) | (j << 1) | (tid & 1u);
-          const uint32_t s0 = bnd[R], len = bnd[R + 1] - s0;
-          t[j] = s0 - acc;
-          if (j) t[3 + j] = acc;
-          acc += len;
-        }
-        t[7] = acc;
+        misc[9 + tid] = lo;
       }
       __syncthreads();
     }
-    // the rank of the part's t-th open cell
-    auto part_rank = [&](uint32_t h, uint32_t t) -> uint32_t {
-      if constexpr (NH == 1) {
-        return t;
-      } else {
-        const uint32_t* pt = bnd + 20u + 8u * h;
-        const uint32_t j = (t >= pt[4]) + (t >= pt[5]) + (t >= pt[6]);
-        return t + pt[j];
-      }
-    };
-    // the level-(L-1) cell of part-local index pl, and the offset of its (0,0,0) child in the part
-    auto part_cell = [&](uint32_t h, uint32_t pl) -> uint32_t {
-      if constexpr (NH == 1) {
-        return pl;
-      } else {
-        const uint32_t j = pl >> RB;
-        return ((((h >> 1) << 3) | (j << 1) | (h & 1u)) << RB) | (pl & (RUN - 1u));
-      }
-    };
 #pragma unroll 1
     for (uint32_t h = 0; h < NH; ++h) {
-      const uint32_t nopen = NH > 1 ? bnd[20u + 8u * h + 7u] : npar;
+      const uint32_t rb = h ? misc[8 + h] : 0u, re = (h + 1 < NH) ? misc[9 + h] : npar;
 #pragma unroll(PC <= 16u ? PC : 8u)
       for (uint32_t k = 0; k < PC; ++k) {
-        const uint32_t pl = tl + k * NT;  // with NT a power of two, pl's bits are tl's plus k * NT's
-        const uint32_t p = part_cell(h, pl);
+        const uint32_t pl = tid + k * NT;  // with NT a power of two, pl's bits are tid's plus k * NT's
+        const uint32_t p = h * hcells + pl;
         if (pl < hcells && !open_cell(L - 1u, p, nsofs_prev)) {
           const uint32_t g = Gp[p];
-          // flin is additive over disjoint bits, and the z bits of the part are its offset
-          uint32_t f0;
-          if constexpr (NH == 1) {
-            f0 = hcells > NT ? ftid + flin<L>(k * NT) : flin<L>(pl);
-          } else {
-            const uint32_t j = (tl >> RB) + k * (NT >> RB);
-            f0 = ftid + flin<L>(((j >> 1) << (CB - 2)) | ((j & 1u) << (CB - 3)));
-          }
+          const uint32_t f0 = hcells > NT ? ftid + flin<L>(k * NT) : flin<L>(pl);
           store_pair<GT>(fg, f0, g, g);
           store_pair<GT>(fg, f0 + b, g, g);
           store_pair<GT>(fg, f0 + b * b, g, g);
           store_pair<GT>(fg, f0 + b * b + b, g, g);
         }
       }
-      for (uint32_t t = tid; t < nopen; t += NT) {
-        const uint32_t r = part_rank(h, t);
+      for (uint32_t r = rb + tid; r < re; r += NT) {
         const uint32_t p = plist[r];
         uint32_t v[8];
         decode8(off + 8u * r, Gp[p], compact3(p), compact3(p >> 1), compact3(p >> 2), true, v);
@@ -784,9 +737,9 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
       // hop out of a later part lands on the kept plane, whose values are final)
       // (one row of 2 voxels per thread, 4 threads per block: the chains are short, dependent
       // loads, so spread them out)
-      for (uint32_t cc = tid; cc < 4u * nopen; cc += NT) {
+      for (uint32_t cc = tid; cc < 4u * (re - rb); cc += NT) {
         const uint32_t row = cc & 3u;
-        const uint32_t pos0 = flin<L>(plist[part_rank(h, cc >> 2)]) - h * hvox + (row & 1u) * b + (row >> 1) * (b * b);
+        const uint32_t pos0 = flin<L>(plist[rb + (cc >> 2)]) - h * hvox + (row & 1u) * b + (row >> 1) * (b * b);
 #pragma unroll
         for (uint32_t i = 0; i < 2; ++i) {
           const uint32_t pos = pos0 + i;
