@@ -28,7 +28,7 @@
 //          thread decodes 8 children at once (SWAR classes of the 8 operation nibbles); neighbour
 //          copies are written as marks and then resolved, one child per thread, by walking at
 //          most three hops (each hop turns an even coordinate odd, and a copy needs an even one).
-//       4. finest level, in four z quarters for b = 32: stopped cells fill their 2^3 blocks of the
+//       4. finest level, in two z halves for b = 32: stopped cells fill their 2^3 blocks of the
 //          index grid (two cells per store row), stop-0 cells decode their 8 operations, marks are
 //          resolved, and the output pass maps indices to labels (16-byte stores) or packs palette
 //          indices (cache paletting).
@@ -239,13 +239,12 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   s.list1_cap = cap[1];
   s.list_off = o; o += align16(2u * (s.list0_cap + cap[1]));
   const uint32_t span_bytes = o - s.mask_off;
-  // the finest index grid holds one z quarter at a time for b = 32 (plus the last plane of the
-  // previous quarter)
-  const uint32_t nh = L == 5 ? 4u : 1u;
+  // the finest index grid holds one z half at a time for b = 32 (plus the last plane of the first)
+  const uint32_t nh = L == 5 ? 2u : 1u;
   s.fg_off = o;
   s.fg_bytes = align16(s.gt_bytes * b * b * b / nh);
   o += s.fg_bytes;
-  s.plane_off = o; o += nh > 1 ? align16(s.gt_bytes * b * b) : 0u;
+  s.plane_off = o; o += nh == 2 ? align16(s.gt_bytes * b * b) : 0u;
   // private palette copy (frees the stage early); byte grids: a power of two >= max_pal (indices
   // are masked with pal_cap - 1, so any byte stays in bounds)
   uint32_t p2 = 16u;

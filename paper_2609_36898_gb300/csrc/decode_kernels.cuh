@@ -679,36 +679,32 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   if (finest) {
     // 4. finest level: constant blocks of stopped level-(L-1) cells, then the 8 operations of each
     // stop-0 cell (from the rank list), the neighbour marks, the output. For b = 32 the index grid
-    // holds one z quarter at a time (levels are in Morton order, whose top bits are z's, so each
-    // quarter of the level-(L-1) cells and a run of the rank list cover b / 4 planes); the last
-    // plane of each quarter is kept for the -z neighbours of the next.
+    // holds one z half at a time (levels are in Morton order, whose top bit is z's, so the first
+    // half of the level-(L-1) cells and of the rank list covers z < b / 2); the last plane of the
+    // first half is kept for the -z neighbours of the second.
     if (tid == 0 && off + 8u * npar != c.n_nodes) set_err(s_err, VC_ERR_CORRUPT);
     const GT* Gp = G + gofs_prev;
     constexpr uint32_t pcells = 1u << (3 * (L - 1));
-    constexpr uint32_t NH = L == 5 ? 4u : 1u;  // z parts (b = 64 works in global scratch: one)
-    constexpr uint32_t hcells = pcells / NH;                 // level-(L-1) cells per part
-    constexpr uint32_t hvox = b * b * b / NH;                // voxels per part
+    constexpr uint32_t NH = L == 5 ? 2u : 1u;  // z halves (b = 64 works in global scratch: one)
+    constexpr uint32_t hcells = pcells / NH;                 // level-(L-1) cells per half
+    constexpr uint32_t hvox = b * b * b / NH;                // voxels per half
     constexpr uint32_t PC = (hcells + NT - 1) / NT;
     const uint32_t ftid = flin<L>(tid & (NT - 1u) & (hcells - 1u));
     const uint16_t* plist = lists[(L - 1u) & 1u];
-    GT* plane = reinterpret_cast<GT*>(sm + SL.plane_off);  // the previous part's last plane, resolved
-    // first rank of each part after the first: open cells are listed in increasing Morton order
-    // (one binary search per boundary, misc words 9 ..)
-    if (NH > 1) {
-      if (tid + 1u < NH) {
-        const uint32_t cell = (tid + 1u) * hcells;
-        uint32_t lo = 0, hi = npar;
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (plist[mid] < cell) lo = mid + 1; else hi = mid;
-        }
-        misc[9 + tid] = lo;
+    GT* plane = reinterpret_cast<GT*>(sm + SL.plane_off);  // z = b/2 - 1, resolved (NH == 2)
+    // ranks of the first half: open cells are listed in increasing Morton order
+    uint32_t rsplit = npar;
+    if (NH == 2) {
+      uint32_t lo = 0, hi = npar;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (plist[mid] < hcells) lo = mid + 1; else hi = mid;
       }
-      __syncthreads();
+      rsplit = lo;
     }
 #pragma unroll 1
     for (uint32_t h = 0; h < NH; ++h) {
-      const uint32_t rb = h ? misc[8 + h] : 0u, re = (h + 1 < NH) ? misc[9 + h] : npar;
+      const uint32_t rb = h ? rsplit : 0u, re = (h + 1 < NH) ? rsplit : npar;
 #pragma unroll(PC <= 16u ? PC : 8u)
       for (uint32_t k = 0; k < PC; ++k) {
         const uint32_t pl = tid + k * NT;  // with NT a power of two, pl's bits are tid's plus k * NT's
@@ -733,8 +729,8 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
         store_pair<GT>(fg, f0 + b * b + b, v[6], v[7]);
       }
       __syncthreads();
-      // neighbour marks of this part, resolved per decoded block (at most three hops each; a -z
-      // hop out of a later part lands on the kept plane, whose values are final)
+      // neighbour marks of this half, resolved per decoded block (at most three hops each; a -z
+      // hop out of the second half lands on the kept plane, whose values are final)
       // (one row of 2 voxels per thread, 4 threads per block: the chains are short, dependent
       // loads, so spread them out)
       for (uint32_t cc = tid; cc < 4u * (re - rb); cc += NT) {
@@ -750,7 +746,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
             for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
               const uint32_t a = g - MARK;
               q -= a == 0 ? 1 : (a == 1 ? (int32_t)b : (int32_t)(b * b));
-              g = q >= 0 ? (uint32_t)fg[q] : (NH > 1 ? (uint32_t)plane[q + (int32_t)(b * b)] : MARK + 3u);
+              g = q >= 0 ? (uint32_t)fg[q] : (NH == 2 ? (uint32_t)plane[q + (int32_t)(b * b)] : MARK + 3u);
             }
             if (g >= MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
             fg[pos] = (GT)g;
@@ -768,18 +764,18 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
         for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
           const uint32_t a = g - MARK;
           q -= a == 0 ? 1 : (a == 1 ? (int32_t)b : (int32_t)(b * b));
-          g = q >= 0 ? (uint32_t)fg[q] : (NH > 1 ? (uint32_t)plane[q + (int32_t)(b * b)] : MARK + 3u);
+          g = q >= 0 ? (uint32_t)fg[q] : (NH == 2 ? (uint32_t)plane[q + (int32_t)(b * b)] : MARK + 3u);
         }
         if (g >= MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
         return g;
       };
       if (P.pal_bits) {
         // cache paletting (Methods, "Cache paletting"): pal_per indices of pal_bits bits in each
-        // u32 word, voxels in x-fastest order. A word that straddles two parts is written with the
-        // later one, which reads the earlier part's last voxels from the kept plane.
+        // u32 word, voxels in x-fastest order. A word that straddles the two halves is written
+        // with the second, which reads the first half's last voxels from the kept plane.
         const uint32_t E = P.pal_per, I = P.pal_bits;
-        const uint32_t wlo = (h * hvox) / E;
-        const uint32_t whi = h + 1 < NH ? ((h + 1u) * hvox) / E : (b * b * b + E - 1u) / E;
+        const uint32_t wlo = h ? hvox / E : 0u;
+        const uint32_t whi = h + 1 < NH ? hvox / E : (b * b * b + E - 1u) / E;
         for (uint32_t w = wlo + tid; w < whi; w += NT) {
           const uint32_t v0 = w * E;
           uint32_t word = 0;
@@ -797,7 +793,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
             for (uint32_t i = 0; i < E; ++i) {
               const uint32_t v = v0 + i;
               if (v >= b * b * b) break;
-              const uint32_t g = v >= h * hvox ? (uint32_t)fg[v - h * hvox] : (uint32_t)plane[v + b * b - h * hvox];
+              const uint32_t g = v >= h * hvox ? (uint32_t)fg[v - h * hvox] : (uint32_t)plane[v + b * b - hvox];
               word |= g << (I * i);
             }
           }
@@ -833,7 +829,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
         }
       }
       if (h + 1 < NH) {
-        // keep the last plane of this part, then the grid takes the next part
+        // keep the last plane of this half, then the grid takes the next half
         for (uint32_t i = tid; i < b * b; i += NT) plane[i] = fg[hvox - b * b + i];
         __syncthreads();
       }
@@ -938,12 +934,11 @@ __device__ __forceinline__ ItemSrc item_src(const Params& P, uint32_t item, uint
 }
 
 // One thread block per request item (grid and per-brick schedules).
-// 256-thread blocks are held to 40 registers so that six fit an SM (48 warps); the batched kernel,
-// which keeps more state across bricks, to 48 (five per SM)
-constexpr int min_blocks(int NT, bool batched) { return NT == 256 ? (batched ? 5 : 6) : 1; }
+// 256-thread blocks are held to 48 registers so that five fit an SM (40 warps)
+constexpr int min_blocks(int NT) { return NT == 256 ? 5 : 1; }
 
 template <int L, typename GT, bool RANS, int NT>
-__global__ void __launch_bounds__(NT, min_blocks(NT, false)) decode_grid_kernel(const __grid_constant__ Params P) {
+__global__ void __launch_bounds__(NT, min_blocks(NT)) decode_grid_kernel(const __grid_constant__ Params P) {
   extern __shared__ __align__(128) unsigned char sm[];
   const SmemLayout& SL = P.v.sm;
   int* s_err = reinterpret_cast<int*>(sm + SL.misc_off);
@@ -982,7 +977,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, false)) decode_grid_kernel(
 // decoded, the next brick's record (and symbols) are already being copied into the other stage
 // buffer by the TMA engine.
 template <int L, typename GT, bool RANS, int NT>
-__global__ void __launch_bounds__(NT, min_blocks(NT, true)) decode_batched_kernel(const __grid_constant__ Params P) {
+__global__ void __launch_bounds__(NT, min_blocks(NT)) decode_batched_kernel(const __grid_constant__ Params P) {
   extern __shared__ __align__(128) unsigned char sm[];
   const SmemLayout& SL = P.v.sm;
   uint32_t* misc = reinterpret_cast<uint32_t*>(sm + SL.misc_off);

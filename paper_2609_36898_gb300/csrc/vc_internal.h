@@ -40,8 +40,8 @@ struct SmemLayout {
   uint32_t dlist_cap;
   uint32_t g_off;        // palette index per cell of levels 0..L-1 (gt_bytes each)
   uint32_t ns_off;       // per level, one byte per parent cell: which children have stop bit 0
-  uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each; one z quarter for b = 32)
-  uint32_t plane_off;    // b = 32: the last z plane of the previous quarter (for its -z neighbours)
+  uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each; one z half for b = 32)
+  uint32_t plane_off;    // b = 32: the last z plane of the first half (for -z neighbours of the second)
   uint32_t fg_bytes;     // bytes of the finest grid region
   uint32_t wst_off;      // the parse's per-word automaton masks (the finest grid's region)
   uint32_t wst_bytes;
