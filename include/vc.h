@@ -211,6 +211,20 @@ vc_status vc_decode_bricks(vc_volume* vol, const uint32_t* brick_ids, uint32_t n
 vc_status vc_decode_bricks_host(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, uint32_t lod,
                                 uint32_t mode, uint32_t* labels_out, int32_t* status_out, void* cuda_stream);
 
+/* The coarsest level of detail read straight from the encoding, without decoding (Methods,
+ * "Memory management": bricks that do not fit into the cache are accessed in their coarsest level
+ * of detail directly from the encoding; "Brick request limitation": an undecoded brick is seen as
+ * its most frequent label). The root node of every brick is a palette advance, so the root's
+ * label, the top of the brick's mode hierarchy, is its first palette entry: out_labels[i] equals
+ * the single label vc_decode_bricks writes for brick_ids[i] at lod = L.
+ *   brick_ids   device, n x u32
+ *   out_labels  device, n x u32, caller-owned
+ *   status_dev  as in vc_decode_bricks: an id >= n_bricks gives VC_ERR_ARG (and label 0) for that
+ *               item, an empty palette VC_ERR_CORRUPT; the stream itself is not read or checked
+ * One kernel launch on cuda_stream (one thread per item); n = 0 is a no-op. */
+vc_status vc_coarsest_labels(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, uint32_t* out_labels,
+                             int32_t* status_dev, void* cuda_stream);
+
 /* ---- serving: device brick cache, admission, continuous batching ----
  * Paper (Methods, "GPU rendering pipeline"; Results, "GPU-based rendering pipeline"): bricks are
  * requested, cache space is freed from bricks no longer needed and assigned to new bricks, and

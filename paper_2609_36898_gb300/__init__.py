@@ -123,6 +123,7 @@ def _lib_handle():
         lib.vc_decode_bricks.argtypes = [P, P, U32, P, P, U32, U32, P, P]
         lib.vc_decode_bricks_noalloc.argtypes = [P, P, U32, P, P, U32, U32, P, P]
         lib.vc_decode_bricks_host.argtypes = [P, P, U32, U32, U32, P, ctypes.POINTER(I32), P]
+        lib.vc_coarsest_labels.argtypes = [P, P, U32, P, P, P]
         lib.vc_release.argtypes = [P]
         lib.vc_volume_set_profiling.argtypes = [P, ctypes.c_int]
         lib.vc_volume_kernel_stats.argtypes = [P, ctypes.c_int, ctypes.POINTER(vc_kernel_stats)]
@@ -232,6 +233,11 @@ def vc_decode_bricks_noalloc(vol, brick_ids_ptr: int, n: int, cache_slots_ptr: i
                                                   ctypes.c_void_p(cache_slots_ptr), ctypes.c_void_p(cache_ptr), lod,
                                                   mode, ctypes.c_void_p(status_ptr), ctypes.c_void_p(stream)),
            "vc_decode_bricks_noalloc")
+
+
+def vc_coarsest_labels(vol, brick_ids_ptr: int, n: int, out_ptr: int, status_ptr: int, stream: int = 0) -> None:
+    _check(_lib_handle().vc_coarsest_labels(vol, ctypes.c_void_p(brick_ids_ptr), n, ctypes.c_void_p(out_ptr),
+                                            ctypes.c_void_p(status_ptr), ctypes.c_void_p(stream)), "vc_coarsest_labels")
 
 
 def vc_decode_bricks_host(vol, brick_ids: np.ndarray, lod: int, mode: int, labels_out: np.ndarray,

@@ -374,7 +374,45 @@ uint32_t scratch_grid(const Volume& v, uint32_t n) {
   return std::min(n, std::max(1u, v.sms) * per_sm);
 }
 
+// The coarsest level of detail straight from the encoding: the first palette entry of each brick
+// (the root is always a palette advance).
+__global__ void __launch_bounds__(256) coarsest_kernel(const __grid_constant__ Params P, uint32_t* out) {
+  const uint32_t i = blockIdx.x * 256u + threadIdx.x;
+  if (i >= P.n) return;
+  const uint32_t brick = P.ids[i];
+  if (brick >= P.v.n_bricks) {
+    out[i] = 0u;
+    report(P.status, VC_ERR_ARG, i);
+    return;
+  }
+  const uint32_t* rec = P.v.records + P.v.starts[brick];
+  const uint32_t np = rec[0], S = rec[1];
+  const uint32_t ns = P.v.coder == 1 ? (S < 32u ? S : 32u) : 0u;
+  if (np == 0u) {
+    out[i] = 0u;
+    report(P.status, VC_ERR_CORRUPT, i);
+    return;
+  }
+  out[i] = rec[4u + ns];
+}
+
 }  // namespace
+
+vc_status launch_coarsest(Volume& v, const uint32_t* ids, uint32_t n, uint32_t* out, int32_t* status,
+                          cudaStream_t stream) {
+  if (n == 0) return VC_OK;
+  Params P{};
+  P.v = v.dv;
+  P.ids = ids;
+  P.n = n;
+  P.status = status;
+  void* args[] = {&P, &out};
+  if (cudaLaunchKernel(reinterpret_cast<void*>(&coarsest_kernel), dim3((n + 255u) / 256u), dim3(256), args, 0,
+                       stream) != cudaSuccess)
+    return VC_ERR_CUDA;
+  ++v.launches;
+  return VC_OK;
+}
 
 size_t decode_ws_bytes(const Volume& v, uint32_t n) {
   const SmemLayout& SL = v.dv.sm;

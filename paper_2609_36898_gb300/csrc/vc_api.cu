@@ -293,6 +293,16 @@ vc_status vc_volume_get_schedule(const vc_volume* vol, vc_schedule* sched) {
   return VC_OK;
 }
 
+vc_status vc_coarsest_labels(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, uint32_t* out_labels,
+                             int32_t* status_dev, void* cuda_stream) {
+  Volume* v = reinterpret_cast<Volume*>(vol);
+  if (!v || v->kind != kHandleVolume) return VC_ERR_ARG;
+  if (n == 0) return VC_OK;
+  if (!brick_ids || !out_labels || !status_dev) return VC_ERR_ARG;
+  DeviceGuard g(v->device);
+  return launch_coarsest(*v, brick_ids, n, out_labels, status_dev, static_cast<cudaStream_t>(cuda_stream));
+}
+
 vc_status vc_decode_bricks(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, const uint32_t* cache_slots,
                            uint32_t* cache, uint32_t lod, uint32_t mode, int32_t* status_dev, void* cuda_stream) {
   Volume* v = reinterpret_cast<Volume*>(vol);

@@ -129,6 +129,9 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
 // more in the grid / batched schedules run longest record first)
 vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
                         uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream, bool presorted = false);
+// The coarsest level of detail (first palette entry) of n bricks, one launch on stream.
+vc_status launch_coarsest(Volume& v, const uint32_t* ids, uint32_t n, uint32_t* out, int32_t* status,
+                          cudaStream_t stream);
 // Workspace bytes a decode of n items may use (rANS symbols, then b = 64 scratch slices); 0 if none.
 size_t decode_ws_bytes(const Volume& v, uint32_t n);
 // Same as launch_decode, with the workspace supplied by the caller (ws_ext, ws_cap bytes, 256-byte

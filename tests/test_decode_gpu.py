@@ -336,3 +336,32 @@ def test_parity_all_distinct_worst_case(log2b):
         out, st = gpu_decode(enc, ids, 0, "grid")
         assert st[0] == 0
         assert np.array_equal(out, oracle_bricks(enc, ids, 0))
+
+
+@pytest.mark.parametrize("log2b,coder", [(4, 0), (5, 1), (6, 1), (3, 0)])
+def test_coarsest_labels_straight_from_the_encoding(log2b, coder):
+    """vc_coarsest_labels reads each brick's first palette entry without decoding: it equals the
+    single label of a decode at lod = L (the top of the mode hierarchy), for every brick; an id out
+    of range reports VC_ERR_ARG for its item."""
+    V = synth.fill(synth.small(dims=(160, 96, 80), seed=40 + log2b, grid=16, diameter=18.0, bg=0.3))
+    enc = vc.vc_encode_volume(V, log2b, op_mask=0x7F, coder=coder)
+    n = oracle.header(enc)["n_bricks"]
+    vol = vc.Volume(enc)
+    try:
+        ids_np = np.concatenate([np.arange(n), np.arange(n)[::-1]]).astype(np.uint32)
+        ids = torch.from_numpy(ids_np.view(np.int32)).cuda()
+        out = torch.full((ids_np.size,), -1, dtype=torch.int32, device="cuda")
+        st = torch.zeros(vc.VC_STATUS_WORDS, dtype=torch.int32, device="cuda")
+        vc.vc_coarsest_labels(vol.handle, ids.data_ptr(), ids_np.size, out.data_ptr(), st.data_ptr(),
+                              torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert int(st[0]) == 0
+        got = out.cpu().numpy().view(np.uint32)
+        want = np.array([oracle.decode_brick(enc, int(i), log2b).reshape(-1)[0] for i in ids_np], dtype=np.uint32)
+        assert np.array_equal(got, want)
+        bad = torch.tensor([0, n + 1, 1], dtype=torch.int32, device="cuda")
+        vc.vc_coarsest_labels(vol.handle, bad.data_ptr(), 3, out.data_ptr(), st.data_ptr(), 0)
+        torch.cuda.synchronize()
+        assert int(st[0]) == vc.VC_ERR_ARG and int(st[1]) == 1 and int(out[1]) == 0
+    finally:
+        vol.release()
