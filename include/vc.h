@@ -31,7 +31,8 @@
  *     u32 magic = 0x315A4356 ("VCZ1")   u32 version = 1
  *     u32 dims[3] (voxels x, y, z)      u32 log2b (L, 1..6; brick edge b = 2^L)
  *     u32 op_mask (bit o = operation o enabled; bit 4, palette advance, always set)
- *     u32 coder (0 = plain 4-bit, 1 = rANS)   u32 flags (bit 0 = no stop bits were written)
+ *     u32 coder (0 = plain 4-bit, 1 = rANS)   u32 flags (bit 0 = no stop bits were written;
+ *                                                        bit 1 = limited delta, see DELTA)
  *     u32 n_bricks = prod ceil(dims[a] / b)   u32 max_pal   u32 max_sym  (maxima over bricks)
  *     u32 freq[16] (rANS symbol frequencies, sum 4096; zero for plain)
  *     u32 records_words (size of the record area in 32-bit words), 12 reserved bytes
@@ -61,7 +62,9 @@
  *     4 ADV      palette[k], then k += 1 (k = palette entries advanced so far in this brick)
  *     5 LAST     palette[k - 1]
  *     6 DELTA    followed by entries e (1..7 of them): delta = (delta << 3) | (e & 7) while e & 8;
- *                label palette[k - delta], 1 <= delta <= k
+ *                label palette[k - delta], 1 <= delta <= k. With flags bit 1 (limited delta, the
+ *                earlier encoding's bounded back references, Methods "Cache paletting"): exactly
+ *                one entry, delta = e (so delta <= 15; a label further back is appended again)
  *     7          invalid
  *   The stop bit is 0 at level L (and everywhere when flags bit 0 is set). A record is valid iff
  *   every symbol is legal, the stream ends exactly after the last node of level L, k ends at
@@ -414,7 +417,7 @@ vc_status vc_release(void* handle);
 
 /* Encodes a volume (host, dims[0] * dims[1] * dims[2] uint32 labels, x fastest) into VCZ1 bytes.
  * log2b in 1..6; op_mask as in the format (bit 4 required); coder 0 (plain) or 1 (rANS); flags bit 0
- * = write no stop bits. Uses `threads` worker threads (0 = all cores). The operation of each node
+ * = write no stop bits, bit 1 = limited delta (one entry per delta operation, delta <= 15). Uses `threads` worker threads (0 = all cores). The operation of each node
  * is the first applicable enabled one in the order parent, x, y, z neighbour, last, delta
  * (smallest), advance; coarse nodes hold the mode of their 2^3 children (ties to the smallest
  * label). *out_bytes is allocated by the library; free it with vc_free_bytes. */

@@ -62,6 +62,12 @@
 #define CODER_PLAIN 0u
 #define CODER_RANS 1u
 #define FLAG_NO_STOP 1u /* encoder wrote no stop bits; a set stop bit is corrupt */
+/* limited back references, the earlier encoding's form (Methods, "Cache paletting": its limited
+ * palette back-reference distances could duplicate labels in a palette): a delta operation is
+ * followed by exactly one 4-bit entry that holds delta itself, so delta <= 15; a label further
+ * back is appended to the palette again */
+#define FLAG_SHORT_DELTA 2u
+#define SHORT_DELTA_MAX 15u
 
 #define RANS_BITS 12
 #define RANS_M (1u << RANS_BITS)
@@ -320,6 +326,7 @@ static int encode_brick(const uint32_t* brick, int L, uint32_t op_mask, uint32_t
   if (rc) return rc;
   memset(out, 0, sizeof(*out));
   const int use_stop = !(flags & FLAG_NO_STOP);
+  const int short_delta = (flags & FLAG_SHORT_DELTA) != 0;
   uint8_t* expanded[7]; /* emitted with stop = 0 */
   for (int l = 0; l <= L; ++l) {
     expanded[l] = (uint8_t*)calloc((size_t)1 << (3 * l), 1);
@@ -348,15 +355,21 @@ static int encode_brick(const uint32_t* brick, int L, uint32_t op_mask, uint32_t
       }
       if (op < 0 && (op_mask >> OP_LAST & 1) && out->n_pal >= 1 && out->pal[out->n_pal - 1] == label) op = OP_LAST;
       if (op < 0 && (op_mask >> OP_DELTA & 1)) {
-        for (uint32_t d = 2; d <= out->n_pal; ++d)
+        uint32_t reach = out->n_pal;
+        if (short_delta && reach > SHORT_DELTA_MAX) reach = SHORT_DELTA_MAX;
+        for (uint32_t d = 2; d <= reach; ++d)
           if (out->pal[out->n_pal - d] == label) { op = OP_DELTA; delta = d; break; }
       }
       if (op < 0) { op = OP_ADV; rc = push_pal(out, label); }
       if (!rc) rc = push_sym(out, (uint8_t)(op | (stop << 3)));
       if (!rc && op == OP_DELTA) {
-        uint8_t e[11];
-        int ne = oracle_delta_nibbles(delta, e);
-        for (int i = 0; i < ne && !rc; ++i) rc = push_sym(out, e[i]);
+        if (short_delta) {
+          rc = push_sym(out, (uint8_t)delta); /* one entry: delta itself */
+        } else {
+          uint8_t e[11];
+          int ne = oracle_delta_nibbles(delta, e);
+          for (int i = 0; i < ne && !rc; ++i) rc = push_sym(out, e[i]);
+        }
         out->n_delta++;
       }
     }
@@ -380,7 +393,7 @@ int oracle_encode_volume(const uint32_t* V, const uint32_t dims[3], uint32_t log
   if (!V || !dims || !out_bytes || !out_size) return O_ERR_ARG;
   if (log2b < 1 || log2b > 6) return O_ERR_ARG;
   if (!(op_mask & (1u << OP_ADV)) || (op_mask & ~OP_ALL)) return O_ERR_ARG;
-  if (coder > CODER_RANS || (flags & ~FLAG_NO_STOP)) return O_ERR_ARG;
+  if (coder > CODER_RANS || (flags & ~(FLAG_NO_STOP | FLAG_SHORT_DELTA))) return O_ERR_ARG;
   for (int a = 0; a < 3; ++a) if (dims[a] == 0) return O_ERR_ARG;
   const uint32_t b = 1u << log2b;
   const int L = (int)log2b;
@@ -524,7 +537,7 @@ static int parse_volume(const uint8_t* v, size_t size, vol_view* o) {
   o->records_words = rd32(v + 112);
   if (o->L < 1 || o->L > 6) return O_ERR_FORMAT;
   if (!(o->op_mask & (1u << OP_ADV)) || (o->op_mask & ~OP_ALL)) return O_ERR_FORMAT;
-  if (o->coder > CODER_RANS || (o->flags & ~FLAG_NO_STOP)) return O_ERR_FORMAT;
+  if (o->coder > CODER_RANS || (o->flags & ~(FLAG_NO_STOP | FLAG_SHORT_DELTA))) return O_ERR_FORMAT;
   uint32_t b = 1u << o->L;
   uint64_t nb = 1;
   for (int a = 0; a < 3; ++a) {
@@ -651,13 +664,18 @@ static int replay(const vol_view* V, uint32_t id, uint32_t lod, uint32_t* out, o
           label = rd32(pal + 4 * (size_t)(k - 1));
           break;
         case OP_DELTA: {
-          int entries = 0;
-          for (;;) {
-            if (i >= S || entries == MAX_DELTA_ENTRIES) { rc = O_ERR_CORRUPT; break; }
-            uint32_t e = sym[i++];
-            ++entries;
-            delta = (delta << 3) | (e & 7u);
-            if (!(e & 8u)) break;
+          if (V->flags & FLAG_SHORT_DELTA) { /* one entry holding delta */
+            if (i >= S) { rc = O_ERR_CORRUPT; break; }
+            delta = sym[i++];
+          } else {
+            int entries = 0;
+            for (;;) {
+              if (i >= S || entries == MAX_DELTA_ENTRIES) { rc = O_ERR_CORRUPT; break; }
+              uint32_t e = sym[i++];
+              ++entries;
+              delta = (delta << 3) | (e & 7u);
+              if (!(e & 8u)) break;
+            }
           }
           if (rc) break;
           ++deltas;

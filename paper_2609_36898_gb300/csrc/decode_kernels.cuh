@@ -151,8 +151,10 @@ __device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t& pa
 // and the state becomes 1 iff it is a delta operation (low 3 bits = 6); from state 1 the nibble is
 // an entry and the state stays 1 iff its bit 3 ("another entry follows") is set.
 
-// delta from the entries at nibble i..; 0 when invalid (runs past S or needs an eighth entry)
-__device__ __forceinline__ uint32_t read_delta(const uint32_t* sw, uint32_t i, uint32_t S) {
+// delta from the entries at nibble i..; 0 when invalid (runs past S or needs an eighth entry).
+// short_delta: one entry holding delta itself.
+__device__ __forceinline__ uint32_t read_delta(const uint32_t* sw, uint32_t i, uint32_t S, bool short_delta) {
+  if (short_delta) return i < S ? nib_at(sw, i) : 0u;
   uint32_t d = 0;
 #pragma unroll 1
   for (uint32_t e = 0; e < 7u; ++e) {
@@ -171,10 +173,11 @@ struct ParseOut {
 
 // For the 8 nibbles of stream word x: D = nibbles whose low 3 bits are 6 (delta operations if they
 // are operations); A / B = bit i holds the state after nibble i when the word is entered in state
-// 0 / 1. The per-nibble transitions are composed by prefix doubling on 8-bit masks.
-__device__ __forceinline__ void word_states(uint32_t x, uint32_t& D, uint32_t& A, uint32_t& B) {
+// 0 / 1. The per-nibble transitions are composed by prefix doubling on 8-bit masks. An entry is
+// followed by another while its bit 3 is set, or never (short_delta: one entry per delta).
+__device__ __forceinline__ void word_states(uint32_t x, uint32_t& D, uint32_t& A, uint32_t& B, bool short_delta) {
   D = nib_eq8(x, OP_DELTA);
-  uint32_t a = D, e = gather_nib_bits((x >> 3) & 0x11111111u);  // after nibble i from 0 / from 1
+  uint32_t a = D, e = short_delta ? 0u : gather_nib_bits((x >> 3) & 0x11111111u);  // after nibble i from 0 / 1
 #pragma unroll
   for (uint32_t k = 1; k < 8; k <<= 1) {
     const uint32_t ha = a << k, hb = (e << k) | ((1u << k) - 1u);  // identity below bit k
@@ -244,7 +247,8 @@ __device__ __forceinline__ Fn2<ND> fn_shfl_up(const Fn2<ND>& f, uint32_t d) {
 // nodes in 32 bits (needed from 2^16 nodes on, b = 64), otherwise in 16.
 template <int NT, bool WIDE>
 __device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes, uint32_t nodes_words,
-                                 uint32_t* dlist, uint32_t dcap, uint32_t* scan_tmp, uint32_t* wst, int* s_err) {
+                                 uint32_t* dlist, uint32_t dcap, uint32_t* scan_tmp, uint32_t* wst, int* s_err,
+                                 bool short_delta) {
   using ND = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
   using F = Fn2<ND>;
   constexpr uint32_t K = WIDE ? 32u : 16u;
@@ -264,7 +268,7 @@ __device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes
       const uint32_t x = sw[w];
       const uint32_t nv = min(8u, S - 8u * w);
       uint32_t D, A, B, e0, e1;
-      word_states(x, D, A, B);
+      word_states(x, D, A, B, short_delta);
       const uint32_t m0 = word_ops(A, B, s0, nv, &e0), m1 = word_ops(A, B, s1, nv, &e1);
       if (wst) wst[w] = m0 | (m1 << 8) | (D << 16);  // this word's operations on both paths
       f.nd0 += (ND)__popc(m0) | ((ND)__popc(m0 & D) << K);
@@ -324,7 +328,7 @@ __device__ ParseOut parse_stream(const uint32_t* sw, uint32_t S, uint32_t* nodes
       D = v >> 16;
     } else {
       uint32_t A, B, end;
-      word_states(x, D, A, B);
+      word_states(x, D, A, B, short_delta);
       m = word_ops(A, B, st, nv, &end);
       st = end;
     }
@@ -414,6 +418,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   uint32_t* scan_tmp = misc + 48;  // 5 NW + 5 words (48..255), 8-byte aligned
 
   const uint32_t n_pal = head[0], S = head[1], nd = head[3];
+  const bool short_delta = (P.v.flags & kFlagShortDelta) != 0;
   const uint32_t ns = RANS ? (S < 32u ? S : 32u) : 0u;
 
   BrickCtx c;
@@ -448,13 +453,14 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     uint32_t* nodes = reinterpret_cast<uint32_t*>(sm + SL.nodes_off);
     // the finest grid's region is idle during the parse: it keeps the per-word automaton masks
     uint32_t* wst = ((S + 7u) >> 3) * 4u <= SL.wst_bytes ? reinterpret_cast<uint32_t*>(sm + SL.wst_off) : nullptr;
-    const ParseOut po = parse_stream<NT, (L >= 6)>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap, scan_tmp, wst, s_err);
+    const ParseOut po = parse_stream<NT, (L >= 6)>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap, scan_tmp, wst, s_err,
+                                                   short_delta);
     c.nodes = nodes;
     c.n_nodes = po.n_nodes;
     if (po.n_delta != nd) set_err(s_err, VC_ERR_CORRUPT);
     // delta values from their entries, one delta operation per thread (visible after the barriers
     // of step 2)
-    for (uint32_t d = tid; d < c.dlist_cap; d += NT) dlist[d] = read_delta(sw, dlist[d], S);
+    for (uint32_t d = tid; d < c.dlist_cap; d += NT) dlist[d] = read_delta(sw, dlist[d], S, short_delta);
     if (SL.stage_alias) __syncthreads();  // the stage is read up to here; step 2 overwrites it
   }
 

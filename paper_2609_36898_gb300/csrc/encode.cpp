@@ -17,6 +17,7 @@
 namespace {
 
 constexpr uint32_t kOpParent = 0, kOpNx = 1, kOpLast = 5, kOpDelta = 6, kOpAdv = 4;
+constexpr uint32_t kShortDeltaMax = 15;  // flags bit 1: the largest delta one 4-bit entry holds
 constexpr uint32_t kM = 4096;
 
 inline void put32(uint8_t* p, uint32_t v) {
@@ -109,7 +110,8 @@ uint32_t mode_of_8(const uint32_t* c) {
 }
 
 void encode_one(const uint32_t* V, const uint32_t dims[3], uint32_t L, uint32_t id, const uint32_t nb[3],
-                uint32_t op_mask, bool use_stop, const std::vector<uint32_t>& sp, Scratch& s, Brick& out) {
+                uint32_t op_mask, bool use_stop, bool short_delta, const std::vector<uint32_t>& sp, Scratch& s,
+                Brick& out) {
   const uint32_t b = 1u << L;
   const uint32_t bx = id % nb[0], by = (id / nb[0]) % nb[1], bz = id / (nb[0] * nb[1]);
   for (uint32_t l = 0; l <= L; ++l) {
@@ -171,7 +173,7 @@ void encode_one(const uint32_t* V, const uint32_t dims[3], uint32_t L, uint32_t 
       if (op == 8 && ((op_mask >> kOpLast) & 1u) && k >= 1 && out.pal[k - 1] == t) op = kOpLast;
       if (op == 8 && ((op_mask >> kOpDelta) & 1u)) {
         const int32_t pos = s.idx.recent_at_most(t, k - 2);
-        if (pos >= 0) {
+        if (pos >= 0 && (!short_delta || k - pos <= (int32_t)kShortDeltaMax)) {
           op = kOpDelta;
           delta = (uint32_t)(k - pos);
         }
@@ -188,10 +190,14 @@ void encode_one(const uint32_t* V, const uint32_t dims[3], uint32_t L, uint32_t 
       }
       out.sym.push_back((uint8_t)(op | (stop << 3)));
       if (op == kOpDelta) {
-        // octal digits of delta, most significant first; bit 3 = another entry follows
-        int nd = 1;
-        while ((delta >> (3 * nd)) != 0) ++nd;
-        for (int i = nd - 1; i >= 0; --i) out.sym.push_back((uint8_t)(((delta >> (3 * i)) & 7u) | (i ? 8u : 0u)));
+        if (short_delta) {
+          out.sym.push_back((uint8_t)delta);  // one entry holding delta (<= 15)
+        } else {
+          // octal digits of delta, most significant first; bit 3 = another entry follows
+          int nd = 1;
+          while ((delta >> (3 * nd)) != 0) ++nd;
+          for (int i = nd - 1; i >= 0; --i) out.sym.push_back((uint8_t)(((delta >> (3 * i)) & 7u) | (i ? 8u : 0u)));
+        }
         ++out.n_delta;
       }
     }
@@ -273,7 +279,7 @@ vc_status vc_encode_volume(const uint32_t* voxels, const uint32_t dims[3], uint3
   if (!voxels || !dims || !out_bytes || !out_size) return VC_ERR_ARG;
   *out_bytes = nullptr;
   *out_size = 0;
-  if (log2b < 1 || log2b > 6 || !(op_mask & (1u << kOpAdv)) || (op_mask & ~0x7Fu) || coder > 1 || (flags & ~1u))
+  if (log2b < 1 || log2b > 6 || !(op_mask & (1u << kOpAdv)) || (op_mask & ~0x7Fu) || coder > 1 || (flags & ~3u))
     return VC_ERR_ARG;
   if (!dims[0] || !dims[1] || !dims[2]) return VC_ERR_ARG;
   const uint32_t b = 1u << log2b;
@@ -298,8 +304,9 @@ vc_status vc_encode_volume(const uint32_t* voxels, const uint32_t dims[3], uint3
     return VC_ERR_OOM;
   }
   const bool use_stop = !(flags & 1u);
+  const bool short_delta = (flags & 2u) != 0;  // one 4-bit entry per delta operation: delta <= 15
   parallel_for(n, threads, [&](uint32_t id, uint32_t tid) {
-    encode_one(voxels, dims, log2b, id, nb, op_mask, use_stop, sp, scratch[tid], bricks[id]);
+    encode_one(voxels, dims, log2b, id, nb, op_mask, use_stop, short_delta, sp, scratch[tid], bricks[id]);
   });
   scratch.clear();
   uint32_t freq[16] = {0}, cum[17] = {0};

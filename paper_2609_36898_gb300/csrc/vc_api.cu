@@ -111,7 +111,7 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   const uint32_t records_words = le32(p + 112);
   if (L < 1 || L > 6) return VC_ERR_FORMAT;
   if (!(op_mask & (1u << 4)) || (op_mask & ~0x7Fu)) return VC_ERR_FORMAT;
-  if (coder > 1 || (flags & ~kFlagNoStop)) return VC_ERR_FORMAT;
+  if (coder > 1 || (flags & ~(kFlagNoStop | kFlagShortDelta))) return VC_ERR_FORMAT;
   const uint32_t b = 1u << L;
   uint32_t nb[3];
   uint64_t nbt = 1;

@@ -62,7 +62,7 @@ def test_load_rejects_bad_bytes_before_touching_a_device(lib):
 def test_encoder_matches_oracle_bytes(lib, log2b, coder):
     V = synth.fill(synth.small(dims=(37, 21, 18), seed=4, diameter=9.0, bg=0.25))
     for mask in (0x7F, 0x7F & ~(1 << 5), 0x7F & ~(1 << 6), (1 << 4) | 1, 1 << 4):
-        for flags in (0, 1):
+        for flags in (0, 1, 2, 3):
             a = oracle.encode_volume(V, log2b, op_mask=mask, coder=coder, flags=flags)
             b = vc.vc_encode_volume(V, log2b, op_mask=mask, coder=coder, flags=flags, threads=3)
             assert a.size == b.size and np.array_equal(a, b), (mask, flags)

@@ -344,6 +344,82 @@ def test_corrupt_streams_rejected(coder):
         assert _status(s, p, nd, mask, flags, coder) == C, (s, p, nd, mask, flags)
 
 
+# ---------------------------------------------------------------- limited delta (flags bit 1)
+
+def reuse_volume(seed: int = 3) -> np.ndarray:
+    """16 x 16 x 32 voxels whose 48 labels come back only after many others (2^3 cells in a
+    shuffled cyclic pattern): palettes longer than one 4-bit entry can reach."""
+    rng = np.random.default_rng(seed)
+    labels = rng.permutation(np.arange(1, 49, dtype=np.uint32) * 7919)
+    z, y, x = np.meshgrid(np.arange(16), np.arange(16), np.arange(32), indexing="ij")
+    return labels[(x // 2 + 5 * (y // 2) + 11 * (z // 2)) % 48].astype(np.uint32)
+
+
+@pytest.mark.parametrize("coder", [oracle.CODER_PLAIN, oracle.CODER_RANS])
+def test_short_delta_roundtrip_one_entry_per_delta(small_volume, coder):
+    """Limited delta (the earlier encoding's bounded back references, Methods "Cache paletting"):
+    lossless, every delta operation carries exactly one entry (S = emitted nodes + delta
+    operations) and every delta is in 2..15."""
+    F = oracle.FLAG_SHORT_DELTA
+    for V in (small_volume, reuse_volume()):
+        for log2b in (2, 3, 4, 5):
+            enc = oracle.encode_volume(V, log2b, coder=coder, flags=F)
+            assert oracle.header(enc)["flags"] == F
+            assert np.array_equal(oracle.decode_volume(enc), V)
+            for bid in range(oracle.header(enc)["n_bricks"]):
+                nodes = oracle.brick_nodes(enc, bid)
+                rec = oracle.brick_record(enc, bid)
+                assert rec["n_sym"] == len(nodes) + rec["n_delta"]
+                d = nodes["delta"][nodes["op"] == OP_DELTA]
+                assert len(d) == rec["n_delta"] and ((d >= 2) & (d <= 15)).all()
+
+
+def test_short_delta_duplicates_only_beyond_reach():
+    """With limited delta a palette holds a label twice only when its previous copy is more than
+    15 entries back (the duplicates the paper attributes to the earlier encoding); the unlimited
+    encoding of the same data holds none."""
+    V = reuse_volume()
+    dup = 0
+    for log2b in (3, 4, 5):
+        b = 1 << log2b
+        enc = oracle.encode_volume(V, log2b, flags=oracle.FLAG_SHORT_DELTA)
+        ref = oracle.encode_volume(V, log2b)
+        for bid in range(oracle.header(enc)["n_bricks"]):
+            pal = oracle.brick_record(enc, bid)["palette"].tolist()
+            assert set(pal) == set(np.unique(padded_brick(V, b, bid)).tolist())
+            last = {}
+            for k, x in enumerate(pal):
+                if x in last:
+                    assert k - last[x] > 15, (log2b, bid, k)
+                    dup += 1
+                last[x] = k
+            pal_u = oracle.brick_record(ref, bid)["palette"].tolist()
+            assert len(pal_u) == len(set(pal_u))
+    assert dup > 0
+
+
+def test_short_delta_streams_checked():
+    sym, pal = _golden_stream()
+    F = oracle.FLAG_SHORT_DELTA
+    C = oracle.ERR_CORRUPT
+    # the LAST at (1,0,0) (k = 2) as delta 1 or 2 in one entry: legal
+    assert _status(list(sym[:10]) + [OP_DELTA, 1] + sym[11:], pal, 1, 0x7F, F) == 0
+    s2 = list(sym[:10]) + [OP_DELTA, 2] + sym[11:]
+    assert _status(s2, pal, 1, 0x7F, F) == 0
+    # delta 2 re-reads palette entry 0 where the stream had entry 1
+    want = oracle.decode_brick(oracle.pack_single_brick(2, sym, pal, 0), 0)
+    got = oracle.decode_brick(oracle.pack_single_brick(2, s2, pal, 1, flags=F), 0)
+    assert (got != want).sum() >= 1 and set(np.unique(got).tolist()) <= set(pal)
+    # an entry is a plain 4-bit value: bit 3 does not chain (8 + 1 -> delta 9 > k), 0 is invalid,
+    # and a delta operation needs its entry
+    assert _status(list(sym[:10]) + [OP_DELTA, 9] + sym[11:], pal, 1, 0x7F, F) == C
+    assert _status(list(sym[:10]) + [OP_DELTA, 8, 1] + sym[11:], pal, 1, 0x7F, F) == C
+    assert _status(list(sym[:10]) + [OP_DELTA, 0] + sym[11:], pal, 1, 0x7F, F) == C
+    assert _status(list(sym[:-1]) + [OP_DELTA], pal, 1, 0x7F, F) == C
+    # without the flag the same two entries chain: delta = (0 << 3) | 1 = 1, legal
+    assert _status(list(sym[:10]) + [OP_DELTA, 8, 1] + sym[11:], pal, 1, 0x7F, 0) == 0
+
+
 def test_long_legal_delta_chain_accepted():
     sym, pal = _golden_stream()
     # replace the LAST at (1,0,0) (palette index 1 = k - 1) by delta 1 written with 7 entries:
