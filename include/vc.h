@@ -128,6 +128,8 @@ typedef struct vc_volume_info {
   uint64_t device_bytes;   /* device memory owned by the volume */
   uint32_t smem_bytes;     /* dynamic shared memory per thread block of the decoder (0 for b = 64) */
   uint32_t device;
+  uint32_t split;          /* 1: loaded by vc_load_compressed_split */
+  uint64_t host_bytes;     /* split volumes: pinned host memory owned by the volume (whole encoding) */
 } vc_volume_info;
 
 /* Parses and validates `nbytes` host bytes of a VCZ1 volume (header, Brick Starts, every record's
@@ -142,6 +144,25 @@ typedef struct vc_volume_info {
  * decoded on demand, Methods "Volcanite rendering".) */
 vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, void* cuda_stream,
                              vc_volume** out);
+
+/* Detail split (Methods, "Encoding buffer optimizations": the finest level of detail can be kept
+ * out of GPU memory and brought in only for bricks needed at full resolution). Same input and
+ * errors as vc_load_compressed (VC_ERR_FORMAT also for a record whose symbols do not decode). The
+ * device copy holds, per brick, a record of the coarse levels 0 .. L-1 alone (its palette prefix,
+ * symbol and delta counts; same coder), so decodes at lod >= 1 read device memory only. The whole
+ * encoding is copied to pinned host memory that the volume owns and that is mapped into the
+ * device's address space: decodes at lod = 0 read those records over the host link (NVLink-C2C
+ * on GB300) with plain loads, with no copy in between (the batched schedule runs as the grid
+ * schedule there). device_bytes counts the device copy, host_bytes the pinned host copy. Every
+ * other call treats the volume like any other. */
+vc_status vc_load_compressed_split(const void* host_bytes, size_t nbytes, int device, void* cuda_stream,
+                                   vc_volume** out);
+
+/* Host-only view of the split of one brick (no CUDA calls): out[0] = its symbols S, out[1] = the
+ * symbols of levels 0 .. L-1, out[2] = the palette advances and out[3] = the delta operations
+ * among those. VC_ERR_ARG / VC_ERR_FORMAT as for loading; VC_ERR_CORRUPT if the stream ends inside
+ * the coarse levels or its coded words do not decode. */
+vc_status vc_split_counts(const void* host_bytes, size_t nbytes, uint32_t brick_id, uint32_t out[4]);
 
 /* Fills *info. Host only, no CUDA calls. */
 vc_status vc_volume_info_get(const vc_volume* vol, vc_volume_info* info);

@@ -53,6 +53,8 @@ class vc_volume_info(ctypes.Structure):
         ("device_bytes", ctypes.c_uint64),
         ("smem_bytes", ctypes.c_uint32),
         ("device", ctypes.c_uint32),
+        ("split", ctypes.c_uint32),
+        ("host_bytes", ctypes.c_uint64),
     ]
 
 
@@ -117,6 +119,8 @@ def _lib_handle():
         lib = ctypes.CDLL(LIB_PATH)
         P, U32, I32, SZ = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32, ctypes.c_size_t
         lib.vc_load_compressed.argtypes = [P, SZ, ctypes.c_int, P, ctypes.POINTER(P)]
+        lib.vc_load_compressed_split.argtypes = [P, SZ, ctypes.c_int, P, ctypes.POINTER(P)]
+        lib.vc_split_counts.argtypes = [P, SZ, U32, P]
         lib.vc_volume_info_get.argtypes = [P, ctypes.POINTER(vc_volume_info)]
         lib.vc_volume_set_schedule.argtypes = [P, ctypes.POINTER(vc_schedule)]
         lib.vc_volume_get_schedule.argtypes = [P, ctypes.POINTER(vc_schedule)]
@@ -182,6 +186,22 @@ def vc_load_compressed(host_bytes: np.ndarray, device: int = 0, stream: int = 0)
     _check(_lib_handle().vc_load_compressed(b.ctypes.data, b.size, device, ctypes.c_void_p(stream),
                                             ctypes.byref(out)), "vc_load_compressed")
     return out
+
+
+def vc_load_compressed_split(host_bytes: np.ndarray, device: int = 0, stream: int = 0) -> ctypes.c_void_p:
+    b = np.ascontiguousarray(host_bytes, dtype=np.uint8)
+    out = ctypes.c_void_p()
+    _check(_lib_handle().vc_load_compressed_split(b.ctypes.data, b.size, device, ctypes.c_void_p(stream),
+                                                  ctypes.byref(out)), "vc_load_compressed_split")
+    return out
+
+
+def vc_split_counts(host_bytes: np.ndarray, brick_id: int) -> tuple:
+    """(S, coarse symbols, coarse palette advances, coarse delta operations) of one brick."""
+    b = np.ascontiguousarray(host_bytes, dtype=np.uint8)
+    out = np.zeros(4, dtype=np.uint32)
+    _check(_lib_handle().vc_split_counts(b.ctypes.data, b.size, brick_id, out.ctypes.data), "vc_split_counts")
+    return tuple(int(x) for x in out)
 
 
 def vc_volume_info_get(vol) -> vc_volume_info:
@@ -415,11 +435,12 @@ def vc_brick_cache_stats_get(cache) -> vc_brick_cache_stats:
 class Volume:
     """A compressed volume resident on a CUDA device."""
 
-    def __init__(self, encoded: np.ndarray, device: int = 0, stream=None):
+    def __init__(self, encoded: np.ndarray, device: int = 0, stream=None, split: bool = False):
         import torch
         self.device = device
         s = stream if stream is not None else torch.cuda.current_stream(device)
-        self.handle = vc_load_compressed(encoded, device, s.cuda_stream)
+        load = vc_load_compressed_split if split else vc_load_compressed
+        self.handle = load(encoded, device, s.cuda_stream)
         self.info = vc_volume_info_get(self.handle)
         self.b = int(self.info.brick_size)
         self.L = int(self.info.log2b)

@@ -432,6 +432,13 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   const bool rans = v.coder == 1;
   Params P;
   P.v = v.dv;
+  if (v.split && lod == 0) {
+    // the finest level is in host memory only: whole records over the host link, read with
+    // plain loads (the bulk-copy prefetch of the batched kernel is not used on them)
+    P.v.records = v.full_records;
+    P.v.starts = v.full_starts;
+    if ((mode & ~VC_MODE_PALETTED) == VC_MODE_BATCHED) mode = (mode & VC_MODE_PALETTED) | VC_MODE_GRID;
+  }
   P.ids = ids;
   P.slots = slots;
   P.n = n;

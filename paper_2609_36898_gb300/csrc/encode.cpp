@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "vc.h"
+#include "vc_internal.h"
 
 namespace {
 
@@ -229,28 +230,8 @@ void quantize(const uint64_t counts[16], uint32_t f[16]) {
   }
 }
 
-// 32-way interleaved rANS (symbol i on state i mod 32); words come out in the decoder's read order.
 void rans_brick(Brick& br, const uint32_t f[16], const uint32_t cum[17]) {
-  const uint32_t S = (uint32_t)br.sym.size();
-  uint32_t x[32];
-  for (int l = 0; l < 32; ++l) x[l] = 1u << 16;
-  br.words.clear();
-  const uint32_t steps = (S + 31) / 32;
-  for (uint32_t t = steps; t-- > 0;) {
-    for (int l = 31; l >= 0; --l) {
-      const uint32_t i = t * 32 + (uint32_t)l;
-      if (i >= S) continue;
-      const uint32_t sy = br.sym[i], fs = f[sy];
-      if ((uint64_t)x[l] >= ((uint64_t)fs << 20)) {
-        br.words.push_back((uint16_t)x[l]);
-        x[l] >>= 16;
-      }
-      x[l] = ((x[l] / fs) << 12) + (x[l] % fs) + cum[sy];
-    }
-  }
-  std::reverse(br.words.begin(), br.words.end());
-  br.n_states = std::min<uint32_t>(S, 32);
-  for (uint32_t l = 0; l < br.n_states; ++l) br.states[l] = x[l];
+  vc::rans_encode(br.sym.data(), (uint32_t)br.sym.size(), f, cum, br.words, br.states, &br.n_states);
   br.coded_bytes = 2 * (uint32_t)br.words.size();
 }
 
@@ -271,6 +252,30 @@ void parallel_for(uint32_t n, uint32_t threads, F&& fn) {
 }
 
 }  // namespace
+
+// 32-way interleaved rANS (symbol i on state i mod 32); words come out in the decoder's read order.
+void vc::rans_encode(const uint8_t* sym, uint32_t S, const uint32_t f[16], const uint32_t cum[17],
+                     std::vector<uint16_t>& words, uint32_t states[32], uint32_t* n_states) {
+  uint32_t x[32];
+  for (int l = 0; l < 32; ++l) x[l] = 1u << 16;
+  words.clear();
+  const uint32_t steps = (S + 31) / 32;
+  for (uint32_t t = steps; t-- > 0;) {
+    for (int l = 31; l >= 0; --l) {
+      const uint32_t i = t * 32 + (uint32_t)l;
+      if (i >= S) continue;
+      const uint32_t sy = sym[i], fs = f[sy];
+      if ((uint64_t)x[l] >= ((uint64_t)fs << 20)) {
+        words.push_back((uint16_t)x[l]);
+        x[l] >>= 16;
+      }
+      x[l] = ((x[l] / fs) << 12) + (x[l] % fs) + cum[sy];
+    }
+  }
+  std::reverse(words.begin(), words.end());
+  *n_states = std::min<uint32_t>(S, 32);
+  for (uint32_t l = 0; l < *n_states; ++l) states[l] = x[l];
+}
 
 extern "C" {
 

@@ -72,6 +72,7 @@ void free_volume(Volume* v) {
   cudaFree(v->d_host_slots);
   cudaFree(v->d_host_cache);
   cudaFree(v->d_host_status);
+  if (v->h_full) cudaFreeHost(v->h_full);
   std::free(v->h_rec_words);
   v->kind = 0;
   delete v;
@@ -96,11 +97,12 @@ const char* vc_status_string(vc_status s) {
   }
 }
 
-vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, void* cuda_stream, vc_volume** out) {
-  if (!out) return VC_ERR_ARG;
-  *out = nullptr;
-  if (!host_bytes) return VC_ERR_ARG;
-  const uint8_t* p = static_cast<const uint8_t*>(host_bytes);
+}  // extern "C"
+
+namespace vc {
+
+vc_status scan_volume(const uint8_t* p, size_t nbytes, VolumeScan* out) {
+  VolumeScan& sc = *out;
   if (nbytes < kHeaderBytes) return VC_ERR_FORMAT;
   if (le32(p) != kMagic || le32(p + 4) != kVersion) return VC_ERR_FORMAT;
   uint32_t dims[3] = {le32(p + 8), le32(p + 12), le32(p + 16)};
@@ -164,6 +166,42 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   if (le32(st + 4 * (size_t)n_bricks) != records_words) return VC_ERR_FORMAT;
   if (max_pal > hdr_max_pal || max_sym > hdr_max_sym) return VC_ERR_FORMAT;
   if (max_pal >= kMaxIdx16) return VC_ERR_UNSUPPORTED;  // palette indices are kept in 16 bits
+
+  for (int a = 0; a < 3; ++a) { sc.dims[a] = dims[a]; sc.nb[a] = nb[a]; }
+  sc.L = L; sc.op_mask = op_mask; sc.coder = coder; sc.flags = flags; sc.n_bricks = n_bricks;
+  for (int q = 0; q < 16; ++q) sc.freq[q] = freq[q];
+  sc.records_words = records_words;
+  sc.rec_off = rec_off;
+  sc.max_pal = max_pal; sc.max_sym = max_sym; sc.max_delta = max_delta; sc.max_words = max_words;
+  sc.max_stage = max_stage; sc.max_nodes = max_nodes;
+  sc.bflags.swap(bflags);
+  return VC_OK;
+}
+
+}  // namespace vc
+
+extern "C" {
+
+vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, void* cuda_stream, vc_volume** out) {
+  if (!out) return VC_ERR_ARG;
+  *out = nullptr;
+  if (!host_bytes) return VC_ERR_ARG;
+  const uint8_t* p = static_cast<const uint8_t*>(host_bytes);
+  VolumeScan sc;
+  {
+    const vc_status rc0 = scan_volume(p, nbytes, &sc);
+    if (rc0 != VC_OK) return rc0;
+  }
+  const uint32_t* dims = sc.dims;
+  const uint32_t* nb = sc.nb;
+  const uint32_t L = sc.L, op_mask = sc.op_mask, coder = sc.coder, flags = sc.flags, n_bricks = sc.n_bricks;
+  const uint32_t* freq = sc.freq;
+  const size_t rec_off = sc.rec_off;
+  const uint32_t records_words = sc.records_words;
+  const uint32_t max_pal = sc.max_pal, max_sym = sc.max_sym, max_delta = sc.max_delta, max_words = sc.max_words;
+  const uint32_t max_stage = sc.max_stage, max_nodes = sc.max_nodes;
+  const std::vector<uint8_t>& bflags = sc.bflags;
+  const uint8_t* st = p + kHeaderBytes;
 
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return VC_ERR_ARG;
@@ -267,6 +305,8 @@ vc_status vc_volume_info_get(const vc_volume* vol, vc_volume_info* info) {
   info->encoded_bytes = v->encoded_bytes;
   info->device_bytes = v->device_bytes;
   info->smem_bytes = v->dv.sm.gscratch ? 0u : v->dv.sm.total;
+  info->split = v->split ? 1u : 0u;
+  info->host_bytes = v->host_bytes;
   info->device = (uint32_t)v->device;
   return VC_OK;
 }

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "vc.h"
 
 namespace vc {
@@ -97,6 +99,14 @@ struct Volume {
   uint32_t* d_host_cache;
   int32_t* d_host_status;
   uint32_t* h_rec_words;  // host copy: record size of each brick in 32-bit words (work ordering)
+  // detail split (vc_load_compressed_split): the device copy holds the coarse levels only; the
+  // whole encoding lives in pinned host memory mapped into the device's address space, read by
+  // finest-level decodes
+  bool split;
+  uint8_t* h_full;
+  const uint32_t* full_records;  // device addresses of the mapped host copy
+  const uint32_t* full_starts;
+  uint64_t host_bytes;
   size_t host_cap_items, host_cap_words;
   // kernel accounting: launches are always counted; with prof set, each grid / batched decode call
   // records three timing events (before the symbol kernel, between, after the reconstruction)
@@ -120,6 +130,21 @@ constexpr size_t kCamDevBytes = 76;  // per camera, pinned host staging
 vc_status launch_camera_requests(const Volume& v, const vc_camera* cams, uint32_t ncams, uint32_t max_lod,
                                  uint32_t cap, uint8_t* d_scratch, void* h_cams_pinned, uint32_t* d_counts,
                                  uint32_t* d_ids, uint32_t* d_lods, cudaStream_t stream);
+
+// vc_api.cu: the host-side checks of a VCZ1 file (header, Brick Starts, every record's sizes) and
+// the maxima the decoder's layouts are sized by
+struct VolumeScan {
+  uint32_t dims[3], nb[3], L, op_mask, coder, flags, n_bricks, freq[16], records_words;
+  size_t rec_off;  // byte offset of the record area
+  uint32_t max_pal, max_sym, max_delta, max_words, max_stage, max_nodes;
+  std::vector<uint8_t> bflags;  // per brick: bit 0 = palette holds label 0, bit 1 = another label
+};
+vc_status scan_volume(const uint8_t* p, size_t nbytes, VolumeScan* out);
+
+// encode.cpp: 32-way interleaved rANS of S symbols with the volume's table (states of the first
+// min(S, 32) lanes, words in the decoder's read order)
+void rans_encode(const uint8_t* sym, uint32_t S, const uint32_t f[16], const uint32_t cum[17],
+                 std::vector<uint16_t>& words, uint32_t states[32], uint32_t* n_states);
 
 // decode.cu
 // cache paletting: bits per palette index (ceil(log2 max_pal), >= 1) and indices per u32 word
