@@ -594,6 +594,37 @@ def run_ours(args):
     e2e_val = world * vox_per_step * e2e_steps / e2e_s / 1e9
     assert np.array_equal(labels_np[: e ** 3].reshape(e, e, e), V[:e, :e, :e])
 
+    # detail split: the same volume with its finest level left in (mapped, pinned) host memory
+    split = None
+    if not args.no_split:
+        sv = vc.Volume(enc, device=local, split=True)
+        sinfo, finfo = vc.vc_volume_info_get(sv.handle), vc.vc_volume_info_get(vol.handle)
+        smode = vc.MODES["grid"]
+        split = {"device_bytes": int(sinfo.device_bytes), "device_bytes_unsplit": int(finfo.device_bytes),
+                 "host_bytes": int(sinfo.host_bytes),
+                 "device_saving": 1.0 - sinfo.device_bytes / finfo.device_bytes}
+        for lod in (0, 1):
+            e_l = e >> lod
+            words_l = n * e_l ** 3
+            vc.vc_decode_bricks(sv.handle, ids.data_ptr(), n, ids.data_ptr(), cache.data_ptr(), lod, smode,
+                                status.data_ptr(), stream.cuda_stream)
+            tot, reps = 0.0, 5
+            for _ in range(reps):
+                flush.fill_(7)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                vc.vc_decode_bricks(sv.handle, ids.data_ptr(), n, ids.data_ptr(), cache.data_ptr(), lod, smode,
+                                    status.data_ptr(), stream.cuda_stream)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                tot += ev0.elapsed_time(ev1)
+            split[f"lod{lod}_gvoxel_s"] = words_l * reps / (tot / 1000.0) / 1e9
+            split[f"lod{lod}_reads"] = "whole records from mapped host memory" if lod == 0 else \
+                "coarse-level records in device memory"
+        if int(status[0]) != 0:
+            raise RuntimeError(f"split decode status {status.tolist()}")
+        sv.release()
+
     serving = None
     if args.serve_frames > 0:
         serving = serving_leg(args, local)
@@ -633,6 +664,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "schedules_gvoxel_s": modes,
             "paletted": paletted,
+            "detail_split": split,
             "serving": serving,
             "mixed_serving": mixed,
             "wall_s_timed_region": wall,
@@ -653,6 +685,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="auto", choices=["auto", "grid", "batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-split", action="store_true", help="skip the detail-split leg")
     ap.add_argument("--serve-frames", type=int, default=8, help="frames of the serving leg (0 = skip it)")
     ap.add_argument("--serve-size", type=int, default=1024, help="edge of the serving volume")
     ap.add_argument("--serve-cameras", type=int, default=64)
