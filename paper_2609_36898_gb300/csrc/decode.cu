@@ -114,10 +114,10 @@ __global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_kernel(const __g
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint32_t k = P.item_base + blockIdx.x * kRansWarps + warp;
   if (k >= P.n) return;
-  uint32_t item;
-  ItemSrc src;
-  if (!scheduled<true>(P, k, item, src)) return;  // reported by the reconstruction kernel
-  const uint32_t* rec = src.rec;
+  const uint32_t item = scheduled_item(P, k);
+  const uint32_t brick = P.ids[item];
+  if (brick >= P.v.n_bricks) return;  // reported by the reconstruction kernel
+  const uint32_t* rec = P.v.records + P.v.starts[brick];
   const uint32_t np = rec[0], S = rec[1], cb = rec[2];
   const uint32_t ns = S < 32u ? S : 32u;
   const uint32_t nw = cb >> 1;
@@ -131,20 +131,17 @@ __global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_kernel(const __g
 }
 
 // ------------------------------------------------------------------------------------------
-// Size-aware schedule: the request's items sorted longest record first (a counting sort into 256
+// Size-aware order: the request's items sorted longest record first (a counting sort into 256
 // buckets of record size, one block), so that the longest bricks do not start last and stretch
-// the tail of the launch. Entry k = the item scheduled k-th with the word offset of its record and
-// the bytes to stage (one 16-byte load for the decode kernels instead of a chain of three);
-// ties keep no particular order.
+// the tail of the launch. order[k] = the item scheduled k-th; ties keep no particular order.
 constexpr uint32_t kOrderBuckets = 256u;
 constexpr uint32_t kOrderThreads = 1024u;
 constexpr uint32_t kOrderMin = 1024u;  // smaller requests keep their own order
 
 __global__ void __launch_bounds__(kOrderThreads) order_kernel(const __grid_constant__ Params P, uint32_t max_words,
-                                                               uint4* sched) {
-  constexpr uint32_t KEEP = 8;  // buckets of a thread's first items are kept in registers
+                                                               uint32_t* order) {
   __shared__ uint32_t cnt[kOrderBuckets];
-  const uint32_t tid = threadIdx.x, lane = tid & 31u;
+  const uint32_t tid = threadIdx.x;
   for (uint32_t i = tid; i < kOrderBuckets; i += kOrderThreads) cnt[i] = 0u;
   __syncthreads();
   auto bucket = [&](uint32_t item) -> uint32_t {  // 0 = longest
@@ -153,39 +150,7 @@ __global__ void __launch_bounds__(kOrderThreads) order_kernel(const __grid_const
     const uint32_t w = min(P.v.starts[brick + 1] - P.v.starts[brick], max_words);
     return (uint32_t)(((uint64_t)(max_words - w) * (kOrderBuckets - 1u)) / max_words);
   };
-  auto entry = [&](uint32_t item) -> uint4 {  // the same sizes the decode kernels compute
-    const uint32_t brick = P.ids[item];
-    if (brick >= P.v.n_bricks) return make_uint4(item, kNoRecord, 0u, 0u);
-    const uint32_t a = P.v.starts[brick], e = P.v.starts[brick + 1];
-    if (P.v.coder == 1) {
-      const uint32_t np = P.v.records[a], S = P.v.records[a + 1];
-      const uint32_t ns = S < 32u ? S : 32u;
-      return make_uint4(item, a, (16u + 4u * ns + 4u * np + 15u) & ~15u, (((S + 1u) >> 1) + 15u) & ~15u);
-    }
-    return make_uint4(item, a, (e - a) * 4u, 0u);
-  };
-  // one shared-memory atomic per distinct bucket in a warp (lanes with equal buckets grouped)
-  auto warp_add = [&](bool valid, uint32_t bk) -> uint32_t {
-    const uint32_t key = valid ? bk : 0xFFFFFFFFu;
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
-    const uint32_t leader = __ffs(peers) - 1u;
-    uint32_t base = 0;
-    if (valid && lane == leader) base = atomicAdd(&cnt[bk], __popc(peers));
-    base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    return base + __popc(peers & lanemask_lt());
-  };
-  uint32_t kept[KEEP];
-  const uint32_t rounds = (P.n + kOrderThreads - 1u) / kOrderThreads;
-#pragma unroll
-  for (uint32_t r = 0; r < KEEP; ++r) {
-    const uint32_t i = r * kOrderThreads + tid;
-    kept[r] = r < rounds && i < P.n ? bucket(i) : 0u;
-    if (r < rounds) warp_add(i < P.n, kept[r]);
-  }
-  for (uint32_t r = KEEP; r < rounds; ++r) {
-    const uint32_t i = r * kOrderThreads + tid;
-    warp_add(i < P.n, i < P.n ? bucket(i) : 0u);
-  }
+  for (uint32_t i = tid; i < P.n; i += kOrderThreads) atomicAdd(&cnt[bucket(i)], 1u);
   __syncthreads();
   if (tid < 32u) {  // exclusive scan of the counts, 8 buckets per lane
     constexpr uint32_t per = kOrderBuckets / 32u;
@@ -203,19 +168,7 @@ __global__ void __launch_bounds__(kOrderThreads) order_kernel(const __grid_const
     for (uint32_t j = 0; j < per; ++j) { cnt[tid * per + j] = base; base += v[j]; }
   }
   __syncthreads();
-#pragma unroll
-  for (uint32_t r = 0; r < KEEP; ++r) {
-    const uint32_t i = r * kOrderThreads + tid;
-    if (r < rounds) {
-      const uint32_t pos = warp_add(i < P.n, kept[r]);
-      if (i < P.n) sched[pos] = entry(i);
-    }
-  }
-  for (uint32_t r = KEEP; r < rounds; ++r) {
-    const uint32_t i = r * kOrderThreads + tid;
-    const uint32_t pos = warp_add(i < P.n, i < P.n ? bucket(i) : 0u);
-    if (i < P.n) sched[pos] = entry(i);
-  }
+  for (uint32_t i = tid; i < P.n; i += kOrderThreads) order[atomicAdd(&cnt[bucket(i)], 1u)] = i;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -495,7 +448,7 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   P.item_base = 0;
   P.ws = nullptr;
   P.ws_item0 = 0;
-  P.sched = nullptr;
+  P.order = nullptr;
   const uint32_t edge = (1u << v.L) >> lod;
   P.out_words = edge * edge * edge;
   P.pal_bits = P.pal_per = 0;
@@ -534,13 +487,13 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   } else if (rans && ws_ext && (size_t)n * SL.ws_stride > ws_cap) {
     return VC_ERR_ARG;
   }
-  // size-aware schedule (one-launch schedules of large requests): 16 n bytes after the rest
+  // size-aware order (one-launch schedules of large requests): 4 n bytes after the rest
   const size_t base_need = sym_bytes + (size_t)sgrid * SL.gscratch;
   const bool want_order = !presorted && n >= kOrderMin && mode != VC_MODE_PLAIN &&
-                          (!ws_ext || base_need + 16ull * n <= ws_cap);
+                          (!ws_ext || base_need + 4ull * n <= ws_cap);
   uint8_t* ws = nullptr;  // allocated here (freed at the end); none with a caller-provided workspace
   uint8_t* wsb = ws_ext;
-  const size_t need = base_need + (want_order ? 16ull * n : 0ull);
+  const size_t need = base_need + (want_order ? 4ull * n : 0ull);
   if (!ws_ext && need) {
     if (cudaMallocAsync(reinterpret_cast<void**>(&ws), need, stream) != cudaSuccess) {
       cudaGetLastError();
@@ -552,15 +505,15 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   uint8_t* scr = scratch ? wsb + sym_bytes : nullptr;
   vc_status rc = VC_OK;
   if (want_order) {
-    uint4* sched = reinterpret_cast<uint4*>(wsb + base_need);
-    void* args[] = {&P, &v.max_rec_words, &sched};
+    uint32_t* order = reinterpret_cast<uint32_t*>(wsb + base_need);
+    void* args[] = {&P, &v.max_rec_words, &order};
     if (cudaLaunchKernel(reinterpret_cast<void*>(&order_kernel), dim3(1), dim3(kOrderThreads), args, 0, stream) !=
         cudaSuccess) {
       if (ws) cudaFreeAsync(ws, stream);
       return VC_ERR_CUDA;
     }
     ++v.launches;
-    P.sched = sched;
+    P.order = order;
   }
   // timing events of this call (grid and batched schedules), if profiling is on and a set is free
   cudaEvent_t* ev = nullptr;

@@ -29,11 +29,11 @@ struct Params {
   uint32_t out_words; // u32 words per cache slot
   uint32_t pal_bits;  // 0: labels; else cache paletting: pal_bits-bit palette indices,
   uint32_t pal_per;   //   pal_per of them per u32 word (none straddles a word)
-  // size-aware schedule (nullptr: the k-th item is item k): entry k = {item, word offset of its
-  // record (kNoRecord: brick id out of range), staged head bytes, staged stream bytes}
-  const uint4* sched;
+  const uint32_t* order;  // size-aware order: the k-th scheduled item is order[k] (nullptr: k)
 };
-constexpr uint32_t kNoRecord = 0xFFFFFFFFu;
+
+// The item scheduled k-th (k < P.n).
+__device__ __forceinline__ uint32_t scheduled_item(const Params& P, uint32_t k) { return P.order ? P.order[k] : k; }
 
 template <typename GT>
 struct GridT {
@@ -915,47 +915,28 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // Where one request item's data lives: the record, and the bytes to stage in shared memory.
 struct ItemSrc {
   const uint32_t* rec;     // record in global memory
-  const uint32_t* stream;  // rANS: the decoded symbols in the workspace; plain: nullptr (the symbols
-                           // follow the palette in the record: rec + 4 + rec[0])
+  const uint32_t* stream;  // symbols in global memory (record for plain, workspace for rANS)
   uint32_t head_bytes;     // staged head (whole record for plain)
   uint32_t stream_bytes;   // staged symbols after the head (rANS only)
 };
 
 template <bool RANS>
-__device__ __forceinline__ const uint32_t* ws_symbols(const Params& P, uint32_t item) {
-  return reinterpret_cast<const uint32_t*>(P.ws + (size_t)(item - P.ws_item0) * P.v.sm.ws_stride);
-}
-
-// The item scheduled k-th (k < P.n) and where its data lives; false if its brick id is out of
-// range. With a size-aware schedule one 16-byte load, else the id, Brick Starts and record header.
-template <bool RANS>
-__device__ __forceinline__ bool scheduled(const Params& P, uint32_t k, uint32_t& item, ItemSrc& s) {
-  s.stream = nullptr;
-  if (P.sched) {
-    const uint4 d = P.sched[k];
-    item = d.x;
-    if (d.y == kNoRecord) return false;
-    s.rec = P.v.records + d.y;
-    s.head_bytes = d.z;
-    s.stream_bytes = d.w;
+__device__ __forceinline__ ItemSrc item_src(const Params& P, uint32_t item, uint32_t brick) {
+  ItemSrc s;
+  const uint32_t a = P.v.starts[brick], e = P.v.starts[brick + 1];
+  s.rec = P.v.records + a;
+  if (RANS) {
+    const uint32_t np = s.rec[0], S = s.rec[1];
+    const uint32_t ns = S < 32u ? S : 32u;
+    s.head_bytes = (16u + 4u * ns + 4u * np + 15u) & ~15u;
+    s.stream = reinterpret_cast<const uint32_t*>(P.ws + (size_t)(item - P.ws_item0) * P.v.sm.ws_stride);
+    s.stream_bytes = (((S + 1u) >> 1) + 15u) & ~15u;
   } else {
-    item = k;
-    const uint32_t brick = P.ids[item];
-    if (brick >= P.v.n_bricks) return false;
-    const uint32_t a = P.v.starts[brick], e = P.v.starts[brick + 1];
-    s.rec = P.v.records + a;
-    if (RANS) {
-      const uint32_t np = s.rec[0], S = s.rec[1];
-      const uint32_t ns = S < 32u ? S : 32u;
-      s.head_bytes = (16u + 4u * ns + 4u * np + 15u) & ~15u;
-      s.stream_bytes = (((S + 1u) >> 1) + 15u) & ~15u;
-    } else {
-      s.head_bytes = (e - a) * 4u;
-      s.stream_bytes = 0;
-    }
+    s.head_bytes = (e - a) * 4u;
+    s.stream = s.rec + 4u + s.rec[0];
+    s.stream_bytes = 0;
   }
-  if (RANS) s.stream = ws_symbols<RANS>(P, item);
-  return true;
+  return s;
 }
 
 // One thread block per request item (grid and per-brick schedules).
@@ -969,15 +950,16 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) decode_grid_kernel(const _
   int* s_err = reinterpret_cast<int*>(sm + SL.misc_off);
   const uint32_t k = P.item_base + blockIdx.x;
   if (k >= P.n) return;
-  uint32_t item;
-  ItemSrc src;
-  if (!scheduled<RANS>(P, k, item, src)) {
+  const uint32_t item = scheduled_item(P, k);
+  const uint32_t brick = P.ids[item];
+  if (brick >= P.v.n_bricks) {
     if (threadIdx.x == 0) report(P.status, VC_ERR_ARG, item);
     return;
   }
   if (threadIdx.x == 0) *s_err = 0;
+  const ItemSrc src = item_src<RANS>(P, item, brick);
   const uint32_t* head = src.rec;
-  const uint32_t* sw = RANS ? src.stream : src.rec + 4u + src.rec[0];
+  const uint32_t* sw = src.stream;
   if (src.head_bytes + src.stream_bytes <= SL.stage_bytes) {
     uint4* dst = reinterpret_cast<uint4*>(sm + SL.stage_off);
     const uint4* h = reinterpret_cast<const uint4*>(src.rec);
@@ -1011,16 +993,17 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) decode_batched_kernel(cons
   unsigned char* stage[2] = {sm + SL.stage_off, sm + SL.stage_off + SL.stage_bytes};
   const uint32_t tid = threadIdx.x;
 
-  // thread 0: claims the next schedule position and, if its data fit, starts copying them into
-  // stage[buf]
+  // thread 0: claims the next item and, if it fits, starts copying its data into stage[buf]
   auto claim_and_issue = [&](uint32_t buf) {
     const uint32_t k = atomicAdd(counter, 1u);
-    misc[1 + buf] = k;  // >= P.n: no more items
+    const uint32_t item = k < P.n ? scheduled_item(P, k) : k;  // >= P.n: no more items
+    misc[1 + buf] = item;
     uint32_t bytes = 0;
     ItemSrc src{};
-    if (k < P.n) {
-      uint32_t item;
-      if (scheduled<RANS>(P, k, item, src)) {
+    if (item < P.n) {
+      const uint32_t brick = P.ids[item];
+      if (brick < P.v.n_bricks) {
+        src = item_src<RANS>(P, item, brick);
         bytes = src.head_bytes + src.stream_bytes;
         if (bytes > SL.stage_bytes) bytes = 0;
       }
@@ -1049,11 +1032,8 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) decode_batched_kernel(cons
   uint32_t buf = 0;
   for (;;) {
     __syncthreads();
-    const uint32_t k = misc[1 + buf];
-    if (k >= P.n) break;
-    uint32_t item;
-    ItemSrc src;
-    const bool in_range = scheduled<RANS>(P, k, item, src);
+    const uint32_t item = misc[1 + buf];
+    if (item >= P.n) break;
     if (tid == 0) {
       *s_err = 0;
       if (prefetch) claim_and_issue(buf ^ 1u);
@@ -1069,14 +1049,17 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) decode_batched_kernel(cons
       }
       return;
     }
+    const uint32_t brick = P.ids[item];
     bool released = false;
-    if (!in_range) {
+    if (brick >= P.v.n_bricks) {
       if (tid == 0) report(P.status, VC_ERR_ARG, item);
     } else {
+      const ItemSrc src = item_src<RANS>(P, item, brick);
       const bool staged = src.head_bytes + src.stream_bytes <= SL.stage_bytes;
       const uint32_t* head = staged ? reinterpret_cast<const uint32_t*>(stage[buf]) : src.rec;
-      const uint32_t* sw = RANS ? (staged ? reinterpret_cast<const uint32_t*>(stage[buf] + src.head_bytes) : src.stream)
-                                : head + 4u + head[0];
+      const uint32_t* sw = !staged ? src.stream
+                                   : (RANS ? reinterpret_cast<const uint32_t*>(stage[buf] + src.head_bytes)
+                                           : head + 4u + head[0]);
       uint32_t* out = P.cache + (size_t)P.slots[item] * P.out_words;
       // depth 1: the next item's copy starts as soon as this brick's stage is free
       decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, s_err, [&] {
@@ -1107,20 +1090,20 @@ __global__ void __launch_bounds__(NT) decode_scratch_kernel(const __grid_constan
   uint32_t* counter = reinterpret_cast<uint32_t*>(P.status) + 2;
   for (;;) {
     if (threadIdx.x == 0) {
-      s_item = P.item_base + atomicAdd(counter, 1u);  // schedule position; >= P.n: no more items
+      const uint32_t k = P.item_base + atomicAdd(counter, 1u);
+      s_item = k < P.n ? scheduled_item(P, k) : k;  // >= P.n: no more items
       s_err = 0;
     }
     __syncthreads();
-    const uint32_t k = s_item;
-    if (k >= P.n) break;
-    uint32_t item;
-    ItemSrc src;
-    if (!scheduled<RANS>(P, k, item, src)) {
+    const uint32_t item = s_item;
+    if (item >= P.n) break;
+    const uint32_t brick = P.ids[item];
+    if (brick >= P.v.n_bricks) {
       if (threadIdx.x == 0) report(P.status, VC_ERR_ARG, item);
     } else {
+      const ItemSrc src = item_src<RANS>(P, item, brick);
       uint32_t* out = P.cache + (size_t)P.slots[item] * P.out_words;
-      const uint32_t* sw = RANS ? src.stream : src.rec + 4u + src.rec[0];
-      decode_brick<L, GT, RANS, NT>(P, src.rec, sw, out, sm, &s_err, [] {});
+      decode_brick<L, GT, RANS, NT>(P, src.rec, src.stream, out, sm, &s_err, [] {});
       __syncthreads();
       if (threadIdx.x == 0 && s_err) report(P.status, s_err, item);
     }
