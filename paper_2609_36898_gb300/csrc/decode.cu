@@ -140,8 +140,9 @@ constexpr uint32_t kOrderMin = 1024u;  // smaller requests keep their own order
 
 __global__ void __launch_bounds__(kOrderThreads) order_kernel(const __grid_constant__ Params P, uint32_t max_words,
                                                                uint32_t* order) {
+  constexpr uint32_t KEEP = 8;  // buckets of a thread's first items are kept in registers
   __shared__ uint32_t cnt[kOrderBuckets];
-  const uint32_t tid = threadIdx.x;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u;
   for (uint32_t i = tid; i < kOrderBuckets; i += kOrderThreads) cnt[i] = 0u;
   __syncthreads();
   auto bucket = [&](uint32_t item) -> uint32_t {  // 0 = longest
@@ -150,7 +151,28 @@ __global__ void __launch_bounds__(kOrderThreads) order_kernel(const __grid_const
     const uint32_t w = min(P.v.starts[brick + 1] - P.v.starts[brick], max_words);
     return (uint32_t)(((uint64_t)(max_words - w) * (kOrderBuckets - 1u)) / max_words);
   };
-  for (uint32_t i = tid; i < P.n; i += kOrderThreads) atomicAdd(&cnt[bucket(i)], 1u);
+  // one shared-memory atomic per distinct bucket in a warp (lanes with equal buckets grouped)
+  auto warp_add = [&](bool valid, uint32_t bk) -> uint32_t {
+    const uint32_t key = valid ? bk : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
+    const uint32_t leader = __ffs(peers) - 1u;
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&cnt[bk], __popc(peers));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    return base + __popc(peers & lanemask_lt());
+  };
+  uint32_t kept[KEEP];
+  const uint32_t rounds = (P.n + kOrderThreads - 1u) / kOrderThreads;
+#pragma unroll
+  for (uint32_t r = 0; r < KEEP; ++r) {
+    const uint32_t i = r * kOrderThreads + tid;
+    kept[r] = r < rounds && i < P.n ? bucket(i) : 0u;
+    if (r < rounds) warp_add(i < P.n, kept[r]);
+  }
+  for (uint32_t r = KEEP; r < rounds; ++r) {
+    const uint32_t i = r * kOrderThreads + tid;
+    warp_add(i < P.n, i < P.n ? bucket(i) : 0u);
+  }
   __syncthreads();
   if (tid < 32u) {  // exclusive scan of the counts, 8 buckets per lane
     constexpr uint32_t per = kOrderBuckets / 32u;
@@ -168,7 +190,19 @@ __global__ void __launch_bounds__(kOrderThreads) order_kernel(const __grid_const
     for (uint32_t j = 0; j < per; ++j) { cnt[tid * per + j] = base; base += v[j]; }
   }
   __syncthreads();
-  for (uint32_t i = tid; i < P.n; i += kOrderThreads) order[atomicAdd(&cnt[bucket(i)], 1u)] = i;
+#pragma unroll
+  for (uint32_t r = 0; r < KEEP; ++r) {
+    const uint32_t i = r * kOrderThreads + tid;
+    if (r < rounds) {
+      const uint32_t pos = warp_add(i < P.n, kept[r]);
+      if (i < P.n) order[pos] = i;
+    }
+  }
+  for (uint32_t r = KEEP; r < rounds; ++r) {
+    const uint32_t i = r * kOrderThreads + tid;
+    const uint32_t pos = warp_add(i < P.n, i < P.n ? bucket(i) : 0u);
+    if (i < P.n) order[pos] = i;
+  }
 }
 
 // ------------------------------------------------------------------------------------------
