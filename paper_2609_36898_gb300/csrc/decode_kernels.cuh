@@ -199,15 +199,16 @@ __device__ __forceinline__ uint32_t word_ops(uint32_t A, uint32_t B, uint32_t st
 
 // The nibbles of x selected by m, packed from nibble 0 upwards.
 __device__ __forceinline__ uint32_t pack_nibbles(uint32_t x, uint32_t m) {
-  if (m == 0xFFu) return x;
-  uint32_t out = 0, pos = 0;
-#pragma unroll
-  for (uint32_t i = 0; i < 8; ++i) {
-    const uint32_t take = (m >> i) & 1u;
-    out |= (take ? (x >> (4u * i)) & 15u : 0u) << pos;
-    pos += 4u * take;
+  // remove the unselected nibbles (few: delta entries, or past the stream's end), highest first,
+  // so that the positions below stay put; zeros shift in at the top
+  uint32_t drop = ~m & 0xFFu;
+  while (drop) {
+    const uint32_t p = 31u - __clz(drop);
+    const uint32_t low = (1u << (4u * p)) - 1u;
+    x = (x & low) | ((x >> 4) & ~low);
+    drop &= ~(1u << p);
   }
-  return out;
+  return x;
 }
 
 // A chunk summary for both entering states: bit s of e = the state after the chunk entered in
@@ -647,12 +648,15 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     }
     if (lane == 31) wtot[warp] = inc;
     __syncthreads();
-    uint32_t base = inc - cnt, total = 0;
-    for (uint32_t w = 0; w < NW; ++w) {
-      const uint32_t t = wtot[w];
-      if (w < warp) base += t;
-      total += t;
+    // the warp totals, scanned by every warp with shuffles
+    uint32_t wt = lane < NW ? wtot[lane] : 0u;
+#pragma unroll
+    for (uint32_t o = 1; o < NW; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, wt, o);
+      if (lane >= o) wt += t;
     }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, wt, NW - 1u);
+    uint32_t base = inc - cnt + (warp ? __shfl_sync(0xFFFFFFFFu, wt, warp - 1u) : 0u);
     // list this level's stop-0 cells by rank (a corrupt stream may claim more than the buffer
     // holds: flagged, and the list is cut); resolve the neighbour marks among the children
     const uint32_t lcap = (l & 1u) ? SL.list1_cap : SL.list0_cap;
