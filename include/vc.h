@@ -126,7 +126,8 @@ typedef struct vc_volume_info {
   uint32_t max_pal, max_sym, max_delta;
   uint64_t encoded_bytes;  /* bytes passed to vc_load_compressed */
   uint64_t device_bytes;   /* device memory owned by the volume */
-  uint32_t smem_bytes;     /* dynamic shared memory per thread block of the decoder (0 for b = 64) */
+  uint32_t smem_bytes;     /* dynamic shared memory per thread block of the decoder (b = 64: the
+                              small regions; 0 when all of a brick's regions are in global scratch) */
   uint32_t device;
   uint32_t split;          /* 1: loaded by vc_load_compressed_split */
   uint64_t host_bytes;     /* split volumes: pinned host memory owned by the volume (whole encoding) */
@@ -138,8 +139,10 @@ typedef struct vc_volume_info {
  * the call synchronises that stream before returning, so the caller may free `host_bytes` at once.
  * Errors: VC_ERR_ARG (NULL pointer), VC_ERR_FORMAT (invalid bytes), VC_ERR_UNSUPPORTED (a brick
  * of b <= 32 needs more shared memory than a thread block has, or a palette of 65520 entries or
- * more), VC_ERR_OOM, VC_ERR_CUDA. Bricks of b = 64 are decoded with their working set in global
- * scratch memory (about a megabyte per persistent thread block, allocated per decode call). On error *out is
+ * more), VC_ERR_OOM, VC_ERR_CUDA. Bricks of b = 64 are decoded with the large parts of their
+ * working set (node operations, cursor masks, the 64^3 index grid) in global scratch memory (a
+ * few hundred KB per persistent thread block, allocated per decode call) and the rest in shared
+ * memory. On error *out is
  * NULL and nothing is leaked. (Paper: the compressed volume is uploaded to GPU memory once and
  * decoded on demand, Methods "Volcanite rendering".) */
 vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, void* cuda_stream,

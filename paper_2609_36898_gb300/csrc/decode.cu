@@ -238,53 +238,68 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   int optin = 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
     return VC_ERR_CUDA;
-  SmemLayout s{};
-  s.gt_bytes = v.max_pal < kMaxIdx8 ? 1u : 2u;
-  const uint32_t b = 1u << L;
-  const uint32_t ncells = ((1u << (3 * L)) - 1u) / 7u;  // levels 0..L-1
-  uint32_t o = 0;
-  // misc: words 0..15 (flags, items, mbarriers), 16..47 warp totals, then 5 (NT / 32) + 5 words of
-  // scan scratch
-  s.misc_off = o; o += align16(4u * (48u + 5u * (threads / 32u) + 5u));
-  // b = 64 bricks keep their regions in global scratch (see SmemLayout::gscratch)
+  // b = 64 bricks: the large regions (node operations, delta values, cursor masks, the finest
+  // index grid) live in a global scratch slice per block, the rest in shared memory when it fits
+  // (attempt 0), else everything in the slice (attempt 1); see SmemLayout::gscratch
   const bool global = L >= 6;
-  // a single stage may alias the regions a brick fills only after its parse (see stage_alias)
-  const bool pal_always_copied = s.gt_bytes == 1 || v.max_pal <= 1024u;
-  const bool may_alias = nstage == 1 && pal_always_copied && !global;
-  // node operations: written by the parse; bricks without delta operations use their staged
-  // symbols directly, or a copy here when the stage is aliased
-  s.nodes_words = (v.max_nodes + 7u) / 8u + 4u;
-  s.nodes_off = o; o += (v.max_delta || may_alias) ? align16(4 * s.nodes_words) : 0u;
-  s.dlist_cap = v.max_delta;
-  s.dlist_off = o; o += align16(4 * (v.max_delta ? v.max_delta : 1u));
-  // cursor masks, level grids, stop bytes and rank lists: one contiguous span
-  s.nwords = (v.max_nodes + 31u) / 32u + 2u;
-  s.mask_off = o; o += align16((global ? 16 : 12) * s.nwords);  // 2 u32 masks + 2 prefixes per word
-  s.g_off = o; o += align16(s.gt_bytes * (ncells + 7u));  // level 1 starts at cell 8 (alignment)
-  // per level l >= 1 below L, one byte per level-(l-1) cell: its children's stop-0 bits
-  const uint32_t ns_bytes = ((1u << (3 * (L - 1))) - 1u) / 7u;
-  s.ns_off = o; o += align16(ns_bytes ? ns_bytes : 1u);
-  // the stop-0 cells of each level by rank, two buffers (even / odd levels); a level's stop-0 cells
-  // have 8 emitted children each, so there are at most max_nodes / 8 of them
-  uint32_t cap[2] = {1u, 1u};
-  for (uint32_t l = 0; l + 1 <= L; ++l)
-    cap[l & 1u] = std::max(cap[l & 1u], std::min(1u << (3 * l), v.max_nodes / 8u + 1u));
-  s.list0_cap = (cap[0] + 7u) & ~7u;
-  s.list1_cap = cap[1];
-  s.list_off = o; o += align16(2u * (s.list0_cap + cap[1]));
-  const uint32_t span_bytes = o - s.mask_off;
-  // the finest index grid holds one z half at a time for b = 32 (plus the last plane of the first)
-  const uint32_t nh = L == 5 ? 2u : 1u;
-  s.fg_off = o;
-  s.fg_bytes = align16(s.gt_bytes * b * b * b / nh);
-  o += s.fg_bytes;
-  s.plane_off = o; o += nh == 2 ? align16(s.gt_bytes * b * b) : 0u;
-  // private palette copy (frees the stage early); byte grids: a power of two >= max_pal (indices
-  // are masked with pal_cap - 1, so any byte stays in bounds)
-  uint32_t p2 = 16u;
-  while (p2 < v.max_pal) p2 <<= 1;
-  s.pal_cap = s.gt_bytes == 1 ? p2 : (v.max_pal <= 1024u ? v.max_pal : 0u);
-  s.pal_off = o; o += align16(4u * s.pal_cap);
+  SmemLayout s{};
+  uint32_t o = 0, og = 0;  // shared / global scratch bytes placed
+  for (int attempt = 0; attempt < (global ? 2 : 1); ++attempt) {
+    s = SmemLayout{};
+    o = 0;
+    og = 0;
+    const bool all_global = attempt == 1;
+    auto put = [&](bool large, uint32_t bytes) -> uint32_t {  // offset of a region of `bytes`
+      uint32_t& c = global && (large || all_global) ? og : o;
+      const uint32_t at = c;
+      c += bytes;
+      return at;
+    };
+    s.gt_bytes = v.max_pal < kMaxIdx8 ? 1u : 2u;
+    const uint32_t b = 1u << L;
+    const uint32_t ncells = ((1u << (3 * L)) - 1u) / 7u;  // levels 0..L-1
+    // misc: words 0..15 (flags, items, mbarriers), 16..47 warp totals, then 5 (NT / 32) + 5 words
+    // of scan scratch
+    s.misc_off = put(false, align16(4u * (48u + 5u * (threads / 32u) + 5u)));
+    // a single stage may alias the regions a brick fills only after its parse (see stage_alias)
+    const bool pal_always_copied = s.gt_bytes == 1 || v.max_pal <= 1024u;
+    const bool may_alias = nstage == 1 && pal_always_copied && !global;
+    // node operations: written by the parse; bricks without delta operations use their staged
+    // symbols directly, or a copy here when the stage is aliased
+    s.nodes_words = (v.max_nodes + 7u) / 8u + 4u;
+    s.nodes_off = put(true, (v.max_delta || may_alias) ? align16(4 * s.nodes_words) : 0u);
+    s.dlist_cap = v.max_delta;
+    s.dlist_off = put(true, align16(4 * (v.max_delta ? v.max_delta : 1u)));
+    // cursor masks (2 u32 masks + 2 prefixes per word of 32 nodes), level grids, stop bytes and
+    // rank lists: one contiguous span unless b = 64
+    s.nwords = (v.max_nodes + 31u) / 32u + 2u;
+    s.mask_off = put(true, align16((global ? 16 : 12) * s.nwords));
+    s.g_off = put(false, align16(s.gt_bytes * (ncells + 7u)));  // level 1 starts at cell 8 (alignment)
+    // per level l >= 1 below L, one byte per level-(l-1) cell: its children's stop-0 bits
+    const uint32_t ns_bytes = ((1u << (3 * (L - 1))) - 1u) / 7u;
+    s.ns_off = put(false, align16(ns_bytes ? ns_bytes : 1u));
+    // the stop-0 cells of each level by rank, two buffers (even / odd levels); a level's stop-0
+    // cells have 8 emitted children each, so there are at most max_nodes / 8 of them
+    uint32_t cap[2] = {1u, 1u};
+    for (uint32_t l = 0; l + 1 <= L; ++l)
+      cap[l & 1u] = std::max(cap[l & 1u], std::min(1u << (3 * l), v.max_nodes / 8u + 1u));
+    s.list0_cap = (cap[0] + 7u) & ~7u;
+    s.list1_cap = cap[1];
+    s.list_off = put(false, align16(2u * (s.list0_cap + cap[1])));
+    // the finest index grid holds one z half at a time for b = 32 (plus the last plane of the first)
+    const uint32_t nh = L == 5 ? 2u : 1u;
+    s.fg_bytes = align16(s.gt_bytes * b * b * b / nh);
+    s.fg_off = put(true, s.fg_bytes);
+    s.plane_off = put(false, nh == 2 ? align16(s.gt_bytes * b * b) : 0u);
+    // private palette copy (frees the stage early); byte grids: a power of two >= max_pal (indices
+    // are masked with pal_cap - 1, so any byte stays in bounds)
+    uint32_t p2 = 16u;
+    while (p2 < v.max_pal) p2 <<= 1;
+    s.pal_cap = s.gt_bytes == 1 ? p2 : (v.max_pal <= 1024u ? v.max_pal : 0u);
+    s.pal_off = put(false, align16(4u * s.pal_cap));
+    if (!global || o + 64u <= (uint32_t)optin) break;  // (+ the kernel's static shared words)
+  }
+  const uint32_t span_bytes = s.fg_off - s.mask_off;  // masks .. rank lists (b <= 32)
   if (global) {  // nothing staged: the record and symbols are read where they are
     s.stage_alias = 0;
     s.wst_off = s.fg_off;
@@ -292,14 +307,15 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
     s.stage_bytes = 0;
     s.nstage = nstage;
     s.stage_off = o;
-    s.total = o;
-    s.gscratch = (o + 255u) & ~255u;
+    s.total = o;  // shared bytes (0: everything in the slice)
+    s.gscratch = (og + 255u) & ~255u;
     s.ws_stride = align16((v.max_sym + 1u) / 2u) + 16u;
     s.a_buf = 0;
     s.a_smem = 4u * kRansM;
     *out = s;
     return VC_OK;
   }
+  const bool may_alias = nstage == 1 && (s.gt_bytes == 1 || v.max_pal <= 1024u);
   const uint32_t fixed = o;
   uint32_t stage = align16(v.max_stage) + 16u;  // slack for 8-nibble windows at the end
   s.wst_off = s.fg_off;
@@ -503,7 +519,7 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   const uint32_t nt = v.sched.threads;
   void* k = pick_kernel(v.L, nt, SL.gt_bytes == 2, rans, batched);
   if (!k) return VC_ERR_UNSUPPORTED;
-  const uint32_t smem = scratch ? 0u : SL.total;
+  const uint32_t smem = SL.total;  // b = 64: the small regions in shared memory (0: all in the scratch slice)
   if (!set_smem(k, smem)) return VC_ERR_CUDA;
   if (rans && !set_smem(reinterpret_cast<void*>(&rans_symbols_kernel), SL.a_smem)) return VC_ERR_CUDA;
   // workspace: the rANS symbols of the n items, then (b = 64) one scratch slice per block
@@ -511,7 +527,7 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   uint32_t sgrid = 0;
   if (scratch) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)nt, 0) != cudaSuccess) return VC_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)nt, smem) != cudaSuccess) return VC_ERR_CUDA;
     if (per_sm < 1) return VC_ERR_UNSUPPORTED;
     sgrid = std::min(scratch_grid(v, n), std::max(1u, v.sms) * (uint32_t)per_sm);
     if (ws_ext) {

@@ -409,7 +409,7 @@ __device__ __forceinline__ void store_pair(GT* fg, uint32_t pos, uint32_t lo, ui
 // read: right after the finest grid is filled when the palette fits its shared copy, else at the end.
 template <int L, typename GT, bool RANS, int NT, typename Hook>
 __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32_t* sw, uint32_t* out,
-                             unsigned char* sm, int* s_err, Hook&& on_stage_free) {
+                             unsigned char* sm, unsigned char* gm, int* s_err, Hook&& on_stage_free) {
   constexpr uint32_t NW = NT / 32;
   constexpr uint32_t MARK = GridT<GT>::MARK;
   const SmemLayout& SL = P.v.sm;
@@ -434,14 +434,14 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   }
   c.op_mask = P.v.op_mask;
   c.s_err = s_err;
-  uint32_t* dlist = reinterpret_cast<uint32_t*>(sm + SL.dlist_off);
+  uint32_t* dlist = reinterpret_cast<uint32_t*>(gm + SL.dlist_off);
   c.dlist = dlist;
   c.dlist_cap = nd < SL.dlist_cap ? nd : SL.dlist_cap;
 
   // 1. operations per node
   if (nd == 0 && SL.stage_alias) {
     // the symbols are the operations; copied out of the stage, which step 2 overwrites
-    uint32_t* nodes = reinterpret_cast<uint32_t*>(sm + SL.nodes_off);
+    uint32_t* nodes = reinterpret_cast<uint32_t*>(gm + SL.nodes_off);
     const uint32_t nw = min((S + 7u) / 8u + 2u, SL.nodes_words);
     for (uint32_t i = tid; i < nw; i += NT) nodes[i] = sw[i];
     c.nodes = nodes;
@@ -451,9 +451,9 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     c.nodes = sw;
     c.n_nodes = S;
   } else {
-    uint32_t* nodes = reinterpret_cast<uint32_t*>(sm + SL.nodes_off);
+    uint32_t* nodes = reinterpret_cast<uint32_t*>(gm + SL.nodes_off);
     // the finest grid's region is idle during the parse: it keeps the per-word automaton masks
-    uint32_t* wst = ((S + 7u) >> 3) * 4u <= SL.wst_bytes ? reinterpret_cast<uint32_t*>(sm + SL.wst_off) : nullptr;
+    uint32_t* wst = ((S + 7u) >> 3) * 4u <= SL.wst_bytes ? reinterpret_cast<uint32_t*>(gm + SL.wst_off) : nullptr;
     const ParseOut po = parse_stream<NT, (L >= 6)>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap, scan_tmp, wst, s_err,
                                                    short_delta);
     c.nodes = nodes;
@@ -466,7 +466,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   }
 
   // 2. palette-cursor masks and prefix counts (32 nodes per word)
-  uint32_t* adv_mask = reinterpret_cast<uint32_t*>(sm + SL.mask_off);
+  uint32_t* adv_mask = reinterpret_cast<uint32_t*>(gm + SL.mask_off);
   uint32_t* del_mask = adv_mask + SL.nwords;
   // prefix counts: 16 bits while a brick has fewer than 2^16 nodes (b <= 32), 32 bits beyond
   using Pre = typename std::conditional<(L >= 6), uint32_t, uint16_t>::type;
@@ -515,7 +515,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   const bool no_stop = (P.v.flags & kFlagNoStop) != 0;
   constexpr uint32_t b = 1u << L;
   const bool finest = Lout == (uint32_t)L;
-  GT* fg = reinterpret_cast<GT*>(sm + SL.fg_off);
+  GT* fg = reinterpret_cast<GT*>(gm + SL.fg_off);
 
   // the 8 children (nodes j0 .. j0+7) of a stop-0 cell with index gp at coordinates (px, py, pz):
   // palette indices or neighbour marks into v, returns the children emitted with stop bit 0
@@ -978,7 +978,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) decode_grid_kernel(const _
   }
   __syncthreads();
   uint32_t* out = P.cache + (size_t)P.slots[item] * P.out_words;
-  decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, s_err, [] {});
+  decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, sm, s_err, [] {});
   __syncthreads();
   if (threadIdx.x == 0 && *s_err) report(P.status, *s_err, item);
 }
@@ -1066,7 +1066,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) decode_batched_kernel(cons
                                            : head + 4u + head[0]);
       uint32_t* out = P.cache + (size_t)P.slots[item] * P.out_words;
       // depth 1: the next item's copy starts as soon as this brick's stage is free
-      decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, s_err, [&] {
+      decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, sm, s_err, [&] {
         if (!prefetch && tid == 0) claim_and_issue(0);
         released = true;
       });
@@ -1083,14 +1083,19 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) decode_batched_kernel(cons
 }
 
 // b = 64: the working set of one brick (about a megabyte: nodes, masks, grids) is beyond shared
-// memory, so each persistent block keeps its regions in its own slice (P.v.sm.gscratch bytes) of
-// a global-memory scratch buffer, largely L2-resident, and reads the record and symbols where they
-// are. Blocks pull items from the work counter in status[2] (items item_base + counter).
+// memory, so each persistent block keeps the large regions (node operations, delta values, cursor
+// masks, the 64^3 index grid) in its own slice (P.v.sm.gscratch bytes) of a global-memory
+// scratch buffer, largely L2-resident, and the rest (scan scratch, palette copy, level grids, stop
+// bytes, rank lists) in shared memory, or everything in the slice when those do not fit
+// (P.v.sm.total = 0). It reads the record and symbols where they are. Blocks pull items from the
+// work counter in status[2] (items item_base + counter).
 template <int L, typename GT, bool RANS, int NT>
 __global__ void __launch_bounds__(NT) decode_scratch_kernel(const __grid_constant__ Params P, uint8_t* scratch) {
+  extern __shared__ __align__(128) unsigned char dyn_sm[];
   __shared__ int s_err;
   __shared__ uint32_t s_item;
-  unsigned char* sm = scratch + (size_t)blockIdx.x * P.v.sm.gscratch;
+  unsigned char* gm = scratch + (size_t)blockIdx.x * P.v.sm.gscratch;
+  unsigned char* sm = P.v.sm.total ? dyn_sm : gm;
   uint32_t* counter = reinterpret_cast<uint32_t*>(P.status) + 2;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -1107,7 +1112,7 @@ __global__ void __launch_bounds__(NT) decode_scratch_kernel(const __grid_constan
     } else {
       const ItemSrc src = item_src<RANS>(P, item, brick);
       uint32_t* out = P.cache + (size_t)P.slots[item] * P.out_words;
-      decode_brick<L, GT, RANS, NT>(P, src.rec, src.stream, out, sm, &s_err, [] {});
+      decode_brick<L, GT, RANS, NT>(P, src.rec, src.stream, out, sm, gm, &s_err, [] {});
       __syncthreads();
       if (threadIdx.x == 0 && s_err) report(P.status, s_err, item);
     }

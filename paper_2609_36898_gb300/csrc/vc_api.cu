@@ -304,7 +304,7 @@ vc_status vc_volume_info_get(const vc_volume* vol, vc_volume_info* info) {
   info->max_delta = v->max_delta;
   info->encoded_bytes = v->encoded_bytes;
   info->device_bytes = v->device_bytes;
-  info->smem_bytes = v->dv.sm.gscratch ? 0u : v->dv.sm.total;
+  info->smem_bytes = v->dv.sm.total;
   info->split = v->split ? 1u : 0u;
   info->host_bytes = v->host_bytes;
   info->device = (uint32_t)v->device;

@@ -2,7 +2,7 @@
 
 A 64^3 brick's working set (node operations, cursor masks, level grids, the 64^3 index grid) is
 beyond a thread block's shared memory, so these bricks are decoded by persistent blocks that keep
-it in global scratch slices. Bit-exact against the CPU oracle on every brick of ragged volumes,
+its large parts in global scratch slices and the rest in shared memory. Bit-exact against the CPU oracle on every brick of ragged volumes,
 both coders, every schedule and thread count, several levels of detail, 8- and 16-bit index
 grids, cache paletting, the allocation-free entry point, the serving runtime with graph-launched
 batches, and per-item error reporting.
@@ -69,7 +69,7 @@ def test_b64_parity_every_brick_every_schedule(ragged, coder):
     vol = vc.Volume(enc)
     try:
         info = vc.vc_volume_info_get(vol.handle)
-        assert info.brick_size == 64 and info.smem_bytes == 0
+        assert info.brick_size == 64 and 0 < info.smem_bytes <= 227 * 1024  # the small regions only
         assert vc.vc_volume_get_schedule(vol.handle)[0] == 512
         ids = np.arange(vol.n_bricks)
         for lod in (0, 1, 2, 4, 6):
