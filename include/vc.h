@@ -183,7 +183,7 @@ typedef struct vc_schedule {
 /* Sets the schedule used by later decode calls on this volume (host only; not while a decode of
  * this volume is being enqueued from another thread). VC_ERR_UNSUPPORTED if the combination
  * is not built or its shared memory does not fit; the previous schedule then stays. The default
- * after loading is {256, 1, 0, 512} ({512, 1, 0, 512} for b = 64). For b = 64 every schedule runs
+ * after loading is {256, 1, 0, 512} ({1024, 1, 0, 512} for b = 64). For b = 64 every schedule runs
  * one persistent kernel (blocks_per_sm, 0 = 2, blocks per SM, each with its own global scratch
  * slice); stage_depth and chunk have no effect there. */
 vc_status vc_volume_set_schedule(vc_volume* vol, const vc_schedule* sched);

@@ -219,7 +219,7 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   if (!v->h_rec_words) { delete v; return VC_ERR_OOM; }
   for (uint32_t i = 0; i < n_bricks; ++i) v->h_rec_words[i] = le32(st + 4 * ((size_t)i + 1)) - le32(st + 4 * (size_t)i);
   v->encoded_bytes = nbytes;
-  v->sched.threads = L >= 6 ? 512 : 256;  // b = 64: more threads per (much larger) brick
+  v->sched.threads = L >= 6 ? 1024 : 256;  // b = 64: more threads per (much larger) brick
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     std::free(v->h_rec_words);

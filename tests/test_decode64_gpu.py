@@ -70,7 +70,7 @@ def test_b64_parity_every_brick_every_schedule(ragged, coder):
     try:
         info = vc.vc_volume_info_get(vol.handle)
         assert info.brick_size == 64 and 0 < info.smem_bytes <= 227 * 1024  # the small regions only
-        assert vc.vc_volume_get_schedule(vol.handle)[0] == 512
+        assert vc.vc_volume_get_schedule(vol.handle)[0] == 1024
         ids = np.arange(vol.n_bricks)
         for lod in (0, 1, 2, 4, 6):
             ref = oracle_bricks(enc, ids, lod)
