@@ -233,8 +233,12 @@ vc_status vc_decode_bricks(vc_volume* vol, const uint32_t* brick_ids, uint32_t n
 /* Same as vc_decode_bricks with host arrays: copies brick_ids (host, n x u32) to the device,
  * decodes brick i into slot i of the volume's own device staging cache and copies the labels back
  * to labels_out (host, n * (b >> lod)^3 u32, brick i at offset i * (b >> lod)^3). Synchronous.
- * *status_out receives the device status word 0. Host buffers are best pinned. The staging
- * buffers are allocated on first use and grow as needed (owned by the volume). */
+ * *status_out receives the device status word 0. If labels_out is pinned host memory that CUDA
+ * maps into the device's address space (cudaHostAlloc, or cudaHostRegister with mapping; 16-byte
+ * aligned), the decode kernels write the labels into it directly over the host link (NVLink-C2C
+ * on GB300) and no device staging buffer or copy is used; otherwise the labels go through a
+ * device staging buffer and one device-to-host copy. The staging buffers are allocated on first
+ * use and grow as needed (owned by the volume). */
 vc_status vc_decode_bricks_host(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, uint32_t lod,
                                 uint32_t mode, uint32_t* labels_out, int32_t* status_out, void* cuda_stream);
 

@@ -383,7 +383,18 @@ vc_status vc_decode_bricks_host(vc_volume* vol, const uint32_t* brick_ids, uint3
       return VC_ERR_CUDA;
     v->host_cap_items = n;
   }
-  if (words > v->host_cap_words) {
+  // pinned host memory that CUDA maps into the device's address space: the decode kernels write
+  // the labels there directly (over NVLink-C2C on GB300), with no staging buffer and no copy
+  uint32_t* direct = nullptr;
+  {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, labels_out) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer && !(reinterpret_cast<uintptr_t>(pa.devicePointer) & 15u))
+      direct = static_cast<uint32_t*>(pa.devicePointer);
+    else
+      cudaGetLastError();
+  }
+  if (!direct && words > v->host_cap_words) {
     cudaFree(v->d_host_cache);
     v->d_host_cache = nullptr;
     v->host_cap_words = 0;
@@ -396,10 +407,11 @@ vc_status vc_decode_bricks_host(vc_volume* vol, const uint32_t* brick_ids, uint3
   if (cudaMemsetAsync(v->d_host_status, 0, 4 * VC_STATUS_WORDS, stream) != cudaSuccess) return VC_ERR_CUDA;
   if (cudaMemcpyAsync(v->d_host_ids, brick_ids, 4 * (size_t)n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return VC_ERR_CUDA;
-  vc_status rc = launch_decode(*v, v->d_host_ids, n, v->d_host_slots, v->d_host_cache, lod, mode, v->d_host_status,
-                               stream);
+  vc_status rc = launch_decode(*v, v->d_host_ids, n, v->d_host_slots, direct ? direct : v->d_host_cache, lod, mode,
+                               v->d_host_status, stream);
   if (rc != VC_OK) return rc;
-  if (cudaMemcpyAsync(labels_out, v->d_host_cache, 4 * words, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+  if (!direct &&
+      cudaMemcpyAsync(labels_out, v->d_host_cache, 4 * words, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
     return VC_ERR_CUDA;
   int32_t st = 0;
   if (cudaMemcpyAsync(&st, v->d_host_status, 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess) return VC_ERR_CUDA;

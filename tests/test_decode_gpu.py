@@ -181,16 +181,26 @@ def test_out_of_range_brick_id_reports_arg(small_volume):
 
 
 def test_host_entry_point_matches_device_path(small_volume):
+    """Pageable output goes through a device staging buffer and a copy; pinned (mapped) output is
+    written by the decode kernels directly. Both give the oracle's labels, in every schedule."""
     enc = oracle.encode_volume(small_volume, 4, coder=1)
     n = oracle.header(enc)["n_bricks"]
     vol = vc.Volume(enc)
     try:
+        ids = np.arange(n, dtype=np.uint32)[::-1].copy()
         for lod in (0, 1):
             e = 16 >> lod
-            labels = np.empty((n, e, e, e), dtype=np.uint32)
-            st = vc.vc_decode_bricks_host(vol.handle, np.arange(n, dtype=np.uint32), lod, vc.VC_MODE_BATCHED, labels)
-            assert st == 0
-            assert np.array_equal(labels, oracle_bricks(enc, range(n), lod))
+            ref = oracle_bricks(enc, ids, lod)
+            for pinned in (False, True):
+                for mode in (vc.VC_MODE_BATCHED, vc.VC_MODE_GRID, vc.VC_MODE_PIPELINED):
+                    if pinned:
+                        buf = torch.full((n * e ** 3,), -1, dtype=torch.int32, pin_memory=True)
+                        labels = buf.numpy().view(np.uint32).reshape(n, e, e, e)
+                    else:
+                        labels = np.full((n, e, e, e), 0xFFFFFFFF, dtype=np.uint32)
+                    st = vc.vc_decode_bricks_host(vol.handle, ids, lod, mode, labels)
+                    assert st == 0
+                    assert np.array_equal(labels, ref), (lod, pinned, mode)
     finally:
         vol.release()
 
