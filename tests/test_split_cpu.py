@@ -41,3 +41,26 @@ def test_split_counts_uniform_and_corrupt():
     assert ex.value.code == vc.VC_ERR_CORRUPT
     with pytest.raises(vc.VCError):
         vc.vc_split_counts(enc, 1)  # no such brick
+
+
+def test_split_load_rejects_undecodable_records_before_touching_a_device():
+    """The split loader decodes every record on the host first: a record whose rANS words do not
+    decode, or whose stream ends inside the coarse levels, fails with VC_ERR_FORMAT before any
+    CUDA call."""
+    V = synth.fill(synth.small(dims=(64, 64, 32), seed=5, diameter=10.0, bg=0.2))
+    enc = vc.vc_encode_volume(V, 4, op_mask=0x7F, coder=1)
+    h = oracle.header(enc)
+    rec0 = (128 + 4 * (h["n_bricks"] + 1) + 15) & ~15
+    rec = oracle.brick_record(enc, 3)
+    # brick 3's coded word count: one word short of what its states consume
+    off = rec0 + 4 * rec["offset_words"] + 8
+    bad = enc.copy()
+    bad[off:off + 4] = np.frombuffer(np.uint32(rec["coded_bytes"] - 2).tobytes(), np.uint8)
+    with pytest.raises(vc.VCError) as ex:
+        vc.vc_load_compressed_split(bad, 0, 0)
+    assert ex.value.code in (vc.VC_ERR_FORMAT,)
+    # a plain-coded brick whose stream stops after the root
+    g = oracle.pack_single_brick(3, [oracle.OP_ADV], [7], 0)
+    with pytest.raises(vc.VCError) as ex:
+        vc.vc_load_compressed_split(g, 0, 0)
+    assert ex.value.code == vc.VC_ERR_FORMAT
