@@ -226,7 +226,9 @@ vc_status vc_volume_slot_words(const vc_volume* vol, uint32_t lod, uint32_t pale
  * Returns VC_ERR_ARG for bad host-side arguments and VC_ERR_CUDA if a launch fails; stream-side
  * errors (an id >= n_bricks: VC_ERR_ARG; an invalid record: VC_ERR_CORRUPT) land in status_dev.
  * At lod > 0 only the levels needed are decoded, so corruption in finer levels may go unreported.
- * n = 0 is a no-op. Calls that overlap on the GPU must not share a status buffer. */
+ * Requests of 1024 or more items in the grid and batched schedules run longest record first (one
+ * small sorting kernel; the result does not depend on the order). n = 0 is a no-op. Calls that
+ * overlap on the GPU must not share a status buffer. */
 vc_status vc_decode_bricks(vc_volume* vol, const uint32_t* brick_ids, uint32_t n, const uint32_t* cache_slots,
                            uint32_t* cache, uint32_t lod, uint32_t mode, int32_t* status_dev, void* cuda_stream);
 
