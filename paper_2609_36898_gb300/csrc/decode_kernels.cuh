@@ -577,10 +577,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
 #pragma unroll
       for (int o = 0; o < 8; ++o) v[o] = 0;  // keep invalid indices out of the grids
     }
-    // children with stop bit 0; at the finest level (no children) the children that are
-    // neighbour copies instead
-    if (at_finest) return bad ? 0u : (m_nx | m_ny | m_nz);
-    return gather_nib_bits((~ops & 0x88888888u) >> 3);
+    return gather_nib_bits((~ops & 0x88888888u) >> 3);  // children with stop bit 0
   };
   auto store8 = [&](GT* dst, const uint32_t (&v)[8]) {  // 8 consecutive cells
     if constexpr (sizeof(GT) == 1) {
@@ -704,12 +701,6 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     constexpr uint32_t PC = (hcells + NT - 1) / NT;
     const uint32_t ftid = flin<L>(tid & (NT - 1u) & (hcells - 1u));
     const uint16_t* plist = lists[(L - 1u) & 1u];
-    uint16_t* plist_w = lists[(L - 1u) & 1u];
-    // rank-list entries are level-(L-1) cells (CBITS bits); after a block's operations are decoded
-    // its entry's spare high bits say which of its rows hold neighbour marks (one bit for b = 64)
-    constexpr uint32_t CBITS = 3 * (L - 1);
-    constexpr bool ROWBITS = CBITS + 4 <= 16;
-    constexpr uint32_t CMASK = (1u << CBITS) - 1u;
     GT* plane = reinterpret_cast<GT*>(sm + SL.plane_off);  // z = b/2 - 1, resolved (NH == 2)
     // ranks of the first half: open cells are listed in increasing Morton order
     uint32_t rsplit = npar;
@@ -740,17 +731,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
       for (uint32_t r = rb + tid; r < re; r += NT) {
         const uint32_t p = plist[r];
         uint32_t v[8];
-        const uint32_t mk = decode8(off + 8u * r, Gp[p], compact3(p), compact3(p >> 1), compact3(p >> 2), true, v);
-        // the rows of this block that hold neighbour marks, in the rank list's spare high bits
-        if (mk) {
-          if constexpr (ROWBITS) {
-            const uint32_t t = (mk | (mk >> 1)) & 0x55u;
-            const uint32_t rows = (t & 1u) | ((t >> 1) & 2u) | ((t >> 2) & 4u) | ((t >> 3) & 8u);
-            plist_w[r] = (uint16_t)(p | (rows << CBITS));
-          } else {
-            plist_w[r] = (uint16_t)(p | 0x8000u);
-          }
-        }
+        decode8(off + 8u * r, Gp[p], compact3(p), compact3(p >> 1), compact3(p >> 2), true, v);
         const uint32_t f0 = flin<L>(p) - h * hvox;
         store_pair<GT>(fg, f0, v[0], v[1]);
         store_pair<GT>(fg, f0 + b, v[2], v[3]);
@@ -764,9 +745,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
       // loads, so spread them out)
       for (uint32_t cc = tid; cc < 4u * (re - rb); cc += NT) {
         const uint32_t row = cc & 3u;
-        const uint32_t e = plist[rb + (cc >> 2)];
-        if (ROWBITS ? !((e >> (CBITS + row)) & 1u) : !(e >> 15)) continue;  // no marks in this row
-        const uint32_t pos0 = flin<L>(e & CMASK) - h * hvox + (row & 1u) * b + (row >> 1) * (b * b);
+        const uint32_t pos0 = flin<L>(plist[rb + (cc >> 2)]) - h * hvox + (row & 1u) * b + (row >> 1) * (b * b);
 #pragma unroll
         for (uint32_t i = 0; i < 2; ++i) {
           const uint32_t pos = pos0 + i;
