@@ -84,7 +84,7 @@ __device__ __forceinline__ bool rans_steps(const uint32_t* tab, const uint16_t* 
       w3 = ld(wb + 96u + lane);
     }
   };
-#pragma unroll 4
+#pragma unroll 8
   for (uint32_t base = 0; base < full; base += 32u) {
     uint32_t s = 0;
     step(true, s);
