@@ -21,7 +21,7 @@ OP_PARENT, OP_NX, OP_NY, OP_NZ, OP_ADV, OP_LAST, OP_DELTA = range(7)
 OP_ALL = 0x7F
 CODER_PLAIN, CODER_RANS = 0, 1
 FLAG_NO_STOP = 1
-FLAG_SHORT_DELTA = 2  # limited delta: one 4-bit entry per delta operation, delta <= 15
+FLAG_SHORT_DELTA = 2  # limited delta: one 4-bit entry per delta operation holding delta - 1, 2 <= delta <= 16
 ERR_ARG, ERR_FORMAT, ERR_OOM, ERR_CORRUPT = -1, -2, -3, -5
 
 NODE_DTYPE = np.dtype([("level", "<i4"), ("morton", "<u4"), ("op", "<i4"), ("stop", "<i4"),

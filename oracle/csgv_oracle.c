@@ -62,12 +62,15 @@
 #define CODER_PLAIN 0u
 #define CODER_RANS 1u
 #define FLAG_NO_STOP 1u /* encoder wrote no stop bits; a set stop bit is corrupt */
-/* limited back references, the earlier encoding's form (Methods, "Cache paletting": its limited
- * palette back-reference distances could duplicate labels in a palette): a delta operation is
- * followed by exactly one 4-bit entry that holds delta itself, so delta <= 15; a label further
- * back is appended to the palette again */
+/* limited back references, the earlier encoding's form (Results, "CSGV segmentation volume
+ * compression", and Supplementary Fig. "CSGV ablation" caption: the original back reference
+ * stores 1 < delta <= 16 in one 4-bit entry of the operation stream; Methods, "Compressed
+ * segmentation volumes": that entry is limited to 4 bits). Reading of the 4 bits: the entry
+ * holds delta - 1, so entries 1..15 give delta 2..16 and entry 0 (delta 1) is corrupt; bit 3
+ * does not chain. A label further back than 16 entries is appended to the palette again. */
 #define FLAG_SHORT_DELTA 2u
-#define SHORT_DELTA_MAX 15u
+#define SHORT_DELTA_MIN 2u
+#define SHORT_DELTA_MAX 16u
 
 #define RANS_BITS 12
 #define RANS_M (1u << RANS_BITS)
@@ -364,7 +367,7 @@ static int encode_brick(const uint32_t* brick, int L, uint32_t op_mask, uint32_t
       if (!rc) rc = push_sym(out, (uint8_t)(op | (stop << 3)));
       if (!rc && op == OP_DELTA) {
         if (short_delta) {
-          rc = push_sym(out, (uint8_t)delta); /* one entry: delta itself */
+          rc = push_sym(out, (uint8_t)(delta - 1u)); /* one entry: delta - 1 */
         } else {
           uint8_t e[11];
           int ne = oracle_delta_nibbles(delta, e);
@@ -664,9 +667,10 @@ static int replay(const vol_view* V, uint32_t id, uint32_t lod, uint32_t* out, o
           label = rd32(pal + 4 * (size_t)(k - 1));
           break;
         case OP_DELTA: {
-          if (V->flags & FLAG_SHORT_DELTA) { /* one entry holding delta */
+          if (V->flags & FLAG_SHORT_DELTA) { /* one entry holding delta - 1; 2 <= delta <= 16 */
             if (i >= S) { rc = O_ERR_CORRUPT; break; }
-            delta = sym[i++];
+            delta = (uint32_t)sym[i++] + 1u;
+            if (delta < SHORT_DELTA_MIN) { rc = O_ERR_CORRUPT; break; }
           } else {
             int entries = 0;
             for (;;) {

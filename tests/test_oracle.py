@@ -357,10 +357,12 @@ def reuse_volume(seed: int = 3) -> np.ndarray:
 
 @pytest.mark.parametrize("coder", [oracle.CODER_PLAIN, oracle.CODER_RANS])
 def test_short_delta_roundtrip_one_entry_per_delta(small_volume, coder):
-    """Limited delta (the earlier encoding's bounded back references, Methods "Cache paletting"):
+    """Limited delta (the original back reference, which stores 1 < delta <= 16 in one 4-bit
+    entry: Results, "CSGV segmentation volume compression"; Supplementary Fig. "CSGV ablation"):
     lossless, every delta operation carries exactly one entry (S = emitted nodes + delta
-    operations) and every delta is in 2..15."""
+    operations), every delta is in 2..16, and the encoder reaches 16."""
     F = oracle.FLAG_SHORT_DELTA
+    seen = set()
     for V in (small_volume, reuse_volume()):
         for log2b in (2, 3, 4, 5):
             enc = oracle.encode_volume(V, log2b, coder=coder, flags=F)
@@ -371,15 +373,19 @@ def test_short_delta_roundtrip_one_entry_per_delta(small_volume, coder):
                 rec = oracle.brick_record(enc, bid)
                 assert rec["n_sym"] == len(nodes) + rec["n_delta"]
                 d = nodes["delta"][nodes["op"] == OP_DELTA]
-                assert len(d) == rec["n_delta"] and ((d >= 2) & (d <= 15)).all()
+                assert len(d) == rec["n_delta"] and ((d >= 2) & (d <= 16)).all()
+                seen.update(d.tolist())
+    assert 16 in seen and 2 in seen
 
 
 def test_short_delta_duplicates_only_beyond_reach():
     """With limited delta a palette holds a label twice only when its previous copy is more than
-    15 entries back (the duplicates the paper attributes to the earlier encoding); the unlimited
-    encoding of the same data holds none."""
+    16 entries back (the duplicates the paper attributes to the original back reference,
+    Supplementary Fig. "CSGV ablation" caption); a label exactly 17 entries back is appended
+    again; the unlimited encoding of the same data holds none."""
     V = reuse_volume()
     dup = 0
+    dist = set()
     for log2b in (3, 4, 5):
         b = 1 << log2b
         enc = oracle.encode_volume(V, log2b, flags=oracle.FLAG_SHORT_DELTA)
@@ -390,34 +396,52 @@ def test_short_delta_duplicates_only_beyond_reach():
             last = {}
             for k, x in enumerate(pal):
                 if x in last:
-                    assert k - last[x] > 15, (log2b, bid, k)
+                    assert k - last[x] > 16, (log2b, bid, k)
+                    dist.add(k - last[x])
                     dup += 1
                 last[x] = k
             pal_u = oracle.brick_record(ref, bid)["palette"].tolist()
             assert len(pal_u) == len(set(pal_u))
-    assert dup > 0
+    assert dup > 0 and 17 in dist
 
 
 def test_short_delta_streams_checked():
     sym, pal = _golden_stream()
     F = oracle.FLAG_SHORT_DELTA
     C = oracle.ERR_CORRUPT
-    # the LAST at (1,0,0) (k = 2) as delta 1 or 2 in one entry: legal
-    assert _status(list(sym[:10]) + [OP_DELTA, 1] + sym[11:], pal, 1, 0x7F, F) == 0
-    s2 = list(sym[:10]) + [OP_DELTA, 2] + sym[11:]
+    # the LAST at (1,0,0) (k = 2) as delta 2 (entry 1 = delta - 1): legal; delta 1 (entry 0) is
+    # outside 1 < delta <= 16: corrupt
+    s2 = list(sym[:10]) + [OP_DELTA, 1] + sym[11:]
     assert _status(s2, pal, 1, 0x7F, F) == 0
+    assert _status(list(sym[:10]) + [OP_DELTA, 0] + sym[11:], pal, 1, 0x7F, F) == C
     # delta 2 re-reads palette entry 0 where the stream had entry 1
     want = oracle.decode_brick(oracle.pack_single_brick(2, sym, pal, 0), 0)
     got = oracle.decode_brick(oracle.pack_single_brick(2, s2, pal, 1, flags=F), 0)
     assert (got != want).sum() >= 1 and set(np.unique(got).tolist()) <= set(pal)
-    # an entry is a plain 4-bit value: bit 3 does not chain (8 + 1 -> delta 9 > k), 0 is invalid,
-    # and a delta operation needs its entry
+    # an entry is a plain 4-bit value: bit 3 does not chain (entry 8 -> delta 9 > k, then 1 is
+    # read as an operation), delta beyond k is corrupt, and a delta operation needs its entry
     assert _status(list(sym[:10]) + [OP_DELTA, 9] + sym[11:], pal, 1, 0x7F, F) == C
     assert _status(list(sym[:10]) + [OP_DELTA, 8, 1] + sym[11:], pal, 1, 0x7F, F) == C
-    assert _status(list(sym[:10]) + [OP_DELTA, 0] + sym[11:], pal, 1, 0x7F, F) == C
+    assert _status(list(sym[:10]) + [OP_DELTA, 2] + sym[11:], pal, 1, 0x7F, F) == C
     assert _status(list(sym[:-1]) + [OP_DELTA], pal, 1, 0x7F, F) == C
     # without the flag the same two entries chain: delta = (0 << 3) | 1 = 1, legal
     assert _status(list(sym[:10]) + [OP_DELTA, 8, 1] + sym[11:], pal, 1, 0x7F, 0) == 0
+
+
+def test_short_delta_reaches_sixteen():
+    """Limited delta reaches the paper's upper bound delta = 16 with one entry (entry 15): a 4^3
+    brick with 17 palette entries, advanced through in order, then one delta operation that
+    re-reads palette[k - 16] = palette[1]. Without the flag entry 15 chains (bit 3 set) and the
+    stream is corrupt."""
+    F = oracle.FLAG_SHORT_DELTA
+    pal = [1000 + 13 * i for i in range(17)]
+    sym = [OP_ADV] + [OP_ADV] * 8 + [OP_ADV] * 8 + [OP_DELTA, 15] + [OP_PARENT] * 55
+    assert _status(sym, pal, 1, 0x7F, F) == 0
+    out = oracle.decode_brick(oracle.pack_single_brick(2, sym, pal, 1, flags=F), 0)
+    # level-2 node 8 in Morton order is child 0 of level-1 cell (1, 0, 0): voxel (2, 0, 0)
+    assert int(out[0, 0, 2]) == pal[1]
+    assert int(out[0, 0, 0]) == pal[9] and int(out[0, 0, 1]) == pal[10] and int(out[0, 0, 3]) == pal[2]
+    assert _status(sym, pal, 1, 0x7F, 0) == oracle.ERR_CORRUPT
 
 
 def test_long_legal_delta_chain_accepted():
