@@ -63,8 +63,10 @@
  *     5 LAST     palette[k - 1]
  *     6 DELTA    followed by entries e (1..7 of them): delta = (delta << 3) | (e & 7) while e & 8;
  *                label palette[k - delta], 1 <= delta <= k. With flags bit 1 (limited delta, the
- *                earlier encoding's bounded back references, Methods "Cache paletting"): exactly
- *                one entry, delta = e (so delta <= 15; a label further back is appended again)
+ *                original back reference that stores 1 < delta <= 16 in one 4-bit entry: Results,
+ *                "CSGV segmentation volume compression"): exactly one entry, delta = e + 1 with
+ *                e >= 1 (so 2 <= delta <= 16; e = 0 is corrupt; a label further back is appended
+ *                again)
  *     7          invalid
  *   The stop bit is 0 at level L (and everywhere when flags bit 0 is set). A record is valid iff
  *   every symbol is legal, the stream ends exactly after the last node of level L, k ends at
@@ -447,7 +449,7 @@ vc_status vc_release(void* handle);
 
 /* Encodes a volume (host, dims[0] * dims[1] * dims[2] uint32 labels, x fastest) into VCZ1 bytes.
  * log2b in 1..6; op_mask as in the format (bit 4 required); coder 0 (plain) or 1 (rANS); flags bit 0
- * = write no stop bits, bit 1 = limited delta (one entry per delta operation, delta <= 15). Uses `threads` worker threads (0 = all cores). The operation of each node
+ * = write no stop bits, bit 1 = limited delta (one entry per delta operation, 2 <= delta <= 16). Uses `threads` worker threads (0 = all cores). The operation of each node
  * is the first applicable enabled one in the order parent, x, y, z neighbour, last, delta
  * (smallest), advance; coarse nodes hold the mode of their 2^3 children (ties to the smallest
  * label). *out_bytes is allocated by the library; free it with vc_free_bytes. */

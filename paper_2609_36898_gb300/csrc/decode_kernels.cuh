@@ -152,9 +152,12 @@ __device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t& pa
 // an entry and the state stays 1 iff its bit 3 ("another entry follows") is set.
 
 // delta from the entries at nibble i..; 0 when invalid (runs past S or needs an eighth entry).
-// short_delta: one entry holding delta itself.
+// short_delta: one entry holding delta - 1 (2 <= delta <= 16; entry 0 is invalid).
 __device__ __forceinline__ uint32_t read_delta(const uint32_t* sw, uint32_t i, uint32_t S, bool short_delta) {
-  if (short_delta) return i < S ? nib_at(sw, i) : 0u;
+  if (short_delta) {
+    const uint32_t v = i < S ? nib_at(sw, i) : 0u;
+    return v ? v + 1u : 0u;
+  }
   uint32_t d = 0;
 #pragma unroll 1
   for (uint32_t e = 0; e < 7u; ++e) {

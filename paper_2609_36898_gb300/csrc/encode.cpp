@@ -18,7 +18,7 @@
 namespace {
 
 constexpr uint32_t kOpParent = 0, kOpNx = 1, kOpLast = 5, kOpDelta = 6, kOpAdv = 4;
-constexpr uint32_t kShortDeltaMax = 15;  // flags bit 1: the largest delta one 4-bit entry holds
+constexpr uint32_t kShortDeltaMax = 16;  // flags bit 1: one 4-bit entry holds delta - 1, 2 <= delta <= 16
 constexpr uint32_t kM = 4096;
 
 inline void put32(uint8_t* p, uint32_t v) {
@@ -192,7 +192,7 @@ void encode_one(const uint32_t* V, const uint32_t dims[3], uint32_t L, uint32_t 
       out.sym.push_back((uint8_t)(op | (stop << 3)));
       if (op == kOpDelta) {
         if (short_delta) {
-          out.sym.push_back((uint8_t)delta);  // one entry holding delta (<= 15)
+          out.sym.push_back((uint8_t)(delta - 1u));  // one entry holding delta - 1 (delta <= 16)
         } else {
           // octal digits of delta, most significant first; bit 3 = another entry follows
           int nd = 1;
@@ -309,7 +309,7 @@ vc_status vc_encode_volume(const uint32_t* voxels, const uint32_t dims[3], uint3
     return VC_ERR_OOM;
   }
   const bool use_stop = !(flags & 1u);
-  const bool short_delta = (flags & 2u) != 0;  // one 4-bit entry per delta operation: delta <= 15
+  const bool short_delta = (flags & 2u) != 0;  // one 4-bit entry per delta operation: delta <= 16
   parallel_for(n, threads, [&](uint32_t id, uint32_t tid) {
     encode_one(voxels, dims, log2b, id, nb, op_mask, use_stop, short_delta, sp, scratch[tid], bricks[id]);
   });

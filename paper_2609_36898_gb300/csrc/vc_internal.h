@@ -19,7 +19,7 @@ constexpr uint32_t kRansM = 4096u;
 constexpr uint32_t kMaxIdx8 = 0xFCu;      // palette indices below this fit 8-bit grids (marks above)
 constexpr uint32_t kMaxIdx16 = 0xFFF0u;   // same for 16-bit grids
 constexpr uint32_t kFlagNoStop = 1u;
-constexpr uint32_t kFlagShortDelta = 2u;  // a delta operation carries one 4-bit entry: delta itself
+constexpr uint32_t kFlagShortDelta = 2u;  // a delta operation carries one 4-bit entry: delta - 1
 constexpr uint32_t kHandleVolume = 0x564F4C31u;  // "VOL1"
 constexpr uint32_t kHandleServer = 0x53525631u;  // "SRV1"
 constexpr uint32_t kHandleCache = 0x43484331u;   // "CHC1"

@@ -379,10 +379,11 @@ def test_coarsest_labels_straight_from_the_encoding(log2b, coder):
 
 @pytest.mark.parametrize("coder", [0, 1])
 def test_parity_short_delta_variant(small_volume, coder):
-    """Limited delta (flags bit 1: one 4-bit entry per delta operation, delta <= 15): every brick,
-    several levels of detail, every schedule, on a volume whose palettes need re-appended labels
-    and on the small workload; delta operations without their entry or with an invalid one are
-    flagged for exactly their item."""
+    """Limited delta (flags bit 1: one 4-bit entry per delta operation holding delta - 1,
+    2 <= delta <= 16): every brick, several levels of detail, every schedule, on a volume whose
+    palettes need re-appended labels and on the small workload; a hand-packed brick that reaches
+    delta = 16; delta operations without their entry or with an invalid one (entry 0, or delta
+    beyond the palette cursor) are flagged for exactly their item."""
     from test_oracle import reuse_volume
     F = oracle.FLAG_SHORT_DELTA
     for V, log2b in ((reuse_volume(), 3), (reuse_volume(), 5), (small_volume, 4)):
@@ -398,13 +399,18 @@ def test_parity_short_delta_variant(small_volume, coder):
     sym, pal, _ = _corrupt_cases()
     good = (sym, pal, 0)
     for s in (list(sym[:-1]) + [OP_DELTA], list(sym[:10]) + [OP_DELTA, 9] + sym[11:],
-              list(sym[:10]) + [OP_DELTA, 0] + sym[11:]):
+              list(sym[:10]) + [OP_DELTA, 0] + sym[11:], list(sym[:10]) + [OP_DELTA, 2] + sym[11:]):
         enc = oracle.pack_bricks(2, [good, (s, pal, 1), good], coder=coder, flags=F)
         assert oracle.decode_brick_status(enc, 1) == oracle.ERR_CORRUPT
         for mode in MODES:
             out, st = gpu_decode(enc, [0, 1, 2], 0, mode)
             assert st[0] == vc.VC_ERR_CORRUPT and st[1] == 1, (s, mode, st)
-    legal = list(sym[:10]) + [OP_DELTA, 2] + sym[11:]
-    enc = oracle.pack_bricks(2, [good, (legal, pal, 1)], coder=coder, flags=F)
-    out, st = gpu_decode(enc, [0, 1], 0, "batched")
-    assert st[0] == 0 and np.array_equal(out, oracle_bricks(enc, [0, 1], 0))
+    legal = list(sym[:10]) + [OP_DELTA, 1] + sym[11:]
+    pal16 = [1000 + 13 * i for i in range(17)]
+    sym16 = [OP_ADV] * 17 + [OP_DELTA, 15] + [0] * 55  # delta 16 re-reads palette[1]
+    enc = oracle.pack_bricks(2, [good, (legal, pal, 1), (sym16, pal16, 1)], coder=coder, flags=F)
+    ref = oracle_bricks(enc, [0, 1, 2], 0)
+    assert int(ref[2].reshape(4, 4, 4)[0, 0, 2]) == pal16[1]
+    for mode in MODES:
+        out, st = gpu_decode(enc, [0, 1, 2], 0, mode)
+        assert st[0] == 0 and np.array_equal(out, ref), mode
