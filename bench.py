@@ -19,6 +19,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -57,17 +58,34 @@ def job_rate(world: int, units_per_rank_step: int, steps: int, slowest_s: float)
     return world * units_per_rank_step * steps / slowest_s / 1e9
 
 
-def make_workload():
+def make_workload(encoder: str = "library"):
+    """The 512^3 volume and its encoding: by the library's encoder, or (reference arm) by the
+    oracle's, whose bytes are identical."""
     import synth
-    import paper_2609_36898_gb300 as vc
     spec = synth.c2()
     t = time.time()
     V = synth.fill(spec)
     t_gen = time.time() - t
     t = time.time()
-    enc = vc.vc_encode_volume(V, B_LOG2, op_mask=0x7F, coder=CODER_RANS)
+    if encoder == "oracle":
+        import oracle
+        oracle.build()
+        enc = oracle.encode_volume(V, B_LOG2, op_mask=0x7F, coder=CODER_RANS)
+    else:
+        import paper_2609_36898_gb300 as vc
+        enc = vc.vc_encode_volume(V, B_LOG2, op_mask=0x7F, coder=CODER_RANS)
     t_enc = time.time() - t
     return spec, V, enc, t_gen, t_enc
+
+
+def verify_all(cache, V: np.ndarray, e: int, what: str) -> None:
+    """Every decoded brick (slot i = brick i) equals the input volume's voxels."""
+    nz, ny, nx = (s // e for s in V.shape)
+    want = V.reshape(nz, e, ny, e, nx, e).transpose(0, 2, 4, 1, 3, 5).reshape(-1)
+    got = cache[: want.size].cpu().numpy().view(np.uint32)
+    if not np.array_equal(got, want):
+        bad = np.flatnonzero((got != want).reshape(-1, e ** 3).any(axis=1))
+        raise AssertionError(f"{what}: {bad.size} decoded bricks differ from the input volume, first {bad[:8].tolist()}")
 
 
 def algorithmic_bytes(enc: np.ndarray, n_bricks: int, edge: int) -> int:
@@ -83,7 +101,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"vc_bench_clocks_{os.getpid()}.csv")
 
     def __enter__(self):  # noqa: D105
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -193,9 +211,8 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    spec, V, enc, _, _ = make_workload()
+    spec, V, enc, _, _ = make_workload(encoder="oracle")
     import oracle
-    oracle.build()
     total_vox, total_t, nb = 0, 0.0, 0
     for _ in range(args.warmup):
         oracle.decode_brick(enc, 0, 0)
@@ -546,9 +563,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     if int(status[0]) != 0:
         raise RuntimeError(f"decode status {status.tolist()}")
-    # correctness spot check of the warm-up output against the generator (lossless)
-    got = cache[: e ** 3].cpu().numpy().view(np.uint32).reshape(e, e, e)
-    assert np.array_equal(got, V[:e, :e, :e]), "decoded brick 0 differs from the input volume"
+    # correctness of the whole warm-up output against the generator (lossless), every brick,
+    # outside the timed region
+    verify_all(cache, V, e, "warm-up")
 
     vc.vc_volume_kernel_stats(vol.handle, reset=True)
     vc.vc_volume_set_profiling(vol.handle, True)
@@ -575,6 +592,7 @@ def run_ours(args):
     dev_s = max_over_ranks(sum(step_ms) / 1000.0, dev)
     if int(status[0]) != 0:
         raise RuntimeError(f"decode status {status.tolist()}")
+    verify_all(cache, V, e, "timed steps")  # outside the timed region
     vox_per_step = n * e ** 3
     value = job_rate(world, vox_per_step, args.steps, dev_s)
     algo = algorithmic_bytes(enc, n, e)
@@ -647,7 +665,9 @@ def run_ours(args):
             raise RuntimeError(f"host decode status {st}")
     e2e_s = time.perf_counter() - t0
     e2e_val = world * vox_per_step * e2e_steps / e2e_s / 1e9
-    assert np.array_equal(labels_np[: e ** 3].reshape(e, e, e), V[:e, :e, :e])
+    nz, ny, nx = (s // e for s in V.shape)
+    if not np.array_equal(labels_np, V.reshape(nz, e, ny, e, nx, e).transpose(0, 2, 4, 1, 3, 5).reshape(-1)):
+        raise AssertionError("end-to-end decode differs from the input volume")
 
     # detail split: the same volume with its finest level left in (mapped, pinned) host memory
     split = None

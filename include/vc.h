@@ -393,9 +393,10 @@ vc_status vc_brick_cache_invalidate(vc_brick_cache* c, uint32_t entry);
 vc_status vc_brick_cache_stats_get(vc_brick_cache* c, vc_brick_cache_stats* out);
 
 /* ---- decode without allocation (the paper has no counterpart) ----
- * For callers that must not allocate device memory while decoding: code that runs inside CUDA
- * stream capture, real-time loops that cannot wait for the allocator, processes whose device
- * memory is reserved up front. vc_decode_bricks allocates the rANS symbol workspace per call
+ * For callers that must not allocate device memory while decoding: real-time loops that cannot
+ * wait for the allocator (an allocation may block on other streams' frees), processes whose device
+ * memory is reserved up front by another allocator and may be exhausted on purpose.
+ * vc_decode_bricks allocates the rANS symbol workspace per call
  * (stream-ordered); this entry point uses one statically reserved device array of
  * VC_NOALLOC_WS_BYTES per device instead and allocates nothing (no cudaMalloc, no cudaMallocAsync,
  * no library that allocates).
@@ -403,13 +404,16 @@ vc_status vc_brick_cache_stats_get(vc_brick_cache* c, vc_brick_cache_stats* out)
  *   VC_MODE_BATCHED only (VC_ERR_ARG otherwise).
  *   Size limit: for rANS volumes, n x (16 * ceil(ceil(max_sym / 2) / 16) + 16) bytes (rounded up
  *   to 256) must fit in VC_NOALLOC_WS_BYTES, else VC_ERR_ARG and nothing is enqueued; plain-coded
- *   volumes of b <= 32 use no workspace and have no limit. For b = 64 the rest of the array must
- *   also hold at least one scratch slice of the decoder (VC_ERR_ARG otherwise); the persistent
- *   grid is cut to the slices that fit.
+ *   volumes of b <= 32 need no symbol workspace and have no size limit. Requests of 1024 or more
+ *   bricks also keep their size-aware order (4 n bytes) in the array when it fits after the
+ *   symbols (else they run unordered, with the same result), plain-coded ones included, so they
+ *   share the array too. For b = 64 the rest of the array must also hold at least one scratch
+ *   slice of the decoder (VC_ERR_ARG otherwise); the persistent grid is cut to the slices that
+ *   fit.
  *   Zeroing: the workspace needs none; as for vc_decode_bricks, the caller zeroes status words
  *   0..1 before the first call.
  *   Set-up: the first call on a device (with that device current) looks up the array's device
- *   address once; make that first call outside any stream capture.
+ *   address once (cudaGetSymbolAddress); make that first call before any stream capture.
  *   Concurrency: all calls on one device share the one workspace, so calls whose work may
  *   overlap on the GPU (other streams, other host threads) race on it and corrupt each other's
  *   output; order them on one stream or with events. */

@@ -1,9 +1,9 @@
-// vc_decode_bricks_noalloc: the grid / batched decode with its one piece of scratch memory (the
-// rANS symbol workspace) in a fixed, statically reserved device array instead of stream-ordered
-// allocations. It is meant for callers that must not allocate device memory while decoding:
-// code running inside CUDA stream capture (an allocation inside a capture becomes part of the
-// graph or fails), real-time loops that cannot afford the allocator's latency or its
-// synchronisation, and processes whose device memory is reserved up front.
+// vc_decode_bricks_noalloc: the grid / batched decode with its scratch memory (the rANS symbol
+// workspace, the size-aware order of large requests, the 64^3 decoder's scratch slices) in a
+// fixed, statically reserved device array instead of stream-ordered allocations. It is meant for
+// callers that must not allocate device memory while decoding: real-time loops that cannot
+// afford the allocator's latency or its synchronisation, and processes whose device memory is
+// reserved up front by another allocator.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -13,6 +13,9 @@
 namespace {
 
 constexpr size_t kNoAllocWsBytes = VC_NOALLOC_WS_BYTES;
+// The early size check below compares n * ws_stride with the array size, while the launch rounds
+// the symbol bytes up to 256; the two agree because the size is a multiple of 256.
+static_assert(kNoAllocWsBytes % 256 == 0, "the no-alloc workspace size must be a multiple of 256 bytes");
 constexpr int kMaxDevices = 64;
 
 // Scratch of the rANS symbol kernel for every call of this entry point on a device. Nothing in it

@@ -123,6 +123,46 @@ def test_parity_full_size_512cube_batched(coder):
     assert st2[0] == 0 and np.array_equal(out2, _bricks_of(sub, 32))
 
 
+@pytest.mark.parametrize("mode", ["auto", "grid", "batched"])
+def test_parity_full_size_512cube_bench_path(mode):
+    """The benchmark's exact configuration at full size: the 512^3 volume (rANS, 32^3 bricks, all
+    operations), all 4096 bricks in one call, ids = slots = 0..4095, with the schedule the library's
+    autotuner picks on that very request ("auto": the grid schedule on GB300 with the size-aware
+    order, 256 threads) and with the grid and batched schedules fixed; every brick against the
+    generator's voxels and sampled bricks against the oracle."""
+    spec = synth.c2()
+    V = synth.fill(spec)
+    enc = vc.vc_encode_volume(V, 5, op_mask=0x7F, coder=1)
+    want = _bricks_of(V, 32)
+    vol = vc.Volume(enc, device=0)
+    try:
+        n = vol.n_bricks
+        assert n == 4096
+        ids = torch.arange(n, dtype=torch.int32, device="cuda")
+        cache = torch.full((n * 32 ** 3,), -1, dtype=torch.int32, device="cuda")
+        st = torch.zeros(vc.VC_STATUS_WORDS, dtype=torch.int32, device="cuda")
+        s = torch.cuda.current_stream().cuda_stream
+        if mode == "auto":
+            _, m, _ = vc.vc_volume_autotune(vol.handle, ids.data_ptr(), n, ids.data_ptr(), cache.data_ptr(), 0,
+                                            st.data_ptr(), s, reps=1)
+            torch.cuda.synchronize()
+            st.zero_()
+            cache.fill_(-1)
+        else:
+            m = vc.MODES[mode]
+        for call in range(2):
+            vc.vc_decode_bricks(vol.handle, ids.data_ptr(), n, ids.data_ptr(), cache.data_ptr(), 0, m, st.data_ptr(), s)
+            torch.cuda.synchronize()
+            assert int(st[0]) == 0, st.tolist()
+            out = cache.cpu().numpy().view(np.uint32).reshape(n, 32, 32, 32)
+            bad = np.flatnonzero((out != want).reshape(n, -1).any(axis=1))
+            assert bad.size == 0, f"{mode} call {call}: {bad.size} bricks differ, first {bad[:8].tolist()}"
+        for i in np.random.default_rng(3).choice(n, size=16, replace=False):
+            assert np.array_equal(out[i], oracle.decode_brick(enc, int(i)))
+    finally:
+        vol.release()
+
+
 def test_random_order_duplicates_and_scattered_slots(small_volume):
     enc = oracle.encode_volume(small_volume, 3, coder=1)
     n = oracle.header(enc)["n_bricks"]
