@@ -276,7 +276,8 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
     s.mask_off = put(true, align16((global ? 16 : 12) * s.nwords));
     s.g_off = put(false, align16(s.gt_bytes * (ncells + 7u)));  // level 1 starts at cell 8 (alignment)
     // per level l >= 1 below L, one byte per level-(l-1) cell: its children's stop-0 bits
-    const uint32_t ns_bytes = ((1u << (3 * (L - 1))) - 1u) / 7u;
+    uint32_t ns_bytes = 0;
+    for (uint32_t l = 1; l < L; ++l) ns_bytes += ((1u << (3 * (l - 1))) + 3u) & ~3u;
     s.ns_off = put(false, align16(ns_bytes ? ns_bytes : 1u));
     // the stop-0 cells of each level by rank, two buffers (even / odd levels); a level's stop-0
     // cells have 8 emitted children each, so there are at most max_nodes / 8 of them
@@ -288,15 +289,27 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
     s.list_off = put(false, align16(2u * (s.list0_cap + cap[1])));
     // the finest index grid holds one z half at a time for b = 32 (plus the last plane of the first)
     const uint32_t nh = L == 5 ? 2u : 1u;
-    s.fg_bytes = align16(s.gt_bytes * b * b * b / nh);
+    // label output of b <= 32 bricks keeps 8 children per open level-(L-1) cell instead
+    const uint32_t cap_open = (L - 1u) & 1u ? s.list1_cap : s.list0_cap;  // open level-(L-1) cells
+    const uint32_t cb_bytes = L >= 2 && L <= 5 ? s.gt_bytes * 8u * cap_open : 0u;
+    s.fg_bytes = align16(std::max(s.gt_bytes * b * b * b / nh, cb_bytes));
     s.fg_off = put(true, s.fg_bytes);
     s.plane_off = put(false, nh == 2 ? align16(s.gt_bytes * b * b) : 0u);
-    // private palette copy (frees the stage early); byte grids: a power of two >= max_pal (indices
-    // are masked with pal_cap - 1, so any byte stays in bounds)
+    // private palette copy (frees the stage early); byte grids: a power of two >= max_pal, zero
+    // padded (indices are masked with pal_cap - 1, so any byte stays in bounds)
     uint32_t p2 = 16u;
     while (p2 < v.max_pal) p2 <<= 1;
     s.pal_cap = s.gt_bytes == 1 ? p2 : (v.max_pal <= 1024u ? v.max_pal : 0u);
     s.pal_off = put(false, align16(4u * s.pal_cap));
+    s.rank_off = put(false, align16(2u * std::max(1u, (1u << (3 * (L - 1))) / 32u)));
+    // the queue of open cells with palette reads: the rank list of level L-2, no longer read then
+    s.pq_off = s.list_off + (L & 1u ? 2u * s.list0_cap : 0u);
+    s.pq_cap = L & 1u ? s.list1_cap : s.list0_cap;
+    // per warp a queue of up to 32 x 7 neighbour marks; the node operations, delta values and
+    // cursor masks are no longer read when the queues are filled
+    const uint32_t mq_bytes = 224u * (threads / 32u);
+    const uint32_t dead_span = s.mask_off + 12u * s.nwords - s.nodes_off;
+    s.mq_off = global ? 0u : dead_span >= mq_bytes ? s.nodes_off : put(false, align16(mq_bytes));
     if (!global || o + 64u <= (uint32_t)optin) break;  // (+ the kernel's static shared words)
   }
   const uint32_t span_bytes = s.fg_off - s.mask_off;  // masks .. rank lists (b <= 32)

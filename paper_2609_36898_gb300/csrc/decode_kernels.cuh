@@ -111,6 +111,75 @@ __device__ __forceinline__ uint32_t nib_eq8(uint32_t x, uint32_t v) {
   return z;
 }
 
+// The 4 nibbles in bits 0..15 of x spread to the 4 bytes of the result (nibble i -> byte i).
+__device__ __forceinline__ uint32_t nib4_to_bytes(uint32_t x) {
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  return (x | (x << 4)) & 0x0F0F0F0Fu;
+}
+// The most significant bits of the 4 bytes of x gathered into bits 0..3 (byte i -> bit i).
+__device__ __forceinline__ uint32_t byte_msbs(uint32_t x) { return ((x & 0x80808080u) * 0x00204081u) >> 28; }
+
+// The 8 cells of one sibling group (children 0..7 of a parent, child o = x | y << 1 | z << 2):
+// palette indices or neighbour marks, gt_bytes each, as u32 words (8-bit grids: child o in byte
+// o & 3 of word o >> 2; 16-bit grids: child o in half o & 1 of word o >> 1).
+template <typename GT>
+struct Cells8 {
+  uint32_t w[sizeof(GT) == 1 ? 2 : 4];
+};
+template <typename GT>
+__device__ __forceinline__ void store_cells8(GT* dst, const Cells8<GT>& v) {
+  if constexpr (sizeof(GT) == 1) *reinterpret_cast<uint2*>(dst) = make_uint2(v.w[0], v.w[1]);
+  else *reinterpret_cast<uint4*>(dst) = make_uint4(v.w[0], v.w[1], v.w[2], v.w[3]);
+}
+template <typename GT>
+__device__ __forceinline__ Cells8<GT> load_cells8(const GT* src) {
+  Cells8<GT> v;
+  if constexpr (sizeof(GT) == 1) {
+    const uint2 t = *reinterpret_cast<const uint2*>(src);
+    v.w[0] = t.x; v.w[1] = t.y;
+  } else {
+    const uint4 t = *reinterpret_cast<const uint4*>(src);
+    v.w[0] = t.x; v.w[1] = t.y; v.w[2] = t.z; v.w[3] = t.w;
+  }
+  return v;
+}
+template <typename GT>
+__device__ __forceinline__ uint32_t cell_of(const Cells8<GT>& v, uint32_t o) {
+  if constexpr (sizeof(GT) == 1) return (v.w[o >> 2] >> (8u * (o & 3u))) & 0xFFu;
+  else return (v.w[o >> 1] >> (16u * (o & 1u))) & 0xFFFFu;
+}
+template <typename GT>
+__device__ __forceinline__ void set_cell(Cells8<GT>& v, uint32_t o, uint32_t x) {
+  if constexpr (sizeof(GT) == 1) {
+    const uint32_t sh = 8u * (o & 3u);
+    if (o < 4u) v.w[0] = (v.w[0] & ~(0xFFu << sh)) | (x << sh);
+    else v.w[1] = (v.w[1] & ~(0xFFu << sh)) | (x << sh);
+  } else {
+    const uint32_t sh = 16u * (o & 1u);
+#pragma unroll
+    for (uint32_t i = 0; i < 4; ++i)
+      if ((o >> 1) == i) v.w[i] = (v.w[i] & ~(0xFFFFu << sh)) | (x << sh);
+  }
+}
+
+// Bit o set iff child o of v holds a neighbour mark (8-bit grids: >= 0xFD; 16-bit: >= 0xFFFD).
+template <typename GT>
+__device__ __forceinline__ uint32_t mark_bits(const Cells8<GT>& v) {
+  if constexpr (sizeof(GT) == 1) {
+    const uint32_t a = ((v.w[0] & 0x7F7F7F7Fu) + 0x03030303u) & v.w[0];
+    const uint32_t b = ((v.w[1] & 0x7F7F7F7Fu) + 0x03030303u) & v.w[1];
+    return byte_msbs(a) | (byte_msbs(b) << 4);
+  } else {
+    uint32_t m = 0u;
+#pragma unroll
+    for (uint32_t i = 0; i < 4; ++i) {
+      const uint32_t t = ((v.w[i] & 0x7FFF7FFFu) + 0x00030003u) & v.w[i] & 0x80008000u;
+      m |= (((t >> 15) & 1u) | ((t >> 30) & 2u)) << (2u * i);
+    }
+    return m;
+  }
+}
+
 // Inclusive warp scan of two counters.
 __device__ __forceinline__ void warp_scan2(uint32_t& a, uint32_t& b, uint32_t lane) {
 #pragma unroll
@@ -592,6 +661,150 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     }
   };
 
+  // The same decode as decode8 for parent cell p (Morton code) with the children's cells packed
+  // (Cells8) and the neighbour legality, class masks and marks taken by SWAR over op bytes; the
+  // children emitted with stop bit 0 go to open8.
+  // Palette reads of the sibling group at nodes j0 .. j0+7 (operations ops; e: child o's
+  // operation in byte o & 3 of e[o >> 2]): the cursor k0 (advances before node j0) and the delta
+  // operations dd0 before it come from the masks; per child, exclusive prefix counts within the
+  // group. The advance / last / delta children of v get their palette indices.
+  auto palette8 = [&](uint32_t j0, uint32_t ops, const uint32_t (&e)[2], Cells8<GT>& v, bool& bad) {
+    uint32_t adv[2], lst[2], del[2], palm[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t x = e[h];
+      const uint32_t ge4 = (x + 0x7C7C7C7Cu) & 0x80808080u, ge5 = (x + 0x7B7B7B7Bu) & 0x80808080u;
+      const uint32_t ge6 = (x + 0x7A7A7A7Au) & 0x80808080u, eq7 = (x + 0x79797979u) & 0x80808080u;
+      adv[h] = (ge4 & ~ge5) >> 7;  // 0x01 per advance byte
+      lst[h] = (ge5 & ~ge6) >> 7;
+      del[h] = (ge6 & ~eq7) >> 7;
+      palm[h] = ((ge4 & ~eq7) >> 7) * 0xFFu;
+    }
+    const uint32_t w = j0 >> 5, lt = (1u << (j0 & 31u)) - 1u;
+    const uint32_t k0 = adv_pre[w] + __popc(adv_mask[w] & lt);
+    const uint32_t dd0 = del_pre[w] + __popc(del_mask[w] & lt);
+    const uint32_t na0 = (adv[0] * 0x01010101u) >> 24, nd0 = (del[0] * 0x01010101u) >> 24;
+    const uint32_t ndel = nd0 + ((del[1] * 0x01010101u) >> 24);
+    bool bytewise = false;
+    if constexpr (sizeof(GT) == 1) bytewise = ndel <= 4u;
+    if (bytewise) {
+      // 8-bit grids: indices and the cursor stay below 252 in a valid brick, so all eight
+      // children are computed bytewise: k per byte, the group's delta values by byte permutation
+      // (up to four of them; more in one group take the loop below)
+      const uint32_t K[2] = {k0 * 0x01010101u + adv[0] * 0x01010100u,
+                             (k0 + na0) * 0x01010101u + adv[1] * 0x01010100u};
+      const uint32_t Dp[2] = {del[0] * 0x01010100u, nd0 * 0x01010101u + del[1] * 0x01010100u};
+      uint32_t d4 = 0u;
+#pragma unroll
+      for (uint32_t i = 0; i < 4; ++i) {
+        const uint32_t di = dd0 + i;
+        if (i < ndel) d4 |= (di < c.dlist_cap ? min(dlist[di], 255u) : 0u) << (8u * i);
+      }
+      const uint32_t np4 = n_pal * 0x01010101u;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t t = Dp[h] | (Dp[h] >> 4);
+        t &= 0x00FF00FFu;
+        const uint32_t sel = (t | (t >> 8)) & 0xFFFFu;  // byte i of Dp -> nibble i
+        const uint32_t delm = del[h] * 0xFFu, advm = adv[h] * 0xFFu, lstm = lst[h] * 0xFFu;
+        const uint32_t D = __byte_perm(d4, 0u, sel) & delm;
+        bad |= (~__vcmpltu4(K[h], np4) & advm) != 0u;                    // advance: k < |P|
+        bad |= (__vcmpeq4(K[h], 0u) & lstm) != 0u;                        // last: k >= 1
+        bad |= ((__vcmpeq4(D, 0u) | __vcmpgtu4(D, K[h])) & delm) != 0u;   // delta: 1 <= delta <= k
+        const uint32_t idx = K[h] - lst[h] - D;
+        v.w[h] = (v.w[h] & ~palm[h]) | (idx & palm[h]);
+      }
+    } else {
+      // 16-bit grids, or more than four delta operations in the group: child by child
+      const uint32_t adv8 = byte_msbs(adv[0] << 7) | (byte_msbs(adv[1] << 7) << 4);
+      const uint32_t del8 = byte_msbs(del[0] << 7) | (byte_msbs(del[1] << 7) << 4);
+      uint32_t mp = byte_msbs(palm[0]) | (byte_msbs(palm[1]) << 4);
+      while (mp) {
+        const uint32_t o = __ffs(mp) - 1u;
+        mp &= mp - 1u;
+        const uint32_t op = (ops >> (4u * o)) & 7u;
+        const uint32_t below = (1u << o) - 1u;
+        const uint32_t k = k0 + __popc(adv8 & below);
+        uint32_t idx;
+        if (op == OP_ADV) {
+          bad |= k >= n_pal;
+          idx = k;
+        } else if (op == OP_LAST) {
+          bad |= k == 0u;
+          idx = k - 1u;
+        } else {
+          const uint32_t di = dd0 + __popc(del8 & below);
+          const uint32_t delta = di < c.dlist_cap ? dlist[di] : 0u;
+          bad |= delta == 0u || delta > k;
+          idx = k - delta;
+        }
+        set_cell<GT>(v, o, idx & (sizeof(GT) == 1 ? 0xFFu : 0xFFFFu));
+      }
+    }
+  };
+  // The same decode as decode8 for parent cell p (Morton code), with the children's cells packed
+  // (Cells8): the checks run on the 8 operation nibbles at once, parent copies and neighbour
+  // marks are merged bytewise. The children emitted with stop bit 0 go to open8. With defer_pal
+  // the palette reads are left to the caller (has_pal: the group has some; their cells hold gp).
+  auto decode8p = [&](uint32_t j0, uint32_t gp, uint32_t p, bool at_finest, bool defer_pal, uint32_t& open8,
+                      bool& has_pal) -> Cells8<GT> {
+    Cells8<GT> v;
+    if (j0 + 8u > c.n_nodes) {
+      set_err(s_err, VC_ERR_CORRUPT);
+#pragma unroll
+      for (auto& x : v.w) x = 0u;
+      open8 = 0u;
+      has_pal = false;
+      return v;
+    }
+    const uint32_t ops = nib8_at(c.nodes, j0);
+    if (!at_finest) open8 = gather_nib_bits((~ops & 0x88888888u) >> 3);
+    bool bad = (ops & 0x88888888u) != 0u && (at_finest || no_stop);
+    // per operation nibble (low 3 bits): >= 1, >= 4, == 7
+    const uint32_t x = ops & 0x77777777u;
+    const uint32_t ge1 = (x + 0x77777777u) & 0x88888888u, ge4 = (x + 0x44444444u) & 0x88888888u;
+    const uint32_t eq7 = (x + 0x11111111u) & 0x88888888u;
+    // a neighbour copy along axis a is legal only for children whose coordinate a is even, in a
+    // parent whose coordinate a is > 0: allowed axes of child o = (7 - o) & (positive axes of p)
+    const uint32_t axm = ((p & 0x09249249u) ? 1u : 0u) | ((p & 0x12492492u) ? 2u : 0u) | ((p & 0x24924924u) ? 4u : 0u);
+    const uint32_t axis_bit = x + (x & (x >> 1) & 0x11111111u);  // ops 1, 2, 3 -> 1, 2, 4
+    const uint32_t nbn = ((ge1 & ~ge4) >> 3) * 0xFu;            // nibbles of neighbour copies
+    bad |= (axis_bit & ~(0x01234567u & (axm * 0x11111111u)) & nbn) != 0u || eq7 != 0u;
+    has_pal = (ge4 & ~eq7) != 0u;
+    // child o's operation in byte o & 3 of e[o >> 2]
+    const uint32_t e[2] = {nib4_to_bytes(x & 0xFFFFu), nib4_to_bytes(x >> 16)};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t xb = e[h];
+      const uint32_t nbm = ((((xb + 0x7F7F7F7Fu) & ~(xb + 0x7C7C7C7Cu)) & 0x80808080u) >> 7) * 0xFFu;
+      if constexpr (sizeof(GT) == 1) {
+        v.w[h] = ((gp * 0x01010101u) & ~nbm) | ((xb | 0xFCFCFCFCu) & nbm);  // MARK + axis = 0xFC | op
+      } else {
+        // 16-bit cells: two children per word
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const uint32_t lo = (xb >> (16 * q)) & 0xFFu, hi = (xb >> (16 * q + 8)) & 0xFFu;
+          const uint32_t vlo = (lo >= 1u && lo <= 3u) ? 0xFFFCu | lo : gp;
+          const uint32_t vhi = (hi >= 1u && hi <= 3u) ? 0xFFFCu | hi : gp;
+          v.w[2 * h + q] = vlo | (vhi << 16);
+        }
+      }
+    }
+    if (c.op_mask != 0x7Fu) {
+#pragma unroll
+      for (uint32_t o = 0; o < 7; ++o)
+        if (!((c.op_mask >> o) & 1u)) bad |= nib_eq8(ops, o) != 0;
+    }
+    if (has_pal && !defer_pal) palette8(j0, ops, e, v, bad);
+    if (bad) {
+      set_err(s_err, VC_ERR_CORRUPT);
+#pragma unroll
+      for (auto& w : v.w) w = 0u;  // keep invalid indices out of the grids
+      has_pal = false;
+    }
+    return v;
+  };
+
   // level 0: the root (node 0) must be a palette advance
   if (tid == 0) {
     uint32_t ns0 = 0, g0 = 0;
@@ -605,6 +818,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     G[0] = (GT)g0;
     lists[0][0] = 0;
     misc[8] = ns0;
+    misc[9] = 0u;  // finest level, label output: open cells queued for palette reads
   }
   __syncthreads();
   const bool root_open = misc[8] != 0;
@@ -637,9 +851,9 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     uint32_t cnt = 0;
     for (uint32_t r = r0; r < r1; ++r) {
       const uint32_t p = list_prev[r];
-      uint32_t v[8];
-      const uint32_t open8 = decode8(off + 8u * r, Gp[p], compact3(p), compact3(p >> 1), compact3(p >> 2), false, v);
-      store8(Gl + 8u * p, v);
+      uint32_t open8;
+      bool has_pal;
+      store_cells8<GT>(Gl + 8u * p, decode8p(off + 8u * r, Gp[p], p, false, false, open8, has_pal));
       NSl[p] = (uint8_t)open8;
       cnt += __popc(open8);
     }
@@ -686,10 +900,196 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     gofs_prev = gofs;
     gofs += 1u << (3u * l);
     nsofs_prev = nsofs;
-    nsofs += parents;
+    nsofs += (parents + 3u) & ~3u;  // the next level's bytes start 4-byte aligned
   }
 
-  if (finest) {
+  bool cells_path = false;
+  if constexpr (L >= 2 && L <= 5) {
+    if (finest && !P.pal_bits) {
+      // 4'. finest level with label output. The finest voxels of a level-(L-1) cell that was not
+      // emitted with stop bit 0 all hold that cell's index (in the level grid); only the open
+      // cells' 8 children are decoded, into a buffer by rank (Cells8 each). The output pass then
+      // reads, per pair of x-adjacent cells, the level grid or the children, and writes 4 rows
+      // of 4 labels.
+      cells_path = true;
+      if (tid == 0 && off + 8u * npar != c.n_nodes) set_err(s_err, VC_ERR_CORRUPT);
+      const GT* Gp = G + gofs_prev;  // level L-1, neighbour marks resolved
+      // open level-(L-1) cells as a bit array in Morton order (the level's stop bytes)
+      const uint32_t* ns32 = reinterpret_cast<const uint32_t*>(NS + nsofs_prev);
+      uint16_t* rpre = reinterpret_cast<uint16_t*>(sm + SL.rank_off);  // rank of the first open cell of each 32
+      const uint16_t* plist = lists[(L - 1u) & 1u];
+      GT* cb = reinterpret_cast<GT*>(gm + SL.fg_off);
+      // rank of open cell m (bit m of ns32 set)
+      auto rank_of = [&](uint32_t m, uint32_t w) -> uint32_t {
+        return rpre[m >> 5] + __popc(w & ((1u << (m & 31u)) - 1u));
+      };
+      // 8-bit grids leave the palette reads to a pass over the queued cells only (about a third
+      // of them), so that the warps do not all run them; cells beyond the queue's capacity read
+      // the palette here
+      uint16_t* pq = reinterpret_cast<uint16_t*>(sm + SL.pq_off);
+      constexpr bool defer = sizeof(GT) == 1;
+      for (uint32_t r = tid; r < npar; r += NT) {
+        const uint32_t p = plist[r];
+        if ((ns32[p >> 5] & ((1u << (p & 31u)) - 1u)) == 0u) rpre[p >> 5] = (uint16_t)r;
+        uint32_t open8;
+        bool has_pal;
+        const uint32_t j0 = off + 8u * r;
+        Cells8<GT> v = decode8p(j0, Gp[p], p, true, defer, open8, has_pal);
+        if (defer) {
+          const uint32_t act = __activemask();
+          const uint32_t bal = __ballot_sync(act, has_pal);
+          if (bal) {
+            const uint32_t leader = __ffs(act) - 1u;
+            uint32_t base = 0u;
+            if (lane == leader) base = atomicAdd(misc + 9, (uint32_t)__popc(bal));
+            base = __shfl_sync(act, base, leader);
+            const uint32_t at = base + __popc(bal & lanemask_lt());
+            if (has_pal && at < SL.pq_cap) {
+              pq[at] = (uint16_t)r;
+            } else if (has_pal) {
+              const uint32_t ops = nib8_at(c.nodes, j0);
+              const uint32_t x = ops & 0x77777777u;
+              const uint32_t e[2] = {nib4_to_bytes(x & 0xFFFFu), nib4_to_bytes(x >> 16)};
+              bool bad = false;
+              palette8(j0, ops, e, v, bad);
+              if (bad) {
+                set_err(s_err, VC_ERR_CORRUPT);
+#pragma unroll
+                for (auto& w : v.w) w = 0u;
+              }
+            }
+          }
+        }
+        store_cells8<GT>(cb + 8u * r, v);
+      }
+      __syncthreads();
+      if constexpr (defer) {
+        const uint32_t nq = min(misc[9], SL.pq_cap);
+        for (uint32_t i = tid; i < nq; i += NT) {
+          const uint32_t r = pq[i], j0 = off + 8u * r;
+          const uint32_t ops = nib8_at(c.nodes, j0);
+          const uint32_t x = ops & 0x77777777u;
+          const uint32_t e[2] = {nib4_to_bytes(x & 0xFFFFu), nib4_to_bytes(x >> 16)};
+          Cells8<GT> v = load_cells8<GT>(cb + 8u * r);
+          bool bad = false;
+          palette8(j0, ops, e, v, bad);
+          if (bad) {
+            set_err(s_err, VC_ERR_CORRUPT);
+#pragma unroll
+            for (auto& w : v.w) w = 0u;
+          }
+          store_cells8<GT>(cb + 8u * r, v);
+        }
+        __syncthreads();
+      }
+      // neighbour marks, one per lane: each warp takes 32 open cells (ranks) at a time, lists
+      // their marks in its queue (lane << 3 | child) and its lanes take them in turn. Child o of
+      // cell p copying along axis a takes child o | 1 << a of cell p - e_a (a mark again at most
+      // twice more: the chain is followed); cells that are not open hold their level-grid value.
+      // Marks are replaced in place: a chain that meets a replaced value stops there, with the
+      // same result.
+      uint8_t* mq = gm + SL.mq_off + 224u * warp;
+      for (uint32_t r0 = warp * 32u; r0 < npar; r0 += NT) {
+        const uint32_t r = r0 + lane;
+        const uint32_t mm = r < npar ? mark_bits<GT>(load_cells8<GT>(cb + 8u * r)) : 0u;
+        const uint32_t cnt = __popc(mm);
+        uint32_t inc = cnt;
+#pragma unroll
+        for (uint32_t d = 1; d < 32u; d <<= 1) {
+          const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+          if (lane >= d) inc += t;
+        }
+        const uint32_t T = __shfl_sync(0xFFFFFFFFu, inc, 31);
+        uint32_t pos = inc - cnt;
+#pragma unroll
+        for (uint32_t o = 0; o < 7; ++o)  // child 7 has every coordinate odd: never a mark
+          if ((mm >> o) & 1u) mq[pos++] = (uint8_t)((lane << 3) | o);
+        __syncwarp();
+        for (uint32_t t = lane; t < T; t += 32u) {
+          const uint32_t q = mq[t];
+          const uint32_t rr = r0 + (q >> 3), o = q & 7u;
+          uint32_t p = plist[rr], oo = o;
+          uint32_t g = cb[8u * rr + o];
+#pragma unroll 1
+          for (int hop = 0; hop < 3 && g >= MARK; ++hop) {
+            const uint32_t a = g - MARK;
+            p = morton_dec(p, a);
+            oo |= 1u << a;
+            const uint32_t w = ns32[p >> 5];
+            g = ((w >> (p & 31u)) & 1u) ? (uint32_t)cb[8u * rank_of(p, w) + oo] : (uint32_t)Gp[p];
+          }
+          if (g >= MARK) { set_err(s_err, VC_ERR_CORRUPT); g = 0; }
+          cb[8u * rr + o] = (GT)g;
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+      // output: pair q = (k, cy, cz) covers level-(L-1) cells (2k, cy, cz) and (2k + 1, cy, cz),
+      // i.e. voxels x = 4k .. 4k + 3 of rows y = 2cy, 2cy + 1 and z = 2cz, 2cz + 1. Both the
+      // cells' Morton code and the rows' offset are additive over disjoint bits of q, so the
+      // thread's part and the (unrolled) iteration's part are computed apart.
+      constexpr uint32_t n = 1u << (L - 1);           // level-(L-1) cells per axis
+      constexpr uint32_t KB = L - 2;                  // bits of k
+      constexpr uint32_t NPAIR = n * n * n / 2u;
+      auto pair_morton = [](uint32_t q) -> uint32_t {
+        const uint32_t k = q & ((n >> 1) - 1u), cy = (q >> KB) & (n - 1u), cz = q >> (KB + L - 1);
+        return spread3(2u * k) | (spread3(cy) << 1) | (spread3(cz) << 2);
+      };
+      auto pair_offset = [](uint32_t q) -> uint32_t {
+        const uint32_t k = q & ((n >> 1) - 1u), cy = (q >> KB) & (n - 1u), cz = q >> (KB + L - 1);
+        return (2u * cz * b + 2u * cy) * b + 4u * k;
+      };
+      const uint32_t m_t = pair_morton(tid & (NT - 1u)), o_t = pair_offset(tid & (NT - 1u));
+      const uint32_t pmask = pal_copied && sizeof(GT) == 1 ? SL.pal_cap - 1u : 0xFFFFFFFFu;
+      auto lab = [&](uint32_t idx) -> uint32_t {
+        if constexpr (sizeof(GT) == 1) {
+          if (pal_copied) return c.pal[idx & pmask];
+        }
+        return label_of(c, idx);
+      };
+#pragma unroll
+      for (uint32_t i = 0; i < (NPAIR + NT - 1u) / NT; ++i) {
+        if (NPAIR % NT != 0u && tid + i * NT >= NPAIR) break;
+        const uint32_t m0 = m_t + pair_morton(i * NT);
+        uint32_t* o = out + o_t + pair_offset(i * NT);
+        const uint32_t w = ns32[m0 >> 5];
+        const uint32_t open2 = (w >> (m0 & 31u)) & 3u;
+        const uint32_t ga = Gp[m0], gb = Gp[m0 + 1u];
+        const uint32_t r0 = rank_of(m0, w);  // meaningful only if one of the two is open
+        Cells8<GT> A, B;
+        constexpr uint32_t rep = sizeof(GT) == 1 ? 0x01010101u : 0x00010001u;
+        if (open2 & 1u) {
+          A = load_cells8<GT>(cb + 8u * r0);
+        } else {
+#pragma unroll
+          for (auto& x : A.w) x = ga * rep;
+        }
+        if (open2 & 2u) {
+          B = load_cells8<GT>(cb + 8u * (r0 + (open2 & 1u)));
+        } else {
+#pragma unroll
+          for (auto& x : B.w) x = gb * rep;
+        }
+#pragma unroll
+        for (uint32_t row = 0; row < 4; ++row) {  // row = dy | dz << 1: children 2 row, 2 row + 1
+          uint32_t* dst = o + (row & 1u) * b + (row >> 1) * b * b;
+          if constexpr (sizeof(GT) == 1) {
+            if (pal_copied) {  // zero-padded power-of-two palette copy: masked bytes index it
+              const uint32_t wa = A.w[row >> 1], wb = B.w[row >> 1], k = 2u * (row & 1u);
+              store16(dst, c.pal[__byte_perm(wa, 0u, 0x4440u | k) & pmask],
+                      c.pal[__byte_perm(wa, 0u, 0x4441u | k) & pmask], c.pal[__byte_perm(wb, 0u, 0x4440u | k) & pmask],
+                      c.pal[__byte_perm(wb, 0u, 0x4441u | k) & pmask]);
+              continue;
+            }
+          }
+          store16(dst, lab(cell_of<GT>(A, 2u * row)), lab(cell_of<GT>(A, 2u * row + 1u)),
+                  lab(cell_of<GT>(B, 2u * row)), lab(cell_of<GT>(B, 2u * row + 1u)));
+        }
+      }
+    }
+  }
+  if (cells_path) {
+  } else if (finest) {
     // 4. finest level: constant blocks of stopped level-(L-1) cells, then the 8 operations of each
     // stop-0 cell (from the rank list), the neighbour marks, the output. For b = 32 the index grid
     // holds one z half at a time (levels are in Morton order, whose top bit is z's, so the first
@@ -879,7 +1279,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
       out[0] = label_of(c, Gl[0]);
     }
   }
-  if (!finest || !pal_copied) {
+  if (cells_path || !finest || !pal_copied) {
     __syncthreads();
     on_stage_free();
   }

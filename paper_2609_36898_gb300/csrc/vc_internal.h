@@ -43,7 +43,15 @@ struct SmemLayout {
   uint32_t dlist_cap;
   uint32_t g_off;        // palette index per cell of levels 0..L-1 (gt_bytes each)
   uint32_t ns_off;       // per level, one byte per parent cell: which children have stop bit 0
-  uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each; one z half for b = 32)
+                         // (each level's bytes start 4-byte aligned, so that the level's open
+                         // cells read as a bit array of u32 words in Morton order)
+  uint32_t rank_off;     // u16 per 32 cells of level L-1: rank of the first open cell among them
+  uint32_t pq_off;       // label output, 8-bit grids: ranks of the open cells whose children read the
+  uint32_t pq_cap;       // palette (u16 each, over the rank list of level L-2; pq_cap entries)
+  uint32_t mq_off;       // label output: one 224-byte queue of neighbour marks per warp (over the
+                         // node operations .. cursor masks span, dead by then, or its own region)
+  uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each; one z half for b = 32),
+                         // or (label output, b <= 32) the 8 children of each open level-(L-1) cell by rank
   uint32_t plane_off;    // b = 32: the last z plane of the first half (for -z neighbours of the second)
   uint32_t fg_bytes;     // bytes of the finest grid region
   uint32_t wst_off;      // the parse's per-word automaton masks (the finest grid's region)
