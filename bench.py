@@ -78,6 +78,63 @@ def make_workload(encoder: str = "library"):
     return spec, V, enc, t_gen, t_enc
 
 
+def full_table(freq) -> np.ndarray:
+    """A rANS table with every symbol at least 1 (taken from the largest entry), summing to 4096, so
+    that it codes any slab of a volume."""
+    f = np.asarray(freq, dtype=np.int64).copy()
+    short = int((f == 0).sum())
+    f[f == 0] = 1
+    f[int(np.argmax(f))] -= short
+    return f.astype(np.uint32)
+
+
+def generate_encode(spec, log2b: int, coder: int = CODER_RANS, max_slab_voxels: int = 1 << 28):
+    """VCZ1 bytes of a synthetic volume: generated on the GPU (synth_fill_gpu, the CPU generator's
+    voxels) in z slabs of whole bricks, each slab copied to pinned host memory and encoded on the
+    host cores by the library's encoder while the next slab is generated; all slabs share the rANS
+    table of the first (every symbol kept >= 1) and are joined with vc_concat_volumes_z. Returns
+    (bytes, seconds)."""
+    import torch
+    import synth
+    import paper_2609_36898_gb300 as vc
+    t0 = time.time()
+    nx, ny, nz = (int(d) for d in spec.dims)
+    b = 1 << log2b
+    slab = max(b, min(-(-nz // b) * b, (max_slab_voxels // (nx * ny)) // b * b))
+    z0s = list(range(0, nz, slab))
+    dev = torch.empty((slab, ny, nx), dtype=torch.int32, device="cuda")
+    host = [torch.empty((slab, ny, nx), dtype=torch.int32, pin_memory=True) for _ in range(min(2, len(z0s)))]
+    stream = torch.cuda.current_stream()
+
+    def start(k):
+        t = min(slab, nz - z0s[k])
+        synth.fill_gpu(spec, (0, 0, z0s[k]), (nx, ny, t), dev.data_ptr(), stream.cuda_stream)
+        host[k % len(host)][:t].copy_(dev[:t], non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        return ev, t
+
+    parts, table = [], None
+    pending = start(0)
+    for k in range(len(z0s)):
+        ev, t = pending
+        ev.synchronize()
+        if k + 1 < len(z0s):
+            pending = start(k + 1)  # the GPU generates the next slab while this one is encoded
+        V = host[k % len(host)][:t].numpy().view(np.uint32)
+        if len(z0s) == 1:
+            parts.append(vc.vc_encode_volume(V, log2b, op_mask=0x7F, coder=coder))
+            break
+        if table is None and coder == CODER_RANS:
+            first = vc.vc_encode_volume(V, log2b, op_mask=0x7F, coder=coder)
+            h = np.frombuffer(first[:128].tobytes(), dtype="<u4")
+            table = full_table(h[12:28])
+        parts.append(vc.vc_encode_volume(V, log2b, op_mask=0x7F, coder=coder, freq=table))
+    torch.cuda.synchronize()
+    enc = parts[0] if len(parts) == 1 else vc.vc_concat_volumes_z(parts)
+    return enc, time.time() - t0
+
+
 def verify_all(cache, V: np.ndarray, e: int, what: str) -> None:
     """Every decoded brick (slot i = brick i) equals the input volume's voxels."""
     nz, ny, nx = (s // e for s in V.shape)
@@ -252,31 +309,30 @@ def orbit_camera(vc, i: int, frame: int, dims, width: int, height: int, fov: flo
 
 
 def serving_leg(args, local: int):
-    """Camera-driven serving on the 4096^3 recipe scaled to n^3 (n = --serve-size): 64 orbiting
-    cameras at 1920x1080 request their visible bricks every frame (request stage on the GPU), the
-    server admits, batches and decodes them into a 2 GiB cache; versus plain per-request decoding
-    (one launch per brick, one request after the other, no cache)."""
+    """Camera-driven serving on the 4096^3 hash-grid Voronoi volume (one seed per 16^3 grid cell,
+    ~16M cells; --serve-size n runs the same recipe on n^3 with the image scaled by n/4096): 64
+    orbiting cameras at 1920x1080 request their visible bricks every frame (request stage on the
+    GPU), the server admits, batches and decodes them into a 2 GiB cache, and each request is
+    released as soon as it is complete (the client has used its bricks); versus plain per-request
+    decoding (one launch per brick, no cache)."""
     import torch
     import synth
     import paper_2609_36898_gb300 as vc
     n = args.serve_size
-    spec = synth.c4_scaled(n)
-    t = time.time()
-    V = synth.fill(spec)
-    enc = vc.vc_encode_volume(V, B_LOG2, op_mask=0x7F, coder=CODER_RANS)
-    del V
-    prep = time.time() - t
+    spec = synth.c4() if n == 4096 else synth.c4_scaled(n)
+    enc, prep = generate_encode(spec, B_LOG2)
     stream = torch.cuda.current_stream(local)
     vol = vc.vc_load_compressed(enc, local, stream.cuda_stream)
+    enc_bytes = int(enc.size)
+    del enc
     srv = vc.vc_server_create(2 << 30, local)
     vi = vc.vc_server_add_volume(srv, vol)
     dims = (n, n, n)
-    # 1920 x 1080 on the 4096^3 volume; scaled with the volume edge so that a voxel covers the same
-    # share of the image (the level-of-detail rule sees the same voxel-to-pixel ratios)
+    # 1920 x 1080 on the 4096^3 volume; scaled with the volume edge on smaller stand-ins so that a
+    # voxel covers the same share of the image (the level-of-detail rule sees the same ratios)
     ncam, max_lod = args.serve_cameras, 3
     W, H = max(16, 1920 * n // 4096), max(9, 1080 * n // 4096)
-    lat, rstage, frame_ms = [], [], []
-    prev = []
+    lat, rstage, frame_ms, per_cam = [], [], [], []
     delivered = 0
     t_all = time.perf_counter()
     for f in range(args.serve_frames):
@@ -285,22 +341,18 @@ def serving_leg(args, local: int):
         rids = vc.vc_request_bricks(srv, vi, cams, max_lod)
         t1 = time.perf_counter()
         for r in rids:
-            if vc.vc_wait(srv, r, 120000) != vc.VC_REQ_DONE:
+            if vc.vc_wait(srv, r, 300000) != vc.VC_REQ_DONE:
                 raise RuntimeError("serving request failed")
-        t2 = time.perf_counter()
-        for r in prev:
-            vc.vc_request_release(srv, r)
-        for r in rids:
             info = vc.vc_request_info_get(srv, r)
             lat.append((info.t_done_ns - info.t_submit_ns) / 1e6)
             delivered += info.bytes // 4
-        prev = rids
+            per_cam.append(int(info.n_bricks))
+            vc.vc_request_release(srv, r)
+        t2 = time.perf_counter()
         rstage.append(1000 * (t1 - t0))
         frame_ms.append(1000 * (t2 - t0))
     wall = time.perf_counter() - t_all
     st = vc.vc_server_stats_get(srv)
-    for r in prev:
-        vc.vc_request_release(srv, r)
     vox = st.voxels_decoded
     vc.vc_release(srv)
     cams0 = [orbit_camera(vc, i, 0, dims, W, H) for i in range(ncam)]
@@ -333,22 +385,24 @@ def serving_leg(args, local: int):
     plain_lat = [e[0].elapsed_time(e[c + 1]) for c in range(len(lists))]
     plain_s = plain_lat[-1] / 1000.0
     vc.vc_release(vol)
+    del cache
     pct = lambda a, q: float(np.percentile(np.asarray(a), q)) if len(a) else None  # noqa: E731
     return {
-        "workload": f"{n}^3 Voronoi (4096^3 recipe: one seed per 16^3 cell, 10% background), 32^3 bricks, rANS; "
-                    f"{ncam} orbiting cameras at {W}x{H} (1920x1080 scaled by {n}/4096), {args.serve_frames} frames, "
-                    f"2 GiB cache, lod <= {max_lod}",
+        "workload": f"{n}^3 Voronoi (hash grid, one seed per 16^3 cell, 10% background), 32^3 bricks, rANS "
+                    f"({8.0 * enc_bytes / n ** 3:.2f} bit/voxel, resident on the device); {ncam} orbiting cameras at "
+                    f"{W}x{H}, {args.serve_frames} frames, 2 GiB cache, lod <= {max_lod}; each request released when "
+                    "complete",
         "served": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "requests": len(lat),
                    "gvoxel_s": delivered / wall / 1e9, "decoded_gvoxel_s": vox / wall / 1e9,
                    "request_stage_ms_median": pct(rstage, 50),
                    "camera_stage_alone_ms": camera_stage_ms,
-                   "bricks_requested_per_camera": float(np.mean([len(i) for i, _ in lists])),
+                   "bricks_requested_per_camera": float(np.mean(per_cam)) if per_cam else None,
                    "frame_ms_median": pct(frame_ms, 50), "bricks_decoded": int(st.bricks_decoded),
                    "bricks_hit": int(st.bricks_hit), "batches": int(st.batches), "evictions": int(st.evictions)},
         "plain": {"p50_ms": pct(plain_lat, 50), "p99_ms": pct(plain_lat, 99), "requests": len(lists),
                   "gvoxel_s": plain_vox / plain_s / 1e9 if plain_s > 0 else None,
-                  "note": f"frame 0's requests of the first {len(lists)} cameras, all submitted at once, decoded one "
-                          "after the other with one launch per brick, no cache"},
+                  "note": f"frame 0's requests of the first {len(lists)} cameras, decoded one after the other with one "
+                          "launch per brick, no cache"},
         "metrics": "gvoxel_s = voxels delivered to requests (hits and decodes) per second of the frame loop; "
                    "decoded_gvoxel_s = voxels the server decoded per second; latency = submit to resident",
         "status": int(status[0]),
@@ -357,88 +411,117 @@ def serving_leg(args, local: int):
 
 
 def mixed_serving_leg(args, local: int):
-    """The mixed serving workload: 8 resident volumes (the 8-volume recipe at 256^3 each, brick
-    sizes 16, 32 and 64), Poisson-arriving requests of log-uniform
-    size (1..4096 bricks) of a random volume at about 80 % of the server's measured capacity, a
-    cache budget smaller than the data so that most bricks are decoded; latency submit -> resident.
-    Versus plain per-request decoding of the same arrivals: one launch per brick, one request
-    after another, no cache."""
+    """The mixed serving workload: 8 resident volumes of the 8-volume recipe at their stated sizes
+    (256^3 .. 2048^3, cell diameters 8..64 voxels, 0..40 % background, bricks of 16^3 / 32^3 / 64^3),
+    Poisson-arriving requests of log-uniform size (1..4096 bricks, at most half the cache) of a
+    random volume, a 4 GiB cache (the volumes decode to ~78 GB, so most bricks are decoded),
+    admission by free cache memory; arrival rates of 50, 80 and 95 % of the server's measured
+    capacity (the same requests back to back); latency submit -> resident. Versus plain
+    per-request decoding of the 80 % arrivals: one launch per brick, one request after another,
+    no cache."""
+    import queue
     import threading
     import torch
     import synth
     import paper_2609_36898_gb300 as vc
     rng = np.random.default_rng(77)
-    vols, encs = [], []
-    t = time.time()
+    cache_bytes = 4 << 30
+    vols, edges, names = [], [], []
+    prep = 0.0
+    stream = torch.cuda.current_stream(local)
+    enc_bytes = 0
     for sp in synth.c5():
         b = sp.brick
-        spec = synth.VolumeSpec(dims=(256, 256, 256), grid=sp.grid, seed=sp.seed, lam=sp.lam, bg=sp.bg, brick=b)
-        enc = vc.vc_encode_volume(synth.fill(spec), b.bit_length() - 1, op_mask=0x7F, coder=CODER_RANS)
-        encs.append((enc, b))
-    prep = time.time() - t
-    stream = torch.cuda.current_stream(local)
-    srv = vc.vc_server_create(96 << 20, local, max_batch_items=16384, flags=vc.VC_SERVER_GRAPHS)
-    for enc, b in encs:
-        h = vc.vc_load_compressed(enc, local, stream.cuda_stream)
-        vols.append(h)
-        vc.vc_server_add_volume(srv, h)
+        enc, t = generate_encode(sp, b.bit_length() - 1)
+        prep += t
+        enc_bytes += int(enc.size)
+        vols.append(vc.vc_load_compressed(enc, local, stream.cuda_stream))
+        edges.append(b)
+        names.append(f"{sp.dims[0]}^3/b{b}")
+        del enc
     nreq = args.mixed_requests
     reqs = []
     for _ in range(nreq):
-        vi = int(rng.integers(len(encs)))
+        vi = int(rng.integers(len(vols)))
         nb = int(vc.vc_volume_info_get(vols[vi]).n_bricks)
-        size = int(min(nb, max(1, round(float(np.exp(rng.uniform(0, np.log(4096))))))))
+        cap = (cache_bytes // 2) // (4 * edges[vi] ** 3)
+        size = int(min(nb, cap, max(1, round(float(np.exp(rng.uniform(0, np.log(4096))))))))
         reqs.append((vi, rng.choice(nb, size=size, replace=False).astype(np.uint32)))
-    vox_of = [sum(int(encs[vi][1]) ** 3 for _ in range(len(ids))) for vi, ids in reqs]
+    vox_of = [len(ids) * edges[vi] ** 3 for vi, ids in reqs]
 
-    # capacity: the same requests back to back with no pacing
+    def new_server():
+        srv = vc.vc_server_create(cache_bytes, local, max_batch_items=16384, flags=vc.VC_SERVER_GRAPHS)
+        for h in vols:
+            vc.vc_server_add_volume(srv, h)
+        return srv
+
+    # capacity: the same requests back to back with no pacing (after a warm-up pass of the graphs)
+    srv = new_server()
+    for vi, ids in reqs[:20]:
+        r = vc.vc_submit_bricks(srv, vi, ids)
+        vc.vc_wait(srv, r, 300000)
+        vc.vc_request_release(srv, r)
+    vc.vc_release(srv)
+    srv = new_server()
     t0 = time.perf_counter()
     rids = [vc.vc_submit_bricks(srv, vi, ids) for vi, ids in reqs]
     for r in rids:
-        vc.vc_wait(srv, r, 120000)
+        vc.vc_wait(srv, r, 300000)
         vc.vc_request_release(srv, r)
     cap_s = time.perf_counter() - t0
-    rate = 0.8 * nreq / cap_s  # requests per second at 80 % of capacity
-    vc.vc_release(srv)
-    srv = vc.vc_server_create(96 << 20, local, max_batch_items=16384, flags=vc.VC_SERVER_GRAPHS)
-    for h in vols:
-        vc.vc_server_add_volume(srv, h)
-    gaps = rng.exponential(1.0 / rate, size=nreq)
-    arrivals = np.cumsum(gaps)
-    import queue
-    lat = []
-    q = queue.Queue()
-
-    def waiter():  # completes (and releases) requests in arrival order while more arrive
-        for _ in range(nreq):
-            r = q.get()
-            vc.vc_wait(srv, r, 120000)
-            info = vc.vc_request_info_get(srv, r)
-            lat.append((info.t_done_ns - info.t_submit_ns) / 1e6)
-            vc.vc_request_release(srv, r)
-
-    th = threading.Thread(target=waiter)
-    th.start()
-    t0 = time.perf_counter()
-    for (vi, ids), at in zip(reqs, arrivals):
-        while time.perf_counter() - t0 < at:
-            pass
-        q.put(vc.vc_submit_bricks(srv, vi, ids))
-    th.join()
-    wall = time.perf_counter() - t0
-    st = vc.vc_server_stats_get(srv)
+    cap_rate = nreq / cap_s
     vc.vc_release(srv)
 
-    # plain: the same arrivals, each request decoded on arrival (or when the previous one ends)
-    # with one launch per brick
+    def run_at(frac):
+        srv = new_server()
+        rate = frac * cap_rate
+        arrivals = np.cumsum(np.random.default_rng(78).exponential(1.0 / rate, size=nreq))
+        lat = []
+        q = queue.Queue()
+
+        def waiter():  # completes (and releases) requests in arrival order while more arrive
+            for _ in range(nreq):
+                r = q.get()
+                vc.vc_wait(srv, r, 300000)
+                info = vc.vc_request_info_get(srv, r)
+                lat.append((info.t_done_ns - info.t_submit_ns) / 1e6)
+                vc.vc_request_release(srv, r)
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t0 = time.perf_counter()
+        for (vi, ids), at in zip(reqs, arrivals):
+            while time.perf_counter() - t0 < at:
+                pass
+            q.put(vc.vc_submit_bricks(srv, vi, ids))
+        th.join()
+        wall = time.perf_counter() - t0
+        st = vc.vc_server_stats_get(srv)
+        vc.vc_release(srv)
+        pct = lambda a, p: float(np.percentile(np.asarray(a), p))  # noqa: E731
+        return {"load": frac, "requests_per_s": rate, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                "decoded_gvoxel_s": st.voxels_decoded / wall / 1e9, "delivered_gvoxel_s": sum(vox_of) / wall / 1e9,
+                "bricks_hit": int(st.bricks_hit), "bricks_decoded": int(st.bricks_decoded),
+                "evictions": int(st.evictions), "graph_launches": int(st.graph_launches)}, arrivals
+
+    served = []
+    arrivals80 = None
+    for frac in (0.5, 0.8, 0.95):
+        res, arr = run_at(frac)
+        served.append(res)
+        if frac == 0.8:
+            arrivals80 = arr
+
+    # plain: the first requests of the 80 % arrivals, each decoded on arrival (or when the previous
+    # one ends) with one launch per brick
     status = torch.zeros(vc.VC_STATUS_WORDS, dtype=torch.int32, device="cuda")
-    maxn = max(len(ids) for _, ids in reqs)
-    cache = torch.empty(max(len(ids) * encs[vi][1] ** 3 for vi, ids in reqs), dtype=torch.int32, device="cuda")
+    n_plain = min(nreq, args.mixed_plain_requests)
+    maxn = max(len(ids) for _, ids in reqs[:n_plain])
+    cache = torch.empty(max(len(ids) * edges[vi] ** 3 for vi, ids in reqs[:n_plain]), dtype=torch.int32, device="cuda")
     slots = torch.arange(maxn, dtype=torch.int32, device="cuda")
     plain_lat = []
-    n_plain = min(nreq, args.mixed_plain_requests)
     t0 = time.perf_counter()
-    for (vi, ids), at in zip(reqs[:n_plain], arrivals[:n_plain]):
+    for (vi, ids), at in zip(reqs[:n_plain], arrivals80[:n_plain]):
         while time.perf_counter() - t0 < at:
             pass
         ids_t = torch.from_numpy(ids.view(np.int32)).cuda()
@@ -446,21 +529,18 @@ def mixed_serving_leg(args, local: int):
                             vc.VC_MODE_PLAIN, status.data_ptr(), stream.cuda_stream)
         torch.cuda.synchronize()
         plain_lat.append(1000 * (time.perf_counter() - t0 - at))
+    del cache
     for h in vols:
         vc.vc_release(h)
     pct = lambda a, q: float(np.percentile(np.asarray(a), q)) if len(a) else None  # noqa: E731
     return {
-        "workload": f"8 volumes of the mixed recipe at 256^3 (brick 16, 32 or 64), rANS; {nreq} Poisson requests of "
-                    f"1..4096 bricks at 80 % of capacity ({rate:.0f} requests/s); 96 MiB cache (the data are 512 MiB); "
-                    "CUDA-graph batches",
-        "served": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "requests": len(lat),
-                   "decoded_gvoxel_s": st.voxels_decoded / wall / 1e9,
-                   "delivered_gvoxel_s": sum(vox_of) / wall / 1e9,
-                   "capacity_gvoxel_s": sum(vox_of) / cap_s / 1e9, "bricks_hit": int(st.bricks_hit),
-                   "bricks_decoded": int(st.bricks_decoded), "evictions": int(st.evictions),
-                   "graph_launches": int(st.graph_launches)},
+        "workload": "8 volumes of the mixed recipe at their stated sizes (" + ", ".join(names) + f"; {enc_bytes / 2**30:.2f} "
+                    f"GiB encoded, resident), rANS; {nreq} Poisson requests of 1..4096 bricks (at most half the cache) "
+                    "at 50 / 80 / 95 % of the measured capacity; 4 GiB cache; CUDA-graph batches",
+        "capacity": {"requests_per_s": cap_rate, "gvoxel_s": sum(vox_of) / cap_s / 1e9},
+        "served": served,
         "plain": {"p50_ms": pct(plain_lat, 50), "p99_ms": pct(plain_lat, 99), "requests": len(plain_lat),
-                  "note": "the first requests of the same arrival sequence, decoded one after the other with one "
+                  "note": "the first requests of the 80 % arrival sequence, decoded one after the other with one "
                           "launch per brick, no cache; latency from arrival to completion"},
         "status": int(status[0]),
         "prep_s": prep,
@@ -471,17 +551,12 @@ def subsets_leg(args, local: int):
     """The uneven power-diagram workload (2048 x 2048 x 1024, ~2M cells, log-normal radii, 30 %
     forced-uniform bricks, 131,072 bricks of 32^3): random subsets of 100,000 distinct bricks
     (seeds 30 ..), each decoded in one call with the autotuned schedule into a 13.1 GB slot array;
-    inputs resident, CUDA events around each call. Opt-in (--subsets K): generating and encoding
-    the 17 GB volume takes the host a minute or more."""
+    inputs resident, CUDA events around each call (--subsets K of them)."""
     import torch
     import synth
     import paper_2609_36898_gb300 as vc
-    t = time.time()
     spec = synth.c3()
-    V = synth.fill(spec)
-    enc = vc.vc_encode_volume(V, B_LOG2, op_mask=0x7F, coder=CODER_RANS)
-    del V
-    prep = time.time() - t
+    enc, prep = generate_encode(spec, B_LOG2)
     vol = vc.Volume(enc, device=local)
     n_all, e = vol.n_bricks, vol.b
     stream = torch.cuda.current_stream(local)
@@ -520,6 +595,33 @@ def subsets_leg(args, local: int):
             "subsets": len(rates), "gvoxel_s": rates, "gvoxel_s_mean": float(np.mean(rates)),
             "algorithmic_gbs_mean": float(np.mean([a * r / (n * e ** 3) for a, r in zip(algo, rates)])),
             "bits_per_voxel": 8.0 * enc.size / (2048 * 2048 * 1024), "prep_s": prep}
+
+
+ABLATION_PREFIXES = [("P", 0x10, 0), ("P+parent", 0x11, 0), ("P+parent+x", 0x13, 0), ("P+parent+x+y", 0x17, 0),
+                     ("P+parent+x+y+z", 0x1F, 0), ("P+parent+x+y+z+last", 0x3F, 0),
+                     ("P+parent+x+y+z+last+delta(limited, 1<d<=16)", 0x7F, 2), ("P+parent+x+y+z+last+delta", 0x7F, 0)]
+
+
+def ablation_leg(V: np.ndarray) -> list:
+    """Compression of the 512^3 volume with the palette operation plus each prefix of the ordered
+    operation set {parent, x, y, z, last, delta} (the delta in its limited and unlimited form),
+    stored plain (4 bits per symbol) and rANS coded: the synthetic counterpart of the paper's
+    operation ablation (Supplementary Fig. "CSGV ablation"). Library encoder on the host cores."""
+    import paper_2609_36898_gb300 as vc
+    rows = []
+    for name, mask, flags in ABLATION_PREFIXES:
+        for coder in (0, 1):
+            enc = vc.vc_encode_volume(V, B_LOG2, op_mask=mask, coder=coder, flags=flags)
+            h = np.frombuffer(enc[:128].tobytes(), dtype="<u4")
+            n = int(h[9])
+            starts = np.frombuffer(enc[128:128 + 4 * (n + 1)].tobytes(), dtype="<u4").astype(np.int64)
+            rec0 = (128 + 4 * (n + 1) + 15) & ~15
+            words = np.frombuffer(enc[rec0:].tobytes(), dtype="<u4")
+            n_pal = words[starts[:-1]]
+            rows.append({"operations": name, "coder": "rANS" if coder else "plain",
+                         "bits_per_voxel": 8.0 * enc.size / V.size, "percent_of_raw": 100.0 * enc.size / (4.0 * V.size),
+                         "palette_mean": float(n_pal.mean()), "palette_max": int(n_pal.max())})
+    return rows
 
 
 def run_ours(args):
@@ -700,6 +802,7 @@ def run_ours(args):
             raise RuntimeError(f"split decode status {status.tolist()}")
         sv.release()
 
+    ablation = ablation_leg(V) if not args.no_ablation else None
     serving = None
     if args.serve_frames > 0:
         serving = serving_leg(args, local)
@@ -747,6 +850,7 @@ def run_ours(args):
             "serving": serving,
             "mixed_serving": mixed,
             "power_diagram_subsets": subsets,
+            "operation_ablation": ablation,
             "wall_s_timed_region": wall,
             "prep_s": {"generate": t_gen, "encode": t_enc},
         }
@@ -766,12 +870,13 @@ def main():
     ap.add_argument("--mode", default="auto", choices=["auto", "grid", "batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-split", action="store_true", help="skip the detail-split leg")
-    ap.add_argument("--subsets", type=int, default=0,
-                    help="random 100,000-brick subsets of the 2048x2048x1024 power-diagram volume to time (opt-in)")
-    ap.add_argument("--serve-frames", type=int, default=8, help="frames of the serving leg (0 = skip it)")
-    ap.add_argument("--serve-size", type=int, default=1024, help="edge of the serving volume")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the operation-prefix compression sweep")
+    ap.add_argument("--subsets", type=int, default=3,
+                    help="random 100,000-brick subsets of the 2048x2048x1024 power-diagram volume to time (0 = skip)")
+    ap.add_argument("--serve-frames", type=int, default=4, help="frames of the serving leg (0 = skip it)")
+    ap.add_argument("--serve-size", type=int, default=4096, help="edge of the serving volume")
     ap.add_argument("--serve-cameras", type=int, default=64)
-    ap.add_argument("--serve-plain-cameras", type=int, default=4)
+    ap.add_argument("--serve-plain-cameras", type=int, default=1)
     ap.add_argument("--mixed-requests", type=int, default=300, help="requests of the mixed serving leg (0 = skip)")
     ap.add_argument("--mixed-plain-requests", type=int, default=40)
     args = ap.parse_args()

@@ -331,6 +331,16 @@ vc_status vc_submit_bricks(vc_server* srv, uint32_t volume_index, const uint32_t
 vc_status vc_poll(vc_server* srv, uint64_t request_id, int32_t* state, uint64_t* offsets_out);
 /* Blocks until the request is done or failed, or timeout_ms passed (VC_ERR_TIMEOUT). */
 vc_status vc_wait(vc_server* srv, uint64_t request_id, uint32_t timeout_ms, int32_t* state);
+/* The coarsest level of detail of a request's bricks, read straight from the encoding without cache
+ * space (Methods, "Memory management": bricks that cannot be held in the cache are accessed in their
+ * coarsest level of detail directly from the encoding). For a request that waits for cache space
+ * (vc_poll state VC_REQ_WAITING) or whose decode is in flight (VC_REQ_ADMITTED), a client can show
+ * these labels until the request is done: labels_dev[i] (device, one u32 per brick of the request,
+ * in submission order, caller-owned) receives the single label the brick has at lod = L, as
+ * vc_coarsest_labels. status_dev: as in vc_decode_bricks. Any state but a released request;
+ * asynchronous on cuda_stream (the brick list is copied before the call returns). */
+vc_status vc_request_coarsest(vc_server* srv, uint64_t request_id, uint32_t* labels_dev, int32_t* status_dev,
+                              void* cuda_stream);
 vc_status vc_request_info_get(vc_server* srv, uint64_t request_id, vc_request_info* info);
 /* Unpins a done or failed request's bricks (they become evictable) and forgets the request.
  * VC_ERR_BUSY while it is still waiting or admitted. */
@@ -460,6 +470,26 @@ vc_status vc_release(void* handle);
 vc_status vc_encode_volume(const uint32_t* voxels, const uint32_t dims[3], uint32_t log2b, uint32_t op_mask,
                            uint32_t coder, uint32_t flags, uint32_t threads, uint8_t** out_bytes,
                            size_t* out_size);
+/* The same with the rANS frequency table given (freq_in: 16 entries summing to 4096, nonzero for
+ * every symbol the volume's streams use; NULL = quantised from the volume's own symbol counts,
+ * as vc_encode_volume does). A volume too large to encode at once can so be encoded in z slabs of
+ * whole bricks that share one table and whose records are concatenated (Brick Starts offset by
+ * the records before each slab). VC_ERR_ARG if the table does not cover a symbol or does not sum
+ * to 4096. */
+vc_status vc_encode_volume_freq(const uint32_t* voxels, const uint32_t dims[3], uint32_t log2b, uint32_t op_mask,
+                                uint32_t coder, uint32_t flags, uint32_t threads, const uint32_t* freq_in,
+                                uint8_t** out_bytes, size_t* out_size);
+/* Joins VCZ1 volumes stacked in z into one: parts[k] (sizes[k] bytes, host) must share the brick
+ * size, operation mask, coder, flags, x / y extent and rANS table, and every part but the last must
+ * cover whole bricks in z. The result's bricks are the parts' bricks in order (brick ids of part k
+ * follow those of parts 0..k-1, which is the x-fastest id order of the stacked volume), its
+ * records the parts' records with Brick Starts offset accordingly. *out_bytes is allocated by the
+ * library (vc_free_bytes). VC_ERR_FORMAT for a malformed part, VC_ERR_ARG for parts that do not
+ * match. Not in the paper; with vc_encode_volume_freq it encodes volumes too large for one pass,
+ * the way the paper's encoder imports large volumes in chunks (Methods, "Compressed segmentation
+ * volumes"). */
+vc_status vc_concat_volumes_z(const uint8_t* const* parts, const size_t* sizes, uint32_t nparts, uint8_t** out_bytes,
+                              size_t* out_size);
 void vc_free_bytes(uint8_t* bytes);
 
 /* Human-readable name of a status code (static string). */

@@ -132,6 +132,8 @@ def _lib_handle():
         lib.vc_volume_set_profiling.argtypes = [P, ctypes.c_int]
         lib.vc_volume_kernel_stats.argtypes = [P, ctypes.c_int, ctypes.POINTER(vc_kernel_stats)]
         lib.vc_encode_volume.argtypes = [P, P, U32, U32, U32, U32, U32, ctypes.POINTER(P), ctypes.POINTER(SZ)]
+        lib.vc_encode_volume_freq.argtypes = [P, P, U32, U32, U32, U32, U32, P, ctypes.POINTER(P), ctypes.POINTER(SZ)]
+        lib.vc_concat_volumes_z.argtypes = [P, P, U32, ctypes.POINTER(P), ctypes.POINTER(SZ)]
         PU64 = ctypes.POINTER(ctypes.c_uint64)
         lib.vc_server_create.argtypes = [ctypes.POINTER(vc_server_config), ctypes.POINTER(P)]
         lib.vc_server_add_volume.argtypes = [P, P, ctypes.POINTER(U32)]
@@ -156,7 +158,9 @@ def _lib_handle():
         lib.vc_brick_cache_unpin.argtypes = [P, P, U32]
         lib.vc_brick_cache_invalidate.argtypes = [P, U32]
         lib.vc_brick_cache_stats_get.argtypes = [P, ctypes.POINTER(vc_brick_cache_stats)]
+        lib.vc_request_coarsest.argtypes = [P, ctypes.c_uint64, P, P, P]
         for f in ("vc_server_create", "vc_server_add_volume", "vc_submit_bricks", "vc_poll", "vc_wait",
+                  "vc_request_coarsest",
                   "vc_request_info_get", "vc_request_release", "vc_server_cache", "vc_server_stats_get",
                   "vc_brick_cache_create", "vc_brick_cache_acquire", "vc_brick_cache_unpin",
                   "vc_brick_cache_invalidate", "vc_brick_cache_stats_get"):
@@ -166,7 +170,7 @@ def _lib_handle():
         lib.vc_status_string.argtypes = [I32]
         lib.vc_status_string.restype = ctypes.c_char_p
         for f in ("vc_load_compressed", "vc_volume_info_get", "vc_decode_bricks", "vc_decode_bricks_host",
-                  "vc_release", "vc_encode_volume", "vc_volume_set_schedule", "vc_volume_get_schedule",
+                  "vc_release", "vc_encode_volume", "vc_encode_volume_freq", "vc_concat_volumes_z", "vc_volume_set_schedule", "vc_volume_get_schedule",
                   "vc_volume_set_profiling", "vc_volume_kernel_stats", "vc_decode_bricks_noalloc"):
             getattr(lib, f).restype = I32
         _lib = lib
@@ -284,18 +288,41 @@ def vc_release(handle) -> None:
     _check(_lib_handle().vc_release(handle), "vc_release")
 
 
+def _take_bytes(lib, ptr, size) -> np.ndarray:
+    out = np.empty(size.value, dtype=np.uint8)
+    ctypes.memmove(out.ctypes.data, ptr, size.value)
+    lib.vc_free_bytes(ptr)
+    return out
+
+
 def vc_encode_volume(V: np.ndarray, log2b: int, op_mask: int = 0x7F, coder: int = 0, flags: int = 0,
-                     threads: int = 0) -> np.ndarray:
-    """Encode a (z, y, x) uint32 volume with the library's multi-threaded CPU encoder."""
+                     threads: int = 0, freq=None) -> np.ndarray:
+    """Encode a (z, y, x) uint32 volume with the library's multi-threaded CPU encoder (freq: a fixed
+    16-entry rANS frequency table, vc_encode_volume_freq)."""
     V = np.ascontiguousarray(V, dtype=np.uint32)
     dims = (ctypes.c_uint32 * 3)(V.shape[2], V.shape[1], V.shape[0])
     ptr, size = ctypes.c_void_p(), ctypes.c_size_t()
     lib = _lib_handle()
-    _check(lib.vc_encode_volume(V.ctypes.data, dims, log2b, op_mask, coder, flags, threads, ctypes.byref(ptr),
-                                ctypes.byref(size)), "vc_encode_volume")
-    out = np.frombuffer(ctypes.string_at(ptr, size.value), dtype=np.uint8).copy()
-    lib.vc_free_bytes(ptr)
-    return out
+    if freq is None:
+        _check(lib.vc_encode_volume(V.ctypes.data, dims, log2b, op_mask, coder, flags, threads, ctypes.byref(ptr),
+                                    ctypes.byref(size)), "vc_encode_volume")
+    else:
+        f = np.ascontiguousarray(freq, dtype=np.uint32)
+        _check(lib.vc_encode_volume_freq(V.ctypes.data, dims, log2b, op_mask, coder, flags, threads, f.ctypes.data,
+                                         ctypes.byref(ptr), ctypes.byref(size)), "vc_encode_volume_freq")
+    return _take_bytes(lib, ptr, size)
+
+
+def vc_concat_volumes_z(parts) -> np.ndarray:
+    """Joins VCZ1 volumes stacked in z (vc_concat_volumes_z)."""
+    parts = [np.ascontiguousarray(p, dtype=np.uint8) for p in parts]
+    ptrs = (ctypes.c_void_p * len(parts))(*[p.ctypes.data for p in parts])
+    sizes = (ctypes.c_size_t * len(parts))(*[p.size for p in parts])
+    ptr, size = ctypes.c_void_p(), ctypes.c_size_t()
+    lib = _lib_handle()
+    _check(lib.vc_concat_volumes_z(ptrs, sizes, len(parts), ctypes.byref(ptr), ctypes.byref(size)),
+           "vc_concat_volumes_z")
+    return _take_bytes(lib, ptr, size)
 
 
 # ---- serving
@@ -341,6 +368,12 @@ def vc_wait(srv, request_id: int, timeout_ms: int = 60000) -> int:
     st = ctypes.c_int32()
     _check(_lib_handle().vc_wait(srv, request_id, timeout_ms, ctypes.byref(st)), "vc_wait")
     return st.value
+
+
+def vc_request_coarsest(srv, request_id: int, labels_ptr: int, status_ptr: int, stream: int = 0) -> None:
+    _check(_lib_handle().vc_request_coarsest(srv, ctypes.c_uint64(request_id), ctypes.c_void_p(labels_ptr),
+                                             ctypes.c_void_p(status_ptr), ctypes.c_void_p(stream)),
+           "vc_request_coarsest")
 
 
 def vc_request_info_get(srv, request_id: int) -> vc_request_info:

@@ -279,8 +279,9 @@ void vc::rans_encode(const uint8_t* sym, uint32_t S, const uint32_t f[16], const
 
 extern "C" {
 
-vc_status vc_encode_volume(const uint32_t* voxels, const uint32_t dims[3], uint32_t log2b, uint32_t op_mask,
-                           uint32_t coder, uint32_t flags, uint32_t threads, uint8_t** out_bytes, size_t* out_size) {
+vc_status vc_encode_volume_freq(const uint32_t* voxels, const uint32_t dims[3], uint32_t log2b, uint32_t op_mask,
+                                uint32_t coder, uint32_t flags, uint32_t threads, const uint32_t* freq_in,
+                                uint8_t** out_bytes, size_t* out_size) {
   if (!voxels || !dims || !out_bytes || !out_size) return VC_ERR_ARG;
   *out_bytes = nullptr;
   *out_size = 0;
@@ -319,7 +320,17 @@ vc_status vc_encode_volume(const uint32_t* voxels, const uint32_t dims[3], uint3
     uint64_t counts[16] = {0};
     for (const Brick& br : bricks)
       for (uint8_t v : br.sym) ++counts[v];
-    quantize(counts, freq);
+    if (freq_in) {  // the caller's table: it must sum to M and cover every symbol that occurs
+      uint32_t sum = 0;
+      for (int i = 0; i < 16; ++i) {
+        sum += freq_in[i];
+        if (counts[i] && !freq_in[i]) return VC_ERR_ARG;
+      }
+      if (sum != kM) return VC_ERR_ARG;
+      std::memcpy(freq, freq_in, sizeof(freq));
+    } else {
+      quantize(counts, freq);
+    }
     for (int i = 0; i < 16; ++i) cum[i + 1] = cum[i] + freq[i];
     parallel_for(n, threads, [&](uint32_t id, uint32_t) { rans_brick(bricks[id], freq, cum); });
   }
@@ -365,6 +376,70 @@ vc_status vc_encode_volume(const uint32_t* voxels, const uint32_t dims[3], uint3
       for (size_t i = 0; i < br.sym.size(); ++i) q[i >> 1] |= (uint8_t)(br.sym[i] << ((i & 1) * 4));
     }
   });
+  *out_bytes = o;
+  *out_size = size;
+  return VC_OK;
+}
+
+vc_status vc_encode_volume(const uint32_t* voxels, const uint32_t dims[3], uint32_t log2b, uint32_t op_mask,
+                           uint32_t coder, uint32_t flags, uint32_t threads, uint8_t** out_bytes, size_t* out_size) {
+  return vc_encode_volume_freq(voxels, dims, log2b, op_mask, coder, flags, threads, nullptr, out_bytes, out_size);
+}
+
+vc_status vc_concat_volumes_z(const uint8_t* const* parts, const size_t* sizes, uint32_t nparts, uint8_t** out_bytes,
+                              size_t* out_size) {
+  if (!parts || !sizes || !nparts || !out_bytes || !out_size) return VC_ERR_ARG;
+  *out_bytes = nullptr;
+  *out_size = 0;
+  auto get32 = [](const uint8_t* p) {
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+  };
+  uint32_t dz = 0, max_pal = 0, max_sym = 0;
+  uint64_t n_total = 0, words_total = 0;
+  for (uint32_t k = 0; k < nparts; ++k) {
+    const uint8_t* p = parts[k];
+    if (!p || sizes[k] < 128 || get32(p) != 0x315A4356u || get32(p + 4) != 1u) return VC_ERR_FORMAT;
+    const uint32_t log2b = get32(p + 20), b = 1u << (log2b & 7u);
+    const uint32_t n = get32(p + 36), words = get32(p + 112);
+    const size_t rec_off = (128 + 4 * ((size_t)n + 1) + 15) & ~(size_t)15;
+    if (log2b < 1 || log2b > 6 || sizes[k] < rec_off + 4ull * words) return VC_ERR_FORMAT;
+    // the same brick size, operations, coder, flags, x / y extent and rANS table in every part;
+    // every part but the last covers whole bricks in z
+    if (k > 0 && (std::memcmp(p + 8, parts[0] + 8, 8) != 0 || std::memcmp(p + 20, parts[0] + 20, 16) != 0 ||
+                  std::memcmp(p + 48, parts[0] + 48, 64) != 0))
+      return VC_ERR_ARG;
+    if (k + 1 < nparts && get32(p + 16) % b != 0) return VC_ERR_ARG;
+    dz += get32(p + 16);
+    n_total += n;
+    words_total += words;
+    max_pal = std::max(max_pal, get32(p + 40));
+    max_sym = std::max(max_sym, get32(p + 44));
+  }
+  if (n_total >= 0xFFFFFFFFull || words_total >= 0xFFFFFFFFull) return VC_ERR_ARG;
+  const uint32_t n = (uint32_t)n_total;
+  const size_t rec_off = (128 + 4 * ((size_t)n + 1) + 15) & ~(size_t)15;
+  const size_t size = rec_off + 4 * words_total;
+  uint8_t* o = static_cast<uint8_t*>(std::calloc(size, 1));
+  if (!o) return VC_ERR_OOM;
+  std::memcpy(o, parts[0], 128);
+  put32(o + 16, dz);
+  put32(o + 36, n);
+  put32(o + 40, max_pal);
+  put32(o + 44, max_sym);
+  put32(o + 112, (uint32_t)words_total);
+  uint32_t id = 0, wbase = 0;
+  size_t rpos = rec_off;
+  for (uint32_t k = 0; k < nparts; ++k) {
+    const uint8_t* p = parts[k];
+    const uint32_t pn = get32(p + 36), words = get32(p + 112);
+    const size_t prec = (128 + 4 * ((size_t)pn + 1) + 15) & ~(size_t)15;
+    for (uint32_t i = 0; i < pn; ++i) put32(o + 128 + 4 * (size_t)(id + i), wbase + get32(p + 128 + 4 * (size_t)i));
+    std::memcpy(o + rpos, p + prec, 4ull * words);
+    id += pn;
+    wbase += words;
+    rpos += 4ull * words;
+  }
+  put32(o + 128 + 4 * (size_t)n, wbase);
   *out_bytes = o;
   *out_size = size;
   return VC_OK;

@@ -657,6 +657,37 @@ vc_status vc_wait(vc_server* srv, uint64_t request_id, uint32_t timeout_ms, int3
   return r->state == VC_REQ_FAILED ? r->status : VC_OK;
 }
 
+vc_status vc_request_coarsest(vc_server* srv, uint64_t request_id, uint32_t* labels_dev, int32_t* status_dev,
+                              void* cuda_stream) {
+  Server* s = reinterpret_cast<Server*>(srv);
+  if (!s || s->kind != kHandleServer || !labels_dev || !status_dev) return VC_ERR_ARG;
+  std::vector<uint32_t> ids;
+  Volume* v = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->requests.find(request_id);
+    if (it == s->requests.end()) return VC_ERR_ARG;
+    ids = it->second->bricks;
+    v = s->volumes[it->second->vol];
+  }
+  if (ids.empty()) return VC_OK;
+  DeviceGuard g(s->device);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  uint32_t* d_ids = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&d_ids), 4 * ids.size(), st) != cudaSuccess) {
+    cudaGetLastError();
+    return VC_ERR_OOM;
+  }
+  // the request's brick list is host memory owned here: copy it before this call returns
+  vc_status rc = cudaMemcpyAsync(d_ids, ids.data(), 4 * ids.size(), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+                         cudaStreamSynchronize(st) == cudaSuccess
+                     ? VC_OK
+                     : VC_ERR_CUDA;
+  if (rc == VC_OK) rc = launch_coarsest(*v, d_ids, (uint32_t)ids.size(), labels_dev, status_dev, st);
+  cudaFreeAsync(d_ids, st);
+  return rc;
+}
+
 vc_status vc_request_info_get(vc_server* srv, uint64_t request_id, vc_request_info* info) {
   Server* s = reinterpret_cast<Server*>(srv);
   if (!s || s->kind != kHandleServer || !info) return VC_ERR_ARG;

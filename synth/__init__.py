@@ -18,15 +18,33 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "synth.c")
 _LIB = os.path.join(_HERE, "libsynth.so")
+_SRC_GPU = os.path.join(_HERE, "synth_gpu.cu")
+_LIB_GPU = os.path.join(_HERE, "libsynth_gpu.so")
 _lib = None
+_lib_gpu = None
+
+
+def _nvcc() -> str:
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc"):
+        if c and os.path.exists(c):
+            return c
+    return "nvcc"
 
 
 def build(force: bool = False) -> str:
-    """Compile libsynth.so next to its source (gcc, plain C11 + pthreads)."""
+    """Compile libsynth.so next to its source (gcc, plain C11 + pthreads), and the GPU generator
+    libsynth_gpu.so (nvcc, sm_103a) when nvcc is present."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", _SRC, "-o", tmp])
         os.replace(tmp, _LIB)
+    nvcc = _nvcc()
+    if (force or not os.path.exists(_LIB_GPU) or os.path.getmtime(_LIB_GPU) < os.path.getmtime(_SRC_GPU)) and \
+            (os.path.exists(nvcc) or nvcc == "nvcc"):
+        tmp = _LIB_GPU + f".tmp{os.getpid()}"
+        subprocess.check_call([nvcc, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-gencode",
+                               "arch=compute_103a,code=sm_103a", _SRC_GPU, "-o", tmp])
+        os.replace(tmp, _LIB_GPU)
     return _LIB
 
 
@@ -54,6 +72,25 @@ def _load():
         lib.synth_fill.restype = ctypes.c_int
         _lib = lib
     return _lib
+
+
+def _load_gpu():
+    """The GPU generator (libsynth_gpu.so), with the power-diagram weight table of synth.c."""
+    global _lib_gpu
+    if _lib_gpu is None:
+        build()
+        lib = ctypes.CDLL(_LIB_GPU)
+        lib.synth_fill_gpu.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32,
+                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]
+        lib.synth_fill_gpu.restype = ctypes.c_int
+        lib.synth_gpu_set_lognorm.argtypes = [ctypes.c_void_p]
+        lib.synth_gpu_set_lognorm.restype = ctypes.c_int
+        cpu = _load()
+        cpu.synth_lognorm_table.restype = ctypes.c_void_p
+        if lib.synth_gpu_set_lognorm(cpu.synth_lognorm_table()) != 0:
+            raise RuntimeError("synth_gpu_set_lognorm failed")
+        _lib_gpu = lib
+    return _lib_gpu
 
 
 def _q16(x: float) -> int:
@@ -117,6 +154,19 @@ def fill(spec: VolumeSpec, origin=(0, 0, 0), shape=None, nthreads: int | None = 
     if rc != 0:
         raise ValueError("synth_fill rejected the parameters")
     return out
+
+
+def fill_gpu(spec: VolumeSpec, origin, shape, out_ptr: int, stream: int = 0) -> None:
+    """The same labels as fill(), written by the GPU generator into device memory at out_ptr
+    (nx * ny * nz uint32, x fastest), asynchronously on the CUDA stream `stream`."""
+    nx, ny, nz = (int(s) for s in shape)
+    p = spec._c()
+    rc = _load_gpu().synth_fill_gpu(ctypes.byref(p), int(origin[0]), int(origin[1]), int(origin[2]), nx, ny, nz,
+                                    ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream))
+    if rc == -1:
+        raise ValueError("synth_fill_gpu rejected the parameters")
+    if rc != 0:
+        raise RuntimeError("synth_fill_gpu: CUDA error")
 
 
 def _lam_for(grid: int, diameter: float) -> float:

@@ -344,6 +344,10 @@ static void* fill_worker(void* arg) {
   return NULL;
 }
 
+/* The 256-entry log-normal multiplier table of the power-diagram weights (for the GPU generator,
+ * which must use the same values). */
+const uint32_t* synth_lognorm_table(void) { return LOGNORM_Q16; }
+
 /* Fill out[nz][ny][nx] (x fastest) with the labels of the box starting at (x0, y0, z0).
  * Voxels outside dims are generated too (the definition extends to all integer points).
  * Returns 0 on success, -1 on bad parameters. */

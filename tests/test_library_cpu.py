@@ -83,3 +83,41 @@ def test_encoder_argument_checks(lib):
         vc.vc_encode_volume(V, 0)
     with pytest.raises(vc.VCError):
         vc.vc_encode_volume(V, 3, op_mask=0x0F)  # palette advance disabled
+
+
+def _full_table(freq) -> np.ndarray:
+    """The table with every symbol at least 1 (taken from the largest), still summing to 4096."""
+    f = np.asarray(freq, dtype=np.int64).copy()
+    short = int((f == 0).sum())
+    f[f == 0] = 1
+    f[int(np.argmax(f))] -= short
+    assert f.sum() == 4096 and (f >= 1).all()
+    return f.astype(np.uint32)
+
+
+@pytest.mark.parametrize("coder", [0, 1])
+def test_slab_encoding_with_one_table_concatenates_to_a_valid_volume(lib, coder):
+    """A volume encoded in z slabs of whole bricks with one shared rANS table, then joined with
+    vc_concat_volumes_z, decodes (oracle) to the input everywhere; with the volume's own table the
+    fixed-table encoder writes the same bytes as the plain one."""
+    V = synth.fill(synth.small(dims=(48, 40, 70), seed=23, grid=8, diameter=9.0, bg=0.15))
+    whole = vc.vc_encode_volume(V, 4, coder=coder)
+    own = oracle.header(whole)["freq"]
+    if coder == 1:
+        again = vc.vc_encode_volume(V, 4, coder=coder, freq=own)
+        assert np.array_equal(again, whole)
+    table = _full_table(own) if coder == 1 else None
+    parts = [vc.vc_encode_volume(V[z0:z0 + 32], 4, coder=coder, freq=table) for z0 in (0, 32, 64)]
+    joined = vc.vc_concat_volumes_z(parts)
+    h = oracle.header(joined)
+    assert h["dims"] == oracle.header(whole)["dims"] and h["n_bricks"] == oracle.header(whole)["n_bricks"]
+    assert np.array_equal(oracle.decode_volume(joined), V)
+    # mismatched parts are refused
+    other = vc.vc_encode_volume(V[:32], 3, coder=coder)
+    with pytest.raises(vc.VCError):
+        vc.vc_concat_volumes_z([parts[0], other])
+    if coder == 1:
+        bad = table.copy()
+        bad[0] += 1
+        with pytest.raises(vc.VCError):
+            vc.vc_encode_volume(V[:32], 4, coder=coder, freq=bad)

@@ -260,3 +260,43 @@ def test_graph_launched_batches_match_the_oracle(volumes):
         assert st.requests_failed == 0
     finally:
         close_server(srv, vols)
+
+
+def test_waiting_request_reads_the_coarsest_level_from_the_encoding():
+    """A request that cannot be admitted yet (the cache is full of another request's pinned bricks)
+    gets each brick's coarsest level of detail straight from the encoding (Methods, "Memory
+    management"): the oracle's decode at lod = L, brick by brick; once the other request is
+    released it is admitted and decodes to the oracle's finest level."""
+    spec = synth.small(dims=(64, 64, 64), seed=21, grid=16, diameter=12.0, bg=0.2)
+    V = synth.fill(spec)
+    enc = vc.vc_encode_volume(V, 4, op_mask=0x7F, coder=1)
+    block = 4 * 16 ** 3
+    srv = vc.vc_server_create(8 * block, 0, min_class=2, max_class=4)
+    h = vc.vc_load_compressed(enc, 0, torch.cuda.current_stream().cuda_stream)
+    try:
+        vi = vc.vc_server_add_volume(srv, h)
+        first = vc.vc_submit_bricks(srv, vi, np.arange(0, 8, dtype=np.uint32))
+        assert vc.vc_wait(srv, first, 60000) == vc.VC_REQ_DONE
+        ids = np.array([9, 17, 33, 8, 63, 40, 12, 50], dtype=np.uint32)
+        waiting = vc.vc_submit_bricks(srv, vi, ids)
+        assert vc.vc_poll(srv, waiting)[0] == vc.VC_REQ_WAITING
+        labels = torch.full((ids.size,), -1, dtype=torch.int32, device="cuda")
+        st = torch.zeros(vc.VC_STATUS_WORDS, dtype=torch.int32, device="cuda")
+        s = torch.cuda.current_stream()
+        vc.vc_request_coarsest(srv, waiting, labels.data_ptr(), st.data_ptr(), s.cuda_stream)
+        torch.cuda.synchronize()
+        assert int(st[0]) == 0
+        want = np.array([oracle.decode_brick(enc, int(i), 4).reshape(-1)[0] for i in ids], dtype=np.uint32)
+        assert np.array_equal(labels.cpu().numpy().view(np.uint32), want)
+        assert vc.vc_poll(srv, waiting)[0] == vc.VC_REQ_WAITING
+        vc.vc_request_release(srv, first)
+        assert vc.vc_wait(srv, waiting, 60000) == vc.VC_REQ_DONE
+        offsets = vc.vc_poll(srv, waiting, ids.size)[1]
+        got = read_bricks(srv, offsets, [16] * ids.size)
+        for g, i in zip(got, ids):
+            assert np.array_equal(g, oracle.decode_brick(enc, int(i)))
+        vc.vc_request_release(srv, waiting)
+    finally:
+        vc.vc_release(srv)
+        vc.vc_release(h)
+        _views.clear()
