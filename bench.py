@@ -624,6 +624,44 @@ def ablation_leg(V: np.ndarray) -> list:
     return rows
 
 
+RENDER_MATERIALS = np.array([[0.85, 0.35, 0.25, 1.0], [0.25, 0.7, 0.4, 1.0], [0.3, 0.45, 0.9, 1.0],
+                             [0.8, 0.75, 0.2, 1.0], [0.6, 0.3, 0.75, 0.5], [0.2, 0.8, 0.85, 1.0]], np.float32)
+
+
+def render_leg(vol, cache, n: int, e: int, stream, local: int) -> dict:
+    """1920 x 1080 frames of the 512^3 volume from its decoded bricks (every brick at the finest
+    level, brick i in slot i of the benchmark's cache): local shading and path tracing (up to 8
+    bounces), one sample per pixel, CUDA events around each frame."""
+    import torch
+    import paper_2609_36898_gb300 as vc
+    offsets = torch.arange(n, dtype=torch.int64, device="cuda") * (e ** 3)
+    lods = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    W, H = 1920, 1080
+    cam = vc.make_camera((-350.0, 700.0, -520.0), (606.0, -444.0, 776.0), (0.0, 1.0, 0.0), 0.75, W, H)
+    lab = torch.empty(W * H, dtype=torch.int32, device="cuda")
+    rgb = torch.empty(3 * W * H, dtype=torch.float32, device="cuda")
+    out = {"image": f"{W}x{H}", "volume": "512^3, every brick decoded at the finest level", "modes": {}}
+    for name, mode in (("local", vc.VC_SHADE_LOCAL), ("path_tracing", vc.VC_SHADE_PATH)):
+        def frame(f):
+            vc.vc_render(vol, offsets.data_ptr(), lods.data_ptr(), cache.data_ptr(), cam, RENDER_MATERIALS,
+                         lab.data_ptr(), 0, 0, rgb.data_ptr(), stream.cuda_stream, mode=mode, frame=f, jitter=True,
+                         max_bounces=8)
+        frame(0)
+        torch.cuda.synchronize()
+        ms = []
+        for f in range(1, 6):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            frame(f)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        med = float(np.median(ms))
+        out["modes"][name] = {"frame_ms": med, "mrays_s": W * H / med / 1e3,
+                              "hit_fraction": float((lab != 0).float().mean())}
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_2609_36898_gb300 as vc
@@ -803,6 +841,7 @@ def run_ours(args):
         sv.release()
 
     ablation = ablation_leg(V) if not args.no_ablation else None
+    render = render_leg(vol.handle, cache, n, e, stream, local)
     serving = None
     if args.serve_frames > 0:
         serving = serving_leg(args, local)
@@ -851,6 +890,7 @@ def run_ours(args):
             "mixed_serving": mixed,
             "power_diagram_subsets": subsets,
             "operation_ablation": ablation,
+            "render": render,
             "wall_s_timed_region": wall,
             "prep_s": {"generate": t_gen, "encode": t_enc},
         }

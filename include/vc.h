@@ -375,6 +375,65 @@ typedef struct vc_camera {
 vc_status vc_camera_bricks(vc_volume* vol, const vc_camera* cams, uint32_t ncams, uint32_t max_lod, uint32_t cap,
                            uint32_t* counts, uint32_t* brick_ids, uint32_t* lods, void* cuda_stream);
 
+/* ---- rendering from decoded bricks (Methods, "Volcanite rendering": "Shading Modes",
+ * "Transparency", "Ray marching", "Random number generation"; headless: device buffers) ----
+ *
+ * One thread per pixel ray of a pinhole camera (the request stage's camera model) marches the
+ * voxels of the volume front to back. Voxel positions are an integer voxel index plus a sub-voxel
+ * position in [0, 1) per axis (the paper's numerically stable DDA); in a brick decoded at level of
+ * detail k the ray steps through the brick's cells of edge 2^k (the paper's LOD DDA: the position
+ * is taken to the coarse cell, stepped once, and taken back); a brick whose palette holds no label
+ * other than 0 is crossed in one step of edge b; a brick not decoded is seen as one cell holding
+ * its coarsest label (its first palette entry, read from the encoding).
+ *   Labels map to materials: label 0 is background (empty); label l != 0 has material
+ *   materials[hash(l) % n_materials] (rgb albedo in [0, 1], opacity in [0, 1]; opacity 0 = not
+ *   shown). Entering a semi-transparent material (0 < opacity < 1) adds its Lambertian local
+ *   shading times opacity times the throughput and multiplies the throughput by 1 - opacity; an
+ *   opaque material is the surface hit, shaded by the mode:
+ *     VC_SHADE_LOCAL   ambient + (1 - ambient) max(0, n . l) (n the entered face's normal)
+ *     VC_SHADE_SHADOW  the same with the direct term 0 if a ray towards the light hits an opaque
+ *                      voxel before leaving the volume
+ *     VC_SHADE_AO      albedo x sky x (0 if a ray in a random cosine-weighted direction around n
+ *                      hits an opaque voxel within ao_radius voxels, else 1)
+ *     VC_SHADE_PATH    path tracing: Lambertian bounces in random cosine-weighted directions,
+ *                      throughput x albedo per bounce, sky radiance when a path leaves the
+ *                      volume, Russian roulette from the fourth bounce on, at most max_bounces
+ *   Random numbers: PCG2D (Jarzynski and Olano's 2D integer hash) of the pixel and of the frame
+ *   index and bounce; random directions by rejection in the unit ball (bounded tries). With
+ *   jitter set, the primary ray of frame f goes through a sub-pixel offset drawn from a bell-shaped
+ *   approximation of a Blackman-Harris window (temporal anti-aliasing). Every per-ray float step is
+ *   one correctly rounded operation in a fixed order, so results are a pure function of the inputs.
+ * Inputs (device unless noted): brick_offsets (n_bricks u64: word offset in `cache` of the brick's
+ * labels at its level of detail, x fastest, edge b >> brick_lods[i]; UINT64_MAX = not decoded),
+ * brick_lods (n_bricks u8), cache (u32 labels), cam and params (host). Outputs (device, W x H, row
+ * py at py * W, any may be NULL): labels (first opaque label hit, 0 = none), depth (ray distance
+ * in voxels to the entered face of that voxel, +inf = none), face (entered face: 1..6 = -x, +x,
+ * -y, +y, -z, +z side of the voxel, 0 = none or the camera inside it), rgb (3 floats per pixel).
+ * VC_ERR_ARG for bad sizes or parameters; asynchronous on cuda_stream. */
+#define VC_SHADE_LOCAL 0u
+#define VC_SHADE_SHADOW 1u
+#define VC_SHADE_AO 2u
+#define VC_SHADE_PATH 3u
+typedef struct vc_material {
+  float rgb[3];
+  float opacity;
+} vc_material;
+typedef struct vc_render_params {
+  uint32_t mode;         /* VC_SHADE_* */
+  uint32_t frame;        /* sample index */
+  uint32_t jitter;       /* 1 = temporal anti-aliasing jitter of the primary rays */
+  uint32_t max_bounces;  /* path tracing, 1..32 */
+  float light_dir[3];    /* towards the light, any length > 0 */
+  float ambient;         /* local shading's ambient term, [0, 1] */
+  float ao_radius;       /* ambient occlusion reach in voxels, > 0 */
+  float sky;             /* environment radiance */
+  uint32_t n_materials;  /* 1..256 */
+  const vc_material* materials; /* host */
+} vc_render_params;
+vc_status vc_render(vc_volume* vol, const uint64_t* brick_offsets, const uint8_t* brick_lods, const uint32_t* cache,
+                    const vc_camera* cam, const vc_render_params* params, uint32_t* labels_out, float* depth_out,
+                    uint8_t* face_out, float* rgb_out, void* cuda_stream);
+
 /* Serving form of the same: runs the request stage for ncams cameras (on the server's own
  * stream; concurrent callers take turns), then submits one request per camera with its bricks
  * and levels of detail, exactly as vc_submit_bricks would; request_ids_out (host, ncams) receives

@@ -13,7 +13,8 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "csgv_oracle.c"), os.path.join(_HERE, "camera_oracle.c")]
+_SRCS = [os.path.join(_HERE, "csgv_oracle.c"), os.path.join(_HERE, "camera_oracle.c"),
+         os.path.join(_HERE, "render_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -65,6 +66,8 @@ def _load():
         lib.oracle_free.argtypes = [P]
         lib.oracle_camera_bricks.argtypes = [P, SZ, P, P, P, ctypes.c_float, U32, U32, U32, P, P, U32, P]
         lib.oracle_camera_bricks.restype = ctypes.c_int
+        lib.oracle_render.argtypes = [P, SZ, P, P, P, P, P, P, ctypes.c_float, U32, U32, P, P, P, P, P]
+        lib.oracle_render.restype = ctypes.c_int
         for f in ("oracle_encode_volume", "oracle_decode_brick", "oracle_decode_volume", "oracle_brick_nodes",
                   "oracle_brick_symbols", "oracle_delta_nibbles", "oracle_rans_quantize", "oracle_pack_single_brick"):
             getattr(lib, f).restype = ctypes.c_int
@@ -238,3 +241,39 @@ def camera_bricks(vol: np.ndarray, pos, dir, up, fov_y: float, width: int, heigh
     if rc:
         raise OracleError(rc, "camera bricks")
     return ids[:n], lods[:n]
+
+
+class _RenderParams(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_uint32), ("frame", ctypes.c_uint32), ("jitter", ctypes.c_uint32),
+                ("max_bounces", ctypes.c_uint32), ("light_dir", ctypes.c_float * 3), ("ambient", ctypes.c_float),
+                ("ao_radius", ctypes.c_float), ("sky", ctypes.c_float), ("n_materials", ctypes.c_uint32),
+                ("materials", ctypes.c_void_p)]
+
+
+def render(vol: np.ndarray, offsets: np.ndarray, lods: np.ndarray, cache: np.ndarray, pos, dir, up, fov_y: float,
+           width: int, height: int, materials: np.ndarray, mode: int = 0, frame: int = 0, jitter: bool = False,
+           max_bounces: int = 8, light_dir=(0.3, 0.5, 0.8), ambient: float = 0.25, ao_radius: float = 8.0,
+           sky: float = 1.0):
+    """What each pixel ray sees (render_oracle.c): (labels, depth, face, rgb) as (H, W) arrays and
+    (H, W, 3). offsets / lods / cache: per brick the word offset of its labels at its level of
+    detail in cache (x fastest; 2**64 - 1 = not decoded) and the level. materials: (n, 4) float32
+    rows (r, g, b, opacity)."""
+    vol = np.ascontiguousarray(vol, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    lods = np.ascontiguousarray(lods, dtype=np.uint8)
+    cache = np.ascontiguousarray(cache, dtype=np.uint32)
+    mats = np.ascontiguousarray(materials, dtype=np.float32)
+    p = _RenderParams(mode, frame, int(bool(jitter)), max_bounces, (ctypes.c_float * 3)(*light_dir), ambient,
+                      ao_radius, sky, mats.shape[0], mats.ctypes.data)
+    f3 = lambda v: np.ascontiguousarray(v, dtype=np.float32)  # noqa: E731
+    ps, ds, us = f3(pos), f3(dir), f3(up)
+    labels = np.zeros((height, width), np.uint32)
+    depth = np.zeros((height, width), np.float32)
+    face = np.zeros((height, width), np.uint8)
+    rgb = np.zeros((height, width, 3), np.float32)
+    rc = _load().oracle_render(vol.ctypes.data, vol.size, offsets.ctypes.data, lods.ctypes.data, cache.ctypes.data,
+                               ps.ctypes.data, ds.ctypes.data, us.ctypes.data, fov_y, width, height, ctypes.byref(p),
+                               labels.ctypes.data, depth.ctypes.data, face.ctypes.data, rgb.ctypes.data)
+    if rc:
+        raise OracleError(rc, "render")
+    return labels, depth, face, rgb

@@ -36,7 +36,7 @@ static uint32_t crd32(const uint8_t* p) {
 }
 
 /* Per brick: bit 0 = palette holds label 0, bit 1 = palette holds a label other than 0. */
-static int palette_flags(const uint8_t* vol, size_t size, uint32_t nb[3], uint32_t* L_out, uint8_t** flags_out) {
+int oracle_palette_flags(const uint8_t* vol, size_t size, uint32_t nb[3], uint32_t* L_out, uint8_t** flags_out) {
   if (size < C_HEADER_BYTES || crd32(vol) != C_MAGIC) return -2;
   const uint32_t L = crd32(vol + 20), coder = crd32(vol + 28), n = crd32(vol + 36);
   const uint32_t b = 1u << L;
@@ -62,7 +62,7 @@ typedef struct {
   float sxs, sys, inv_w2, inv_h2, lod_s2;
 } cam_frame;
 
-static void camera_frame(const float pos[3], const float dir[3], const float up[3], float fov_y, uint32_t W,
+void oracle_camera_frame(const float pos[3], const float dir[3], const float up[3], float fov_y, uint32_t W,
                          uint32_t H, cam_frame* c) {
   double f[3] = {dir[0], dir[1], dir[2]};
   double fl = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
@@ -179,13 +179,13 @@ int oracle_camera_bricks(const uint8_t* vol, size_t size, const float pos[3], co
   if (!vol || !pos || !dir || !up || !n_out || width == 0 || height == 0) return -1;
   uint32_t nb[3], L;
   uint8_t* fl = NULL;
-  int rc = palette_flags(vol, size, nb, &L, &fl);
+  int rc = oracle_palette_flags(vol, size, nb, &L, &fl);
   if (rc) return rc;
   const uint32_t n = nb[0] * nb[1] * nb[2];
   uint8_t* marked = (uint8_t*)calloc(n ? n : 1, 1);
   if (!marked) { free(fl); return -3; }
   cam_frame c;
-  camera_frame(pos, dir, up, fov_y, width, height, &c);
+  oracle_camera_frame(pos, dir, up, fov_y, width, height, &c);
   const float b = (float)(1u << L);
   for (uint32_t py = 0; py < height; ++py)
     for (uint32_t px = 0; px < width; ++px) march(&c, b, nb, fl, px, py, marked);

@@ -159,6 +159,9 @@ def _lib_handle():
         lib.vc_brick_cache_invalidate.argtypes = [P, U32]
         lib.vc_brick_cache_stats_get.argtypes = [P, ctypes.POINTER(vc_brick_cache_stats)]
         lib.vc_request_coarsest.argtypes = [P, ctypes.c_uint64, P, P, P]
+        lib.vc_render.argtypes = [P, P, P, P, ctypes.POINTER(vc_camera), ctypes.POINTER(vc_render_params), P, P, P, P,
+                                  P]
+        lib.vc_render.restype = I32
         for f in ("vc_server_create", "vc_server_add_volume", "vc_submit_bricks", "vc_poll", "vc_wait",
                   "vc_request_coarsest",
                   "vc_request_info_get", "vc_request_release", "vc_server_cache", "vc_server_stats_get",
@@ -368,6 +371,39 @@ def vc_wait(srv, request_id: int, timeout_ms: int = 60000) -> int:
     st = ctypes.c_int32()
     _check(_lib_handle().vc_wait(srv, request_id, timeout_ms, ctypes.byref(st)), "vc_wait")
     return st.value
+
+
+VC_SHADE_LOCAL, VC_SHADE_SHADOW, VC_SHADE_AO, VC_SHADE_PATH = 0, 1, 2, 3
+
+
+class vc_material(ctypes.Structure):
+    _fields_ = [("rgb", ctypes.c_float * 3), ("opacity", ctypes.c_float)]
+
+
+class vc_render_params(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_uint32), ("frame", ctypes.c_uint32), ("jitter", ctypes.c_uint32),
+                ("max_bounces", ctypes.c_uint32), ("light_dir", ctypes.c_float * 3), ("ambient", ctypes.c_float),
+                ("ao_radius", ctypes.c_float), ("sky", ctypes.c_float), ("n_materials", ctypes.c_uint32),
+                ("materials", ctypes.c_void_p)]
+
+
+def vc_render(vol, brick_offsets_ptr: int, brick_lods_ptr: int, cache_ptr: int, cam: "vc_camera", materials,
+              labels_ptr: int = 0, depth_ptr: int = 0, face_ptr: int = 0, rgb_ptr: int = 0, stream: int = 0,
+              mode: int = VC_SHADE_LOCAL, frame: int = 0, jitter: bool = False, max_bounces: int = 8,
+              light_dir=(0.3, 0.5, 0.8), ambient: float = 0.25, ao_radius: float = 8.0, sky: float = 1.0) -> None:
+    """vc_render: materials is an (n, 4) float array of (r, g, b, opacity) rows (host)."""
+    mats = np.ascontiguousarray(materials, dtype=np.float32)
+    arr = (vc_material * mats.shape[0])()
+    for i, (r, g, b, o) in enumerate(mats):
+        arr[i].rgb[:] = [float(r), float(g), float(b)]
+        arr[i].opacity = float(o)
+    p = vc_render_params(mode, frame, int(bool(jitter)), max_bounces, (ctypes.c_float * 3)(*light_dir), ambient,
+                         ao_radius, sky, mats.shape[0], ctypes.cast(arr, ctypes.c_void_p))
+    _check(_lib_handle().vc_render(vol, ctypes.c_void_p(brick_offsets_ptr), ctypes.c_void_p(brick_lods_ptr),
+                                   ctypes.c_void_p(cache_ptr), ctypes.byref(cam), ctypes.byref(p),
+                                   ctypes.c_void_p(labels_ptr or None), ctypes.c_void_p(depth_ptr or None),
+                                   ctypes.c_void_p(face_ptr or None), ctypes.c_void_p(rgb_ptr or None),
+                                   ctypes.c_void_p(stream)), "vc_render")
 
 
 def vc_request_coarsest(srv, request_id: int, labels_ptr: int, status_ptr: int, stream: int = 0) -> None:

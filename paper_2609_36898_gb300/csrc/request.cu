@@ -22,13 +22,7 @@
 #include "vc_internal.h"
 
 namespace vc {
-namespace {
 
-struct CamDev {
-  float o[3], f[3], r[3], u[3];
-  float sxs, sys, inv_w2, inv_h2, lod_s2;
-  uint32_t W, H;
-};
 static_assert(sizeof(CamDev) == kCamDevBytes, "camera staging size");
 
 void camera_frame(const vc_camera& c, CamDev* d) {
@@ -56,6 +50,8 @@ void camera_frame(const vc_camera& c, CamDev* d) {
   d->W = c.width;
   d->H = c.height;
 }
+
+namespace {
 
 __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }

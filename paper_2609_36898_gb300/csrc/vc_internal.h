@@ -132,6 +132,17 @@ bool release_server(void* handle);
 // cache.cpp: releases a vc_brick_cache (false if the handle is not one)
 bool release_cache(void* handle);
 
+// request.cu: a pinhole camera's frame (forward, right, up), pixel scales and level-of-detail
+// scale, computed in double precision and rounded to float once (shared by the request stage and
+// the renderer): the ray of pixel (px, py) is o + t (f + sx r + sy u), sx = ((px + 1/2) inv_w2 - 1)
+// sxs, sy = (1 - (py + 1/2) inv_h2) sys
+struct CamDev {
+  float o[3], f[3], r[3], u[3];
+  float sxs, sys, inv_w2, inv_h2, lod_s2;
+  uint32_t W, H;
+};
+void camera_frame(const vc_camera& c, CamDev* d);
+
 // request.cu: the camera request stage (rays -> visible bricks and their levels of detail)
 size_t camera_scratch_bytes(const Volume& v, uint32_t ncams);
 constexpr size_t kCamDevBytes = 76;  // per camera, pinned host staging
