@@ -429,10 +429,54 @@ typedef struct vc_render_params {
   float sky;             /* environment radiance */
   uint32_t n_materials;  /* 1..256 */
   const vc_material* materials; /* host */
+  uint32_t subsample;    /* 0 or 1: every pixel; 2, 4 or 8: one pixel of each s x s block per frame
+                            (VC_SUBSET_PIXEL), the others are not written */
 } vc_render_params;
+/* Stratified subsets (Methods, "Upsampling": one pixel of each 2^2, 4^2 or 8^2 block is rendered
+ * per frame, every pixel of a block within s^2 frames; the blocks' sequences are displaced
+ * against each other): pixel (px, py) is rendered in frame f iff
+ * (px mod s) + s (py mod s) == (f + h(px / s, py / s)) mod s^2, h a fixed integer hash of the
+ * block (white noise standing in for the paper's blue-noise displacement). */
 vc_status vc_render(vc_volume* vol, const uint64_t* brick_offsets, const uint8_t* brick_lods, const uint32_t* cache,
                     const vc_camera* cam, const vc_render_params* params, uint32_t* labels_out, float* depth_out,
                     uint8_t* face_out, float* rgb_out, void* cuda_stream);
+
+/* ---- post-processing: accumulation, G-buffer, edge-avoiding À-trous denoising, upsampling
+ * (Methods, "Post-processing": "G-Buffer", "Denoising", "Upsampling") ----
+ *
+ * One call per frame after vc_render, on the pixels that frame rendered (params->subsample and
+ * frame as given to vc_render). `state` (device, vc_post_state_bytes(W, H) bytes, caller-owned)
+ * keeps, per pixel, the accumulated colour and sample count and the G-buffer of the most recent
+ * frame that rendered it: 48 bits, the surface normal (3 bits: axis | (1 if the normal points to
+ * -axis) << 2; 3 = no surface hit, 7 = not rendered yet), the depth (13 bits: the hit distance
+ * normalised to the dataset's bounding sphere as seen from the camera, 0 .. 8191) and the label
+ * (32 bits). reset = 1 clears it (the accumulation restarts, e.g. when the camera moves).
+ *   Then `iterations` passes i = 0, 1, ... each combine 3 x 3 pixels q at distance 2^i around p:
+ *   c_{i+1}(p) = sum h(q) w(q, p) c_i(q) / sum h(q) w(q, p), h = (1, 2, 1) x (1, 2, 1), w = 0 if
+ *   p's and q's normal codes differ, else 1 / (1 + |phi_rho (hsv(albedo_p) - hsv(albedo_q))|^2)
+ *   exp(-phi_d |depth_p - depth_q|) with depths in voxels (albedo: the label's material).
+ *   A pixel not rendered yet takes no part in the filter; instead the passes find its nearest
+ *   rendered pixel (the jump-flood rule o_p <- shortest of o_p and o_q + (q - p)) and it gets
+ *   that pixel's filtered colour. The result is tone mapped (x (2.51 x + 0.03) / (x (2.43 x +
+ *   0.59) + 0.14), Narkowicz's ACES fit, after scaling by `exposure`), gamma corrected and written
+ *   as RGBA8 (x = byte 0 .. alpha = 255 in byte 3) to rgba_out (device, W x H u32).
+ * Inputs (device, W x H, as written by vc_render for this frame): labels, depth, face, rgb.
+ * params->materials: host, as for vc_render. VC_ERR_ARG for bad sizes or parameters;
+ * asynchronous on cuda_stream. */
+typedef struct vc_post_params {
+  uint32_t width, height;
+  uint32_t iterations;          /* 0..10 */
+  uint32_t subsample, frame;    /* as given to vc_render for this frame */
+  uint32_t reset;               /* 1 = clear the state first */
+  float cam_pos[3];             /* the camera position (depth normalisation) */
+  float phi_rho, phi_d;         /* edge-stopping weights: albedo (the paper: 8) and depth per voxel */
+  float exposure, gamma;        /* tone mapping */
+  uint32_t n_materials;
+  const vc_material* materials; /* host */
+} vc_post_params;
+size_t vc_post_state_bytes(uint32_t width, uint32_t height);
+vc_status vc_postprocess(vc_volume* vol, const vc_post_params* params, const uint32_t* labels, const float* depth,
+                         const uint8_t* face, const float* rgb, void* state, uint32_t* rgba_out, void* cuda_stream);
 
 /* Serving form of the same: runs the request stage for ncams cameras (on the server's own
  * stream; concurrent callers take turns), then submits one request per camera with its bricks

@@ -14,7 +14,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRCS = [os.path.join(_HERE, "csgv_oracle.c"), os.path.join(_HERE, "camera_oracle.c"),
-         os.path.join(_HERE, "render_oracle.c")]
+         os.path.join(_HERE, "render_oracle.c"), os.path.join(_HERE, "post_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -68,6 +68,8 @@ def _load():
         lib.oracle_camera_bricks.restype = ctypes.c_int
         lib.oracle_render.argtypes = [P, SZ, P, P, P, P, P, P, ctypes.c_float, U32, U32, P, P, P, P, P]
         lib.oracle_render.restype = ctypes.c_int
+        lib.oracle_post.argtypes = [P] * 14
+        lib.oracle_post.restype = ctypes.c_int
         for f in ("oracle_encode_volume", "oracle_decode_brick", "oracle_decode_volume", "oracle_brick_nodes",
                   "oracle_brick_symbols", "oracle_delta_nibbles", "oracle_rans_quantize", "oracle_pack_single_brick"):
             getattr(lib, f).restype = ctypes.c_int
@@ -247,13 +249,13 @@ class _RenderParams(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("frame", ctypes.c_uint32), ("jitter", ctypes.c_uint32),
                 ("max_bounces", ctypes.c_uint32), ("light_dir", ctypes.c_float * 3), ("ambient", ctypes.c_float),
                 ("ao_radius", ctypes.c_float), ("sky", ctypes.c_float), ("n_materials", ctypes.c_uint32),
-                ("materials", ctypes.c_void_p)]
+                ("materials", ctypes.c_void_p), ("subsample", ctypes.c_uint32)]
 
 
 def render(vol: np.ndarray, offsets: np.ndarray, lods: np.ndarray, cache: np.ndarray, pos, dir, up, fov_y: float,
            width: int, height: int, materials: np.ndarray, mode: int = 0, frame: int = 0, jitter: bool = False,
            max_bounces: int = 8, light_dir=(0.3, 0.5, 0.8), ambient: float = 0.25, ao_radius: float = 8.0,
-           sky: float = 1.0):
+           sky: float = 1.0, subsample: int = 1, out=None):
     """What each pixel ray sees (render_oracle.c): (labels, depth, face, rgb) as (H, W) arrays and
     (H, W, 3). offsets / lods / cache: per brick the word offset of its labels at its level of
     detail in cache (x fastest; 2**64 - 1 = not decoded) and the level. materials: (n, 4) float32
@@ -264,16 +266,54 @@ def render(vol: np.ndarray, offsets: np.ndarray, lods: np.ndarray, cache: np.nda
     cache = np.ascontiguousarray(cache, dtype=np.uint32)
     mats = np.ascontiguousarray(materials, dtype=np.float32)
     p = _RenderParams(mode, frame, int(bool(jitter)), max_bounces, (ctypes.c_float * 3)(*light_dir), ambient,
-                      ao_radius, sky, mats.shape[0], mats.ctypes.data)
+                      ao_radius, sky, mats.shape[0], mats.ctypes.data, subsample)
     f3 = lambda v: np.ascontiguousarray(v, dtype=np.float32)  # noqa: E731
     ps, ds, us = f3(pos), f3(dir), f3(up)
-    labels = np.zeros((height, width), np.uint32)
-    depth = np.zeros((height, width), np.float32)
-    face = np.zeros((height, width), np.uint8)
-    rgb = np.zeros((height, width, 3), np.float32)
+    if out is None:  # pixels outside this frame's subset keep what `out` holds
+        out = (np.zeros((height, width), np.uint32), np.zeros((height, width), np.float32),
+               np.zeros((height, width), np.uint8), np.zeros((height, width, 3), np.float32))
+    labels, depth, face, rgb = out
     rc = _load().oracle_render(vol.ctypes.data, vol.size, offsets.ctypes.data, lods.ctypes.data, cache.ctypes.data,
                                ps.ctypes.data, ds.ctypes.data, us.ctypes.data, fov_y, width, height, ctypes.byref(p),
                                labels.ctypes.data, depth.ctypes.data, face.ctypes.data, rgb.ctypes.data)
     if rc:
         raise OracleError(rc, "render")
     return labels, depth, face, rgb
+
+
+class _PostParams(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32), ("iterations", ctypes.c_uint32),
+                ("subsample", ctypes.c_uint32), ("frame", ctypes.c_uint32), ("reset", ctypes.c_uint32),
+                ("cam_pos", ctypes.c_float * 3), ("phi_rho", ctypes.c_float), ("phi_d", ctypes.c_float),
+                ("exposure", ctypes.c_float), ("gamma", ctypes.c_float), ("n_materials", ctypes.c_uint32),
+                ("materials", ctypes.c_void_p)]
+
+
+def post_state(width: int, height: int) -> dict:
+    """Per-pixel state of post() (kept by the caller between frames)."""
+    n = width * height
+    return {"accum": np.zeros((n, 4), np.float32), "col0": np.zeros((n, 4), np.float32),
+            "col1": np.zeros((n, 4), np.float32), "glabel": np.zeros(n, np.uint32),
+            "gcode": np.full(n, 7, np.uint32), "off0": np.zeros(n, np.int32), "off1": np.zeros(n, np.int32)}
+
+
+def post(state: dict, dims, labels, depth, face, rgb, materials, cam_pos, iterations: int = 3, subsample: int = 1,
+         frame: int = 0, reset: bool = False, phi_rho: float = 8.0, phi_d: float = 1.0, exposure: float = 1.0,
+         gamma: float = 2.2) -> np.ndarray:
+    """One frame of post-processing (post_oracle.c): the (H, W) RGBA8 image as uint32."""
+    H, W = labels.shape
+    mats = np.ascontiguousarray(materials, dtype=np.float32)
+    p = _PostParams(W, H, iterations, subsample, frame, int(bool(reset)), (ctypes.c_float * 3)(*cam_pos), phi_rho,
+                    phi_d, exposure, gamma, mats.shape[0], mats.ctypes.data)
+    dims_a = np.ascontiguousarray(dims, dtype=np.uint32)
+    c = lambda a, t: np.ascontiguousarray(a, dtype=t)  # noqa: E731
+    labels, depth, face, rgb = c(labels, np.uint32), c(depth, np.float32), c(face, np.uint8), c(rgb, np.float32)
+    out = np.zeros((H, W), np.uint32)
+    S = state
+    rc = _load().oracle_post(ctypes.byref(p), dims_a.ctypes.data, labels.ctypes.data, depth.ctypes.data,
+                             face.ctypes.data, rgb.ctypes.data, S["accum"].ctypes.data, S["col0"].ctypes.data,
+                             S["col1"].ctypes.data, S["glabel"].ctypes.data, S["gcode"].ctypes.data,
+                             S["off0"].ctypes.data, S["off1"].ctypes.data, out.ctypes.data)
+    if rc:
+        raise OracleError(rc, "post")
+    return out

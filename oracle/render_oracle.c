@@ -54,7 +54,20 @@ typedef struct {
   float ambient, ao_radius, sky;
   uint32_t n_materials;
   const float* materials; /* n_materials x (r, g, b, opacity) */
+  uint32_t subsample;     /* 0/1 every pixel; 2, 4, 8: one pixel of each s x s block per frame */
 } oracle_render_params;
+
+/* Stratified subsets (Methods, "Upsampling": one pixel of each s^2 block per frame, every pixel
+ * of the block within s^2 frames; block sequences displaced by a fixed integer hash of the block,
+ * standing in for the paper's blue-noise displacement). */
+int oracle_subset_pixel(uint32_t px, uint32_t py, uint32_t s, uint32_t f) {
+  if (s <= 1u) return 1;
+  uint32_t h = (px / s) * 0x8DA6B343u ^ (py / s) * 0xD8163841u;
+  h ^= h >> 13;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 16;
+  return (px % s) + s * (py % s) == (f + h) % (s * s);
+}
 
 #define R_ONE_MINUS 0.99999994f
 #define R_NOT_DECODED (~0ull)
@@ -433,6 +446,7 @@ int oracle_render(const uint8_t* vol, size_t size, const uint64_t* offsets, cons
   for (uint32_t py = 0; py < H; ++py)
     for (uint32_t px = 0; px < W; ++px) {
       const size_t i = (size_t)py * W + px;
+      if (!oracle_subset_pixel(px, py, P->subsample, P->frame)) continue;
       render_pixel(&C, &cam, px, py, P->frame, P->jitter != 0, &labels[i], &depth[i], &faces[i], rgb + 3 * i);
     }
   free(fl);

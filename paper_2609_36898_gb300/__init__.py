@@ -162,6 +162,10 @@ def _lib_handle():
         lib.vc_render.argtypes = [P, P, P, P, ctypes.POINTER(vc_camera), ctypes.POINTER(vc_render_params), P, P, P, P,
                                   P]
         lib.vc_render.restype = I32
+        lib.vc_post_state_bytes.argtypes = [U32, U32]
+        lib.vc_post_state_bytes.restype = SZ
+        lib.vc_postprocess.argtypes = [P, ctypes.POINTER(vc_post_params), P, P, P, P, P, P, P]
+        lib.vc_postprocess.restype = I32
         for f in ("vc_server_create", "vc_server_add_volume", "vc_submit_bricks", "vc_poll", "vc_wait",
                   "vc_request_coarsest",
                   "vc_request_info_get", "vc_request_release", "vc_server_cache", "vc_server_stats_get",
@@ -384,13 +388,14 @@ class vc_render_params(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("frame", ctypes.c_uint32), ("jitter", ctypes.c_uint32),
                 ("max_bounces", ctypes.c_uint32), ("light_dir", ctypes.c_float * 3), ("ambient", ctypes.c_float),
                 ("ao_radius", ctypes.c_float), ("sky", ctypes.c_float), ("n_materials", ctypes.c_uint32),
-                ("materials", ctypes.c_void_p)]
+                ("materials", ctypes.c_void_p), ("subsample", ctypes.c_uint32)]
 
 
 def vc_render(vol, brick_offsets_ptr: int, brick_lods_ptr: int, cache_ptr: int, cam: "vc_camera", materials,
               labels_ptr: int = 0, depth_ptr: int = 0, face_ptr: int = 0, rgb_ptr: int = 0, stream: int = 0,
               mode: int = VC_SHADE_LOCAL, frame: int = 0, jitter: bool = False, max_bounces: int = 8,
-              light_dir=(0.3, 0.5, 0.8), ambient: float = 0.25, ao_radius: float = 8.0, sky: float = 1.0) -> None:
+              light_dir=(0.3, 0.5, 0.8), ambient: float = 0.25, ao_radius: float = 8.0, sky: float = 1.0,
+              subsample: int = 1) -> None:
     """vc_render: materials is an (n, 4) float array of (r, g, b, opacity) rows (host)."""
     mats = np.ascontiguousarray(materials, dtype=np.float32)
     arr = (vc_material * mats.shape[0])()
@@ -398,12 +403,40 @@ def vc_render(vol, brick_offsets_ptr: int, brick_lods_ptr: int, cache_ptr: int, 
         arr[i].rgb[:] = [float(r), float(g), float(b)]
         arr[i].opacity = float(o)
     p = vc_render_params(mode, frame, int(bool(jitter)), max_bounces, (ctypes.c_float * 3)(*light_dir), ambient,
-                         ao_radius, sky, mats.shape[0], ctypes.cast(arr, ctypes.c_void_p))
+                         ao_radius, sky, mats.shape[0], ctypes.cast(arr, ctypes.c_void_p), subsample)
     _check(_lib_handle().vc_render(vol, ctypes.c_void_p(brick_offsets_ptr), ctypes.c_void_p(brick_lods_ptr),
                                    ctypes.c_void_p(cache_ptr), ctypes.byref(cam), ctypes.byref(p),
                                    ctypes.c_void_p(labels_ptr or None), ctypes.c_void_p(depth_ptr or None),
                                    ctypes.c_void_p(face_ptr or None), ctypes.c_void_p(rgb_ptr or None),
                                    ctypes.c_void_p(stream)), "vc_render")
+
+
+class vc_post_params(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32), ("iterations", ctypes.c_uint32),
+                ("subsample", ctypes.c_uint32), ("frame", ctypes.c_uint32), ("reset", ctypes.c_uint32),
+                ("cam_pos", ctypes.c_float * 3), ("phi_rho", ctypes.c_float), ("phi_d", ctypes.c_float),
+                ("exposure", ctypes.c_float), ("gamma", ctypes.c_float), ("n_materials", ctypes.c_uint32),
+                ("materials", ctypes.c_void_p)]
+
+
+def vc_post_state_bytes(width: int, height: int) -> int:
+    return int(_lib_handle().vc_post_state_bytes(width, height))
+
+
+def vc_postprocess(vol, width: int, height: int, labels_ptr: int, depth_ptr: int, face_ptr: int, rgb_ptr: int,
+                   state_ptr: int, rgba_ptr: int, materials, cam_pos, iterations: int = 3, subsample: int = 1,
+                   frame: int = 0, reset: bool = False, phi_rho: float = 8.0, phi_d: float = 1.0,
+                   exposure: float = 1.0, gamma: float = 2.2, stream: int = 0) -> None:
+    mats = np.ascontiguousarray(materials, dtype=np.float32)
+    arr = (vc_material * mats.shape[0])()
+    for i, (r, g, b, o) in enumerate(mats):
+        arr[i].rgb[:] = [float(r), float(g), float(b)]
+        arr[i].opacity = float(o)
+    p = vc_post_params(width, height, iterations, subsample, frame, int(bool(reset)), (ctypes.c_float * 3)(*cam_pos),
+                       phi_rho, phi_d, exposure, gamma, mats.shape[0], ctypes.cast(arr, ctypes.c_void_p))
+    _check(_lib_handle().vc_postprocess(vol, ctypes.byref(p), ctypes.c_void_p(labels_ptr), ctypes.c_void_p(depth_ptr),
+                                        ctypes.c_void_p(face_ptr), ctypes.c_void_p(rgb_ptr), ctypes.c_void_p(state_ptr),
+                                        ctypes.c_void_p(rgba_ptr), ctypes.c_void_p(stream)), "vc_postprocess")
 
 
 def vc_request_coarsest(srv, request_id: int, labels_ptr: int, status_ptr: int, stream: int = 0) -> None:

@@ -40,6 +40,7 @@ __device__ __forceinline__ float clamp01(float x) { return x < 0.0f ? 0.0f : (x 
 
 struct RenderDev {
   CamDev cam;
+  uint32_t subsample;
   float light[3];  // unit length, towards the light
   float ambient, ao_radius, sky;
   uint32_t mode, frame, jitter, max_bounces, n_mat;
@@ -254,6 +255,7 @@ __global__ void render_kernel(const RenderDev* __restrict__ Rp, Inputs in, uint3
   const uint32_t npix = c.W * c.H;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += gridDim.x * blockDim.x) {
     const uint32_t px = i % c.W, py = i / c.W;
+    if (!subset_pixel(px, py, R.subsample, R.frame)) continue;
     // primary ray through the pixel centre, or a jittered sub-pixel position (temporal
     // anti-aliasing: offsets from the sum of three uniforms, a bell shape on (-1, 1) standing in
     // for the Blackman-Harris window)
@@ -448,7 +450,8 @@ extern "C" vc_status vc_render(vc_volume* vol, const uint64_t* brick_offsets, co
   if (cam->width == 0 || cam->height == 0 || (uint64_t)cam->width * cam->height > 0x7FFFFFFFull) return VC_ERR_ARG;
   if (P.mode > VC_SHADE_PATH || P.n_materials == 0 || P.n_materials > kMaxMaterials || !P.materials ||
       (P.mode == VC_SHADE_PATH && (P.max_bounces == 0 || P.max_bounces > 32)) ||
-      (P.mode == VC_SHADE_AO && !(P.ao_radius > 0.0f)))
+      (P.mode == VC_SHADE_AO && !(P.ao_radius > 0.0f)) ||
+      !(P.subsample <= 2u || P.subsample == 4u || P.subsample == 8u))
     return VC_ERR_ARG;
   const double l2 = (double)P.light_dir[0] * P.light_dir[0] + (double)P.light_dir[1] * P.light_dir[1] +
                     (double)P.light_dir[2] * P.light_dir[2];
@@ -466,6 +469,7 @@ extern "C" vc_status vc_render(vc_volume* vol, const uint64_t* brick_offsets, co
   R.jitter = P.jitter ? 1u : 0u;
   R.max_bounces = P.max_bounces;
   R.n_mat = P.n_materials;
+  R.subsample = P.subsample;
   for (uint32_t m = 0; m < P.n_materials; ++m) {
     for (int a = 0; a < 3; ++a) R.mat[m][a] = P.materials[m].rgb[a];
     R.mat[m][3] = P.materials[m].opacity;

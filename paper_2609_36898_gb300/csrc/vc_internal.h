@@ -142,6 +142,17 @@ struct CamDev {
   uint32_t W, H;
 };
 void camera_frame(const vc_camera& c, CamDev* d);
+// Stratified subsets of vc_render / vc_postprocess: is pixel (px, py) rendered in frame f when one
+// pixel of each s x s block is? (the block's pixel of frame f: (f + h(block)) mod s^2, h a fixed
+// integer hash)
+__host__ __device__ inline bool subset_pixel(uint32_t px, uint32_t py, uint32_t s, uint32_t f) {
+  if (s <= 1u) return true;
+  uint32_t h = (px / s) * 0x8DA6B343u ^ (py / s) * 0xD8163841u;
+  h ^= h >> 13;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 16;
+  return (px % s) + s * (py % s) == (f + h) % (s * s);
+}
 
 // request.cu: the camera request stage (rays -> visible bricks and their levels of detail)
 size_t camera_scratch_bytes(const Volume& v, uint32_t ncams);
