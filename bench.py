@@ -308,6 +308,87 @@ def orbit_camera(vc, i: int, frame: int, dims, width: int, height: int, fov: flo
     return vc.make_camera(pos, centre - pos, axis, fov, width, height)
 
 
+def frame_cache_leg(vc, vol, dims, ncam: int, W: int, H: int, max_lod: int, frames: int, stream) -> dict:
+    """The same cameras through the device-side cache stages (vc_frame_*: mark, then request,
+    provision, assign and decode on the GPU with no host round trip), 2 GiB of labels. (a) all
+    cameras' brick rays mark, one update per frame for all of them; (b) one camera at W x H
+    rendered with shadow rays, its rays marking the bricks for the next frame's update. CUDA
+    events around each stage; the frame statistics are read after the frame."""
+    import torch
+    pct = lambda a, q: float(np.percentile(np.asarray(a), q)) if len(a) else None  # noqa: E731
+    status = torch.zeros(vc.VC_STATUS_WORDS, dtype=torch.int32, device="cuda")
+    out = {"cache_bytes": 2 << 30}
+    fc = vc.vc_frame_cache_create(vol, 2 << 30)
+    try:
+        view = vc.vc_frame_cache_view_get(fc)
+        out["max_bricks_per_frame"] = int(view.max_bricks_per_frame)
+        mark_ms, upd_ms, dec, vox, rows = [], [], [], [], []
+        prev = vc.vc_frame_stats_get(fc, stream.cuda_stream)
+        for f in range(frames):
+            cams = [orbit_camera(vc, i, f, dims, W, H) for i in range(ncam)]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            vc.vc_frame_mark_cameras(fc, cams, stream.cuda_stream)
+            ev[1].record(stream)
+            vc.vc_frame_update(fc, cams, max_lod, status.data_ptr(), stream.cuda_stream)
+            ev[2].record(stream)
+            st = vc.vc_frame_stats_get(fc, stream.cuda_stream)
+            mark_ms.append(ev[0].elapsed_time(ev[1]))
+            upd_ms.append(ev[1].elapsed_time(ev[2]))
+            dec.append(int(st.last_decoded))
+            vox.append(int(st.voxels_decoded - prev.voxels_decoded))
+            rows.append({"mark_ms": mark_ms[-1], "update_ms": upd_ms[-1], "resident": int(st.last_resident),
+                         "requested": int(st.last_requested), "decoded": int(st.last_decoded),
+                         "freed": int(st.last_freed), "reset": bool(st.resets > prev.resets)})
+            prev = st
+        if int(status[0]) != 0:
+            raise RuntimeError(f"frame cache decode status {status.tolist()}")
+        out["brick_rays"] = {
+            "cameras": ncam, "frames": frames, "update_ms_p50": pct(upd_ms, 50), "update_ms_p99": pct(upd_ms, 99),
+            "mark_ms_p50": pct(mark_ms, 50),
+            "decoded_gvoxel_s": sum(vox) / (sum(upd_ms) / 1000.0) / 1e9 if sum(upd_ms) > 0 else None,
+            "resets": int(prev.resets), "dead_words": int(prev.dead_words), "top_words": int(prev.top_words),
+            "per_frame": rows,
+            "note": "update = request + provision + assign + decode of all cameras' bricks (device counts, no host "
+                    "sync); latency of a frame's bricks = its update time"}
+    finally:
+        vc.vc_release(fc)
+    # (b) the renderer's rays mark: one camera, the paper's per-frame pipeline
+    fc = vc.vc_frame_cache_create(vol, 2 << 30)
+    try:
+        view = vc.vc_frame_cache_view_get(fc)
+        lab = torch.empty(W * H, dtype=torch.int32, device="cuda")
+        rows = []
+        prev = vc.vc_frame_stats_get(fc, stream.cuda_stream)
+        for f in range(frames):
+            cam = orbit_camera(vc, 0, f, dims, W, H)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            vc.vc_frame_update(fc, [cam], max_lod, status.data_ptr(), stream.cuda_stream)
+            ev[1].record(stream)
+            vc.vc_render(vol, view.offsets, view.lods, view.cache, cam, RENDER_MATERIALS, lab.data_ptr(),
+                         stream=stream.cuda_stream, mode=vc.VC_SHADE_SHADOW, frame=f, marks_ptr=view.marks,
+                         request_depth=1)
+            ev[2].record(stream)
+            st = vc.vc_frame_stats_get(fc, stream.cuda_stream)
+            rows.append({"update_ms": ev[0].elapsed_time(ev[1]), "render_ms": ev[1].elapsed_time(ev[2]),
+                         "resident": int(st.last_resident), "decoded": int(st.last_decoded),
+                         "voxels": int(st.voxels_decoded - prev.voxels_decoded)})
+            prev = st
+        if int(status[0]) != 0:
+            raise RuntimeError(f"frame cache decode status {status.tolist()}")
+        upd = [r["update_ms"] for r in rows[1:]]
+        out["render_rays"] = {
+            "image": f"{W}x{H}", "mode": "shadow rays (request depth 1)", "frames": frames,
+            "update_ms_p50": pct(upd, 50), "update_ms_p99": pct(upd, 99),
+            "render_ms_p50": pct([r["render_ms"] for r in rows[1:]], 50), "per_frame": rows,
+            "note": "frame f: update from the marks of frame f-1's render, then render (undecoded bricks show their "
+                    "coarsest label); frame 0 renders an empty cache"}
+    finally:
+        vc.vc_release(fc)
+    return out
+
+
 def serving_leg(args, local: int):
     """Camera-driven serving on the 4096^3 hash-grid Voronoi volume (one seed per 16^3 grid cell,
     ~16M cells; --serve-size n runs the same recipe on n^3 with the image scaled by n/4096): 64
@@ -384,10 +465,12 @@ def serving_leg(args, local: int):
     torch.cuda.synchronize()
     plain_lat = [e[0].elapsed_time(e[c + 1]) for c in range(len(lists))]
     plain_s = plain_lat[-1] / 1000.0
+    gpu_frames = frame_cache_leg(vc, vol, dims, ncam, W, H, max_lod, args.serve_frames + 4, stream)
     vc.vc_release(vol)
     del cache
     pct = lambda a, q: float(np.percentile(np.asarray(a), q)) if len(a) else None  # noqa: E731
     return {
+        "gpu_frames": gpu_frames,
         "workload": f"{n}^3 Voronoi (hash grid, one seed per 16^3 cell, 10% background), 32^3 bricks, rANS "
                     f"({8.0 * enc_bytes / n ** 3:.2f} bit/voxel, resident on the device); {ncam} orbiting cameras at "
                     f"{W}x{H}, {args.serve_frames} frames, 2 GiB cache, lod <= {max_lod}; each request released when "

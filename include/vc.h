@@ -375,6 +375,62 @@ typedef struct vc_camera {
 vc_status vc_camera_bricks(vc_volume* vol, const vc_camera* cams, uint32_t ncams, uint32_t max_lod, uint32_t cap,
                            uint32_t* counts, uint32_t* brick_ids, uint32_t* lods, void* cuda_stream);
 
+/* ---- frame cache: the per-frame cache stages on the device (Methods, "GPU rendering pipeline";
+ * Results, "GPU-based rendering pipeline": no GPU to CPU synchronisation within a frame; Methods,
+ * "Memory management", "Cache defragmentation") ----
+ * A device-resident brick cache of one volume, driven once per frame:
+ *   1. marks: the bricks seen this frame set their bit in the cache's visibility marks, by
+ *      vc_frame_mark_cameras (the request stage's brick rays) and/or by vc_render with
+ *      params->marks = the view's marks (the rays of the renderer, as in the paper);
+ *   2. vc_frame_update runs Request (one thread per brick: a cached brick that is not marked, or is
+ *      marked at another level of detail, frees its region onto its level's free stack; a marked
+ *      brick not cached at its level is pushed onto its level's request stack; the marks are
+ *      cleared), Provision (per level, finest first: requests take regions from the free stack,
+ *      then from the top of the buffer), Assign (brick -> region, offset, level) and Decode (the
+ *      persistent decoder over the assigned bricks of each level), all enqueued on the stream;
+ *   3. vc_render reads the view's offsets / lods / cache (an undecoded brick shows its coarsest
+ *      label, Methods "Brick request limitation").
+ * Level of detail of a marked brick: the request stage's rule for each camera given to the update,
+ * the finest over them. A region of level k holds (b / 2^k)^3 labels, starts at a multiple of its
+ * size and keeps its level while free. A free stack holds free_stack_entries regions; a region
+ * freed onto a full stack stays dead. At most max_bricks_per_frame bricks are assigned per update
+ * (the rest stay undecoded and are requested again while they are marked). When the top of the
+ * buffer runs out and the space held by free regions of other levels, dead regions and the rest of
+ * the buffer would hold what is missing, the next update first empties the cache (defragmentation;
+ * never two updates in a row). Calls on one frame cache must not overlap; every call enqueues on
+ * the caller's stream and only vc_frame_stats_get waits. */
+typedef struct vc_frame_cache vc_frame_cache;
+typedef struct vc_frame_cache_view {
+  uint64_t* offsets;    /* device, n_bricks: label offset of the brick's region, ~0 = not cached */
+  uint8_t* lods;        /* device, n_bricks: its level of detail, 255 = not cached */
+  uint32_t* cache;      /* device, cache_words labels */
+  uint32_t* marks;      /* device, ceil(n_bricks / 32) words of visibility bits */
+  uint64_t cache_words;
+  uint32_t n_bricks, max_bricks_per_frame, free_stack_entries;
+} vc_frame_cache_view;
+typedef struct vc_frame_stats {
+  uint64_t frames, bricks_requested, bricks_decoded, voxels_decoded, bricks_freed, bricks_unassigned;
+  uint64_t resets, level_switches; /* defragmentations; bricks freed while marked (level changed) */
+  uint64_t top_words, dead_words;  /* buffer in use from the bottom; labels in dead regions */
+  uint32_t last_resident, last_requested, last_decoded, last_unassigned, last_freed, reset_pending;
+  uint32_t free_entries[8];        /* per level of detail */
+} vc_frame_stats;
+/* Allocates the cache on the volume's device: cache_bytes of labels (>= 4), max_bricks_per_frame
+ * (0: min(n_bricks, 262144)) and free_stack_entries per level (0: 1,048,576, the paper's). The
+ * decode workspace is sized for max_bricks_per_frame bricks. Released by vc_release. */
+vc_status vc_frame_cache_create(vc_volume* vol, uint64_t cache_bytes, uint32_t max_bricks_per_frame,
+                                uint32_t free_stack_entries, vc_frame_cache** out);
+vc_status vc_frame_cache_view_get(vc_frame_cache* fc, vc_frame_cache_view* out);
+/* The request stage's brick rays of ncams cameras set their bricks' marks (any ncams). */
+vc_status vc_frame_mark_cameras(vc_frame_cache* fc, const vc_camera* cams, uint32_t ncams, void* cuda_stream);
+/* One frame's Request, Provision, Assign and Decode for the marks set since the last update, with
+ * levels of detail from cams (1..256 cameras) up to max_lod (clamped to L). status_dev: as in
+ * vc_decode_bricks (words 0..1 zeroed by the caller; decode errors land there). */
+vc_status vc_frame_update(vc_frame_cache* fc, const vc_camera* cams, uint32_t ncams, uint32_t max_lod,
+                          int32_t* status_dev, void* cuda_stream);
+/* Waits for the stream and reads the counters. */
+vc_status vc_frame_stats_get(vc_frame_cache* fc, vc_frame_stats* out, void* cuda_stream);
+
 /* ---- rendering from decoded bricks (Methods, "Volcanite rendering": "Shading Modes",
  * "Transparency", "Ray marching", "Random number generation"; headless: device buffers) ----
  *
@@ -431,6 +487,15 @@ typedef struct vc_render_params {
   const vc_material* materials; /* host */
   uint32_t subsample;    /* 0 or 1: every pixel; 2, 4 or 8: one pixel of each s x s block per frame
                             (VC_SUBSET_PIXEL), the others are not written */
+  uint32_t* marks;       /* device, ceil(n_bricks / 32) u32, or NULL: visibility marks (Methods, "GPU
+                            rendering pipeline": the rays mark the bricks they access). Bit id % 32
+                            of word id / 32 is set (atomic OR; never cleared here) for every brick
+                            holding a label other than 0 that a ray of path depth <= request_depth
+                            enters, decoded or not. The primary ray has depth 0; shadow and ambient
+                            occlusion rays and the first path-tracing bounce depth 1; bounce k depth
+                            k (Methods, "Brick request limitation": a ray depth limit for requests,
+                            1 by default). A vc_frame_cache's marks take them. */
+  uint32_t request_depth;
 } vc_render_params;
 /* Stratified subsets (Methods, "Upsampling": one pixel of each 2^2, 4^2 or 8^2 block is rendered
  * per frame, every pixel of a block within s^2 frames; the blocks' sequences are displaced

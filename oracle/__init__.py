@@ -66,6 +66,8 @@ def _load():
         lib.oracle_free.argtypes = [P]
         lib.oracle_camera_bricks.argtypes = [P, SZ, P, P, P, ctypes.c_float, U32, U32, U32, P, P, U32, P]
         lib.oracle_camera_bricks.restype = ctypes.c_int
+        lib.oracle_brick_lods.argtypes = [P, SZ, P, P, P, ctypes.c_float, U32, U32, U32, P]
+        lib.oracle_brick_lods.restype = ctypes.c_int
         lib.oracle_render.argtypes = [P, SZ, P, P, P, P, P, P, ctypes.c_float, U32, U32, P, P, P, P, P]
         lib.oracle_render.restype = ctypes.c_int
         lib.oracle_post.argtypes = [P] * 14
@@ -245,28 +247,48 @@ def camera_bricks(vol: np.ndarray, pos, dir, up, fov_y: float, width: int, heigh
     return ids[:n], lods[:n]
 
 
+def brick_lods(vol: np.ndarray, pos, dir, up, fov_y: float, width: int, height: int, max_lod: int = 31) -> np.ndarray:
+    """Every brick's level of detail for one camera (the request stage's centre rule), uint8."""
+    vol = np.ascontiguousarray(vol, dtype=np.uint8)
+    f3 = lambda v: np.ascontiguousarray(np.asarray(v, dtype=np.float32).reshape(3))  # noqa: E731
+    p, d, u = f3(pos), f3(dir), f3(up)
+    out = np.zeros(max(1, int(header(vol)["n_bricks"])), np.uint8)
+    rc = _load().oracle_brick_lods(vol.ctypes.data, vol.size, p.ctypes.data, d.ctypes.data, u.ctypes.data,
+                                   ctypes.c_float(fov_y), width, height, max_lod, out.ctypes.data)
+    if rc:
+        raise OracleError(rc, "brick lods")
+    return out[:int(header(vol)["n_bricks"])]
+
+
 class _RenderParams(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("frame", ctypes.c_uint32), ("jitter", ctypes.c_uint32),
                 ("max_bounces", ctypes.c_uint32), ("light_dir", ctypes.c_float * 3), ("ambient", ctypes.c_float),
                 ("ao_radius", ctypes.c_float), ("sky", ctypes.c_float), ("n_materials", ctypes.c_uint32),
-                ("materials", ctypes.c_void_p), ("subsample", ctypes.c_uint32)]
+                ("materials", ctypes.c_void_p), ("subsample", ctypes.c_uint32), ("visible", ctypes.c_void_p),
+                ("request_depth", ctypes.c_uint32)]
 
 
 def render(vol: np.ndarray, offsets: np.ndarray, lods: np.ndarray, cache: np.ndarray, pos, dir, up, fov_y: float,
            width: int, height: int, materials: np.ndarray, mode: int = 0, frame: int = 0, jitter: bool = False,
            max_bounces: int = 8, light_dir=(0.3, 0.5, 0.8), ambient: float = 0.25, ao_radius: float = 8.0,
-           sky: float = 1.0, subsample: int = 1, out=None):
+           sky: float = 1.0, subsample: int = 1, out=None, visible=None, request_depth: int = 1):
     """What each pixel ray sees (render_oracle.c): (labels, depth, face, rgb) as (H, W) arrays and
     (H, W, 3). offsets / lods / cache: per brick the word offset of its labels at its level of
     detail in cache (x fastest; 2**64 - 1 = not decoded) and the level. materials: (n, 4) float32
-    rows (r, g, b, opacity)."""
+    rows (r, g, b, opacity). visible: a uint8 array of one entry per brick (or None) in which the
+    bricks the rays of path depth <= request_depth access are set to 1."""
     vol = np.ascontiguousarray(vol, dtype=np.uint8)
     offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
     lods = np.ascontiguousarray(lods, dtype=np.uint8)
     cache = np.ascontiguousarray(cache, dtype=np.uint32)
     mats = np.ascontiguousarray(materials, dtype=np.float32)
     p = _RenderParams(mode, frame, int(bool(jitter)), max_bounces, (ctypes.c_float * 3)(*light_dir), ambient,
-                      ao_radius, sky, mats.shape[0], mats.ctypes.data, subsample)
+                      ao_radius, sky, mats.shape[0], mats.ctypes.data, subsample, None, request_depth)
+    if visible is not None:
+        n_bricks = int.from_bytes(bytes(vol[36:40]), "little")
+        if visible.dtype != np.uint8 or not visible.flags.c_contiguous or visible.size < n_bricks:
+            raise ValueError("visible must be a contiguous uint8 array of one entry per brick")
+        p.visible = visible.ctypes.data
     f3 = lambda v: np.ascontiguousarray(v, dtype=np.float32)  # noqa: E731
     ps, ds, us = f3(pos), f3(dir), f3(up)
     if out is None:  # pixels outside this frame's subset keep what `out` holds

@@ -205,3 +205,23 @@ int oracle_camera_bricks(const uint8_t* vol, size_t size, const float pos[3], co
   free(fl);
   return cnt > cap ? -7 : 0;
 }
+
+/* The level of detail of every brick for one camera (the same centre rule; max_lod clamped to
+ * log2 b): lods_out[id], one byte per brick. Returns 0, -1 (argument) or the header's error. */
+int oracle_brick_lods(const uint8_t* vol, size_t size, const float pos[3], const float dir[3], const float up[3],
+                      float fov_y, uint32_t width, uint32_t height, uint32_t max_lod, uint8_t* lods_out) {
+  if (!vol || !pos || !dir || !up || !lods_out || width == 0 || height == 0) return -1;
+  uint32_t nb[3], L;
+  uint8_t* fl = NULL;
+  int rc = oracle_palette_flags(vol, size, nb, &L, &fl);
+  if (rc) return rc;
+  free(fl);
+  cam_frame c;
+  oracle_camera_frame(pos, dir, up, fov_y, width, height, &c);
+  const float b = (float)(1u << L);
+  if (max_lod > L) max_lod = L;
+  const uint32_t n = nb[0] * nb[1] * nb[2];
+  for (uint32_t id = 0; id < n; ++id)
+    lods_out[id] = (uint8_t)brick_lod(&c, b, id % nb[0], (id / nb[0]) % nb[1], id / (nb[0] * nb[1]), max_lod);
+  return 0;
+}

@@ -55,6 +55,12 @@ typedef struct {
   uint32_t n_materials;
   const float* materials; /* n_materials x (r, g, b, opacity) */
   uint32_t subsample;     /* 0/1 every pixel; 2, 4, 8: one pixel of each s x s block per frame */
+  uint8_t* visible;       /* per brick, or NULL: set to 1 for every brick holding a label other than 0
+                             that a ray of path depth <= request_depth enters (Methods, "GPU rendering
+                             pipeline": rays mark the bricks they access; "Brick request limitation":
+                             a ray depth limit for requests). Depth 0 = the primary ray; shadow, ambient
+                             occlusion rays and the first path-tracing bounce 1; bounce k k. */
+  uint32_t request_depth;
 } oracle_render_params;
 
 /* Stratified subsets (Methods, "Upsampling": one pixel of each s^2 block per frame, every pixel
@@ -84,6 +90,8 @@ typedef struct {
   float light[3], ambient, ao_radius, sky;
   uint32_t mode, max_bounces, n_mat;
   const float* mat;
+  uint8_t* visible;
+  uint32_t request_depth;
 } rctx;
 
 static uint32_t rd32(const uint8_t* p) {
@@ -129,8 +137,9 @@ typedef struct {
   uint32_t face; /* 1..6: entered through the -x, +x, -y, +y, -z, +z side; 0 none */
 } ray;
 
-/* Label of the cell holding voxel v, and the cell's edge as a power of two. */
-static uint32_t cell_at(const rctx* C, const int32_t v[3], uint32_t* s_log) {
+/* Label of the cell holding voxel v, and the cell's edge as a power of two; a ray of path depth
+ * `depth` marks the brick as visible. */
+static uint32_t cell_at(const rctx* C, const int32_t v[3], uint32_t* s_log, uint32_t depth) {
   const uint32_t L = C->L, b = 1u << L;
   const uint32_t bx = (uint32_t)v[0] >> L, by = (uint32_t)v[1] >> L, bz = (uint32_t)v[2] >> L;
   const uint32_t id = bx + C->nb[0] * (by + C->nb[1] * bz);
@@ -138,6 +147,7 @@ static uint32_t cell_at(const rctx* C, const int32_t v[3], uint32_t* s_log) {
     *s_log = L;
     return 0u;
   }
+  if (C->visible && depth <= C->request_depth) C->visible[id] = 1u;
   if (C->offsets[id] == R_NOT_DECODED) {
     *s_log = L;
     const uint8_t* rec = C->vol + C->rec_off + 4 * (size_t)rd32(C->vol + 128 + 4 * (size_t)id);
@@ -192,11 +202,11 @@ static int step(const rctx* C, ray* r, uint32_t s_log) {
   return inside;
 }
 
-static int march_opaque(const rctx* C, ray* r, float max_t, uint32_t* hit) {
+static int march_opaque(const rctx* C, ray* r, float max_t, uint32_t* hit, uint32_t depth) {
   const uint32_t max_steps = 3u * (C->dims[0] + C->dims[1] + C->dims[2]) + 64u;
   for (uint32_t k = 0; k < max_steps; ++k) {
     uint32_t s;
-    const uint32_t l = cell_at(C, r->v, &s);
+    const uint32_t l = cell_at(C, r->v, &s, depth);
     if (opaque(C, l)) {
       *hit = l;
       return 1;
@@ -319,7 +329,7 @@ static void render_pixel(const rctx* C, const cam_frame* cam, uint32_t px, uint3
     const uint32_t max_steps = 3u * (C->dims[0] + C->dims[1] + C->dims[2]) + 64u;
     for (uint32_t k = 0; k < max_steps && T >= 0.00390625f; ++k) {
       uint32_t s;
-      const uint32_t l = cell_at(C, r.v, &s);
+      const uint32_t l = cell_at(C, r.v, &s, 0u);
       if (l != prev && l != 0u) {
         const float* m = mat_of(C, l);
         if (m[3] > 0.0f) {
@@ -357,7 +367,7 @@ static void render_pixel(const rctx* C, const cam_frame* cam, uint32_t px, uint3
         if (C->mode == 1 && nl > 0.0f && r.face) {
           ray sr = from_face(&r, C->light);
           uint32_t l2;
-          if (in_volume(C, sr.v) && march_opaque(C, &sr, INFINITY, &l2)) nl = 0.0f;
+          if (in_volume(C, sr.v) && march_opaque(C, &sr, INFINITY, &l2, 1u)) nl = 0.0f;
         }
         const float shade = C->ambient + (1.0f - C->ambient) * nl;
         for (int a = 0; a < 3; ++a) c3[a] = m[a] * shade;
@@ -368,7 +378,7 @@ static void render_pixel(const rctx* C, const cam_frame* cam, uint32_t px, uint3
         if (r.face) {
           ray ar = from_face(&r, dir);
           uint32_t l2;
-          occluded = in_volume(C, ar.v) && march_opaque(C, &ar, C->ao_radius, &l2);
+          occluded = in_volume(C, ar.v) && march_opaque(C, &ar, C->ao_radius, &l2, 1u);
         }
         for (int a = 0; a < 3; ++a) c3[a] = occluded ? 0.0f : m[a] * C->sky;
       } else {
@@ -380,7 +390,7 @@ static void render_pixel(const rctx* C, const cam_frame* cam, uint32_t px, uint3
           cosine_dir(g, nn, dir);
           ray br = from_face(&h, dir);
           uint32_t l2 = 0u;
-          if (!in_volume(C, br.v) || !march_opaque(C, &br, INFINITY, &l2)) {
+          if (!in_volume(C, br.v) || !march_opaque(C, &br, INFINITY, &l2, bounce)) {
             for (int a = 0; a < 3; ++a) c3[a] = c3[a] + tp[a] * C->sky;
             break;
           }
@@ -441,6 +451,8 @@ int oracle_render(const uint8_t* vol, size_t size, const uint64_t* offsets, cons
   C.max_bounces = P->max_bounces;
   C.n_mat = P->n_materials;
   C.mat = P->materials;
+  C.visible = P->visible;
+  C.request_depth = P->request_depth;
   cam_frame cam;
   oracle_camera_frame(pos, dir, up, fov_y, W, H, &cam);
   for (uint32_t py = 0; py < H; ++py)

@@ -107,6 +107,20 @@ def make_camera(pos, dir, up, fov_y: float, width: int, height: int) -> vc_camer
 
 VC_REQ_WAITING, VC_REQ_ADMITTED, VC_REQ_DONE, VC_REQ_FAILED = 0, 1, 2, 3
 
+
+class vc_frame_cache_view(ctypes.Structure):
+    _fields_ = [("offsets", ctypes.c_void_p), ("lods", ctypes.c_void_p), ("cache", ctypes.c_void_p),
+                ("marks", ctypes.c_void_p), ("cache_words", ctypes.c_uint64), ("n_bricks", ctypes.c_uint32),
+                ("max_bricks_per_frame", ctypes.c_uint32), ("free_stack_entries", ctypes.c_uint32)]
+
+
+class vc_frame_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "frames", "bricks_requested", "bricks_decoded", "voxels_decoded", "bricks_freed", "bricks_unassigned",
+        "resets", "level_switches", "top_words", "dead_words")] + [(n, ctypes.c_uint32) for n in (
+            "last_resident", "last_requested", "last_decoded", "last_unassigned", "last_freed", "reset_pending")] + [
+        ("free_entries", ctypes.c_uint32 * 8)]
+
 _lib = None
 
 
@@ -166,6 +180,14 @@ def _lib_handle():
         lib.vc_post_state_bytes.restype = SZ
         lib.vc_postprocess.argtypes = [P, ctypes.POINTER(vc_post_params), P, P, P, P, P, P, P]
         lib.vc_postprocess.restype = I32
+        lib.vc_frame_cache_create.argtypes = [P, ctypes.c_uint64, U32, U32, ctypes.POINTER(P)]
+        lib.vc_frame_cache_view_get.argtypes = [P, ctypes.POINTER(vc_frame_cache_view)]
+        lib.vc_frame_mark_cameras.argtypes = [P, P, U32, P]
+        lib.vc_frame_update.argtypes = [P, P, U32, U32, P, P]
+        lib.vc_frame_stats_get.argtypes = [P, ctypes.POINTER(vc_frame_stats), P]
+        for f in ("vc_frame_cache_create", "vc_frame_cache_view_get", "vc_frame_mark_cameras", "vc_frame_update",
+                  "vc_frame_stats_get"):
+            getattr(lib, f).restype = I32
         for f in ("vc_server_create", "vc_server_add_volume", "vc_submit_bricks", "vc_poll", "vc_wait",
                   "vc_request_coarsest",
                   "vc_request_info_get", "vc_request_release", "vc_server_cache", "vc_server_stats_get",
@@ -388,22 +410,25 @@ class vc_render_params(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("frame", ctypes.c_uint32), ("jitter", ctypes.c_uint32),
                 ("max_bounces", ctypes.c_uint32), ("light_dir", ctypes.c_float * 3), ("ambient", ctypes.c_float),
                 ("ao_radius", ctypes.c_float), ("sky", ctypes.c_float), ("n_materials", ctypes.c_uint32),
-                ("materials", ctypes.c_void_p), ("subsample", ctypes.c_uint32)]
+                ("materials", ctypes.c_void_p), ("subsample", ctypes.c_uint32), ("marks", ctypes.c_void_p),
+                ("request_depth", ctypes.c_uint32)]
 
 
 def vc_render(vol, brick_offsets_ptr: int, brick_lods_ptr: int, cache_ptr: int, cam: "vc_camera", materials,
               labels_ptr: int = 0, depth_ptr: int = 0, face_ptr: int = 0, rgb_ptr: int = 0, stream: int = 0,
               mode: int = VC_SHADE_LOCAL, frame: int = 0, jitter: bool = False, max_bounces: int = 8,
               light_dir=(0.3, 0.5, 0.8), ambient: float = 0.25, ao_radius: float = 8.0, sky: float = 1.0,
-              subsample: int = 1) -> None:
-    """vc_render: materials is an (n, 4) float array of (r, g, b, opacity) rows (host)."""
+              subsample: int = 1, marks_ptr: int = 0, request_depth: int = 1) -> None:
+    """vc_render: materials is an (n, 4) float array of (r, g, b, opacity) rows (host); marks_ptr:
+    device visibility bits (one per brick) or 0."""
     mats = np.ascontiguousarray(materials, dtype=np.float32)
     arr = (vc_material * mats.shape[0])()
     for i, (r, g, b, o) in enumerate(mats):
         arr[i].rgb[:] = [float(r), float(g), float(b)]
         arr[i].opacity = float(o)
     p = vc_render_params(mode, frame, int(bool(jitter)), max_bounces, (ctypes.c_float * 3)(*light_dir), ambient,
-                         ao_radius, sky, mats.shape[0], ctypes.cast(arr, ctypes.c_void_p), subsample)
+                         ao_radius, sky, mats.shape[0], ctypes.cast(arr, ctypes.c_void_p), subsample,
+                         ctypes.c_void_p(marks_ptr or None), request_depth)
     _check(_lib_handle().vc_render(vol, ctypes.c_void_p(brick_offsets_ptr), ctypes.c_void_p(brick_lods_ptr),
                                    ctypes.c_void_p(cache_ptr), ctypes.byref(cam), ctypes.byref(p),
                                    ctypes.c_void_p(labels_ptr or None), ctypes.c_void_p(depth_ptr or None),
@@ -483,6 +508,40 @@ def vc_camera_bricks(vol, cams, max_lod: int = 31, cap: int | None = None, strea
                                 lods.ctypes.data, ctypes.c_void_p(stream)), "vc_camera_bricks")
     return [(ids[i * cap: i * cap + min(int(counts[i]), cap)].copy(), lods[i * cap: i * cap + min(int(counts[i]), cap)].copy())
             for i in range(len(cams))]
+
+
+def vc_frame_cache_create(vol, cache_bytes: int, max_bricks_per_frame: int = 0,
+                          free_stack_entries: int = 0) -> ctypes.c_void_p:
+    out = ctypes.c_void_p()
+    _check(_lib_handle().vc_frame_cache_create(vol, cache_bytes, max_bricks_per_frame, free_stack_entries,
+                                               ctypes.byref(out)), "vc_frame_cache_create")
+    return out
+
+
+def vc_frame_cache_view_get(fc) -> vc_frame_cache_view:
+    v = vc_frame_cache_view()
+    _check(_lib_handle().vc_frame_cache_view_get(fc, ctypes.byref(v)), "vc_frame_cache_view_get")
+    return v
+
+
+def vc_frame_mark_cameras(fc, cams, stream: int = 0) -> None:
+    cams = list(cams)
+    arr = (vc_camera * max(1, len(cams)))(*cams)
+    _check(_lib_handle().vc_frame_mark_cameras(fc, ctypes.byref(arr), len(cams), ctypes.c_void_p(stream)),
+           "vc_frame_mark_cameras")
+
+
+def vc_frame_update(fc, cams, max_lod: int, status_ptr: int, stream: int = 0) -> None:
+    cams = list(cams)
+    arr = (vc_camera * max(1, len(cams)))(*cams)
+    _check(_lib_handle().vc_frame_update(fc, ctypes.byref(arr), len(cams), max_lod, ctypes.c_void_p(status_ptr),
+                                         ctypes.c_void_p(stream)), "vc_frame_update")
+
+
+def vc_frame_stats_get(fc, stream: int = 0) -> vc_frame_stats:
+    st = vc_frame_stats()
+    _check(_lib_handle().vc_frame_stats_get(fc, ctypes.byref(st), ctypes.c_void_p(stream)), "vc_frame_stats_get")
+    return st
 
 
 def vc_request_bricks(srv, volume_index: int, cams, max_lod: int = 31) -> list:

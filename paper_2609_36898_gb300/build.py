@@ -22,6 +22,7 @@ SOURCES = [("decode.cu", "decode", []), ("decode_nt.cu", "decode_nt256", ["-DVC_
            ("request.cu", "request", ["-Xcompiler", "-ffp-contract=off", "--fmad=false"]),
            ("render.cu", "render", ["-Xcompiler", "-ffp-contract=off", "--fmad=false"]),
            ("post.cu", "post", ["-Xcompiler", "-ffp-contract=off", "--fmad=false"]),
+           ("frame.cu", "frame", ["-Xcompiler", "-ffp-contract=off", "--fmad=false"]),
            ("autotune.cpp", "autotune", []), ("split.cpp", "split", [])]
 HEADERS = ["vc_internal.h", "decode_kernels.cuh", "cache.h"]
 

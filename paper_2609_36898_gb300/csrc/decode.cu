@@ -104,16 +104,10 @@ __device__ __forceinline__ bool rans_steps(const uint32_t* tab, const uint16_t* 
   return !__any_sync(0xFFFFFFFFu, bad);
 }
 
-__global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_kernel(const __grid_constant__ Params P,
-                                                                      uint8_t* ws) {
-  extern __shared__ __align__(128) unsigned char sm[];
+// The symbols of the item scheduled k-th, by one warp (tab: the slot table in shared memory).
+__device__ __forceinline__ void rans_symbols_item(const Params& P, const uint32_t* tab, uint8_t* ws, uint32_t k,
+                                                  uint32_t lane) {
   const SmemLayout& SL = P.v.sm;
-  uint32_t* tab = reinterpret_cast<uint32_t*>(sm);
-  for (uint32_t i = threadIdx.x; i < kRansM; i += 32u * kRansWarps) tab[i] = P.v.rans_tab[i];
-  __syncthreads();
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint32_t k = P.item_base + blockIdx.x * kRansWarps + warp;
-  if (k >= P.n) return;
   const uint32_t item = scheduled_item(P, k);
   const uint32_t brick = P.ids[item];
   if (brick >= P.v.n_bricks) return;  // reported by the reconstruction kernel
@@ -128,6 +122,33 @@ __global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_kernel(const __g
   const bool ok = rans_steps(tab, reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(rec) + cofs),
                              nw, S, x0, ns, out, lane);
   if ((!ok || bad_state) && lane == 0) report(P.status, VC_ERR_CORRUPT, item);
+}
+
+__global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_kernel(const __grid_constant__ Params P,
+                                                                      uint8_t* ws) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint32_t* tab = reinterpret_cast<uint32_t*>(sm);
+  for (uint32_t i = threadIdx.x; i < kRansM; i += 32u * kRansWarps) tab[i] = P.v.rans_tab[i];
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t k = P.item_base + blockIdx.x * kRansWarps + warp;
+  if (k >= P.n) return;
+  rans_symbols_item(P, tab, ws, k, lane);
+}
+
+// The same with the item count in device memory (launch_items): persistent warps stride over the
+// items.
+__global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_dev_kernel(const __grid_constant__ Params P,
+                                                                          uint8_t* ws) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint32_t* tab = reinterpret_cast<uint32_t*>(sm);
+  const uint32_t n = launch_items(P);
+  if (blockIdx.x * kRansWarps >= n) return;
+  for (uint32_t i = threadIdx.x; i < kRansM; i += 32u * kRansWarps) tab[i] = P.v.rans_tab[i];
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  for (uint32_t k = blockIdx.x * kRansWarps + warp; k < n; k += gridDim.x * kRansWarps)
+    rans_symbols_item(P, tab, ws, k, lane);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -512,6 +533,7 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   P.ws = nullptr;
   P.ws_item0 = 0;
   P.order = nullptr;
+  P.n_dev = nullptr;
   const uint32_t edge = (1u << v.L) >> lod;
   P.out_words = edge * edge * edge;
   P.pal_bits = P.pal_per = 0;
@@ -634,6 +656,70 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   }
   if (ws) cudaFreeAsync(ws, stream);
   return rc;
+}
+
+// Persistent decode of the first min(cap, *n_dev) items (a count written on the device by an
+// earlier kernel of the stream), without the host reading it: the rANS symbol kernel strides over
+// the items, the batched (b = 64: scratch) kernel pulls them from its work counter. ws (caller's,
+// 256-byte aligned) holds decode_ws_bytes(v, cap) bytes. No size-aware order, no paletting.
+vc_status launch_decode_devcount(Volume& v, const uint32_t* ids, uint32_t cap, const uint32_t* n_dev,
+                                 const uint32_t* slots, uint32_t* cache, uint32_t lod, int32_t* status,
+                                 cudaStream_t stream, uint8_t* ws, size_t ws_cap) {
+  if (cap == 0) return VC_OK;
+  if (v.split && lod == 0) return VC_ERR_UNSUPPORTED;  // bulk copies cannot read the mapped host copy
+  const bool rans = v.coder == 1;
+  const SmemLayout& SL = v.dv.sm;
+  const bool scratch = SL.gscratch != 0;
+  Params P{};
+  P.v = v.dv;
+  P.ids = ids;
+  P.slots = slots;
+  P.n = cap;
+  P.n_dev = n_dev;
+  P.cache = cache;
+  P.lod = lod;
+  P.status = status;
+  const uint32_t edge = (1u << v.L) >> lod;
+  P.out_words = edge * edge * edge;
+  const uint32_t nt = v.sched.threads;
+  void* k = pick_kernel(v.L, nt, SL.gt_bytes == 2, rans, true);
+  if (!k) return VC_ERR_UNSUPPORTED;
+  const uint32_t smem = SL.total;
+  if (!set_smem(k, smem)) return VC_ERR_CUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)nt, smem) != cudaSuccess) return VC_ERR_CUDA;
+  if (per_sm < 1) return VC_ERR_UNSUPPORTED;
+  if (v.sched.blocks_per_sm) per_sm = std::min<int>(per_sm, (int)v.sched.blocks_per_sm);
+  const uint32_t sms = std::max(1u, v.sms);
+  const size_t sym_bytes = rans ? ((size_t)cap * SL.ws_stride + 255u) & ~size_t(255) : 0u;
+  uint32_t grid = std::min<uint32_t>(cap, sms * (uint32_t)per_sm);
+  if (scratch) {
+    grid = std::min(grid, scratch_grid(v, cap));
+    if (ws_cap < sym_bytes + SL.gscratch) return VC_ERR_ARG;
+    grid = (uint32_t)std::min<size_t>(grid, (ws_cap - sym_bytes) / SL.gscratch);
+  } else if (ws_cap < sym_bytes) {
+    return VC_ERR_ARG;
+  }
+  if (rans) {
+    P.ws = ws;
+    if (!set_smem(reinterpret_cast<void*>(&rans_symbols_dev_kernel), SL.a_smem)) return VC_ERR_CUDA;
+    uint8_t* wsp = ws;
+    void* args[] = {&P, &wsp};
+    const uint32_t sblocks = std::min<uint32_t>((cap + kRansWarps - 1) / kRansWarps, sms * 4u);
+    if (cudaLaunchKernel(reinterpret_cast<void*>(&rans_symbols_dev_kernel), dim3(sblocks), dim3(32 * kRansWarps), args,
+                         SL.a_smem, stream) != cudaSuccess)
+      return VC_ERR_CUDA;
+    ++v.launches;
+  }
+  if (cudaMemsetAsync(reinterpret_cast<uint32_t*>(status) + 2, 0, sizeof(uint32_t), stream) != cudaSuccess)
+    return VC_ERR_CUDA;
+  uint8_t* scr = scratch ? ws + sym_bytes : nullptr;
+  void* args[] = {&P};
+  void* args_scratch[] = {&P, &scr};
+  if (cudaLaunchKernel(k, dim3(grid), dim3(nt), scratch ? args_scratch : args, smem, stream) != cudaSuccess)
+    return VC_ERR_CUDA;
+  ++v.launches;
+  return VC_OK;
 }
 
 }  // namespace vc

@@ -30,7 +30,14 @@ struct Params {
   uint32_t pal_bits;  // 0: labels; else cache paletting: pal_bits-bit palette indices,
   uint32_t pal_per;   //   pal_per of them per u32 word (none straddles a word)
   const uint32_t* order;  // size-aware order: the k-th scheduled item is order[k] (nullptr: k)
+  const uint32_t* n_dev;  // persistent schedules: the item count in device memory, read at launch
+                          // (min(n, *n_dev) items; nullptr: n), for work sized on the device
 };
+
+// Items of a launch of a persistent schedule.
+__device__ __forceinline__ uint32_t launch_items(const Params& P) {
+  return P.n_dev ? min(P.n, *P.n_dev) : P.n;
+}
 
 // The item scheduled k-th (k < P.n).
 __device__ __forceinline__ uint32_t scheduled_item(const Params& P, uint32_t k) { return P.order ? P.order[k] : k; }
@@ -1399,15 +1406,16 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) decode_batched_kernel(cons
   uint32_t* counter = reinterpret_cast<uint32_t*>(P.status) + 2;
   unsigned char* stage[2] = {sm + SL.stage_off, sm + SL.stage_off + SL.stage_bytes};
   const uint32_t tid = threadIdx.x;
+  const uint32_t n = launch_items(P);
 
   // thread 0: claims the next item and, if it fits, starts copying its data into stage[buf]
   auto claim_and_issue = [&](uint32_t buf) {
     const uint32_t k = atomicAdd(counter, 1u);
-    const uint32_t item = k < P.n ? scheduled_item(P, k) : k;  // >= P.n: no more items
+    const uint32_t item = k < n ? scheduled_item(P, k) : k;  // >= n: no more items
     misc[1 + buf] = item;
     uint32_t bytes = 0;
     ItemSrc src{};
-    if (item < P.n) {
+    if (item < n) {
       const uint32_t brick = P.ids[item];
       if (brick < P.v.n_bricks) {
         src = item_src<RANS>(P, item, brick);
@@ -1440,7 +1448,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) decode_batched_kernel(cons
   for (;;) {
     __syncthreads();
     const uint32_t item = misc[1 + buf];
-    if (item >= P.n) break;
+    if (item >= n) break;
     if (tid == 0) {
       *s_err = 0;
       if (prefetch) claim_and_issue(buf ^ 1u);
@@ -1500,15 +1508,16 @@ __global__ void __launch_bounds__(NT) decode_scratch_kernel(const __grid_constan
   unsigned char* gm = scratch + (size_t)blockIdx.x * P.v.sm.gscratch;
   unsigned char* sm = P.v.sm.total ? dyn_sm : gm;
   uint32_t* counter = reinterpret_cast<uint32_t*>(P.status) + 2;
+  const uint32_t n = launch_items(P);
   for (;;) {
     if (threadIdx.x == 0) {
       const uint32_t k = P.item_base + atomicAdd(counter, 1u);
-      s_item = k < P.n ? scheduled_item(P, k) : k;  // >= P.n: no more items
+      s_item = k < n ? scheduled_item(P, k) : k;  // >= n: no more items
       s_err = 0;
     }
     __syncthreads();
     const uint32_t item = s_item;
-    if (item >= P.n) break;
+    if (item >= n) break;
     const uint32_t brick = P.ids[item];
     if (brick >= P.v.n_bricks) {
       if (threadIdx.x == 0) report(P.status, VC_ERR_ARG, item);

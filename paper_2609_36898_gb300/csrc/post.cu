@@ -72,10 +72,9 @@ __host__ __device__ inline State state_at(void* base, size_t n) {
 }
 
 // 1. this frame's samples into the accumulation and the G-buffer; the first colours and offsets
-__global__ void post_accum_kernel(const PostDev* __restrict__ Pp, State S, const uint32_t* __restrict__ labels,
+__global__ void post_accum_kernel(const __grid_constant__ PostDev P, State S, const uint32_t* __restrict__ labels,
                                   const float* __restrict__ depth, const uint8_t* __restrict__ face,
                                   const float* __restrict__ rgb) {
-  const PostDev& P = *Pp;
   const uint32_t n = P.W * P.H;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t px = i % P.W, py = i / P.W;
@@ -117,8 +116,14 @@ __device__ __forceinline__ int32_t off_dy(int32_t o) { return o >> 16; }
 __device__ __forceinline__ int32_t make_off(int32_t dx, int32_t dy) { return (dx & 0xFFFF) | (dy << 16); }
 
 // 2. one pass at distance 2^it: rendered pixels filter, the others search the nearest rendered one
-__global__ void post_pass_kernel(const PostDev* __restrict__ Pp, State S, uint32_t it) {
-  const PostDev& P = *Pp;
+__global__ void __launch_bounds__(256) post_pass_kernel(const __grid_constant__ PostDev P, State S, uint32_t it) {
+  __shared__ float hsv[kMaxMat][3];  // the materials' albedo in HSV
+  for (uint32_t m = threadIdx.x; m < P.n_mat; m += blockDim.x) {
+    hsv[m][0] = P.hsv[m][0];
+    hsv[m][1] = P.hsv[m][1];
+    hsv[m][2] = P.hsv[m][2];
+  }
+  __syncthreads();
   const uint32_t n = P.W * P.H;
   const uint32_t src = it & 1u, dst = src ^ 1u;
   const int32_t step = 1 << it;
@@ -127,7 +132,7 @@ __global__ void post_pass_kernel(const PostDev* __restrict__ Pp, State S, uint32
     const uint32_t code = S.gcode[i];
     if ((code & 7u) != kInvalid) {
       const uint32_t lab = S.glabel[i];
-      const float* hp = P.hsv[lab ? material_of(lab, P.n_mat) : 0u];
+      const float* hp = hsv[lab ? material_of(lab, P.n_mat) : 0u];
       const bool hit_p = (code & 7u) != kNoHit;
       const float dp = (float)(code >> 3);
       float sw = 0.0f, acc[3] = {0.0f, 0.0f, 0.0f};
@@ -142,7 +147,7 @@ __global__ void post_pass_kernel(const PostDev* __restrict__ Pp, State S, uint32
           float w = 1.0f;
           if (hit_p) {
             const uint32_t lq = S.glabel[j];
-            const float* hq = P.hsv[lq ? material_of(lq, P.n_mat) : 0u];
+            const float* hq = hsv[lq ? material_of(lq, P.n_mat) : 0u];
             const float r0 = fmul(fsub(hp[0], hq[0]), P.phi_rho), r1 = fmul(fsub(hp[1], hq[1]), P.phi_rho),
                         r2 = fmul(fsub(hp[2], hq[2]), P.phi_rho);
             const float rr = fadd(fadd(fmul(r0, r0), fmul(r1, r1)), fmul(r2, r2));
@@ -189,8 +194,8 @@ __device__ __forceinline__ float aces(float x) {
 }
 
 // 3. colours of the not-yet-rendered pixels from their nearest rendered pixel; tone map, gamma
-__global__ void post_final_kernel(const PostDev* __restrict__ Pp, State S, uint32_t fin, uint32_t* __restrict__ out) {
-  const PostDev& P = *Pp;
+__global__ void post_final_kernel(const __grid_constant__ PostDev P, State S, uint32_t fin,
+                                  uint32_t* __restrict__ out) {
   const uint32_t n = P.W * P.H;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int32_t px = (int32_t)(i % P.W), py = (int32_t)(i / P.W);
@@ -250,6 +255,7 @@ extern "C" vc_status vc_postprocess(vc_volume* vol, const vc_post_params* params
       Q.iterations > 10 || !(Q.subsample <= 2u || Q.subsample == 4u || Q.subsample == 8u) || Q.n_materials == 0 ||
       Q.n_materials > kMaxMat || !Q.materials || !(Q.gamma > 0.0f) || (reinterpret_cast<uintptr_t>(state) & 15u))
     return VC_ERR_ARG;
+  static_assert(sizeof(PostDev) < 32000, "kernel parameter space");
   PostDev P;
   std::memset(&P, 0, sizeof(P));
   P.W = Q.width;
@@ -276,25 +282,14 @@ extern "C" vc_status vc_postprocess(vc_volume* vol, const vc_post_params* params
   P.n_mat = Q.n_materials;
   for (uint32_t m = 0; m < Q.n_materials; ++m) rgb_to_hsv(Q.materials[m].rgb, P.hsv[m]);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  PostDev* d_P = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&d_P), sizeof(PostDev), st) != cudaSuccess) {
-    cudaGetLastError();
-    return VC_ERR_OOM;
-  }
-  vc_status rc = VC_OK;
-  if (cudaMemcpyAsync(d_P, &P, sizeof(P), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess) {
-    rc = VC_ERR_CUDA;
-  } else {
-    const size_t n = (size_t)P.W * P.H;
-    const State S = state_at(state, n);
-    const uint32_t blocks = (uint32_t)std::min<size_t>((n + 255) / 256, (size_t)std::max(1u, v->sms) * 16u);
-    post_accum_kernel<<<blocks, 256, 0, st>>>(d_P, S, labels, depth, face, rgb);
-    for (uint32_t it = 0; it < P.iterations; ++it) post_pass_kernel<<<blocks, 256, 0, st>>>(d_P, S, it);
-    post_final_kernel<<<blocks, 256, 0, st>>>(d_P, S, P.iterations & 1u, rgba_out);
-    if (cudaGetLastError() != cudaSuccess) rc = VC_ERR_CUDA;
-    else v->launches += 2u + P.iterations;
-  }
-  cudaFreeAsync(d_P, st);
-  return rc;
+  // the parameter block travels with each launch (kernel parameter space): no staging copy, no wait
+  const size_t n = (size_t)P.W * P.H;
+  const State S = state_at(state, n);
+  const uint32_t blocks = (uint32_t)std::min<size_t>((n + 255) / 256, (size_t)std::max(1u, v->sms) * 16u);
+  post_accum_kernel<<<blocks, 256, 0, st>>>(P, S, labels, depth, face, rgb);
+  for (uint32_t it = 0; it < P.iterations; ++it) post_pass_kernel<<<blocks, 256, 0, st>>>(P, S, it);
+  post_final_kernel<<<blocks, 256, 0, st>>>(P, S, P.iterations & 1u, rgba_out);
+  if (cudaGetLastError() != cudaSuccess) return VC_ERR_CUDA;
+  v->launches += 2u + P.iterations;
+  return VC_OK;
 }

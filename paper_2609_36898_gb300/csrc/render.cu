@@ -56,6 +56,8 @@ struct Inputs {
   const uint32_t* starts;   // encoding: Brick Starts (words)
   const uint32_t* records;  // encoding: records
   uint32_t coder;
+  uint32_t* marks;          // visibility bits (one per brick) set by rays of depth <= request_depth, or null
+  uint32_t request_depth;
 };
 
 // Jarzynski and Olano's PCG2D integer hash (Hash Functions for GPU Rendering, 2020).
@@ -99,14 +101,26 @@ struct RayState {
   uint32_t face;  // entered face of the current voxel (0 = none)
 };
 
-// Label and cell size (log2) of the cell containing voxel v.
-__device__ __forceinline__ uint32_t cell_at(const RenderDev& R, const Inputs& in, const int32_t v[3], uint32_t* s_log) {
+// Marks brick id as visible (Methods, "GPU rendering pipeline": rays mark the bricks they
+// access), once per brick entered: `last` is the ray's previously marked brick.
+__device__ __forceinline__ void mark_brick(uint32_t* marks, uint32_t id, uint32_t& last) {
+  if (!marks || id == last) return;
+  last = id;
+  const uint32_t bit = 1u << (id & 31u);
+  if (!(marks[id >> 5] & bit)) atomicOr(&marks[id >> 5], bit);
+}
+
+// Label and cell size (log2) of the cell containing voxel v; bricks holding a visible label are
+// marked in `marks` (null: no marking).
+__device__ __forceinline__ uint32_t cell_at(const RenderDev& R, const Inputs& in, const int32_t v[3], uint32_t* s_log,
+                                            uint32_t* marks, uint32_t& last) {
   const uint32_t L = R.L, b = 1u << L;
   const uint32_t id = ((uint32_t)v[0] >> L) + R.nb[0] * (((uint32_t)v[1] >> L) + R.nb[1] * ((uint32_t)v[2] >> L));
   if (!(in.flags[id] & 2u)) {  // nothing but background: cross the brick in one step
     *s_log = L;
     return 0u;
   }
+  mark_brick(marks, id, last);
   const uint64_t off = in.offsets[id];
   if (off == kNotDecoded) {  // the coarsest label, straight from the encoding
     *s_log = L;
@@ -166,15 +180,21 @@ __device__ bool dda_step(const RenderDev& R, RayState& r, uint32_t s_log) {
   return inside;
 }
 
-__device__ __forceinline__ bool opaque(const RenderDev& R, uint32_t l) { return l != 0u && R.mat[material_of(l, R.n_mat)][3] >= 1.0f; }
+// Materials (rgb albedo, opacity), copied into shared memory by each block.
+__device__ __forceinline__ bool opaque(const float4* mat, uint32_t n_mat, uint32_t l) {
+  return l != 0u && mat[material_of(l, n_mat)].w >= 1.0f;
+}
 
-// Marches from r until an opaque voxel (true, its label in *hit) or the volume's end / max_t.
-__device__ bool march_opaque(const RenderDev& R, const Inputs& in, RayState& r, float max_t, uint32_t* hit) {
+// Marches from r until an opaque voxel (true, its label in *hit) or the volume's end / max_t;
+// marks the bricks it accesses in `marks` (null: none).
+__device__ bool march_opaque(const RenderDev& R, const Inputs& in, const float4* mat, RayState& r, float max_t,
+                             uint32_t* hit, uint32_t* marks) {
   const uint32_t max_steps = 3u * (R.dims[0] + R.dims[1] + R.dims[2]) + 64u;
+  uint32_t last = ~0u;
   for (uint32_t step = 0; step < max_steps; ++step) {
     uint32_t s;
-    const uint32_t l = cell_at(R, in, r.v, &s);
-    if (opaque(R, l)) {
+    const uint32_t l = cell_at(R, in, r.v, &s, marks, last);
+    if (opaque(mat, R.n_mat, l)) {
       *hit = l;
       return true;
     }
@@ -248,10 +268,17 @@ __device__ void cosine_dir(Rng& g, const float n[3], float out[3]) {
   for (int a = 0; a < 3; ++a) out[a] = n[a];
 }
 
-__global__ void render_kernel(const RenderDev* __restrict__ Rp, Inputs in, uint32_t* labels_out, float* depth_out,
-                              uint8_t* face_out, float* rgb_out) {
-  const RenderDev& R = *Rp;
+__global__ void __launch_bounds__(128) render_kernel(const __grid_constant__ RenderDev R, Inputs in,
+                                                     uint32_t* labels_out, float* depth_out, uint8_t* face_out,
+                                                     float* rgb_out) {
+  __shared__ float4 mat[kMaxMaterials];
+  for (uint32_t m = threadIdx.x; m < R.n_mat; m += blockDim.x)
+    mat[m] = make_float4(R.mat[m][0], R.mat[m][1], R.mat[m][2], R.mat[m][3]);
+  __syncthreads();
   const CamDev& c = R.cam;
+  // rays of path depth <= request_depth mark the bricks they access: the primary ray is depth 0,
+  // shadow, ambient occlusion and the first path-tracing bounce depth 1, bounce k depth k
+  auto marks_at = [&](uint32_t depth) -> uint32_t* { return depth <= in.request_depth ? in.marks : nullptr; };
   const uint32_t npix = c.W * c.H;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += gridDim.x * blockDim.x) {
     const uint32_t px = i % c.W, py = i / c.W;
@@ -323,11 +350,14 @@ __global__ void render_kernel(const RenderDev* __restrict__ Rp, Inputs in, uint3
       uint32_t prev = 0u;
       bool hit = false;
       const uint32_t max_steps = 3u * (R.dims[0] + R.dims[1] + R.dims[2]) + 64u;
+      uint32_t* const mk0 = marks_at(0);
+      uint32_t last = ~0u;
       for (uint32_t step = 0; step < max_steps && T >= 0.00390625f; ++step) {
         uint32_t s;
-        const uint32_t l = cell_at(R, in, r.v, &s);
+        const uint32_t l = cell_at(R, in, r.v, &s, mk0, last);
         if (l != prev && l != 0u) {
-          const float* m = R.mat[material_of(l, R.n_mat)];
+          const float4 mm = mat[material_of(l, R.n_mat)];
+          const float m[4] = {mm.x, mm.y, mm.z, mm.w};
           if (m[3] > 0.0f) {
             float n[3];
             face_normal(r.face, n);
@@ -355,7 +385,8 @@ __global__ void render_kernel(const RenderDev* __restrict__ Rp, Inputs in, uint3
         if (!dda_step(R, r, s)) break;
       }
       if (hit) {
-        const float* m = R.mat[material_of(out_label, R.n_mat)];
+        const float4 mm = mat[material_of(out_label, R.n_mat)];
+        const float m[3] = {mm.x, mm.y, mm.z};
         float n[3];
         face_normal(r.face, n);
         if (!r.face) {
@@ -370,7 +401,7 @@ __global__ void render_kernel(const RenderDev* __restrict__ Rp, Inputs in, uint3
             RayState sr = from_face(r, R.light);
             uint32_t l2;
             if (sr.v[0] >= 0 && sr.v[0] < (int32_t)R.dims[0] && sr.v[1] >= 0 && sr.v[1] < (int32_t)R.dims[1] &&
-                sr.v[2] >= 0 && sr.v[2] < (int32_t)R.dims[2] && march_opaque(R, in, sr, INFINITY, &l2))
+                sr.v[2] >= 0 && sr.v[2] < (int32_t)R.dims[2] && march_opaque(R, in, mat, sr, INFINITY, &l2, marks_at(1)))
               nl = 0.0f;
           }
           const float shade = fadd(R.ambient, fmul(fsub(1.0f, R.ambient), nl));
@@ -384,7 +415,8 @@ __global__ void render_kernel(const RenderDev* __restrict__ Rp, Inputs in, uint3
             RayState ar = from_face(r, dir);
             uint32_t l2;
             occluded = ar.v[0] >= 0 && ar.v[0] < (int32_t)R.dims[0] && ar.v[1] >= 0 && ar.v[1] < (int32_t)R.dims[1] &&
-                       ar.v[2] >= 0 && ar.v[2] < (int32_t)R.dims[2] && march_opaque(R, in, ar, R.ao_radius, &l2);
+                       ar.v[2] >= 0 && ar.v[2] < (int32_t)R.dims[2] &&
+                       march_opaque(R, in, mat, ar, R.ao_radius, &l2, marks_at(1));
           }
 #pragma unroll
           for (int a = 0; a < 3; ++a) c3[a] = occluded ? 0.0f : fmul(m[a], R.sky);
@@ -399,14 +431,15 @@ __global__ void render_kernel(const RenderDev* __restrict__ Rp, Inputs in, uint3
             uint32_t l2 = 0u;
             const bool inside = br.v[0] >= 0 && br.v[0] < (int32_t)R.dims[0] && br.v[1] >= 0 &&
                                 br.v[1] < (int32_t)R.dims[1] && br.v[2] >= 0 && br.v[2] < (int32_t)R.dims[2];
-            if (!inside || !march_opaque(R, in, br, INFINITY, &l2)) {
+            if (!inside || !march_opaque(R, in, mat, br, INFINITY, &l2, marks_at(bounce))) {
 #pragma unroll
               for (int a = 0; a < 3; ++a) c3[a] = fadd(c3[a], fmul(tp[a], R.sky));
               break;
             }
-            const float* m2 = R.mat[material_of(l2, R.n_mat)];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) tp[a] = fmul(tp[a], m2[a]);
+            const float4 m2 = mat[material_of(l2, R.n_mat)];
+            tp[0] = fmul(tp[0], m2.x);
+            tp[1] = fmul(tp[1], m2.y);
+            tp[2] = fmul(tp[2], m2.z);
             if (bounce >= 4u) {  // Russian roulette
               float q = tp[0] > tp[1] ? tp[0] : tp[1];
               if (tp[2] > q) q = tp[2];
@@ -456,6 +489,7 @@ extern "C" vc_status vc_render(vc_volume* vol, const uint64_t* brick_offsets, co
   const double l2 = (double)P.light_dir[0] * P.light_dir[0] + (double)P.light_dir[1] * P.light_dir[1] +
                     (double)P.light_dir[2] * P.light_dir[2];
   if (!(l2 > 0.0)) return VC_ERR_ARG;
+  static_assert(sizeof(RenderDev) < 32000, "kernel parameter space");
   RenderDev R;
   std::memset(&R, 0, sizeof(R));
   camera_frame(*cam, &R.cam);
@@ -480,11 +514,6 @@ extern "C" vc_status vc_render(vc_volume* vol, const uint64_t* brick_offsets, co
     R.nb[a] = v->nb[a];
   }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  RenderDev* d_R = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&d_R), sizeof(RenderDev), st) != cudaSuccess) {
-    cudaGetLastError();
-    return VC_ERR_OOM;
-  }
   Inputs in;
   in.offsets = brick_offsets;
   in.lods = brick_lods;
@@ -493,18 +522,13 @@ extern "C" vc_status vc_render(vc_volume* vol, const uint64_t* brick_offsets, co
   in.starts = v->dv.starts;
   in.records = v->dv.records;
   in.coder = v->coder;
-  vc_status rc = VC_OK;
-  // the parameter block goes through pageable memory: copy and wait before this call returns
-  if (cudaMemcpyAsync(d_R, &R, sizeof(RenderDev), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess) {
-    rc = VC_ERR_CUDA;
-  } else {
-    const uint32_t npix = cam->width * cam->height;
-    const uint32_t blocks = std::min<uint32_t>((npix + 127u) / 128u, std::max(1u, v->sms) * 16u);
-    render_kernel<<<blocks, 128, 0, st>>>(d_R, in, labels_out, depth_out, face_out, rgb_out);
-    if (cudaGetLastError() != cudaSuccess) rc = VC_ERR_CUDA;
-    else ++v->launches;
-  }
-  cudaFreeAsync(d_R, st);
-  return rc;
+  in.marks = P.marks;
+  in.request_depth = P.request_depth;
+  // the parameter block travels with the launch (kernel parameter space): no staging copy, no wait
+  const uint32_t npix = cam->width * cam->height;
+  const uint32_t blocks = std::min<uint32_t>((npix + 127u) / 128u, std::max(1u, v->sms) * 16u);
+  render_kernel<<<blocks, 128, 0, st>>>(R, in, labels_out, depth_out, face_out, rgb_out);
+  if (cudaGetLastError() != cudaSuccess) return VC_ERR_CUDA;
+  ++v->launches;
+  return VC_OK;
 }

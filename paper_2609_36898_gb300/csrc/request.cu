@@ -63,91 +63,112 @@ struct Grid {
   float b;
 };
 
+// The brick ray of pixel i of camera c: marks the visible bricks it passes in mk (one bit per
+// brick) until the first brick with no background.
+__device__ void march_pixel(const CamDev& c, const uint8_t* __restrict__ flags, const Grid& g, uint32_t* mk,
+                            uint32_t i) {
+  const uint32_t px = i % c.W, py = i / c.W;
+  const float sx = fmul(fsub(fmul(fadd((float)px, 0.5f), c.inv_w2), 1.0f), c.sxs);
+  const float sy = fmul(fsub(1.0f, fmul(fadd((float)py, 0.5f), c.inv_h2)), c.sys);
+  float d[3], o[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float da = fadd(fadd(c.f[a], fmul(sx, c.r[a])), fmul(sy, c.u[a]));
+    d[a] = fdiv(da, g.b);
+    o[a] = fdiv(c.o[a], g.b);
+  }
+  float t0 = 0.0f, t1 = INFINITY;
+  bool miss = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float n = (float)g.nb[a];
+    if (d[a] == 0.0f) {
+      if (o[a] < 0.0f || o[a] >= n) miss = true;
+      continue;
+    }
+    float ta = fdiv(fsub(0.0f, o[a]), d[a]), tb = fdiv(fsub(n, o[a]), d[a]);
+    if (ta > tb) { const float x = ta; ta = tb; tb = x; }
+    if (ta > t0) t0 = ta;
+    if (tb < t1) t1 = tb;
+  }
+  if (miss || !(t0 < t1)) return;
+  int32_t cell[3];
+  float s[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float p = fadd(o[a], fmul(t0, d[a]));
+    float fc = floorf(p);
+    if (fc < 0.0f) fc = 0.0f;
+    if (fc > (float)(g.nb[a] - 1)) fc = (float)(g.nb[a] - 1);
+    cell[a] = (int32_t)fc;
+    float q = fsub(p, fc);
+    if (q < 0.0f) q = 0.0f;
+    if (q > 1.0f) q = 1.0f;
+    s[a] = q;
+  }
+  const uint32_t max_steps = g.nb[0] + g.nb[1] + g.nb[2] + 1;
+  for (uint32_t step = 0; step < max_steps; ++step) {
+    const uint32_t id = (uint32_t)cell[0] + g.nb[0] * ((uint32_t)cell[1] + g.nb[1] * (uint32_t)cell[2]);
+    const uint32_t fl = flags[id];
+    if (fl & 2u) {
+      const uint32_t bit = 1u << (id & 31u);
+      if (!(mk[id >> 5] & bit)) atomicOr(&mk[id >> 5], bit);
+    }
+    if (!(fl & 1u)) break;  // no background in this brick: the ray ends here
+    float dist[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (d[a] > 0.0f) dist[a] = fdiv(fsub(1.0f, s[a]), d[a]);
+      else if (d[a] < 0.0f) dist[a] = fdiv(fsub(0.0f, s[a]), d[a]);
+      else dist[a] = INFINITY;
+    }
+    int ax = 0;
+    if (dist[1] < dist[ax]) ax = 1;
+    if (dist[2] < dist[ax]) ax = 2;
+    const float t = dist[ax];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a == ax) continue;
+      float q = fadd(s[a], fmul(t, d[a]));
+      if (q < 0.0f) q = 0.0f;
+      if (q > 1.0f) q = 1.0f;
+      s[a] = q;
+    }
+    if (d[ax] > 0.0f) {
+      cell[ax] += 1;
+      s[ax] = 0.0f;
+      if (cell[ax] >= (int32_t)g.nb[ax]) break;
+    } else {
+      cell[ax] -= 1;
+      s[ax] = 1.0f;
+      if (cell[ax] < 0) break;
+    }
+  }
+}
+
 // One thread per pixel ray (blockIdx.y = camera); marks visible bricks in the camera's bitmask.
 __global__ void camera_march_kernel(const CamDev* __restrict__ cams, const uint8_t* __restrict__ flags, Grid g,
                                     uint32_t* __restrict__ marks, uint32_t words) {
   const CamDev& c = cams[blockIdx.y];
   uint32_t* mk = marks + (size_t)blockIdx.y * words;
   const uint32_t npix = c.W * c.H;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += gridDim.x * blockDim.x) {
-    const uint32_t px = i % c.W, py = i / c.W;
-    const float sx = fmul(fsub(fmul(fadd((float)px, 0.5f), c.inv_w2), 1.0f), c.sxs);
-    const float sy = fmul(fsub(1.0f, fmul(fadd((float)py, 0.5f), c.inv_h2)), c.sys);
-    float d[3], o[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float da = fadd(fadd(c.f[a], fmul(sx, c.r[a])), fmul(sy, c.u[a]));
-      d[a] = fdiv(da, g.b);
-      o[a] = fdiv(c.o[a], g.b);
-    }
-    float t0 = 0.0f, t1 = INFINITY;
-    bool miss = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float n = (float)g.nb[a];
-      if (d[a] == 0.0f) {
-        if (o[a] < 0.0f || o[a] >= n) miss = true;
-        continue;
-      }
-      float ta = fdiv(fsub(0.0f, o[a]), d[a]), tb = fdiv(fsub(n, o[a]), d[a]);
-      if (ta > tb) { const float x = ta; ta = tb; tb = x; }
-      if (ta > t0) t0 = ta;
-      if (tb < t1) t1 = tb;
-    }
-    if (miss || !(t0 < t1)) continue;
-    int32_t cell[3];
-    float s[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float p = fadd(o[a], fmul(t0, d[a]));
-      float fc = floorf(p);
-      if (fc < 0.0f) fc = 0.0f;
-      if (fc > (float)(g.nb[a] - 1)) fc = (float)(g.nb[a] - 1);
-      cell[a] = (int32_t)fc;
-      float q = fsub(p, fc);
-      if (q < 0.0f) q = 0.0f;
-      if (q > 1.0f) q = 1.0f;
-      s[a] = q;
-    }
-    const uint32_t max_steps = g.nb[0] + g.nb[1] + g.nb[2] + 1;
-    for (uint32_t step = 0; step < max_steps; ++step) {
-      const uint32_t id = (uint32_t)cell[0] + g.nb[0] * ((uint32_t)cell[1] + g.nb[1] * (uint32_t)cell[2]);
-      const uint32_t fl = flags[id];
-      if (fl & 2u) {
-        const uint32_t bit = 1u << (id & 31u);
-        if (!(mk[id >> 5] & bit)) atomicOr(&mk[id >> 5], bit);
-      }
-      if (!(fl & 1u)) break;  // no background in this brick: the ray ends here
-      float dist[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (d[a] > 0.0f) dist[a] = fdiv(fsub(1.0f, s[a]), d[a]);
-        else if (d[a] < 0.0f) dist[a] = fdiv(fsub(0.0f, s[a]), d[a]);
-        else dist[a] = INFINITY;
-      }
-      int ax = 0;
-      if (dist[1] < dist[ax]) ax = 1;
-      if (dist[2] < dist[ax]) ax = 2;
-      const float t = dist[ax];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (a == ax) continue;
-        float q = fadd(s[a], fmul(t, d[a]));
-        if (q < 0.0f) q = 0.0f;
-        if (q > 1.0f) q = 1.0f;
-        s[a] = q;
-      }
-      if (d[ax] > 0.0f) {
-        cell[ax] += 1;
-        s[ax] = 0.0f;
-        if (cell[ax] >= (int32_t)g.nb[ax]) break;
-      } else {
-        cell[ax] -= 1;
-        s[ax] = 1.0f;
-        if (cell[ax] < 0) break;
-      }
-    }
-  }
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += gridDim.x * blockDim.x)
+    march_pixel(c, flags, g, mk, i);
+}
+
+// Up to kMarkCams cameras per launch, passed by value (kernel parameter space: nothing to stage).
+constexpr uint32_t kMarkCams = 64;
+struct CamBlock {
+  CamDev c[kMarkCams];
+};
+
+// The same rays of several cameras (blockIdx.y) into one shared bitmask.
+__global__ void shared_march_kernel(const __grid_constant__ CamBlock cams, const uint8_t* __restrict__ flags, Grid g,
+                                    uint32_t* __restrict__ marks) {
+  const CamDev& c = cams.c[blockIdx.y];
+  const uint32_t npix = c.W * c.H;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += gridDim.x * blockDim.x)
+    march_pixel(c, flags, g, marks, i);
 }
 
 constexpr uint32_t kCompactThreads = 1024;
@@ -250,6 +271,28 @@ vc_status launch_camera_requests(const Volume& v, const vc_camera* cams, uint32_
   camera_compact_kernel<<<ncams, kCompactThreads, 0, stream>>>(dc, marks, (uint32_t)words, g, max_lod, cap, d_counts,
                                                                d_ids, d_lods);
   return cudaGetLastError() == cudaSuccess ? VC_OK : VC_ERR_CUDA;
+}
+
+vc_status launch_shared_marks(const Volume& v, const vc_camera* cams, uint32_t ncams, uint32_t* marks,
+                              cudaStream_t stream) {
+  Grid g;
+  for (int a = 0; a < 3; ++a) g.nb[a] = v.nb[a];
+  g.b = (float)(1u << v.L);
+  for (uint32_t c0 = 0; c0 < ncams; c0 += kMarkCams) {
+    const uint32_t nc = std::min(kMarkCams, ncams - c0);
+    CamBlock B;
+    std::memset(&B, 0, sizeof(B));
+    uint32_t max_pix = 0;
+    for (uint32_t i = 0; i < nc; ++i) {
+      camera_frame(cams[c0 + i], &B.c[i]);
+      max_pix = std::max(max_pix, cams[c0 + i].width * cams[c0 + i].height);
+    }
+    const uint32_t threads = 256;
+    const uint32_t bx = std::min<uint32_t>((max_pix + threads - 1) / threads, std::max(1u, 4096u / nc));
+    shared_march_kernel<<<dim3(bx, nc), threads, 0, stream>>>(B, v.d_flags, g, marks);
+    if (cudaGetLastError() != cudaSuccess) return VC_ERR_CUDA;
+  }
+  return VC_OK;
 }
 
 }  // namespace vc

@@ -488,6 +488,7 @@ vc_status vc_release(void* handle) {
   }
   if (release_server(handle)) return VC_OK;
   if (release_cache(handle)) return VC_OK;
+  if (release_frame(handle)) return VC_OK;
   return VC_ERR_ARG;
 }
 

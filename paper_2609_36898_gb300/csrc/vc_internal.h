@@ -131,6 +131,8 @@ constexpr uint32_t kProfCalls = 4096;
 bool release_server(void* handle);
 // cache.cpp: releases a vc_brick_cache (false if the handle is not one)
 bool release_cache(void* handle);
+// frame.cu: releases a vc_frame_cache (false if the handle is not one)
+bool release_frame(void* handle);
 
 // request.cu: a pinhole camera's frame (forward, right, up), pixel scales and level-of-detail
 // scale, computed in double precision and rounded to float once (shared by the request stage and
@@ -160,6 +162,11 @@ constexpr size_t kCamDevBytes = 76;  // per camera, pinned host staging
 vc_status launch_camera_requests(const Volume& v, const vc_camera* cams, uint32_t ncams, uint32_t max_lod,
                                  uint32_t cap, uint8_t* d_scratch, void* h_cams_pinned, uint32_t* d_counts,
                                  uint32_t* d_ids, uint32_t* d_lods, cudaStream_t stream);
+
+// request.cu: the brick rays of ncams cameras (any number; launched in groups) mark the visible
+// bricks they pass in one shared bitmask (device, one bit per brick; bits are only set)
+vc_status launch_shared_marks(const Volume& v, const vc_camera* cams, uint32_t ncams, uint32_t* marks,
+                              cudaStream_t stream);
 
 // vc_api.cu: the host-side checks of a VCZ1 file (header, Brick Starts, every record's sizes) and
 // the maxima the decoder's layouts are sized by
@@ -197,5 +204,12 @@ size_t decode_ws_bytes(const Volume& v, uint32_t n);
 vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
                            uint32_t lod, uint32_t mode, int32_t* status, cudaStream_t stream, uint8_t* ws_ext,
                            size_t ws_cap, bool presorted = false);
+
+// Persistent decode of min(cap, *n_dev) items, the count read on the device (n_dev: device
+// memory written earlier on the stream); ws: decode_ws_bytes(v, cap) bytes, 256-byte aligned.
+// Labels only (no paletting); VC_ERR_UNSUPPORTED for the finest level of a split volume.
+vc_status launch_decode_devcount(Volume& v, const uint32_t* ids, uint32_t cap, const uint32_t* n_dev,
+                                 const uint32_t* slots, uint32_t* cache, uint32_t lod, int32_t* status,
+                                 cudaStream_t stream, uint8_t* ws, size_t ws_cap);
 
 }  // namespace vc

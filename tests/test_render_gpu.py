@@ -166,3 +166,29 @@ def test_stratified_frames_and_postprocessing_match_the_oracle(subsample):
             assert (gb == wb).all(axis=-1).mean() > 0.95
     finally:
         vol.release()
+
+
+@pytest.mark.parametrize("mode,depth", [(0, 0), (1, 0), (1, 1), (2, 1), (3, 1), (3, 2), (3, 5)])
+def test_visibility_marks_match_the_oracle(mode, depth):
+    """The bricks the rays of path depth <= request_depth access (one bit per brick), for every
+    shading mode, equal the oracle's, and the image is unchanged by marking."""
+    V = synth.fill(synth.small(dims=(96, 80, 64), seed=45, grid=16, diameter=14.0, bg=0.45))
+    enc, vol, lods, offsets, cache, ocache = _setup(V, 4, 11)
+    try:
+        n = vol.n_bricks
+        marks = torch.zeros((n + 31) // 32, dtype=torch.int32, device="cuda")
+        for ci, cam in enumerate(CAMERAS):
+            marks.zero_()
+            kw = dict(mode=mode, frame=ci + 1, jitter=True, max_bounces=8, ao_radius=10.0)
+            got = _gpu_render(vol, offsets, lods, cache, cam, marks_ptr=marks.data_ptr(), request_depth=depth, **kw)
+            vis = np.zeros(n, np.uint8)
+            want = oracle.render(enc, offsets, lods, ocache, *cam, materials=MATERIALS, visible=vis, request_depth=depth,
+                                 **kw)
+            m = marks.cpu().numpy().view(np.uint32)
+            bits = (m[np.arange(n) >> 5] >> (np.arange(n) & 31).astype(np.uint32)) & 1
+            assert np.array_equal(bits.astype(bool), vis.astype(bool)), (mode, depth, ci, int((bits != vis).sum()))
+            assert vis.sum() > 0
+            for g, w in zip(got, want):
+                assert np.array_equal(g.view(np.uint8), np.ascontiguousarray(w).view(np.uint8))
+    finally:
+        vol.release()
