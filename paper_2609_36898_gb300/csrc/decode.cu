@@ -8,7 +8,10 @@
 //     interleaved states decode one symbol each per step; the lanes whose state fell below 2^16
 //     take the next 16-bit words in lane order (ballot + popc ranks). The symbols (two per byte,
 //     the same layout as the plain coder) go to a stream-ordered workspace. Decoding is a serial
-//     chain per brick, so many bricks per SM hide its latency.
+//     chain per brick, so many bricks per SM hide its latency. For a level of detail of 2 or
+//     more the warp also tells operations from delta entries (a shuffle scan of the 2-state
+//     automaton per step) and counts each level's nodes, stops after the target level, and leaves
+//     the prefix length for the reconstruction, which parses only that prefix.
 //
 //  B. reconstruct kernels: one thread block per brick (grid) or persistent blocks pulling bricks
 //     from a work counter with a bulk-copy prefetch of the next brick's record (batched):
@@ -104,6 +107,124 @@ __device__ __forceinline__ bool rans_steps(const uint32_t* tab, const uint16_t* 
   return !__any_sync(0xFFFFFFFFu, bad);
 }
 
+// Position (0..31) of the k-th set bit (k >= 1, counted from bit 0) of m; m holds at least k.
+__device__ __forceinline__ uint32_t kth_set_bit(uint32_t m, uint32_t k) {
+  uint32_t lo = 0, hi = 31;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    const uint32_t le = mid == 31u ? 0xFFFFFFFFu : (2u << mid) - 1u;
+    if ((uint32_t)__popc(m & le) >= k) hi = mid;
+    else lo = mid + 1u;
+  }
+  return lo;
+}
+
+// The same decode, stopped once the levels 0 .. T are complete (a coarser level of detail needs
+// no more of the stream): the stream holds the levels one after the other, level l + 1 has 8
+// nodes per node of level l emitted with stop bit 0, and a node's operation may be followed by
+// delta entries. Per step the warp finds which of its 32 symbols are operations (the 2-state
+// operation / entry automaton, composed over the lanes by a shuffle scan) and counts the nodes of
+// the current level. Returns the symbols decoded: up to the first operation after level T's last
+// node (S if there is none); the end-of-stream checks apply only when that is S.
+__device__ __forceinline__ uint32_t rans_steps_prefix(const uint32_t* tab, const uint16_t* words, uint32_t nw,
+                                                      uint32_t S, uint32_t x, uint32_t ns, uint8_t* out,
+                                                      uint32_t lane, uint32_t T, bool no_stop, bool short_delta,
+                                                      bool* ok) {
+  const uint32_t lt = lanemask_lt();
+  uint8_t* o = out + (lane >> 1);
+  const bool even = !(lane & 1u);
+  auto ld = [&](uint32_t i) -> uint32_t { return i < nw ? (uint32_t)__ldg(words + i) : 0u; };
+  uint32_t wb = 0, w0 = ld(lane), w1 = ld(32u + lane), w2 = ld(64u + lane), w3 = ld(96u + lane);
+  uint32_t ptr = 0;
+  uint32_t st = 0;                              // automaton state entering the step (1: an entry is next)
+  uint32_t level = 0, rem = 1, open = 0;        // current level, its nodes still to come, its stop-0 nodes
+  bool wait_op = false;                         // level T is complete: the end is the next operation
+  uint32_t end = S;
+  for (uint32_t base = 0; base < S; base += 32u) {
+    const uint32_t i = base + lane;
+    const bool active = i < S;
+    uint32_t s = 0;
+    if (active) {
+      const uint32_t e = tab[x & (kRansM - 1u)];
+      s = e >> 25;
+      x = (e & 0x1FFFu) * (x >> 12) + ((e >> 13) & 0xFFFu);
+    }
+    const bool need = active && x < (1u << 16);
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
+    const uint32_t r = ptr - wb + __popc(m & lt);
+    const uint32_t v0 = __shfl_sync(0xFFFFFFFFu, w0, r & 31u), v1 = __shfl_sync(0xFFFFFFFFu, w1, r & 31u);
+    if (need) x = (x << 16) | (r < 32u ? v0 : v1);
+    ptr += __popc(m);
+    if (ptr - wb >= 32u) {
+      wb += 32u;
+      w0 = w1;
+      w1 = w2;
+      w2 = w3;
+      w3 = ld(wb + 96u + lane);
+    }
+    const uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, s, 1);
+    if (active && even) o[base >> 1] = (uint8_t)(s | (i + 1 < S ? hi << 4 : 0u));
+    // the state after this symbol from state 0 / 1 (inactive lanes: identity), composed over lanes
+    uint32_t g0 = active ? ((s & 7u) == OP_DELTA ? 1u : 0u) : 0u;
+    uint32_t g1 = active ? (short_delta ? 0u : (s >> 3) & 1u) : 1u;
+#pragma unroll
+    for (uint32_t d = 1; d < 32u; d <<= 1) {
+      const uint32_t p0 = __shfl_up_sync(0xFFFFFFFFu, g0, d), p1 = __shfl_up_sync(0xFFFFFFFFu, g1, d);
+      if (lane >= d) {
+        const uint32_t n0 = p0 ? g1 : g0, n1 = p1 ? g1 : g0;
+        g0 = n0;
+        g1 = n1;
+      }
+    }
+    uint32_t e0 = __shfl_up_sync(0xFFFFFFFFu, g0, 1), e1 = __shfl_up_sync(0xFFFFFFFFu, g1, 1);
+    if (lane == 0) { e0 = 0u; e1 = 1u; }
+    const uint32_t entering = st ? e1 : e0;
+    const bool is_op = active && entering == 0u;
+    uint32_t opm = __ballot_sync(0xFFFFFFFFu, is_op);
+    const uint32_t openm = __ballot_sync(0xFFFFFFFFu, is_op && (no_stop || !(s & 8u)));
+    const uint32_t l0 = __shfl_sync(0xFFFFFFFFu, g0, 31), l1 = __shfl_sync(0xFFFFFFFFu, g1, 31);
+    st = st ? l1 : l0;
+    bool done = false;
+    if (wait_op) {
+      if (opm) {
+        end = base + (__ffs(opm) - 1u);
+        done = true;
+      }
+    } else {
+      while (opm) {
+        const uint32_t c = (uint32_t)__popc(opm);
+        const uint32_t k = rem < c ? rem : c;
+        const uint32_t p = kth_set_bit(opm, k);
+        const uint32_t sel = opm & (p == 31u ? 0xFFFFFFFFu : (2u << p) - 1u);
+        open += (uint32_t)__popc(sel & openm);
+        rem -= k;
+        opm &= ~sel;
+        if (rem == 0u) {
+          if (level == T || open == 0u) {  // the target level (or the last emitted one) is complete
+            wait_op = true;
+            if (opm) {
+              end = base + (__ffs(opm) - 1u);
+              done = true;
+            }
+            break;
+          }
+          ++level;
+          rem = 8u * open;
+          open = 0u;
+        }
+      }
+    }
+    if (done) break;
+  }
+  bool bad = false;
+  if (end == S) {
+    bad |= ptr != nw;
+    bad |= lane < ns && x != (1u << 16);
+  }
+  *ok = !__any_sync(0xFFFFFFFFu, bad);
+  return end;
+}
+
 // The symbols of the item scheduled k-th, by one warp (tab: the slot table in shared memory).
 __device__ __forceinline__ void rans_symbols_item(const Params& P, const uint32_t* tab, uint8_t* ws, uint32_t k,
                                                   uint32_t lane) {
@@ -119,8 +240,18 @@ __device__ __forceinline__ void rans_symbols_item(const Params& P, const uint32_
   const bool bad_state = __any_sync(0xFFFFFFFFu, lane < ns && x0 < (1u << 16));
   uint8_t* out = ws + (size_t)(item - P.ws_item0) * SL.ws_stride;
   const uint32_t cofs = 16u + 4u * ns + 4u * np;
-  const bool ok = rans_steps(tab, reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(rec) + cofs),
-                             nw, S, x0, ns, out, lane);
+  const uint16_t* words = reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(rec) + cofs);
+  bool ok;
+  if (P.lod < kPrefixMinLod) {
+    ok = rans_steps(tab, words, nw, S, x0, ns, out, lane);
+  } else {
+    // a coarse level of detail: the stream up to its level; the symbols decoded go to the
+    // workspace slot's last word for the reconstruction kernel
+    const uint32_t T = P.v.L > P.lod ? P.v.L - P.lod : 0u;
+    const uint32_t used = rans_steps_prefix(tab, words, nw, S, x0, ns, out, lane, T, (P.v.flags & kFlagNoStop) != 0,
+                                            (P.v.flags & kFlagShortDelta) != 0, &ok);
+    if (lane == 0) reinterpret_cast<uint32_t*>(ws + (size_t)(item - P.ws_item0 + 1u) * SL.ws_stride)[-1] = used;
+  }
   if ((!ok || bad_state) && lane == 0) report(P.status, VC_ERR_CORRUPT, item);
 }
 

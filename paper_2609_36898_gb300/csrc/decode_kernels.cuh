@@ -34,6 +34,12 @@ struct Params {
                           // (min(n, *n_dev) items; nullptr: n), for work sized on the device
 };
 
+// From this level of detail on, the rANS symbol kernel decodes only the stream's prefix up to the
+// level needed (levels 0 .. L - lod) and the reconstruction parses that prefix. At level 1 the
+// prefix is still about a quarter of the stream, and the per-step operation scan costs more than
+// it saves (measured on 32^3 bricks of the 512^3 workload).
+constexpr uint32_t kPrefixMinLod = 2;
+
 // Items of a launch of a persistent schedule.
 __device__ __forceinline__ uint32_t launch_items(const Params& P) {
   return P.n_dev ? min(P.n, *P.n_dev) : P.n;
@@ -486,9 +492,11 @@ __device__ __forceinline__ void store_pair(GT* fg, uint32_t pos, uint32_t lo, ui
 // palette indices (P.pal_bits).
 // on_stage_free() is called by every thread exactly once, as soon as the staged record is no longer
 // read: right after the finest grid is filled when the palette fits its shared copy, else at the end.
+// S_use: symbols to parse (0: all; fewer: a coarser level of detail needs only the stream's
+// prefix up to its level, and the counts of the whole stream are then upper bounds).
 template <int L, typename GT, bool RANS, int NT, typename Hook>
 __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32_t* sw, uint32_t* out,
-                             unsigned char* sm, unsigned char* gm, int* s_err, Hook&& on_stage_free) {
+                             unsigned char* sm, unsigned char* gm, int* s_err, uint32_t S_use, Hook&& on_stage_free) {
   constexpr uint32_t NW = NT / 32;
   constexpr uint32_t MARK = GridT<GT>::MARK;
   const SmemLayout& SL = P.v.sm;
@@ -497,9 +505,11 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   uint32_t* wtot = misc + 16;      // NW warp totals (words 16..47)
   uint32_t* scan_tmp = misc + 48;  // 5 NW + 5 words (48..255), 8-byte aligned
 
-  const uint32_t n_pal = head[0], S = head[1], nd = head[3];
+  const uint32_t n_pal = head[0], S_rec = head[1], nd = head[3];
+  const bool truncated = S_use != 0u && S_use < S_rec;
+  const uint32_t S = truncated ? S_use : S_rec;
   const bool short_delta = (P.v.flags & kFlagShortDelta) != 0;
-  const uint32_t ns = RANS ? (S < 32u ? S : 32u) : 0u;
+  const uint32_t ns = RANS ? (S_rec < 32u ? S_rec : 32u) : 0u;
 
   BrickCtx c;
   c.pal = head + 4 + ns;
@@ -537,7 +547,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
                                                    short_delta);
     c.nodes = nodes;
     c.n_nodes = po.n_nodes;
-    if (po.n_delta != nd) set_err(s_err, VC_ERR_CORRUPT);
+    if (truncated ? po.n_delta > nd : po.n_delta != nd) set_err(s_err, VC_ERR_CORRUPT);
     // delta values from their entries, one delta operation per thread (visible after the barriers
     // of step 2)
     for (uint32_t d = tid; d < c.dlist_cap; d += NT) dlist[d] = read_delta(sw, dlist[d], S, short_delta);
@@ -577,7 +587,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
       adv_pre[w] = (Pre)pa; del_pre[w] = (Pre)pd;
       pa += __popc(adv_mask[w]); pd += __popc(del_mask[w]);
     }
-    if (tid == 0 && (ta != n_pal || td != nd)) set_err(s_err, VC_ERR_CORRUPT);
+    if (tid == 0 && (truncated ? (ta > n_pal || td > nd) : (ta != n_pal || td != nd))) set_err(s_err, VC_ERR_CORRUPT);
   }
   __syncthreads();
 
@@ -1332,6 +1342,8 @@ struct ItemSrc {
   const uint32_t* stream;  // symbols in global memory (record for plain, workspace for rANS)
   uint32_t head_bytes;     // staged head (whole record for plain)
   uint32_t stream_bytes;   // staged symbols after the head (rANS only)
+  uint32_t S_use;          // symbols to parse: all (0), or the prefix the rANS symbol kernel decoded
+                           // for a coarser level of detail
 };
 
 template <bool RANS>
@@ -1344,11 +1356,13 @@ __device__ __forceinline__ ItemSrc item_src(const Params& P, uint32_t item, uint
     const uint32_t ns = S < 32u ? S : 32u;
     s.head_bytes = (16u + 4u * ns + 4u * np + 15u) & ~15u;
     s.stream = reinterpret_cast<const uint32_t*>(P.ws + (size_t)(item - P.ws_item0) * P.v.sm.ws_stride);
-    s.stream_bytes = (((S + 1u) >> 1) + 15u) & ~15u;
+    s.S_use = P.lod >= kPrefixMinLod ? min(s.stream[P.v.sm.ws_stride / 4u - 1u], S) : 0u;  // the slot's last word
+    s.stream_bytes = ((((s.S_use ? s.S_use : S) + 1u) >> 1) + 15u) & ~15u;
   } else {
     s.head_bytes = (e - a) * 4u;
     s.stream = s.rec + 4u + s.rec[0];
     s.stream_bytes = 0;
+    s.S_use = 0;
   }
   return s;
 }
@@ -1388,7 +1402,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) decode_grid_kernel(const _
   }
   __syncthreads();
   uint32_t* out = P.cache + (size_t)P.slots[item] * P.out_words;
-  decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, sm, s_err, [] {});
+  decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, sm, s_err, src.S_use, [] {});
   __syncthreads();
   if (threadIdx.x == 0 && *s_err) report(P.status, *s_err, item);
 }
@@ -1477,7 +1491,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) decode_batched_kernel(cons
                                            : head + 4u + head[0]);
       uint32_t* out = P.cache + (size_t)P.slots[item] * P.out_words;
       // depth 1: the next item's copy starts as soon as this brick's stage is free
-      decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, sm, s_err, [&] {
+      decode_brick<L, GT, RANS, NT>(P, head, sw, out, sm, sm, s_err, src.S_use, [&] {
         if (!prefetch && tid == 0) claim_and_issue(0);
         released = true;
       });
@@ -1524,7 +1538,7 @@ __global__ void __launch_bounds__(NT) decode_scratch_kernel(const __grid_constan
     } else {
       const ItemSrc src = item_src<RANS>(P, item, brick);
       uint32_t* out = P.cache + (size_t)P.slots[item] * P.out_words;
-      decode_brick<L, GT, RANS, NT>(P, src.rec, src.stream, out, sm, gm, &s_err, [] {});
+      decode_brick<L, GT, RANS, NT>(P, src.rec, src.stream, out, sm, gm, &s_err, src.S_use, [] {});
       __syncthreads();
       if (threadIdx.x == 0 && s_err) report(P.status, s_err, item);
     }
