@@ -441,9 +441,9 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
     s.list_off = put(false, align16(2u * (s.list0_cap + cap[1])));
     // the finest index grid holds one z half at a time for b = 32 (plus the last plane of the first)
     const uint32_t nh = L == 5 ? 2u : 1u;
-    // label output of b <= 32 bricks keeps 8 children per open level-(L-1) cell instead
+    // label output keeps 8 children per open level-(L-1) cell instead
     const uint32_t cap_open = (L - 1u) & 1u ? s.list1_cap : s.list0_cap;  // open level-(L-1) cells
-    const uint32_t cb_bytes = L >= 2 && L <= 5 ? s.gt_bytes * 8u * cap_open : 0u;
+    const uint32_t cb_bytes = L >= 2 ? s.gt_bytes * 8u * cap_open : 0u;
     s.fg_bytes = align16(std::max(s.gt_bytes * b * b * b / nh, cb_bytes));
     s.fg_off = put(true, s.fg_bytes);
     s.plane_off = put(false, nh == 2 ? align16(s.gt_bytes * b * b) : 0u);
@@ -459,9 +459,10 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
     s.pq_cap = L & 1u ? s.list1_cap : s.list0_cap;
     // per warp a queue of up to 32 x 7 neighbour marks; the node operations, delta values and
     // cursor masks are no longer read when the queues are filled
+    // (b = 64: the same span, in the scratch slice)
     const uint32_t mq_bytes = 224u * (threads / 32u);
-    const uint32_t dead_span = s.mask_off + 12u * s.nwords - s.nodes_off;
-    s.mq_off = global ? 0u : dead_span >= mq_bytes ? s.nodes_off : put(false, align16(mq_bytes));
+    const uint32_t dead_span = s.mask_off + (global ? 16u : 12u) * s.nwords - s.nodes_off;
+    s.mq_off = dead_span >= mq_bytes ? s.nodes_off : put(global, align16(mq_bytes));
     if (!global || o + 64u <= (uint32_t)optin) break;  // (+ the kernel's static shared words)
   }
   const uint32_t span_bytes = s.fg_off - s.mask_off;  // masks .. rank lists (b <= 32)

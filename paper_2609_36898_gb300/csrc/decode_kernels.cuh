@@ -921,7 +921,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   }
 
   bool cells_path = false;
-  if constexpr (L >= 2 && L <= 5) {
+  if constexpr (L >= 2 && L <= 6) {
     if (finest && !P.pal_bits) {
       // 4'. finest level with label output. The finest voxels of a level-(L-1) cell that was not
       // emitted with stop bit 0 all hold that cell's index (in the level grid); only the open

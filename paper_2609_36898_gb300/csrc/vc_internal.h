@@ -51,7 +51,7 @@ struct SmemLayout {
   uint32_t mq_off;       // label output: one 224-byte queue of neighbour marks per warp (over the
                          // node operations .. cursor masks span, dead by then, or its own region)
   uint32_t fg_off;       // finest level: palette index per voxel (gt_bytes each; one z half for b = 32),
-                         // or (label output, b <= 32) the 8 children of each open level-(L-1) cell by rank
+                         // or (label output) the 8 children of each open level-(L-1) cell by rank
   uint32_t plane_off;    // b = 32: the last z plane of the first half (for -z neighbours of the second)
   uint32_t fg_bytes;     // bytes of the finest grid region
   uint32_t wst_off;      // the parse's per-word automaton masks (the finest grid's region)
