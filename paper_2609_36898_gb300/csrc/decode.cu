@@ -4,7 +4,7 @@
 // pipeline"). Here the work of one brick is split into two kernels so that each runs at the
 // parallelism it needs:
 //
-//  A. rans_symbols_kernel (rANS volumes only): one warp per brick, 16 bricks per block. The 32
+//  A. rans_symbols_kernel (rANS volumes only): one warp per brick, 4 to 16 bricks per block. The 32
 //     interleaved states decode one symbol each per step; the lanes whose state fell below 2^16
 //     take the next 16-bit words in lane order (ballot + popc ranks). The symbols (two per byte,
 //     the same layout as the plain coder) go to a stream-ordered workspace. Decoding is a serial
@@ -259,10 +259,10 @@ __global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_kernel(const __g
                                                                       uint8_t* ws) {
   extern __shared__ __align__(128) unsigned char sm[];
   uint32_t* tab = reinterpret_cast<uint32_t*>(sm);
-  for (uint32_t i = threadIdx.x; i < kRansM; i += 32u * kRansWarps) tab[i] = P.v.rans_tab[i];
+  for (uint32_t i = threadIdx.x; i < kRansM; i += blockDim.x) tab[i] = P.v.rans_tab[i];
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint32_t k = P.item_base + blockIdx.x * kRansWarps + warp;
+  const uint32_t k = P.item_base + blockIdx.x * (blockDim.x >> 5) + warp;  // bricks per block: its warps
   if (k >= P.n) return;
   rans_symbols_item(P, tab, ws, k, lane);
 }
@@ -514,14 +514,36 @@ bool set_smem(void* k, uint32_t bytes) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
 }
 
-bool launch_symbols(const Params& P, uint8_t* ws, uint32_t base, uint32_t count, uint32_t smem, cudaStream_t s) {
+// Bricks (warps) per block of the rANS symbol kernel for `count` bricks on `sms` multiprocessors.
+// Each brick is one serial chain, so a launch lasts as long as its slowest chain, and chains that
+// share a scheduler slow each other down: when the launch fits about one wave, the block size
+// (16, 8 or 4 warps) that puts the fewest warps on the busiest multiprocessor wins (ties: the
+// larger block, fewer copies of the slot table); 512 bricks of 64^3 then run on 128
+// multiprocessors, 4 warps each, instead of 32 with 16.
+uint32_t symbol_warps(uint32_t count, uint32_t sms) {
+  if (sms == 0 || count > kRansWarps * sms * 4u) return kRansWarps;
+  uint32_t best = kRansWarps, best_load = ~0u;
+  for (uint32_t w = kRansWarps; w >= 4u; w >>= 1) {
+    const uint32_t blocks = (count + w - 1) / w;
+    const uint32_t load = (blocks + sms - 1) / sms * w;
+    if (load < best_load) {
+      best_load = load;
+      best = w;
+    }
+  }
+  return best;
+}
+
+bool launch_symbols(const Params& P, uint8_t* ws, uint32_t base, uint32_t count, uint32_t smem, uint32_t sms,
+                    cudaStream_t s) {
   Params PA = P;
   PA.item_base = base;
   PA.n = base + count;
   void* args[] = {&PA, &ws};
-  const uint32_t blocks = (count + kRansWarps - 1) / kRansWarps;
-  return cudaLaunchKernel(reinterpret_cast<void*>(&rans_symbols_kernel), dim3(blocks), dim3(32 * kRansWarps), args,
-                          smem, s) == cudaSuccess;
+  const uint32_t w = symbol_warps(count, sms);
+  const uint32_t blocks = (count + w - 1) / w;
+  return cudaLaunchKernel(reinterpret_cast<void*>(&rans_symbols_kernel), dim3(blocks), dim3(32 * w), args, smem, s) ==
+         cudaSuccess;
 }
 
 // The pipelined schedule: chunks of request items flow through the rANS symbol kernel (stream 0)
@@ -567,7 +589,8 @@ vc_status launch_pipelined(Volume& v, Params P, uint32_t n, cudaStream_t stream)
     Q.ws_item0 = base;
     Q.ws = ws + (size_t)slot * chunk * SL.ws_stride;
     if (k >= ring) ok(cudaStreamWaitEvent(sA, v.ev_f[slot], 0));  // slot read by chunk k - ring
-    ok(launch_symbols(Q, const_cast<uint8_t*>(Q.ws), base, cnt, SL.a_smem, sA) ? cudaSuccess : cudaErrorLaunchFailure);
+    ok(launch_symbols(Q, const_cast<uint8_t*>(Q.ws), base, cnt, SL.a_smem, v.sms, sA) ? cudaSuccess
+                                                                                         : cudaErrorLaunchFailure);
     ok(cudaEventRecord(v.ev_a[slot], sA));
     ok(cudaStreamWaitEvent(sF, v.ev_a[slot], 0));
     void* argsF[] = {&Q};
@@ -741,7 +764,7 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
   auto mark = [&](int i) { return !ev || cudaEventRecord(ev[i], stream) == cudaSuccess; };
   auto run_symbols = [&](uint32_t base, uint32_t count) -> bool {
     if (!rans) return true;
-    if (!launch_symbols(P, const_cast<uint8_t*>(P.ws), base, count, v.dv.sm.a_smem, stream)) return false;
+    if (!launch_symbols(P, const_cast<uint8_t*>(P.ws), base, count, v.dv.sm.a_smem, v.sms, stream)) return false;
     ++v.launches;
     return true;
   };
