@@ -663,6 +663,15 @@ void vc_free_bytes(uint8_t* bytes);
 /* Human-readable name of a status code (static string). */
 const char* vc_status_string(vc_status s);
 
+/* Self-test of the bounded device-side wait that the batched schedule uses for its bulk-copy
+ * prefetch (every wait gives up after 1 s of wall-clock time and reports VC_ERR_TIMEOUT instead of
+ * hanging): one thread waits, with a budget of budget_us microseconds (1 .. 10^7), on an mbarrier
+ * that nothing arrives at and no copy is bound to, then returns. Enqueued on `cuda_stream`;
+ * status_dev (device, VC_STATUS_WORDS int32, words 0..1 zeroed by the caller) receives
+ * VC_ERR_TIMEOUT in word 0 and the time waited in nanoseconds in words 2 (low) and 3 (high). The
+ * context stays usable. */
+vc_status vc_selftest_bounded_wait(uint32_t budget_us, int32_t* status_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

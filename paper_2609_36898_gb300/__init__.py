@@ -180,6 +180,8 @@ def _lib_handle():
         lib.vc_post_state_bytes.restype = SZ
         lib.vc_postprocess.argtypes = [P, ctypes.POINTER(vc_post_params), P, P, P, P, P, P, P]
         lib.vc_postprocess.restype = I32
+        lib.vc_selftest_bounded_wait.argtypes = [U32, P, P]
+        lib.vc_selftest_bounded_wait.restype = I32
         lib.vc_frame_cache_create.argtypes = [P, ctypes.c_uint64, U32, U32, ctypes.POINTER(P)]
         lib.vc_frame_cache_view_get.argtypes = [P, ctypes.POINTER(vc_frame_cache_view)]
         lib.vc_frame_mark_cameras.argtypes = [P, P, U32, P]
@@ -542,6 +544,11 @@ def vc_frame_stats_get(fc, stream: int = 0) -> vc_frame_stats:
     st = vc_frame_stats()
     _check(_lib_handle().vc_frame_stats_get(fc, ctypes.byref(st), ctypes.c_void_p(stream)), "vc_frame_stats_get")
     return st
+
+
+def vc_selftest_bounded_wait(budget_us: int, status_ptr: int, stream: int = 0) -> None:
+    _check(_lib_handle().vc_selftest_bounded_wait(budget_us, ctypes.c_void_p(status_ptr), ctypes.c_void_p(stream)),
+           "vc_selftest_bounded_wait")
 
 
 def vc_request_bricks(srv, volume_index: int, cams, max_lod: int = 31) -> list:

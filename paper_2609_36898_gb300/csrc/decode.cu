@@ -613,6 +613,22 @@ uint32_t scratch_grid(const Volume& v, uint32_t n) {
   return std::min(n, std::max(1u, v.sms) * per_sm);
 }
 
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing arrives at (no copy
+// is issued, so nothing is in flight when it gives up) and reports VC_ERR_TIMEOUT, or VC_OK if the
+// wait were to complete; the elapsed wall-clock time goes to status[2..3] (ns, low / high).
+__global__ void wait_selftest_kernel(int32_t* status, uint64_t budget_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  const uint64_t t0 = globaltimer_ns();
+  const bool ok = mbar_wait_bounded(&bar, 0, budget_ns);
+  const uint64_t dt = globaltimer_ns() - t0;
+  if (!ok) atomicCAS(reinterpret_cast<int*>(status), 0, VC_ERR_TIMEOUT);
+  status[2] = (int32_t)(uint32_t)dt;
+  status[3] = (int32_t)(uint32_t)(dt >> 32);
+}
+
 // The coarsest level of detail straight from the encoding: the first palette entry of each brick
 // (the root is always a palette advance).
 __global__ void __launch_bounds__(256) coarsest_kernel(const __grid_constant__ Params P, uint32_t* out) {
@@ -875,6 +891,15 @@ vc_status launch_decode_devcount(Volume& v, const uint32_t* ids, uint32_t cap, c
     return VC_ERR_CUDA;
   ++v.launches;
   return VC_OK;
+}
+
+vc_status launch_wait_selftest(uint32_t budget_us, int32_t* status, cudaStream_t stream) {
+  const uint64_t ns = (uint64_t)budget_us * 1000ull;
+  void* args[] = {&status, const_cast<uint64_t*>(&ns)};
+  return cudaLaunchKernel(reinterpret_cast<void*>(&wait_selftest_kernel), dim3(1), dim3(32), args, 0, stream) ==
+                 cudaSuccess
+             ? VC_OK
+             : VC_ERR_CUDA;
 }
 
 }  // namespace vc

@@ -97,6 +97,11 @@ const char* vc_status_string(vc_status s) {
   }
 }
 
+vc_status vc_selftest_bounded_wait(uint32_t budget_us, int32_t* status_dev, void* cuda_stream) {
+  if (!status_dev || budget_us == 0 || budget_us > 10000000u) return VC_ERR_ARG;
+  return launch_wait_selftest(budget_us, status_dev, static_cast<cudaStream_t>(cuda_stream));
+}
+
 }  // extern "C"
 
 namespace vc {

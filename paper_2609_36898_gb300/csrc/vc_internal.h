@@ -212,4 +212,8 @@ vc_status launch_decode_devcount(Volume& v, const uint32_t* ids, uint32_t cap, c
                                  const uint32_t* slots, uint32_t* cache, uint32_t lod, int32_t* status,
                                  cudaStream_t stream, uint8_t* ws, size_t ws_cap);
 
+// A one-thread kernel waits (bounded, budget_us) on an mbarrier nothing arrives at and reports
+// VC_ERR_TIMEOUT to status[0], the elapsed nanoseconds to status[2..3].
+vc_status launch_wait_selftest(uint32_t budget_us, int32_t* status, cudaStream_t stream);
+
 }  // namespace vc
