@@ -8,7 +8,7 @@
 //     interleaved states decode one symbol each per step; the lanes whose state fell below 2^16
 //     take the next 16-bit words in lane order (ballot + popc ranks). The symbols (two per byte,
 //     the same layout as the plain coder) go to a stream-ordered workspace. Decoding is a serial
-//     chain per brick, so many bricks per SM hide its latency. For a level of detail of 2 or
+//     chain per brick, so many bricks per SM hide its latency. For a level of detail of 1 or
 //     more the warp also tells operations from delta entries (a shuffle scan of the 2-state
 //     automaton per step) and counts each level's nodes, stops after the target level, and leaves
 //     the prefix length for the reconstruction, which parses only that prefix.
@@ -164,32 +164,29 @@ __device__ __forceinline__ uint32_t rans_steps_prefix(const uint32_t* tab, const
     }
     const uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, s, 1);
     if (active && even) o[base >> 1] = (uint8_t)(s | (i + 1 < S ? hi << 4 : 0u));
-    // the state after this symbol from state 0 / 1 (inactive lanes: identity), composed over lanes
-    uint32_t g0 = active ? ((s & 7u) == OP_DELTA ? 1u : 0u) : 0u;
-    uint32_t g1 = active ? (short_delta ? 0u : (s >> 3) & 1u) : 1u;
+    // the state after this symbol entered in state 0 (bit 0) / 1 (bit 1), inactive lanes the
+    // identity; composed over the lanes (p, then g: state s -> bit p(s) of g)
+    uint32_t g = active ? ((s & 7u) == OP_DELTA ? 1u : 0u) | ((short_delta ? 0u : (s >> 3) & 1u) << 1) : 2u;
 #pragma unroll
     for (uint32_t d = 1; d < 32u; d <<= 1) {
-      const uint32_t p0 = __shfl_up_sync(0xFFFFFFFFu, g0, d), p1 = __shfl_up_sync(0xFFFFFFFFu, g1, d);
-      if (lane >= d) {
-        const uint32_t n0 = p0 ? g1 : g0, n1 = p1 ? g1 : g0;
-        g0 = n0;
-        g1 = n1;
-      }
+      const uint32_t p = __shfl_up_sync(0xFFFFFFFFu, g, d);
+      if (lane >= d) g = ((g >> (p & 1u)) & 1u) | (((g >> (p >> 1)) & 1u) << 1);
     }
-    uint32_t e0 = __shfl_up_sync(0xFFFFFFFFu, g0, 1), e1 = __shfl_up_sync(0xFFFFFFFFu, g1, 1);
-    if (lane == 0) { e0 = 0u; e1 = 1u; }
-    const uint32_t entering = st ? e1 : e0;
-    const bool is_op = active && entering == 0u;
+    uint32_t e = __shfl_up_sync(0xFFFFFFFFu, g, 1);
+    if (lane == 0) e = 2u;
+    const bool is_op = active && ((e >> st) & 1u) == 0u;
     uint32_t opm = __ballot_sync(0xFFFFFFFFu, is_op);
     const uint32_t openm = __ballot_sync(0xFFFFFFFFu, is_op && (no_stop || !(s & 8u)));
-    const uint32_t l0 = __shfl_sync(0xFFFFFFFFu, g0, 31), l1 = __shfl_sync(0xFFFFFFFFu, g1, 31);
-    st = st ? l1 : l0;
+    st = (__shfl_sync(0xFFFFFFFFu, g, 31) >> st) & 1u;
     bool done = false;
     if (wait_op) {
       if (opm) {
         end = base + (__ffs(opm) - 1u);
         done = true;
       }
+    } else if ((uint32_t)__popc(opm) < rem) {  // every operation of the step is in the current level
+      open += (uint32_t)__popc(openm);
+      rem -= (uint32_t)__popc(opm);
     } else {
       while (opm) {
         const uint32_t c = (uint32_t)__popc(opm);

@@ -35,10 +35,10 @@ struct Params {
 };
 
 // From this level of detail on, the rANS symbol kernel decodes only the stream's prefix up to the
-// level needed (levels 0 .. L - lod) and the reconstruction parses that prefix. At level 1 the
-// prefix is still about a quarter of the stream, and the per-step operation scan costs more than
-// it saves (measured on 32^3 bricks of the 512^3 workload).
-constexpr uint32_t kPrefixMinLod = 2;
+// level needed (levels 0 .. L - lod) and the reconstruction parses that prefix (level 0 needs the
+// whole stream). At level 1 the prefix is still about a quarter of the stream and the gain is a few
+// percent (32^3 bricks of the 512^3 workload: 0.258 -> 0.246 ms for 4096 bricks).
+constexpr uint32_t kPrefixMinLod = 1;
 
 // Items of a launch of a persistent schedule.
 __device__ __forceinline__ uint32_t launch_items(const Params& P) {
