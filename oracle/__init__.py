@@ -23,6 +23,12 @@ OP_ALL = 0x7F
 CODER_PLAIN, CODER_RANS = 0, 1
 FLAG_NO_STOP = 1
 FLAG_SHORT_DELTA = 2  # limited delta: one 4-bit entry per delta operation holding delta - 1, 2 <= delta <= 16
+FLAG_RUNS_SHIFT = 2   # bits 2..3: log2 of the rANS runs per record (1, 2, 4 or 8 independently coded runs)
+
+
+def runs_flag(k: int) -> int:
+    """The header flag bits of k rANS runs per record (k = 1, 2, 4, 8)."""
+    return {1: 0, 2: 1, 4: 2, 8: 3}[k] << FLAG_RUNS_SHIFT
 ERR_ARG, ERR_FORMAT, ERR_OOM, ERR_CORRUPT = -1, -2, -3, -5
 
 NODE_DTYPE = np.dtype([("level", "<i4"), ("morton", "<u4"), ("op", "<i4"), ("stop", "<i4"),
@@ -68,6 +74,8 @@ def _load():
         lib.oracle_camera_bricks.restype = ctypes.c_int
         lib.oracle_brick_lods.argtypes = [P, SZ, P, P, P, ctypes.c_float, U32, U32, U32, P]
         lib.oracle_brick_lods.restype = ctypes.c_int
+        lib.oracle_head_words.argtypes = [U32, U32, U32]
+        lib.oracle_head_words.restype = U32
         lib.oracle_render.argtypes = [P, SZ, P, P, P, P, P, P, ctypes.c_float, U32, U32, P, P, P, P, P]
         lib.oracle_render.restype = ctypes.c_int
         lib.oracle_post.argtypes = [P] * 14
@@ -173,7 +181,7 @@ def brick_record(vol: np.ndarray, brick_id: int) -> dict:
     r = vol[rec_off + 4 * a: rec_off + 4 * e]
     w = np.frombuffer(r.tobytes(), dtype="<u4")
     n_pal, S, cb, nd = (int(x) for x in w[:4])
-    ns = min(S, 32) if h["coder"] == CODER_RANS else 0
+    ns = int(_load().oracle_head_words(h["coder"], h["flags"], S))
     pal = w[4 + ns: 4 + ns + n_pal].copy()
     return {"n_pal": n_pal, "n_sym": S, "coded_bytes": cb, "n_delta": nd, "palette": pal, "words": e - a,
             "offset_words": a}

@@ -35,10 +35,13 @@ static uint32_t crd32(const uint8_t* p) {
   return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
 }
 
+/* csgv_oracle.c: words between a record's header and its palette (rANS states and run starts). */
+uint32_t oracle_head_words(uint32_t coder, uint32_t flags, uint32_t S);
+
 /* Per brick: bit 0 = palette holds label 0, bit 1 = palette holds a label other than 0. */
 int oracle_palette_flags(const uint8_t* vol, size_t size, uint32_t nb[3], uint32_t* L_out, uint8_t** flags_out) {
   if (size < C_HEADER_BYTES || crd32(vol) != C_MAGIC) return -2;
-  const uint32_t L = crd32(vol + 20), coder = crd32(vol + 28), n = crd32(vol + 36);
+  const uint32_t L = crd32(vol + 20), coder = crd32(vol + 28), flags = crd32(vol + 32), n = crd32(vol + 36);
   const uint32_t b = 1u << L;
   for (int a = 0; a < 3; ++a) nb[a] = (crd32(vol + 8 + 4 * a) + b - 1) / b;
   const size_t rec_off = (C_HEADER_BYTES + 4 * ((size_t)n + 1) + 15) & ~(size_t)15;
@@ -48,7 +51,7 @@ int oracle_palette_flags(const uint8_t* vol, size_t size, uint32_t nb[3], uint32
     const uint32_t a = crd32(vol + C_HEADER_BYTES + 4 * (size_t)i);
     const uint8_t* r = vol + rec_off + 4 * (size_t)a;
     const uint32_t n_pal = crd32(r), S = crd32(r + 4);
-    const uint32_t ns = coder == 1 ? (S < 32 ? S : 32) : 0;
+    const uint32_t ns = oracle_head_words(coder, flags, S);
     const uint8_t* pal = r + 16 + 4 * (size_t)ns;
     for (uint32_t k = 0; k < n_pal; ++k) fl[i] |= crd32(pal + 4 * (size_t)k) == 0 ? 1u : 2u;
   }

@@ -72,6 +72,15 @@
 #define SHORT_DELTA_MIN 2u
 #define SHORT_DELTA_MAX 16u
 
+/* rANS runs (flags bits 2..3 = log2 K, K = 1, 2, 4 or 8; rANS volumes only): a record's S symbols
+ * are cut into runs of Q = 32 ceil(S / 32K) symbols (the last may be shorter, and small records
+ * have fewer than K runs), each coded on its own with 32 interleaved states, so that a decoder can
+ * decode the runs side by side. Not in the paper, which leaves the coder's layout to its encoder
+ * implementations; K = 1 is the single-run record. */
+#define FLAG_RUNS_SHIFT 2u
+#define FLAG_RUNS_MASK (3u << FLAG_RUNS_SHIFT)
+#define FLAGS_ALL (FLAG_NO_STOP | FLAG_SHORT_DELTA | FLAG_RUNS_MASK)
+
 #define RANS_BITS 12
 #define RANS_M (1u << RANS_BITS)
 #define RANS_L (1u << 16)
@@ -187,6 +196,38 @@ static long rans_encode(const uint8_t* sym, uint32_t S, const uint32_t freq[16],
   return nw;
 }
 
+/* Runs of a record of S symbols (see FLAG_RUNS_SHIFT): run length Q and number of runs. */
+static uint32_t runs_of(uint32_t flags) { return 1u << ((flags & FLAG_RUNS_MASK) >> FLAG_RUNS_SHIFT); }
+static uint32_t run_len(uint32_t S, uint32_t K) {
+  const uint32_t per = (S + 32u * K - 1u) / (32u * K);
+  return 32u * (per ? per : 1u);
+}
+static uint32_t run_count(uint32_t S, uint32_t K) {
+  const uint32_t q = run_len(S, K);
+  return S ? (S + q - 1u) / q : 1u;
+}
+static uint32_t run_size(uint32_t S, uint32_t K, uint32_t k) {
+  const uint32_t q = run_len(S, K);
+  const uint32_t len = S > k * q ? S - k * q : 0u;
+  return len < q ? len : q;
+}
+/* Words between a rANS record's header and its palette: every run's final states (min(run, 32)
+ * each, run after run), then the first coded word of every run but the first. */
+static uint32_t rans_head_words(uint32_t S, uint32_t K) {
+  const uint32_t n = run_count(S, K);
+  uint32_t w = n - 1u;
+  for (uint32_t k = 0; k < n; ++k) {
+    const uint32_t len = run_size(S, K, k);
+    w += len < RANS_LANES ? len : RANS_LANES;
+  }
+  return w;
+}
+
+/* Words between a record's header and its palette, for the other oracle files (0 for plain). */
+uint32_t oracle_head_words(uint32_t coder, uint32_t flags, uint32_t S) {
+  return coder == CODER_RANS ? rans_head_words(S, runs_of(flags)) : 0u;
+}
+
 /* Decode S symbols from n_states initial states and nw 16-bit words (little-endian bytes).
  * Every lane decodes its symbol of the step; then, in lane order, each lane whose state fell
  * below 2^16 shifts in the next word. The stream is valid iff no read runs past the words, all
@@ -226,6 +267,56 @@ static int rans_decode(const uint32_t* states0, const uint8_t* wbytes, uint32_t 
   if (ptr != nw) return O_ERR_CORRUPT;
   for (uint32_t l = 0; l < ns; ++l)
     if (x[l] != RANS_L) return O_ERR_CORRUPT;
+  return 0;
+}
+
+/* Code S symbols as run_count(S, K) runs: head[] receives rans_head_words(S, K) words (the runs'
+ * states, then where runs 1.. start in the words), words[] the runs' words one run after the
+ * other (room for S words). Returns the word count, or -1 if a symbol has frequency 0. */
+static long rans_encode_runs(const uint8_t* sym, uint32_t S, const uint32_t freq[16], uint32_t K, uint32_t* head,
+                             uint16_t* words) {
+  const uint32_t n = run_count(S, K), q = run_len(S, K);
+  uint32_t n_states = 0;
+  for (uint32_t k = 0; k < n; ++k) {
+    const uint32_t len = run_size(S, K, k);
+    n_states += len < RANS_LANES ? len : RANS_LANES;
+  }
+  uint32_t hs = 0;
+  long nw = 0;
+  for (uint32_t k = 0; k < n; ++k) {
+    const uint32_t len = run_size(S, K, k);
+    if (k) head[n_states + k - 1u] = (uint32_t)nw;
+    const long w = rans_encode(sym + (size_t)k * q, len, freq, head + hs, words + nw);
+    if (w < 0) return -1;
+    hs += len < RANS_LANES ? len : RANS_LANES;
+    nw += w;
+  }
+  return nw;
+}
+
+/* Decode the runs of a record: head points at its rans_head_words(S, K) words. The run starts
+ * must not decrease and stay within the nw words; every run must read exactly its words. */
+static int rans_decode_runs(const uint8_t* head, uint32_t S, uint32_t K, const uint8_t* wbytes, uint32_t nw,
+                            const uint32_t freq[16], uint8_t* sym) {
+  const uint32_t n = run_count(S, K), q = run_len(S, K);
+  uint32_t n_states = 0;
+  for (uint32_t k = 0; k < n; ++k) {
+    const uint32_t len = run_size(S, K, k);
+    n_states += len < RANS_LANES ? len : RANS_LANES;
+  }
+  uint32_t hs = 0;
+  for (uint32_t k = 0; k < n; ++k) {
+    const uint32_t len = run_size(S, K, k);
+    const uint32_t w0 = k ? rd32(head + 4 * ((size_t)n_states + k - 1u)) : 0u;
+    const uint32_t w1 = k + 1u < n ? rd32(head + 4 * ((size_t)n_states + k)) : nw;
+    if (w0 > w1 || w1 > nw) return O_ERR_CORRUPT;
+    uint32_t st[RANS_LANES];
+    const uint32_t ns = len < RANS_LANES ? len : RANS_LANES;
+    for (uint32_t l = 0; l < ns; ++l) st[l] = rd32(head + 4 * ((size_t)hs + l));
+    const int rc = rans_decode(st, wbytes + 2 * (size_t)w0, w1 - w0, len, freq, sym + (size_t)k * q);
+    if (rc) return rc;
+    hs += ns;
+  }
   return 0;
 }
 
@@ -396,7 +487,8 @@ int oracle_encode_volume(const uint32_t* V, const uint32_t dims[3], uint32_t log
   if (!V || !dims || !out_bytes || !out_size) return O_ERR_ARG;
   if (log2b < 1 || log2b > 6) return O_ERR_ARG;
   if (!(op_mask & (1u << OP_ADV)) || (op_mask & ~OP_ALL)) return O_ERR_ARG;
-  if (coder > CODER_RANS || (flags & ~(FLAG_NO_STOP | FLAG_SHORT_DELTA))) return O_ERR_ARG;
+  if (coder > CODER_RANS || (flags & ~FLAGS_ALL)) return O_ERR_ARG;
+  if (coder != CODER_RANS && (flags & FLAG_RUNS_MASK)) return O_ERR_ARG;
   for (int a = 0; a < 3; ++a) if (dims[a] == 0) return O_ERR_ARG;
   const uint32_t b = 1u << log2b;
   const int L = (int)log2b;
@@ -428,8 +520,9 @@ int oracle_encode_volume(const uint32_t* V, const uint32_t dims[3], uint32_t log
   uint32_t freq[16] = {0};
   if (!rc && coder == CODER_RANS) rc = oracle_rans_quantize(counts, freq);
 
-  /* records: header {n_pal, n_sym, coded_bytes, n_delta}, [rANS states], palette, stream,
-   * zero padding to 16 bytes */
+  /* records: header {n_pal, n_sym, coded_bytes, n_delta}, [rANS states and run starts],
+   * palette, stream, zero padding to 16 bytes */
+  const uint32_t K = runs_of(flags);
   uint8_t** rec = (uint8_t**)calloc(n_bricks, sizeof(uint8_t*));
   uint32_t* rec_words = (uint32_t*)calloc(n_bricks, sizeof(uint32_t));
   uint64_t total_words = 0;
@@ -437,15 +530,15 @@ int oracle_encode_volume(const uint32_t* V, const uint32_t dims[3], uint32_t log
   if (!rec || !rec_words) rc = O_ERR_OOM;
   for (uint32_t id = 0; id < n_bricks && !rc; ++id) {
     brick_stream* s = &bs[id];
-    uint32_t ns = (coder == CODER_RANS) ? (s->n_sym < RANS_LANES ? s->n_sym : RANS_LANES) : 0;
+    uint32_t ns = (coder == CODER_RANS) ? rans_head_words(s->n_sym, K) : 0;
     uint32_t coded_bytes;
     uint16_t* words = NULL;
-    uint32_t states[RANS_LANES];
+    uint32_t states[8 * RANS_LANES + 8];
     if (coder == CODER_RANS) {
       /* a 16-bit word per renormalisation; at most one per symbol */
       words = (uint16_t*)malloc(((size_t)s->n_sym + 1) * sizeof(uint16_t));
       if (!words) { rc = O_ERR_OOM; break; }
-      long nw = rans_encode(s->sym, s->n_sym, freq, states, words);
+      long nw = rans_encode_runs(s->sym, s->n_sym, freq, K, states, words);
       if (nw < 0) { free(words); rc = O_ERR_ARG; break; }
       coded_bytes = (uint32_t)(2 * nw);
     } else {
@@ -540,7 +633,8 @@ static int parse_volume(const uint8_t* v, size_t size, vol_view* o) {
   o->records_words = rd32(v + 112);
   if (o->L < 1 || o->L > 6) return O_ERR_FORMAT;
   if (!(o->op_mask & (1u << OP_ADV)) || (o->op_mask & ~OP_ALL)) return O_ERR_FORMAT;
-  if (o->coder > CODER_RANS || (o->flags & ~(FLAG_NO_STOP | FLAG_SHORT_DELTA))) return O_ERR_FORMAT;
+  if (o->coder > CODER_RANS || (o->flags & ~FLAGS_ALL)) return O_ERR_FORMAT;
+  if (o->coder != CODER_RANS && (o->flags & FLAG_RUNS_MASK)) return O_ERR_FORMAT;
   uint32_t b = 1u << o->L;
   uint64_t nb = 1;
   for (int a = 0; a < 3; ++a) {
@@ -570,7 +664,7 @@ static int brick_symbols(const vol_view* V, uint32_t id, uint8_t** sym_out, uint
   const uint8_t* r = V->records + 4 * (size_t)a;
   size_t avail = 4 * (size_t)(e - a);
   uint32_t n_pal = rd32(r), S = rd32(r + 4), cb = rd32(r + 8), n_delta = rd32(r + 12);
-  uint32_t ns = (V->coder == CODER_RANS) ? (S < RANS_LANES ? S : RANS_LANES) : 0;
+  uint32_t ns = (V->coder == CODER_RANS) ? rans_head_words(S, runs_of(V->flags)) : 0;
   size_t need = 16 + 4 * (size_t)ns + 4 * (size_t)n_pal + cb;
   if (((need + 15) & ~(size_t)15) != avail) return O_ERR_FORMAT;
   if (V->coder == CODER_PLAIN && cb != (S + 1) / 2) return O_ERR_FORMAT;
@@ -584,9 +678,7 @@ static int brick_symbols(const vol_view* V, uint32_t id, uint8_t** sym_out, uint
   if (V->coder == CODER_PLAIN) {
     for (uint32_t i = 0; i < S; ++i) sym[i] = (uint8_t)((coded[i / 2] >> (4 * (i & 1))) & 15u);
   } else {
-    uint32_t st[RANS_LANES];
-    for (uint32_t l = 0; l < ns; ++l) st[l] = rd32(states + 4 * l);
-    int rc = rans_decode(st, coded, cb / 2, S, V->freq, sym);
+    int rc = rans_decode_runs(states, S, runs_of(V->flags), coded, cb / 2, V->freq, sym);
     if (rc) { free(sym); return rc; }
   }
   *sym_out = sym; *S_out = S; *pal_out = pal; *n_pal_out = n_pal; *n_delta_out = n_delta;
@@ -779,16 +871,17 @@ int oracle_pack_single_brick(uint32_t log2b, uint32_t op_mask, uint32_t coder, u
   for (uint32_t i = 0; i < S; ++i) { if (sym[i] > 15) return O_ERR_ARG; counts[sym[i]]++; }
   uint32_t freq[16] = {0};
   uint32_t ns = 0, cb;
-  uint32_t states[RANS_LANES];
+  uint32_t states[8 * RANS_LANES + 8];
   uint16_t* words = NULL;
+  if (coder != CODER_RANS && (flags & FLAG_RUNS_MASK)) return O_ERR_ARG;
   if (coder == CODER_RANS) {
     oracle_rans_quantize(counts, freq);
     words = (uint16_t*)malloc(((size_t)S + 1) * sizeof(uint16_t));
     if (!words) return O_ERR_OOM;
-    long nw = rans_encode(sym, S, freq, states, words);
+    long nw = rans_encode_runs(sym, S, freq, runs_of(flags), states, words);
     if (nw < 0) { free(words); return O_ERR_ARG; }
     cb = (uint32_t)(2 * nw);
-    ns = S < RANS_LANES ? S : RANS_LANES;
+    ns = rans_head_words(S, runs_of(flags));
   } else {
     cb = (S + 1) / 2;
   }
@@ -853,15 +946,16 @@ int oracle_pack_bricks(uint32_t log2b, uint32_t op_mask, uint32_t coder, uint32_
     const uint32_t* p = pal + po;
     uint32_t S = S_each[i], np = npal_each[i];
     uint32_t ns = 0, cb;
-    uint32_t states[RANS_LANES];
+    uint32_t states[8 * RANS_LANES + 8];
     uint16_t* words = NULL;
+    if (coder != CODER_RANS && (flags & FLAG_RUNS_MASK)) { rc = O_ERR_ARG; break; }
     if (coder == CODER_RANS) {
       words = (uint16_t*)malloc(((size_t)S + 1) * sizeof(uint16_t));
       if (!words) { rc = O_ERR_OOM; break; }
-      long nw = rans_encode(s, S, freq, states, words);
+      long nw = rans_encode_runs(s, S, freq, runs_of(flags), states, words);
       if (nw < 0) { free(words); rc = O_ERR_ARG; break; }
       cb = (uint32_t)(2 * nw);
-      ns = S < RANS_LANES ? S : RANS_LANES;
+      ns = rans_head_words(S, runs_of(flags));
     } else {
       cb = (S + 1) / 2;
     }

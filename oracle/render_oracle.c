@@ -44,6 +44,7 @@ typedef struct {
 } cam_frame;
 
 int oracle_palette_flags(const uint8_t* vol, size_t size, uint32_t nb[3], uint32_t* L_out, uint8_t** flags_out);
+uint32_t oracle_head_words(uint32_t coder, uint32_t flags, uint32_t S);
 void oracle_camera_frame(const float pos[3], const float dir[3], const float up[3], float fov_y, uint32_t W,
                          uint32_t H, cam_frame* c);
 
@@ -79,7 +80,7 @@ int oracle_subset_pixel(uint32_t px, uint32_t py, uint32_t s, uint32_t f) {
 #define R_NOT_DECODED (~0ull)
 
 typedef struct {
-  uint32_t dims[3], nb[3], L, coder;
+  uint32_t dims[3], nb[3], L, coder, vflags;
   const uint8_t* vol;
   const uint32_t* starts; /* not 4-byte aligned in general: read through rd32 */
   size_t rec_off;
@@ -152,7 +153,7 @@ static uint32_t cell_at(const rctx* C, const int32_t v[3], uint32_t* s_log, uint
     *s_log = L;
     const uint8_t* rec = C->vol + C->rec_off + 4 * (size_t)rd32(C->vol + 128 + 4 * (size_t)id);
     const uint32_t n_pal = rd32(rec), S = rd32(rec + 4);
-    const uint32_t ns = C->coder == 1 ? (S < 32 ? S : 32) : 0;
+    const uint32_t ns = oracle_head_words(C->coder, C->vflags, S);
     return n_pal ? rd32(rec + 16 + 4 * (size_t)ns) : 0u;
   }
   const uint32_t k = C->lods[id], e = b >> k;
@@ -432,6 +433,7 @@ int oracle_render(const uint8_t* vol, size_t size, const uint64_t* offsets, cons
   if (rc) return rc;
   for (int a = 0; a < 3; ++a) C.dims[a] = rd32(vol + 8 + 4 * a);
   C.coder = rd32(vol + 28);
+  C.vflags = rd32(vol + 32);
   const uint32_t n = rd32(vol + 36);
   C.vol = vol;
   C.rec_off = (128 + 4 * ((size_t)n + 1) + 15) & ~(size_t)15;
