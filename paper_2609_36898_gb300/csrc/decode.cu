@@ -119,30 +119,37 @@ __device__ __forceinline__ uint32_t kth_set_bit(uint32_t m, uint32_t k) {
   return lo;
 }
 
-// The same decode, stopped once the levels 0 .. T are complete (a coarser level of detail needs
-// no more of the stream): the stream holds the levels one after the other, level l + 1 has 8
-// nodes per node of level l emitted with stop bit 0, and a node's operation may be followed by
-// delta entries. Per step the warp finds which of its 32 symbols are operations (the 2-state
-// operation / entry automaton, composed over the lanes by a shuffle scan) and counts the nodes of
-// the current level. Returns the symbols decoded: up to the first operation after level T's last
-// node (S if there is none); the end-of-stream checks apply only when that is S.
-__device__ __forceinline__ uint32_t rans_steps_prefix(const uint32_t* tab, const uint16_t* words, uint32_t nw,
-                                                      uint32_t S, uint32_t x, uint32_t ns, uint8_t* out,
-                                                      uint32_t lane, uint32_t T, bool no_stop, bool short_delta,
-                                                      bool* ok) {
+// The prefix decode's walk over the stream, carried from one rANS run to the next: the
+// operation / entry automaton's state, the current level, its nodes still to come and its nodes
+// emitted with stop bit 0, and whether the target level is complete (then the end is the next
+// operation).
+struct PrefixWalk {
+  uint32_t st, level, rem, open;
+  bool wait_op, done;
+  uint32_t end;
+};
+
+// One run of the prefix decode: the stream's symbols s0 .. s0 + len - 1 (s0 a multiple of 32)
+// from the run's states and its nw words, into the workspace slot `out` (nibbles by stream
+// position). A coarser level of detail needs the levels 0 .. T only, and they come first: level
+// l + 1 has 8 nodes per node of level l emitted with stop bit 0, and an operation may be followed
+// by delta entries. Per step the warp finds which of its 32 symbols are operations (the 2-state
+// automaton, both entering states packed in 2 bits and composed over the lanes by a shuffle
+// scan) and counts the nodes of the current level. W.done once the first operation after level
+// T's last node is reached (W.end: its position). false for a read past the run's words, or, when
+// the run was decoded to its end, words left over or a state that does not end at 2^16.
+__device__ bool prefix_run(const uint32_t* tab, const uint16_t* words, uint32_t nw, uint32_t s0, uint32_t len,
+                           uint32_t x, uint32_t ns, uint8_t* out, uint32_t lane, uint32_t T, bool no_stop,
+                           bool short_delta, PrefixWalk& W) {
   const uint32_t lt = lanemask_lt();
   uint8_t* o = out + (lane >> 1);
   const bool even = !(lane & 1u);
   auto ld = [&](uint32_t i) -> uint32_t { return i < nw ? (uint32_t)__ldg(words + i) : 0u; };
   uint32_t wb = 0, w0 = ld(lane), w1 = ld(32u + lane), w2 = ld(64u + lane), w3 = ld(96u + lane);
   uint32_t ptr = 0;
-  uint32_t st = 0;                              // automaton state entering the step (1: an entry is next)
-  uint32_t level = 0, rem = 1, open = 0;        // current level, its nodes still to come, its stop-0 nodes
-  bool wait_op = false;                         // level T is complete: the end is the next operation
-  uint32_t end = S;
-  for (uint32_t base = 0; base < S; base += 32u) {
+  for (uint32_t base = 0; base < len; base += 32u) {
     const uint32_t i = base + lane;
-    const bool active = i < S;
+    const bool active = i < len;
     uint32_t s = 0;
     if (active) {
       const uint32_t e = tab[x & (kRansM - 1u)];
@@ -163,7 +170,7 @@ __device__ __forceinline__ uint32_t rans_steps_prefix(const uint32_t* tab, const
       w3 = ld(wb + 96u + lane);
     }
     const uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, s, 1);
-    if (active && even) o[base >> 1] = (uint8_t)(s | (i + 1 < S ? hi << 4 : 0u));
+    if (active && even) o[(s0 + base) >> 1] = (uint8_t)(s | (i + 1 < len ? hi << 4 : 0u));
     // the state after this symbol entered in state 0 (bit 0) / 1 (bit 1), inactive lanes the
     // identity; composed over the lanes (p, then g: state s -> bit p(s) of g)
     uint32_t g = active ? ((s & 7u) == OP_DELTA ? 1u : 0u) | ((short_delta ? 0u : (s >> 3) & 1u) << 1) : 2u;
@@ -174,109 +181,124 @@ __device__ __forceinline__ uint32_t rans_steps_prefix(const uint32_t* tab, const
     }
     uint32_t e = __shfl_up_sync(0xFFFFFFFFu, g, 1);
     if (lane == 0) e = 2u;
-    const bool is_op = active && ((e >> st) & 1u) == 0u;
+    const bool is_op = active && ((e >> W.st) & 1u) == 0u;
     uint32_t opm = __ballot_sync(0xFFFFFFFFu, is_op);
     const uint32_t openm = __ballot_sync(0xFFFFFFFFu, is_op && (no_stop || !(s & 8u)));
-    st = (__shfl_sync(0xFFFFFFFFu, g, 31) >> st) & 1u;
-    bool done = false;
-    if (wait_op) {
+    W.st = (__shfl_sync(0xFFFFFFFFu, g, 31) >> W.st) & 1u;
+    if (W.wait_op) {
       if (opm) {
-        end = base + (__ffs(opm) - 1u);
-        done = true;
+        W.end = s0 + base + (__ffs(opm) - 1u);
+        W.done = true;
       }
-    } else if ((uint32_t)__popc(opm) < rem) {  // every operation of the step is in the current level
-      open += (uint32_t)__popc(openm);
-      rem -= (uint32_t)__popc(opm);
+    } else if ((uint32_t)__popc(opm) < W.rem) {  // every operation of the step is in the current level
+      W.open += (uint32_t)__popc(openm);
+      W.rem -= (uint32_t)__popc(opm);
     } else {
       while (opm) {
         const uint32_t c = (uint32_t)__popc(opm);
-        const uint32_t k = rem < c ? rem : c;
+        const uint32_t k = W.rem < c ? W.rem : c;
         const uint32_t p = kth_set_bit(opm, k);
         const uint32_t sel = opm & (p == 31u ? 0xFFFFFFFFu : (2u << p) - 1u);
-        open += (uint32_t)__popc(sel & openm);
-        rem -= k;
+        W.open += (uint32_t)__popc(sel & openm);
+        W.rem -= k;
         opm &= ~sel;
-        if (rem == 0u) {
-          if (level == T || open == 0u) {  // the target level (or the last emitted one) is complete
-            wait_op = true;
+        if (W.rem == 0u) {
+          if (W.level == T || W.open == 0u) {  // the target level (or the last emitted one) is complete
+            W.wait_op = true;
             if (opm) {
-              end = base + (__ffs(opm) - 1u);
-              done = true;
+              W.end = s0 + base + (__ffs(opm) - 1u);
+              W.done = true;
             }
             break;
           }
-          ++level;
-          rem = 8u * open;
-          open = 0u;
+          ++W.level;
+          W.rem = 8u * W.open;
+          W.open = 0u;
         }
       }
     }
-    if (done) break;
+    if (W.done) return true;  // stopped inside the run: its end is not checked
   }
-  bool bad = false;
-  if (end == S) {
-    bad |= ptr != nw;
-    bad |= lane < ns && x != (1u << 16);
-  }
-  *ok = !__any_sync(0xFFFFFFFFu, bad);
-  return end;
+  bool bad = ptr != nw;
+  bad |= lane < ns && x != (1u << 16);
+  return !__any_sync(0xFFFFFFFFu, bad);
 }
 
-// The symbols of the item scheduled k-th, by one warp (tab: the slot table in shared memory).
+// Run `run` of the item scheduled k-th, by one warp (tab: the slot table in shared memory); the
+// runs of a record are independent (vc_internal.h). With wpi = 1 at a coarse level of detail the
+// warp walks the runs in order and stops after the target level; the symbols decoded go to the
+// workspace slot's last word for the reconstruction kernel.
 __device__ __forceinline__ void rans_symbols_item(const Params& P, const uint32_t* tab, uint8_t* ws, uint32_t k,
-                                                  uint32_t lane) {
+                                                  uint32_t run, uint32_t lane) {
   const SmemLayout& SL = P.v.sm;
   const uint32_t item = scheduled_item(P, k);
   const uint32_t brick = P.ids[item];
   if (brick >= P.v.n_bricks) return;  // reported by the reconstruction kernel
   const uint32_t* rec = P.v.records + P.v.starts[brick];
   const uint32_t np = rec[0], S = rec[1], cb = rec[2];
-  const uint32_t ns = S < 32u ? S : 32u;
+  const uint32_t K = runs_k(P.v.flags), nr = run_n(S, K), q = run_q(S, K), hw = head_words(S, K);
+  if (run >= nr) return;
   const uint32_t nw = cb >> 1;
-  const uint32_t x0 = lane < ns ? rec[4 + lane] : (1u << 16);
-  const bool bad_state = __any_sync(0xFFFFFFFFu, lane < ns && x0 < (1u << 16));
+  const uint16_t* words =
+      reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(rec) + 16u + 4u * hw + 4u * np);
   uint8_t* out = ws + (size_t)(item - P.ws_item0) * SL.ws_stride;
-  const uint32_t cofs = 16u + 4u * ns + 4u * np;
-  const uint16_t* words = reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(rec) + cofs);
-  bool ok;
+  // run r: symbols r q .., states at word 4 + 32 r, words from its start to the next run's
+  auto run_words = [&](uint32_t r, uint32_t& w0, uint32_t& w1) -> bool {
+    w0 = r ? rec[4u + hw - (nr - 1u) + (r - 1u)] : 0u;
+    w1 = r + 1u < nr ? rec[4u + hw - (nr - 1u) + r] : nw;
+    return w0 <= w1 && w1 <= nw;
+  };
+  bool ok = true;
   if (P.lod < kPrefixMinLod) {
-    ok = rans_steps(tab, words, nw, S, x0, ns, out, lane);
+    uint32_t w0, w1;
+    const uint32_t len = min(q, S - run * q), ns = min(len, 32u);
+    const uint32_t x0 = lane < ns ? rec[4u + 32u * run + lane] : (1u << 16);
+    ok = run_words(run, w0, w1) && !__any_sync(0xFFFFFFFFu, lane < ns && x0 < (1u << 16));
+    if (ok) ok = rans_steps(tab, words + w0, w1 - w0, len, x0, ns, out + ((run * q) >> 1), lane);
   } else {
-    // a coarse level of detail: the stream up to its level; the symbols decoded go to the
-    // workspace slot's last word for the reconstruction kernel
     const uint32_t T = P.v.L > P.lod ? P.v.L - P.lod : 0u;
-    const uint32_t used = rans_steps_prefix(tab, words, nw, S, x0, ns, out, lane, T, (P.v.flags & kFlagNoStop) != 0,
-                                            (P.v.flags & kFlagShortDelta) != 0, &ok);
-    if (lane == 0) reinterpret_cast<uint32_t*>(ws + (size_t)(item - P.ws_item0 + 1u) * SL.ws_stride)[-1] = used;
+    PrefixWalk W{0u, 0u, 1u, 0u, false, false, S};
+    for (uint32_t r = 0; r < nr && ok && !W.done; ++r) {
+      uint32_t w0, w1;
+      const uint32_t len = min(q, S - r * q), ns = min(len, 32u);
+      const uint32_t x0 = lane < ns ? rec[4u + 32u * r + lane] : (1u << 16);
+      ok = run_words(r, w0, w1) && !__any_sync(0xFFFFFFFFu, lane < ns && x0 < (1u << 16));
+      if (ok)
+        ok = prefix_run(tab, words + w0, w1 - w0, r * q, len, x0, ns, out, lane, T, (P.v.flags & kFlagNoStop) != 0,
+                        (P.v.flags & kFlagShortDelta) != 0, W);
+    }
+    if (lane == 0) reinterpret_cast<uint32_t*>(ws + (size_t)(item - P.ws_item0 + 1u) * SL.ws_stride)[-1] = W.end;
   }
-  if ((!ok || bad_state) && lane == 0) report(P.status, VC_ERR_CORRUPT, item);
+  if (!ok && lane == 0) report(P.status, VC_ERR_CORRUPT, item);
 }
 
+// wpi warps per item (the record's runs side by side; 1 at a coarse level of detail).
 __global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_kernel(const __grid_constant__ Params P,
-                                                                      uint8_t* ws) {
+                                                                      uint8_t* ws, uint32_t wpi) {
   extern __shared__ __align__(128) unsigned char sm[];
   uint32_t* tab = reinterpret_cast<uint32_t*>(sm);
   for (uint32_t i = threadIdx.x; i < kRansM; i += blockDim.x) tab[i] = P.v.rans_tab[i];
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint32_t k = P.item_base + blockIdx.x * (blockDim.x >> 5) + warp;  // bricks per block: its warps
+  const uint32_t g = blockIdx.x * (blockDim.x >> 5) + warp;  // the block's warps take consecutive (item, run)
+  const uint32_t k = P.item_base + g / wpi;
   if (k >= P.n) return;
-  rans_symbols_item(P, tab, ws, k, lane);
+  rans_symbols_item(P, tab, ws, k, g % wpi, lane);
 }
 
 // The same with the item count in device memory (launch_items): persistent warps stride over the
 // items.
 __global__ void __launch_bounds__(32 * kRansWarps) rans_symbols_dev_kernel(const __grid_constant__ Params P,
-                                                                          uint8_t* ws) {
+                                                                          uint8_t* ws, uint32_t wpi) {
   extern __shared__ __align__(128) unsigned char sm[];
   uint32_t* tab = reinterpret_cast<uint32_t*>(sm);
-  const uint32_t n = launch_items(P);
+  const uint32_t n = launch_items(P) * wpi;
   if (blockIdx.x * kRansWarps >= n) return;
   for (uint32_t i = threadIdx.x; i < kRansM; i += 32u * kRansWarps) tab[i] = P.v.rans_tab[i];
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  for (uint32_t k = blockIdx.x * kRansWarps + warp; k < n; k += gridDim.x * kRansWarps)
-    rans_symbols_item(P, tab, ws, k, lane);
+  for (uint32_t g = blockIdx.x * kRansWarps + warp; g < n; g += gridDim.x * kRansWarps)
+    rans_symbols_item(P, tab, ws, g / wpi, g % wpi, lane);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -531,14 +553,19 @@ uint32_t symbol_warps(uint32_t count, uint32_t sms) {
   return best;
 }
 
+// Warps per item of the rANS symbol kernels: one per run of the records (1 at a coarse level of
+// detail, where one warp walks the runs up to the level).
+uint32_t symbol_wpi(const Params& P) { return P.lod < kPrefixMinLod ? runs_k(P.v.flags) : 1u; }
+
 bool launch_symbols(const Params& P, uint8_t* ws, uint32_t base, uint32_t count, uint32_t smem, uint32_t sms,
                     cudaStream_t s) {
   Params PA = P;
   PA.item_base = base;
   PA.n = base + count;
-  void* args[] = {&PA, &ws};
-  const uint32_t w = symbol_warps(count, sms);
-  const uint32_t blocks = (count + w - 1) / w;
+  uint32_t wpi = symbol_wpi(P);
+  void* args[] = {&PA, &ws, &wpi};
+  const uint32_t w = symbol_warps(count * wpi, sms);
+  const uint32_t blocks = (count * wpi + w - 1) / w;
   return cudaLaunchKernel(reinterpret_cast<void*>(&rans_symbols_kernel), dim3(blocks), dim3(32 * w), args, smem, s) ==
          cudaSuccess;
 }
@@ -639,7 +666,7 @@ __global__ void __launch_bounds__(256) coarsest_kernel(const __grid_constant__ P
   }
   const uint32_t* rec = P.v.records + P.v.starts[brick];
   const uint32_t np = rec[0], S = rec[1];
-  const uint32_t ns = P.v.coder == 1 ? (S < 32u ? S : 32u) : 0u;
+  const uint32_t ns = P.v.coder == 1 ? head_words(S, runs_k(P.v.flags)) : 0u;
   if (np == 0u) {
     out[i] = 0u;
     report(P.status, VC_ERR_CORRUPT, i);
@@ -872,8 +899,9 @@ vc_status launch_decode_devcount(Volume& v, const uint32_t* ids, uint32_t cap, c
     P.ws = ws;
     if (!set_smem(reinterpret_cast<void*>(&rans_symbols_dev_kernel), SL.a_smem)) return VC_ERR_CUDA;
     uint8_t* wsp = ws;
-    void* args[] = {&P, &wsp};
-    const uint32_t sblocks = std::min<uint32_t>((cap + kRansWarps - 1) / kRansWarps, sms * 4u);
+    uint32_t wpi = symbol_wpi(P);
+    void* args[] = {&P, &wsp, &wpi};
+    const uint32_t sblocks = std::min<uint32_t>((cap * wpi + kRansWarps - 1) / kRansWarps, sms * 4u);
     if (cudaLaunchKernel(reinterpret_cast<void*>(&rans_symbols_dev_kernel), dim3(sblocks), dim3(32 * kRansWarps), args,
                          SL.a_smem, stream) != cudaSuccess)
       return VC_ERR_CUDA;

@@ -509,7 +509,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   const bool truncated = S_use != 0u && S_use < S_rec;
   const uint32_t S = truncated ? S_use : S_rec;
   const bool short_delta = (P.v.flags & kFlagShortDelta) != 0;
-  const uint32_t ns = RANS ? (S_rec < 32u ? S_rec : 32u) : 0u;
+  const uint32_t ns = RANS ? head_words(S_rec, runs_k(P.v.flags)) : 0u;  // rANS states and run starts
 
   BrickCtx c;
   c.pal = head + 4 + ns;
@@ -1365,7 +1365,7 @@ __device__ __forceinline__ ItemSrc item_src(const Params& P, uint32_t item, uint
   s.rec = P.v.records + a;
   if (RANS) {
     const uint32_t np = s.rec[0], S = s.rec[1];
-    const uint32_t ns = S < 32u ? S : 32u;
+    const uint32_t ns = head_words(S, runs_k(P.v.flags));
     s.head_bytes = (16u + 4u * ns + 4u * np + 15u) & ~15u;
     s.stream = reinterpret_cast<const uint32_t*>(P.ws + (size_t)(item - P.ws_item0) * P.v.sm.ws_stride);
     s.S_use = P.lod >= kPrefixMinLod ? min(s.stream[P.v.sm.ws_stride / 4u - 1u], S) : 0u;  // the slot's last word

@@ -43,9 +43,8 @@ struct Brick {
   std::vector<uint8_t> sym;
   std::vector<uint32_t> pal;
   uint32_t n_delta = 0;
-  std::vector<uint16_t> words;  // rANS
-  uint32_t states[32];
-  uint32_t n_states = 0;
+  std::vector<uint16_t> words;  // rANS: the runs' words one run after the other
+  std::vector<uint32_t> head;   // rANS: the runs' final states, then the starts of runs 1..
   uint32_t coded_bytes = 0;
   uint32_t rec_words = 0;
 };
@@ -230,8 +229,22 @@ void quantize(const uint64_t counts[16], uint32_t f[16]) {
   }
 }
 
-void rans_brick(Brick& br, const uint32_t f[16], const uint32_t cum[17]) {
-  vc::rans_encode(br.sym.data(), (uint32_t)br.sym.size(), f, cum, br.words, br.states, &br.n_states);
+// The record's rANS part: K runs (vc_internal.h), each coded on its own.
+void rans_brick(Brick& br, const uint32_t f[16], const uint32_t cum[17], uint32_t K) {
+  const uint32_t S = (uint32_t)br.sym.size(), q = vc::run_q(S, K), n = vc::run_n(S, K);
+  br.words.clear();
+  br.head.clear();
+  std::vector<uint32_t> starts;
+  std::vector<uint16_t> w;
+  uint32_t st[32], ns = 0;
+  for (uint32_t k = 0; k < n; ++k) {
+    const uint32_t len = std::min(q, S - k * q);
+    if (k) starts.push_back((uint32_t)br.words.size());
+    vc::rans_encode(br.sym.data() + (size_t)k * q, len, f, cum, w, st, &ns);
+    br.head.insert(br.head.end(), st, st + ns);
+    br.words.insert(br.words.end(), w.begin(), w.end());
+  }
+  br.head.insert(br.head.end(), starts.begin(), starts.end());
   br.coded_bytes = 2 * (uint32_t)br.words.size();
 }
 
@@ -285,7 +298,8 @@ vc_status vc_encode_volume_freq(const uint32_t* voxels, const uint32_t dims[3], 
   if (!voxels || !dims || !out_bytes || !out_size) return VC_ERR_ARG;
   *out_bytes = nullptr;
   *out_size = 0;
-  if (log2b < 1 || log2b > 6 || !(op_mask & (1u << kOpAdv)) || (op_mask & ~0x7Fu) || coder > 1 || (flags & ~3u))
+  if (log2b < 1 || log2b > 6 || !(op_mask & (1u << kOpAdv)) || (op_mask & ~0x7Fu) || coder > 1 ||
+      (flags & ~(3u | vc::kFlagRunsMask)) || (coder != 1 && (flags & vc::kFlagRunsMask)))
     return VC_ERR_ARG;
   if (!dims[0] || !dims[1] || !dims[2]) return VC_ERR_ARG;
   const uint32_t b = 1u << log2b;
@@ -332,7 +346,7 @@ vc_status vc_encode_volume_freq(const uint32_t* voxels, const uint32_t dims[3], 
       quantize(counts, freq);
     }
     for (int i = 0; i < 16; ++i) cum[i + 1] = cum[i] + freq[i];
-    parallel_for(n, threads, [&](uint32_t id, uint32_t) { rans_brick(bricks[id], freq, cum); });
+    parallel_for(n, threads, [&](uint32_t id, uint32_t) { rans_brick(bricks[id], freq, cum, vc::runs_k(flags)); });
   }
   uint64_t words = 0;
   uint32_t max_pal = 0, max_sym = 0;
@@ -340,7 +354,7 @@ vc_status vc_encode_volume_freq(const uint32_t* voxels, const uint32_t dims[3], 
   for (uint32_t id = 0; id < n; ++id) {
     Brick& br = bricks[id];
     if (coder == 0) br.coded_bytes = ((uint32_t)br.sym.size() + 1) / 2;
-    const uint64_t bytes = 16 + 4ull * (coder == 1 ? br.n_states : 0) + 4ull * br.pal.size() + br.coded_bytes;
+    const uint64_t bytes = 16 + 4ull * (coder == 1 ? br.head.size() : 0) + 4ull * br.pal.size() + br.coded_bytes;
     br.rec_words = (uint32_t)(((bytes + 15) & ~15ull) / 4);
     starts[id] = (uint32_t)words;
     words += br.rec_words;
@@ -368,7 +382,7 @@ vc_status vc_encode_volume_freq(const uint32_t* voxels, const uint32_t dims[3], 
     put32(r + 12, br.n_delta);
     uint8_t* q = r + 16;
     if (coder == 1)
-      for (uint32_t l = 0; l < br.n_states; ++l, q += 4) put32(q, br.states[l]);
+      for (uint32_t h : br.head) { put32(q, h); q += 4; }
     for (uint32_t v : br.pal) { put32(q, v); q += 4; }
     if (coder == 1) {
       for (size_t w = 0; w < br.words.size(); ++w) { q[2 * w] = (uint8_t)br.words[w]; q[2 * w + 1] = (uint8_t)(br.words[w] >> 8); }

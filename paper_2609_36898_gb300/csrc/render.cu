@@ -55,7 +55,7 @@ struct Inputs {
   const uint8_t* flags;     // per brick: bit 1 = palette holds a label other than 0
   const uint32_t* starts;   // encoding: Brick Starts (words)
   const uint32_t* records;  // encoding: records
-  uint32_t coder;
+  uint32_t coder, vflags;   // the volume's coder and header flags (rANS runs)
   uint32_t* marks;          // visibility bits (one per brick) set by rays of depth <= request_depth, or null
   uint32_t request_depth;
 };
@@ -126,7 +126,7 @@ __device__ __forceinline__ uint32_t cell_at(const RenderDev& R, const Inputs& in
     *s_log = L;
     const uint32_t* rec = in.records + in.starts[id];
     const uint32_t S = rec[1];
-    const uint32_t ns = in.coder == 1 ? (S < 32u ? S : 32u) : 0u;
+    const uint32_t ns = in.coder == 1 ? head_words(S, runs_k(in.vflags)) : 0u;
     return rec[0] ? rec[4 + ns] : 0u;
   }
   const uint32_t k = in.lods[id];
@@ -522,6 +522,7 @@ extern "C" vc_status vc_render(vc_volume* vol, const uint64_t* brick_offsets, co
   in.starts = v->dv.starts;
   in.records = v->dv.records;
   in.coder = v->coder;
+  in.vflags = v->flags;
   in.marks = P.marks;
   in.request_depth = P.request_depth;
   // the parameter block travels with the launch (kernel parameter space): no staging copy, no wait

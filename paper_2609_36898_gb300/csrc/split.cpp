@@ -52,22 +52,14 @@ Tables make_tables(const uint32_t freq[16]) {
 // stream decoded with the volume's table: in each step of 32 symbols every lane decodes one, then
 // the lanes whose state fell below 2^16 read the next 16-bit word in lane order. false if the
 // coded words do not decode exactly.
-bool record_symbols(const uint8_t* r, uint32_t coder, const Tables& t, std::vector<uint8_t>& sym) {
-  const uint32_t n_pal = le32(r), S = le32(r + 4), cb = le32(r + 8);
-  sym.resize(S);
-  if (coder == 0) {
-    const uint8_t* c = r + 16 + 4 * (size_t)n_pal;
-    for (uint32_t i = 0; i < S; ++i) sym[i] = (uint8_t)((c[i >> 1] >> ((i & 1u) * 4u)) & 15u);
-    return true;
-  }
-  const uint32_t ns = std::min<uint32_t>(S, kRansLanes);
+// One run of a rANS record: len symbols into sym from its states and its nw words.
+bool run_symbols(const uint8_t* states, uint32_t len, const uint8_t* w, uint32_t nw, const Tables& t, uint8_t* sym) {
+  const uint32_t ns = std::min<uint32_t>(len, kRansLanes);
   uint32_t x[32];
-  for (uint32_t l = 0; l < 32; ++l) x[l] = l < ns ? le32(r + 16 + 4 * l) : (1u << 16);
-  const uint8_t* w = r + 16 + 4 * (size_t)ns + 4 * (size_t)n_pal;
-  const uint32_t nw = cb / 2;
+  for (uint32_t l = 0; l < 32; ++l) x[l] = l < ns ? le32(states + 4 * l) : (1u << 16);
   uint32_t ptr = 0;
-  for (uint32_t base = 0; base < S; base += 32) {
-    const uint32_t n = std::min<uint32_t>(32, S - base);
+  for (uint32_t base = 0; base < len; base += 32) {
+    const uint32_t n = std::min<uint32_t>(32, len - base);
     for (uint32_t l = 0; l < n; ++l) {
       const uint32_t slot = x[l] & (kRansM - 1u), s = t.slot_sym[slot];
       x[l] = t.f[s] * (x[l] >> 12) + slot - t.cum[s];
@@ -82,6 +74,32 @@ bool record_symbols(const uint8_t* r, uint32_t coder, const Tables& t, std::vect
     }
   }
   return ptr == nw;
+}
+
+// The symbols of one record: plain nibbles (low nibble first), or the rANS runs (vc_internal.h)
+// decoded with the volume's table: in each step of 32 symbols every lane decodes one, then the
+// lanes whose state fell below 2^16 read the next 16-bit word in lane order. false if the coded
+// words do not decode exactly.
+bool record_symbols(const uint8_t* r, uint32_t coder, uint32_t flags, const Tables& t, std::vector<uint8_t>& sym) {
+  const uint32_t n_pal = le32(r), S = le32(r + 4), cb = le32(r + 8);
+  sym.resize(S);
+  if (coder == 0) {
+    const uint8_t* c = r + 16 + 4 * (size_t)n_pal;
+    for (uint32_t i = 0; i < S; ++i) sym[i] = (uint8_t)((c[i >> 1] >> ((i & 1u) * 4u)) & 15u);
+    return true;
+  }
+  const uint32_t K = runs_k(flags), n = run_n(S, K), q = run_q(S, K), hw = head_words(S, K);
+  const uint8_t* w = r + 16 + 4 * (size_t)hw + 4 * (size_t)n_pal;
+  const uint32_t nw = cb / 2;
+  for (uint32_t k = 0; k < n; ++k) {
+    const uint32_t w0 = k ? le32(r + 16 + 4 * ((size_t)hw - (n - 1u) + (k - 1u))) : 0u;
+    const uint32_t w1 = k + 1u < n ? le32(r + 16 + 4 * ((size_t)hw - (n - 1u) + k)) : nw;
+    if (w0 > w1 || w1 > nw) return false;
+    if (!run_symbols(r + 16 + 4 * (size_t)(32u * k), std::min(q, S - k * q), w + 2 * (size_t)w0, w1 - w0, t,
+                     sym.data() + (size_t)k * q))
+      return false;
+  }
+  return true;
 }
 
 // Where the finest level starts. Level 0 is the root; level l + 1 holds the 8 children of every
@@ -156,22 +174,34 @@ vc_status build_coarse(const uint8_t* p, const VolumeScan& sc, std::vector<uint8
     std::vector<uint8_t> sym;
     uint32_t S_c = 0, adv = 0, nd = 0;
     const uint32_t n_pal = le32(r);
-    if (!record_symbols(r, sc.coder, t, sym) || !coarse_prefix(sym.data(), (uint32_t)sym.size(), sc.L, short_delta,
+    if (!record_symbols(r, sc.coder, sc.flags, t, sym) || !coarse_prefix(sym.data(), (uint32_t)sym.size(), sc.L, short_delta,
                                                                &S_c, &adv, &nd) ||
         adv > n_pal || S_c == 0) {
       bad = true;
       return;
     }
-    const uint32_t ns_full = sc.coder == 1 ? std::min<uint32_t>(le32(r + 4), kRansLanes) : 0u;
+    const uint32_t K = runs_k(sc.flags);
+    const uint32_t ns_full = sc.coder == 1 ? head_words(le32(r + 4), K) : 0u;
     const uint8_t* pal = r + 16 + 4 * (size_t)ns_full;
-    std::vector<uint16_t> words;
-    uint32_t states[32], n_states = 0, cb = 0;
+    // the coarse symbols re-coded with the volume's table, in runs as the volume's records are
+    std::vector<uint16_t> words, w;
+    std::vector<uint32_t> head, starts;
+    uint32_t cb = 0;
     if (sc.coder == 1) {
-      rans_encode(sym.data(), S_c, t.f, t.cum, words, states, &n_states);
+      const uint32_t nr = run_n(S_c, K), q = run_q(S_c, K);
+      uint32_t st[32], ns = 0;
+      for (uint32_t k = 0; k < nr; ++k) {
+        if (k) starts.push_back((uint32_t)words.size());
+        rans_encode(sym.data() + (size_t)k * q, std::min(q, S_c - k * q), t.f, t.cum, w, st, &ns);
+        head.insert(head.end(), st, st + ns);
+        words.insert(words.end(), w.begin(), w.end());
+      }
+      head.insert(head.end(), starts.begin(), starts.end());
       cb = 2u * (uint32_t)words.size();
     } else {
       cb = (S_c + 1u) / 2u;
     }
+    const uint32_t n_states = (uint32_t)head.size();
     const size_t bytes = 16 + 4 * (size_t)n_states + 4 * (size_t)adv + cb;
     std::vector<uint8_t>& o = recs[id].bytes;
     o.assign((bytes + 15) & ~(size_t)15, 0);
@@ -180,7 +210,7 @@ vc_status build_coarse(const uint8_t* p, const VolumeScan& sc, std::vector<uint8
     put32(o.data() + 8, cb);
     put32(o.data() + 12, nd);
     uint8_t* q = o.data() + 16;
-    for (uint32_t l = 0; l < n_states; ++l, q += 4) put32(q, states[l]);
+    for (uint32_t l = 0; l < n_states; ++l, q += 4) put32(q, head[l]);
     std::memcpy(q, pal, 4 * (size_t)adv);  // the palette prefix the coarse levels advance through
     q += 4 * (size_t)adv;
     if (sc.coder == 1) {
@@ -235,7 +265,7 @@ vc_status vc_split_counts(const void* host_bytes, size_t nbytes, uint32_t brick_
   const uint8_t* r = p + sc.rec_off + 4 * (size_t)le32(p + kHeaderBytes + 4 * (size_t)brick_id);
   std::vector<uint8_t> sym;
   uint32_t S_c = 0, adv = 0, nd = 0;
-  if (!record_symbols(r, sc.coder, make_tables(sc.freq), sym) ||
+  if (!record_symbols(r, sc.coder, sc.flags, make_tables(sc.freq), sym) ||
       !coarse_prefix(sym.data(), (uint32_t)sym.size(), sc.L, (sc.flags & kFlagShortDelta) != 0, &S_c, &adv, &nd))
     return VC_ERR_CORRUPT;
   out[0] = (uint32_t)sym.size();

@@ -118,7 +118,9 @@ vc_status scan_volume(const uint8_t* p, size_t nbytes, VolumeScan* out) {
   const uint32_t records_words = le32(p + 112);
   if (L < 1 || L > 6) return VC_ERR_FORMAT;
   if (!(op_mask & (1u << 4)) || (op_mask & ~0x7Fu)) return VC_ERR_FORMAT;
-  if (coder > 1 || (flags & ~(kFlagNoStop | kFlagShortDelta))) return VC_ERR_FORMAT;
+  if (coder > 1 || (flags & ~(kFlagNoStop | kFlagShortDelta | kFlagRunsMask))) return VC_ERR_FORMAT;
+  if (coder != 1 && (flags & kFlagRunsMask)) return VC_ERR_FORMAT;
+  const uint32_t K = runs_k(flags);
   const uint32_t b = 1u << L;
   uint32_t nb[3];
   uint64_t nbt = 1;
@@ -149,11 +151,20 @@ vc_status scan_volume(const uint8_t* p, size_t nbytes, VolumeScan* out) {
     const uint8_t* r = rec + 4 * (size_t)a;
     const uint32_t n_pal = le32(r), S = le32(r + 4), cb = le32(r + 8), nd = le32(r + 12);
     if (S == 0) return VC_ERR_FORMAT;
-    const uint64_t ns = coder == 1 ? std::min<uint32_t>(S, kRansLanes) : 0;
+    const uint64_t ns = coder == 1 ? head_words(S, K) : 0;  // rANS states and run starts
     const uint64_t need = 16 + 4 * ns + 4 * (uint64_t)n_pal + cb;
     if (((need + 15) & ~(uint64_t)15) != 4 * (uint64_t)(e - a)) return VC_ERR_FORMAT;
     if (coder == 0 && cb != (S + 1) / 2) return VC_ERR_FORMAT;
     if (coder == 1 && (cb & 1u)) return VC_ERR_FORMAT;
+    if (coder == 1 && K > 1) {  // run starts: not decreasing, within the coded words
+      const uint32_t nr = run_n(S, K);
+      uint32_t prev_start = 0;
+      for (uint32_t k = 1; k < nr; ++k) {
+        const uint32_t w0 = le32(r + 16 + 4 * ((size_t)ns - (nr - 1u) + (k - 1u)));
+        if (w0 < prev_start || w0 > cb / 2) return VC_ERR_FORMAT;
+        prev_start = w0;
+      }
+    }
     if (nd > S) return VC_ERR_FORMAT;
     max_pal = std::max(max_pal, n_pal);
     max_sym = std::max(max_sym, S);

@@ -20,6 +20,32 @@ constexpr uint32_t kMaxIdx8 = 0xFCu;      // palette indices below this fit 8-bi
 constexpr uint32_t kMaxIdx16 = 0xFFF0u;   // same for 16-bit grids
 constexpr uint32_t kFlagNoStop = 1u;
 constexpr uint32_t kFlagShortDelta = 2u;  // a delta operation carries one 4-bit entry: delta - 1
+// rANS runs (flags bits 2..3 = log2 K; rANS volumes only): a record's S symbols are cut into runs
+// of Q = 32 ceil(S / 32K) symbols (the last may be shorter; small records have fewer runs), each
+// coded on its own with 32 interleaved states, so that K warps can decode one brick side by side.
+// Between the record's header and its palette: every run's final states (32 for every run but
+// the last, min(last, 32) for it), then the first coded word of runs 1 .. n-1 (u32 each).
+constexpr uint32_t kFlagRunsShift = 2u;
+constexpr uint32_t kFlagRunsMask = 3u << kFlagRunsShift;
+__host__ __device__ inline uint32_t runs_k(uint32_t flags) { return 1u << ((flags & kFlagRunsMask) >> kFlagRunsShift); }
+// (K is a power of two: shifts, no division)
+__host__ __device__ inline uint32_t run_q(uint32_t S, uint32_t K) {
+  const uint32_t lk = K >= 8u ? 3u : K >= 4u ? 2u : K >= 2u ? 1u : 0u;
+  const uint32_t per = (S + (32u << lk) - 1u) >> (5u + lk);
+  return 32u * (per ? per : 1u);
+}
+__host__ __device__ inline uint32_t run_n(uint32_t S, uint32_t K) {
+  const uint32_t q = run_q(S, K);
+  uint32_t n = 1;
+  for (uint32_t k = 1; k < K; ++k) n += S > k * q ? 1u : 0u;
+  return n;
+}
+// Words between a rANS record's header and its palette (states, then run starts).
+__host__ __device__ inline uint32_t head_words(uint32_t S, uint32_t K) {
+  if (K == 1u) return S < 32u ? S : 32u;
+  const uint32_t n = run_n(S, K), last = S - (n - 1u) * run_q(S, K);
+  return 33u * (n - 1u) + (last < 32u ? last : 32u);
+}
 constexpr uint32_t kHandleVolume = 0x564F4C31u;  // "VOL1"
 constexpr uint32_t kHandleServer = 0x53525631u;  // "SRV1"
 constexpr uint32_t kHandleCache = 0x43484331u;   // "CHC1"

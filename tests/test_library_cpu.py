@@ -68,6 +68,18 @@ def test_encoder_matches_oracle_bytes(lib, log2b, coder):
             assert a.size == b.size and np.array_equal(a, b), (mask, flags)
 
 
+@pytest.mark.parametrize("log2b,K", [(3, 2), (4, 4), (5, 2), (5, 8), (6, 4)])
+def test_encoder_matches_oracle_bytes_with_rans_runs(lib, log2b, K):
+    V = synth.fill(synth.small(dims=(3 * (1 << log2b) - 3, 40, 21), seed=6, diameter=9.0, bg=0.25))
+    for flags in (0, 1, 2):
+        f = flags | oracle.runs_flag(K)
+        a = oracle.encode_volume(V, log2b, coder=1, flags=f)
+        b = vc.vc_encode_volume(V, log2b, coder=1, flags=f, threads=3)
+        assert a.size == b.size and np.array_equal(a, b), (K, flags)
+    with pytest.raises(vc.VCError):  # runs are a rANS option
+        vc.vc_encode_volume(V, log2b, coder=0, flags=oracle.runs_flag(K))
+
+
 def test_encoder_matches_oracle_on_workload_sample(lib):
     spec = synth.c1()
     V = synth.fill(spec)

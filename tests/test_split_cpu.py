@@ -30,6 +30,16 @@ def test_split_counts_match_the_oracle(coder, flags):
             assert vc.vc_split_counts(enc, bid) == _expected(enc, bid, log2b, bool(flags & 2)), (log2b, bid)
 
 
+@pytest.mark.parametrize("K", [2, 4, 8])
+def test_split_counts_with_rans_runs(K):
+    V = synth.fill(synth.small(dims=(72, 40, 36), seed=18, diameter=11.0, bg=0.2))
+    for log2b in (3, 4, 5, 6):
+        enc = vc.vc_encode_volume(V, log2b, op_mask=0x7F, coder=1, flags=oracle.runs_flag(K))
+        n = oracle.header(enc)["n_bricks"]
+        for bid in range(0, n, max(1, n // 24)):
+            assert vc.vc_split_counts(enc, bid) == _expected(enc, bid, log2b, False), (log2b, bid)
+
+
 def test_split_counts_uniform_and_corrupt():
     V = np.full((16, 16, 16), 5, dtype=np.uint32)
     enc = vc.vc_encode_volume(V, 4, coder=1)
