@@ -88,7 +88,7 @@ def full_table(freq) -> np.ndarray:
     return f.astype(np.uint32)
 
 
-def generate_encode(spec, log2b: int, coder: int = CODER_RANS, max_slab_voxels: int = 1 << 28):
+def generate_encode(spec, log2b: int, coder: int = CODER_RANS, max_slab_voxels: int = 1 << 28, flags: int = 0):
     """VCZ1 bytes of a synthetic volume: generated on the GPU (synth_fill_gpu, the CPU generator's
     voxels) in z slabs of whole bricks, each slab copied to pinned host memory and encoded on the
     host cores by the library's encoder while the next slab is generated; all slabs share the rANS
@@ -123,13 +123,13 @@ def generate_encode(spec, log2b: int, coder: int = CODER_RANS, max_slab_voxels: 
             pending = start(k + 1)  # the GPU generates the next slab while this one is encoded
         V = host[k % len(host)][:t].numpy().view(np.uint32)
         if len(z0s) == 1:
-            parts.append(vc.vc_encode_volume(V, log2b, op_mask=0x7F, coder=coder))
+            parts.append(vc.vc_encode_volume(V, log2b, op_mask=0x7F, coder=coder, flags=flags))
             break
         if table is None and coder == CODER_RANS:
-            first = vc.vc_encode_volume(V, log2b, op_mask=0x7F, coder=coder)
+            first = vc.vc_encode_volume(V, log2b, op_mask=0x7F, coder=coder, flags=flags)
             h = np.frombuffer(first[:128].tobytes(), dtype="<u4")
             table = full_table(h[12:28])
-        parts.append(vc.vc_encode_volume(V, log2b, op_mask=0x7F, coder=coder, freq=table))
+        parts.append(vc.vc_encode_volume(V, log2b, op_mask=0x7F, coder=coder, flags=flags, freq=table))
     torch.cuda.synchronize()
     enc = parts[0] if len(parts) == 1 else vc.vc_concat_volumes_z(parts)
     return enc, time.time() - t0
@@ -515,7 +515,8 @@ def mixed_serving_leg(args, local: int):
     enc_bytes = 0
     for sp in synth.c5():
         b = sp.brick
-        enc, t = generate_encode(sp, b.bit_length() - 1)
+        # 64^3 bricks: 4 rANS runs per record, so that 4 warps share each brick's symbol chain
+        enc, t = generate_encode(sp, b.bit_length() - 1, flags=vc.VC_FLAG_RUNS(4) if b == 64 else 0)
         prep += t
         enc_bytes += int(enc.size)
         vols.append(vc.vc_load_compressed(enc, local, stream.cuda_stream))
@@ -618,7 +619,8 @@ def mixed_serving_leg(args, local: int):
     pct = lambda a, q: float(np.percentile(np.asarray(a), q)) if len(a) else None  # noqa: E731
     return {
         "workload": "8 volumes of the mixed recipe at their stated sizes (" + ", ".join(names) + f"; {enc_bytes / 2**30:.2f} "
-                    f"GiB encoded, resident), rANS; {nreq} Poisson requests of 1..4096 bricks (at most half the cache) "
+                    f"GiB encoded, resident), rANS (64^3 bricks in 4 runs per record); {nreq} Poisson requests of "
+                    "1..4096 bricks (at most half the cache) "
                     "at 50 / 80 / 95 % of the measured capacity; 4 GiB cache; CUDA-graph batches",
         "capacity": {"requests_per_s": cap_rate, "gvoxel_s": sum(vox_of) / cap_s / 1e9},
         "served": served,

@@ -32,7 +32,8 @@
  *     u32 dims[3] (voxels x, y, z)      u32 log2b (L, 1..6; brick edge b = 2^L)
  *     u32 op_mask (bit o = operation o enabled; bit 4, palette advance, always set)
  *     u32 coder (0 = plain 4-bit, 1 = rANS)   u32 flags (bit 0 = no stop bits were written;
- *                                                        bit 1 = limited delta, see DELTA)
+ *                                                        bit 1 = limited delta, see DELTA;
+ *                                                        bits 2..3 = log2 K, rANS runs, see rANS)
  *     u32 n_bricks = prod ceil(dims[a] / b)   u32 max_pal   u32 max_sym  (maxima over bricks)
  *     u32 freq[16] (rANS symbol frequencies, sum 4096; zero for plain)
  *     u32 records_words (size of the record area in 32-bit words), 12 reserved bytes
@@ -45,7 +46,7 @@
  *
  *   record of one brick (16-byte aligned, zero padded to 16 bytes):
  *     u32 n_pal, u32 n_sym (S), u32 coded_bytes, u32 n_delta (number of delta operations)
- *     [rANS only: u32 state[min(S, 32)]]
+ *     [rANS only: u32 state[...] of every run, then u32 run_start[runs - 1] (see rANS)]
  *     u32 palette[n_pal]
  *     u8  coded[coded_bytes]: plain = symbol i in byte i/2, low nibble first;
  *                             rANS  = 16-bit words, see below
@@ -77,6 +78,15 @@
  *   slot = x & 4095, s with cum[s] <= slot < cum[s+1], x = freq[s] * (x >> 12) + slot - cum[s];
  *   then, in lane order, every such lane with x < 2^16 shifts in the next 16-bit word. A valid
  *   record reads all words and leaves every used state at 2^16.
+ *   Runs (flags bits 2..3 = log2 K, K = 1, 2, 4 or 8; not in the paper, which leaves its coder's
+ *   layout to the encoder): the S symbols are cut into runs of Q = 32 ceil(S / 32K) symbols (the
+ *   last may be shorter; small records have fewer than K runs), each coded on its own as above
+ *   with its own states, so that K warps decode one brick side by side. The record holds the
+ *   runs' final states one run after the other (min(run length, 32) each), then the first coded
+ *   word of every run but the first; the coded words are the runs' words one run after the other.
+ *   Each run must read exactly its words. K = 1 is the record described above. For 64^3 bricks
+ *   the symbol chain is ~2,250 rANS steps per brick, and 4 runs cut it to a quarter (about 2 %
+ *   more bytes).
  * ------------------------------------------------------------------------------------------
  */
 #ifndef VC_H_
@@ -101,6 +111,11 @@ typedef int32_t vc_status;
 #define VC_ERR_UNSUPPORTED (-8) /* valid volume outside this build's limits */
 
 #define VC_STATUS_WORDS 4
+
+/* Encoding flags (header word 8) */
+#define VC_FLAG_NO_STOP 1u
+#define VC_FLAG_SHORT_DELTA 2u
+#define VC_FLAG_RUNS(k) ((k) >= 8 ? 12u : (k) >= 4 ? 8u : (k) >= 2 ? 4u : 0u) /* k rANS runs per record */
 
 /* decode schedules */
 #define VC_MODE_PLAIN 0   /* one kernel launch per brick (the baseline the paper's frame loop replaces) */
@@ -631,7 +646,9 @@ vc_status vc_release(void* handle);
 
 /* Encodes a volume (host, dims[0] * dims[1] * dims[2] uint32 labels, x fastest) into VCZ1 bytes.
  * log2b in 1..6; op_mask as in the format (bit 4 required); coder 0 (plain) or 1 (rANS); flags bit 0
- * = write no stop bits, bit 1 = limited delta (one entry per delta operation, 2 <= delta <= 16). Uses `threads` worker threads (0 = all cores). The operation of each node
+ * = write no stop bits, bit 1 = limited delta (one entry per delta operation, 2 <= delta <= 16),
+ * bits 2..3 = log2 of the rANS runs per record (VC_FLAG_RUNS(k); rANS only). Uses `threads` worker
+ * threads (0 = all cores). The operation of each node
  * is the first applicable enabled one in the order parent, x, y, z neighbour, last, delta
  * (smallest), advance; coarse nodes hold the mode of their 2^3 children (ties to the smallest
  * label). *out_bytes is allocated by the library; free it with vc_free_bytes. */

@@ -26,6 +26,12 @@ VC_ERR_UNSUPPORTED = -8
 VC_STATUS_WORDS = 4
 VC_MODE_PLAIN, VC_MODE_GRID, VC_MODE_BATCHED, VC_MODE_PIPELINED = 0, 1, 2, 3
 VC_MODE_PALETTED = 0x100
+VC_FLAG_NO_STOP, VC_FLAG_SHORT_DELTA = 1, 2
+
+
+def VC_FLAG_RUNS(k: int) -> int:
+    """Encoding flag bits of k (1, 2, 4, 8) independently coded rANS runs per record."""
+    return {1: 0, 2: 4, 4: 8, 8: 12}[k]
 MODES = {"plain": VC_MODE_PLAIN, "grid": VC_MODE_GRID, "batched": VC_MODE_BATCHED, "pipelined": VC_MODE_PIPELINED}
 
 
