@@ -31,10 +31,20 @@ B_LOG2 = 5
 CODER_RANS = 1
 METRIC = "decoded Gvoxel/s"
 UNIT = "Gvoxel/s"
-def kernel_name(mode: str, threads: int) -> str:
-    return f"decode_{mode}_kernel<L=5,u8 grid,rANS,{threads} threads>"
+def kernel_name(mode: str, threads: int, log2b: int = B_LOG2) -> str:
+    if log2b >= 6:  # 64^3 bricks: one persistent kernel serves every schedule
+        return f"decode_scratch_kernel<L={log2b},u8 grid,rANS,{threads} threads>"
+    return f"decode_{mode}_kernel<L={log2b},u8 grid,rANS,{threads} threads>"
 
-WORKLOAD = "512^3 uint32 Voronoi volume (~20k cells, 10% background), 32^3 bricks (4096), rANS, all operations"
+
+def workload_name(log2b: int = B_LOG2, runs: int = 1) -> str:
+    b = 1 << log2b
+    n = (512 // b) ** 3
+    return (f"512^3 uint32 Voronoi volume (~20k cells, 10% background), {b}^3 bricks ({n}), rANS"
+            + (f" in {runs} runs per record" if runs > 1 else "") + ", all operations")
+
+
+WORKLOAD = workload_name()
 
 
 def dist_env():
@@ -58,22 +68,24 @@ def job_rate(world: int, units_per_rank_step: int, steps: int, slowest_s: float)
     return world * units_per_rank_step * steps / slowest_s / 1e9
 
 
-def make_workload(encoder: str = "library"):
-    """The 512^3 volume and its encoding: by the library's encoder, or (reference arm) by the
-    oracle's, whose bytes are identical."""
+def make_workload(encoder: str = "library", log2b: int = B_LOG2, runs: int = 1):
+    """The 512^3 volume and its encoding (32^3 bricks unless log2b says otherwise; `runs` rANS
+    runs per record): by the library's encoder, or (reference arm) by the oracle's, whose bytes are
+    identical."""
     import synth
     spec = synth.c2()
     t = time.time()
     V = synth.fill(spec)
     t_gen = time.time() - t
     t = time.time()
+    flags = {1: 0, 2: 4, 4: 8, 8: 12}[runs]  # header flag bits 2..3: log2 of the runs
     if encoder == "oracle":
         import oracle
         oracle.build()
-        enc = oracle.encode_volume(V, B_LOG2, op_mask=0x7F, coder=CODER_RANS)
+        enc = oracle.encode_volume(V, log2b, op_mask=0x7F, coder=CODER_RANS, flags=flags)
     else:
         import paper_2609_36898_gb300 as vc
-        enc = vc.vc_encode_volume(V, B_LOG2, op_mask=0x7F, coder=CODER_RANS)
+        enc = vc.vc_encode_volume(V, log2b, op_mask=0x7F, coder=CODER_RANS, flags=flags)
     t_enc = time.time() - t
     return spec, V, enc, t_gen, t_enc
 
@@ -214,13 +226,14 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel_src_hash: str, mode: str, threads: int):
+def ncu_traffic(kernel_src_hash: str, mode: str, threads: int, log2b: int = B_LOG2, runs: int = 1):
     """DRAM bytes per launch from the committed ncu summary of this schedule's kernel, if taken on
-    the current kernel source."""
-    p = os.path.join(ROOT, "profiles", f"decode_{mode}_512cube_b32_rans.json")
+    the current kernel source and the same workload."""
+    tag = f"b{1 << log2b}" + (f"_runs{runs}" if runs > 1 else "")
+    p = os.path.join(ROOT, "profiles", f"decode_{mode if log2b < 6 else 'scratch'}_512cube_{tag}_rans.json")
     try:
         d = json.load(open(p))
-        if d.get("kernel_source_sha256") == kernel_src_hash and d.get("kernel") == kernel_name(mode, threads):
+        if d.get("kernel_source_sha256") == kernel_src_hash and d.get("kernel") == kernel_name(mode, threads, log2b):
             return d.get("dram_bytes_per_launch_full_workload")
     except Exception:
         pass
@@ -254,13 +267,15 @@ def oracle_rate(enc: np.ndarray, seconds: float, max_bricks: int, first: int = 0
     """Single-threaded oracle decode on a bounded sample of the workload's bricks (at least one
     brick, then until `seconds` have passed or `max_bricks` were decoded), cycling over the volume."""
     import oracle
+    h = oracle.header(enc)
+    n_bricks, log2b = h["n_bricks"], h["log2b"]
     n_b = 0
     t0 = time.perf_counter()
     while n_b < 1 or (n_b < max_bricks and time.perf_counter() - t0 < seconds):
-        oracle.decode_brick(enc, (first + n_b) % 4096, 0)
+        oracle.decode_brick(enc, (first + n_b) % n_bricks, 0)
         n_b += 1
     dt = time.perf_counter() - t0
-    vox = n_b * (1 << (3 * B_LOG2))
+    vox = n_b * (1 << (3 * log2b))
     return vox / dt / 1e9, n_b, dt
 
 
@@ -268,7 +283,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    spec, V, enc, _, _ = make_workload(encoder="oracle")
+    spec, V, enc, _, _ = make_workload(encoder="oracle", log2b=args.log2b, runs=args.runs)
     import oracle
     total_vox, total_t, nb = 0, 0.0, 0
     for _ in range(args.warmup):
@@ -276,14 +291,15 @@ def run_reference(args):
     per_step = 20.0 / max(1, args.steps)  # the whole timed run takes about 20 s of one core
     for k in range(args.steps):
         r, n_b, dt = oracle_rate(enc, per_step, 4096, first=nb)
-        total_vox += n_b * 32 ** 3
+        total_vox += n_b * (1 << (3 * args.log2b))
         total_t += dt
         nb += n_b
     value = total_vox / total_t / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total_t / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "bricks_per_step": 4096, "sample": "bounded"},
+            "config": {"workload": workload_name(args.log2b, args.runs),
+                       "bricks_per_step": (512 >> args.log2b) ** 3, "sample": "bounded"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{nb} brick decodes of the 512^3 volume in {total_t:.1f} s, single thread",
                              **host_cpu()},
@@ -782,7 +798,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    spec, V, enc, t_gen, t_enc = make_workload()
+    spec, V, enc, t_gen, t_enc = make_workload(log2b=args.log2b, runs=args.runs)
     vol = vc.Volume(enc, device=local)
     n = vol.n_bricks
     e = vol.b
@@ -856,7 +872,7 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
     achieved = algo / recon_s / 1e9
     step_achieved = algo / (dev_s / args.steps) / 1e9
-    traffic = ncu_traffic(kernel_hash(), mode_name, sched[0])
+    traffic = ncu_traffic(kernel_hash(), mode_name, sched[0], args.log2b, args.runs)
 
     # other schedules on the same data (context): plain = one launch per brick, grid = one launch
     # (the one-launch-per-brick schedule runs on the first 512 bricks only, to bound launch counts)
@@ -972,13 +988,14 @@ def run_ours(args):
             oracle.build()
             r, nb, dt = oracle_rate(enc, 15.0, 10 ** 9)
             cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{nb} brick decodes (bricks 0, 1, ... cycling over all 4096) of the same 512^3 volume, "
+                   "sample": f"{nb} brick decodes (bricks 0, 1, ... cycling over all {n}) of the same 512^3 volume, "
                              f"single-threaded, {dt:.1f} s", **host_cpu()}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * dev_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "bricks_per_step": n, "voxels_per_step": vox_per_step,
+            "config": {"workload": workload_name(args.log2b, args.runs), "bricks_per_step": n,
+                       "voxels_per_step": vox_per_step,
                        "schedule": mode_name, "autotuned": args.mode == "auto",
                        "threads_per_brick": sched[0], "stage_depth": sched[1], "blocks_per_sm": sched[2],
                        "encoded_bytes": int(enc.size),
@@ -986,7 +1003,8 @@ def run_ours(args):
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_launch": algo, "kernel": kernel_name(mode_name, sched[0]),
+                         "algorithmic_bytes_per_launch": algo,
+                         "kernel": kernel_name(mode_name, sched[0], args.log2b),
                          "kernel_ms": 1000.0 * recon_s, "symbol_kernel_ms": 1000.0 * symbol_s,
                          "step_achieved": step_achieved, "step_frac": step_achieved / peak},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
@@ -1019,6 +1037,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="auto", choices=["auto", "grid", "batched"])
+    ap.add_argument("--log2b", type=int, default=B_LOG2, choices=[4, 5, 6],
+                    help="brick size of the main decode leg (5: 32^3 bricks, the benchmark)")
+    ap.add_argument("--runs", type=int, default=1, choices=[1, 2, 4, 8], help="rANS runs per record")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-split", action="store_true", help="skip the detail-split leg")
     ap.add_argument("--no-ablation", action="store_true", help="skip the operation-prefix compression sweep")

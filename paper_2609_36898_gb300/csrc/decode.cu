@@ -403,25 +403,29 @@ bool schedule_supported(uint32_t L, uint32_t threads) {
   return (threads == 512 || threads == 1024) && L >= 4;
 }
 
-vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, SmemLayout* out) {
+vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, SmemLayout* out,
+                         bool paletted) {
   const uint32_t L = v.L;
   if (!schedule_supported(L, threads) || nstage < 1 || nstage > 2) return VC_ERR_UNSUPPORTED;
   int optin = 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
     return VC_ERR_CUDA;
-  // b = 64 bricks: the large regions (node operations, delta values, cursor masks, the finest
-  // index grid) live in a global scratch slice per block, the rest in shared memory when it fits
-  // (attempt 0), else everything in the slice (attempt 1); see SmemLayout::gscratch
+  // b = 64 bricks: with label output the finest level needs only the open cells' children, so
+  // every region may fit one block's shared memory (attempt -1; no scratch slice); otherwise
+  // (and for packed palette indices, whose finest level is a 64^3 index grid) the large regions
+  // (node operations, delta values, cursor masks, the finest grid) live in a global scratch slice
+  // per block, the rest in shared memory when it fits (attempt 0), else everything in the slice
+  // (attempt 1); see SmemLayout::gscratch
   const bool global = L >= 6;
   SmemLayout s{};
   uint32_t o = 0, og = 0;  // shared / global scratch bytes placed
-  for (int attempt = 0; attempt < (global ? 2 : 1); ++attempt) {
+  for (int attempt = global && !paletted ? -1 : 0; attempt < (global ? 2 : 1); ++attempt) {
     s = SmemLayout{};
     o = 0;
     og = 0;
-    const bool all_global = attempt == 1;
+    const bool all_shared = attempt < 0, all_global = attempt == 1;
     auto put = [&](bool large, uint32_t bytes) -> uint32_t {  // offset of a region of `bytes`
-      uint32_t& c = global && (large || all_global) ? og : o;
+      uint32_t& c = global && !all_shared && (large || all_global) ? og : o;
       const uint32_t at = c;
       c += bytes;
       return at;
@@ -463,7 +467,7 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
     // label output keeps 8 children per open level-(L-1) cell instead
     const uint32_t cap_open = (L - 1u) & 1u ? s.list1_cap : s.list0_cap;  // open level-(L-1) cells
     const uint32_t cb_bytes = L >= 2 ? s.gt_bytes * 8u * cap_open : 0u;
-    s.fg_bytes = align16(std::max(s.gt_bytes * b * b * b / nh, cb_bytes));
+    s.fg_bytes = align16(all_shared ? cb_bytes : std::max(s.gt_bytes * b * b * b / nh, cb_bytes));
     s.fg_off = put(true, s.fg_bytes);
     s.plane_off = put(false, nh == 2 ? align16(s.gt_bytes * b * b) : 0u);
     // private palette copy (frees the stage early); byte grids: a power of two >= max_pal, zero
@@ -484,6 +488,7 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
     s.mq_off = dead_span >= mq_bytes ? s.nodes_off : put(global, align16(mq_bytes));
     if (!global || o + 64u <= (uint32_t)optin) break;  // (+ the kernel's static shared words)
   }
+  if (global && o + 64u > (uint32_t)optin) return VC_ERR_UNSUPPORTED;
   const uint32_t span_bytes = s.fg_off - s.mask_off;  // masks .. rank lists (b <= 32)
   if (global) {  // nothing staged: the record and symbols are read where they are
     s.stage_alias = 0;
@@ -696,7 +701,8 @@ vc_status launch_coarsest(Volume& v, const uint32_t* ids, uint32_t n, uint32_t* 
 size_t decode_ws_bytes(const Volume& v, uint32_t n) {
   const SmemLayout& SL = v.dv.sm;
   const size_t sym = v.coder == 1 ? ((size_t)n * SL.ws_stride + 255u) & ~size_t(255) : 0u;
-  return sym + (SL.gscratch ? (size_t)scratch_grid(v, n) * SL.gscratch : 0u);
+  const size_t slice = std::max(SL.gscratch, v.sm_pal.gscratch);  // labels or packed indices
+  return sym + (slice ? (size_t)scratch_grid(v, n) * slice : 0u);
 }
 
 vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
@@ -738,8 +744,9 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
     palette_packing(v.max_pal, &P.pal_bits, &P.pal_per);
     P.out_words = (edge * edge * edge + P.pal_per - 1u) / P.pal_per;
   }
-  const SmemLayout& SL = v.dv.sm;
-  const bool scratch = SL.gscratch != 0;
+  if (P.pal_bits) P.v.sm = v.sm_pal;  // b = 64: packed indices need the voxel index grid
+  const SmemLayout& SL = P.v.sm;
+  const bool scratch = v.L >= 6;     // b = 64: the persistent kernel with its regions in SL
   if (mode == VC_MODE_PIPELINED && ws_ext) return VC_ERR_ARG;  // it allocates its own workspaces
   // coarse levels of detail are written by the reconstruction kernel itself
   if (mode == VC_MODE_PIPELINED && lod == 0 && !scratch) return launch_pipelined(v, P, n, stream);
@@ -760,9 +767,11 @@ vc_status launch_decode_ws(Volume& v, const uint32_t* ids, uint32_t n, const uin
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)nt, smem) != cudaSuccess) return VC_ERR_CUDA;
     if (per_sm < 1) return VC_ERR_UNSUPPORTED;
     sgrid = std::min(scratch_grid(v, n), std::max(1u, v.sms) * (uint32_t)per_sm);
-    if (ws_ext) {
+    if (ws_ext && SL.gscratch) {
       if (ws_cap < sym_bytes + SL.gscratch) return VC_ERR_ARG;
       sgrid = (uint32_t)std::min<size_t>(sgrid, (ws_cap - sym_bytes) / SL.gscratch);
+    } else if (ws_ext && rans && sym_bytes > ws_cap) {
+      return VC_ERR_ARG;
     }
   } else if (rans && ws_ext && (size_t)n * SL.ws_stride > ws_cap) {
     return VC_ERR_ARG;
@@ -864,7 +873,7 @@ vc_status launch_decode_devcount(Volume& v, const uint32_t* ids, uint32_t cap, c
   if (v.split && lod == 0) return VC_ERR_UNSUPPORTED;  // bulk copies cannot read the mapped host copy
   const bool rans = v.coder == 1;
   const SmemLayout& SL = v.dv.sm;
-  const bool scratch = SL.gscratch != 0;
+  const bool scratch = v.L >= 6;
   Params P{};
   P.v = v.dv;
   P.ids = ids;
@@ -888,8 +897,8 @@ vc_status launch_decode_devcount(Volume& v, const uint32_t* ids, uint32_t cap, c
   const uint32_t sms = std::max(1u, v.sms);
   const size_t sym_bytes = rans ? ((size_t)cap * SL.ws_stride + 255u) & ~size_t(255) : 0u;
   uint32_t grid = std::min<uint32_t>(cap, sms * (uint32_t)per_sm);
-  if (scratch) {
-    grid = std::min(grid, scratch_grid(v, cap));
+  if (scratch) grid = std::min(grid, scratch_grid(v, cap));
+  if (scratch && SL.gscratch) {
     if (ws_cap < sym_bytes + SL.gscratch) return VC_ERR_ARG;
     grid = (uint32_t)std::min<size_t>(grid, (ws_cap - sym_bytes) / SL.gscratch);
   } else if (ws_cap < sym_bytes) {

@@ -1531,7 +1531,8 @@ __global__ void __launch_bounds__(NT) decode_scratch_kernel(const __grid_constan
   extern __shared__ __align__(128) unsigned char dyn_sm[];
   __shared__ int s_err;
   __shared__ uint32_t s_item;
-  unsigned char* gm = scratch + (size_t)blockIdx.x * P.v.sm.gscratch;
+  // the large regions: the block's scratch slice, or shared memory when the layout has no slice
+  unsigned char* gm = P.v.sm.gscratch ? scratch + (size_t)blockIdx.x * P.v.sm.gscratch : dyn_sm;
   unsigned char* sm = P.v.sm.total ? dyn_sm : gm;
   uint32_t* counter = reinterpret_cast<uint32_t*>(P.status) + 2;
   const uint32_t n = launch_items(P);

@@ -326,13 +326,15 @@ vc_status vc_load_compressed_split(const void* host_bytes, size_t nbytes, int de
   const uint8_t* st = p + kHeaderBytes;
   for (uint32_t i = 0; i < full.n_bricks; ++i)
     v->h_rec_words[i] = le32(st + 4 * ((size_t)i + 1)) - le32(st + 4 * (size_t)i);
-  SmemLayout sl;
+  SmemLayout sl, sl_pal;
   rc = compute_layout(*v, device, v->sched.threads, v->sched.stage_depth, &sl);
+  if (rc == VC_OK) rc = compute_layout(*v, device, v->sched.threads, v->sched.stage_depth, &sl_pal, true);
   if (rc != VC_OK) {
     vc_release(h);
     return rc;
   }
   v->dv.sm = sl;
+  v->sm_pal = sl_pal;
   if (cudaMemcpy(v->d_flags, full.bflags.data(), full.n_bricks, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();
     vc_release(h);

@@ -246,8 +246,9 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   v->sched.stage_depth = 1;
   v->sched.blocks_per_sm = 0;
   v->sched.chunk = 512;
-  SmemLayout sl;
+  SmemLayout sl, sl_pal;
   vc_status rc = compute_layout(*v, device, v->sched.threads, v->sched.stage_depth, &sl);
+  if (rc == VC_OK) rc = compute_layout(*v, device, v->sched.threads, v->sched.stage_depth, &sl_pal, true);
   if (rc != VC_OK) {
     std::free(v->h_rec_words);
     delete v;
@@ -300,6 +301,7 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   v->dv.coder = coder;
   v->dv.flags = flags;
   v->dv.sm = sl;
+  v->sm_pal = sl_pal;
   *out = reinterpret_cast<vc_volume*>(v);
   return VC_OK;
 }
@@ -333,12 +335,14 @@ vc_status vc_volume_set_schedule(vc_volume* vol, const vc_schedule* sched) {
   if (sched->stage_depth < 1 || sched->stage_depth > 2) return VC_ERR_ARG;
   if (!schedule_supported(v->L, sched->threads)) return VC_ERR_UNSUPPORTED;
   DeviceGuard g(v->device);
-  SmemLayout sl;
-  const vc_status rc = compute_layout(*v, v->device, sched->threads, sched->stage_depth, &sl);
+  SmemLayout sl, sl_pal;
+  vc_status rc = compute_layout(*v, v->device, sched->threads, sched->stage_depth, &sl);
+  if (rc == VC_OK) rc = compute_layout(*v, v->device, sched->threads, sched->stage_depth, &sl_pal, true);
   if (rc != VC_OK) return rc;
   v->sched = *sched;
   if (!v->sched.chunk) v->sched.chunk = 512;
   v->dv.sm = sl;
+  v->sm_pal = sl_pal;
   return VC_OK;
 }
 

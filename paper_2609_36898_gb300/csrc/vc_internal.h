@@ -126,7 +126,8 @@ struct Volume {
   uint8_t* d_file;       // device copy of the whole file (+ slack)
   uint8_t* d_tables;     // rANS table
   uint8_t* d_flags;      // per brick: bit 0 = palette holds label 0, bit 1 = holds another label
-  DevVolume dv;
+  DevVolume dv;          // dv.sm: the layout for label output
+  SmemLayout sm_pal;     // the layout for packed palette indices (differs for b = 64)
   // staging for vc_decode_bricks_host
   uint32_t* d_host_ids;
   uint32_t* d_host_slots;
@@ -213,7 +214,10 @@ void rans_encode(const uint8_t* sym, uint32_t S, const uint32_t f[16], const uin
 // cache paletting: bits per palette index (ceil(log2 max_pal), >= 1) and indices per u32 word
 void palette_packing(uint32_t max_pal, uint32_t* bits, uint32_t* per_word);
 bool schedule_supported(uint32_t L, uint32_t threads);
-vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, SmemLayout* out);
+// paletted: the layout for packed palette indices (b = 64: the finest level needs the voxel index
+// grid, so the large regions stay in a global scratch slice); else for labels.
+vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t nstage, SmemLayout* out,
+                         bool paletted = false);
 // presorted: the items are already in the order they should run (else requests of 1024 items or
 // more in the grid / batched schedules run longest record first)
 vc_status launch_decode(Volume& v, const uint32_t* ids, uint32_t n, const uint32_t* slots, uint32_t* cache,
