@@ -464,12 +464,14 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
     s.list_off = put(false, align16(2u * (s.list0_cap + cap[1])));
     // the finest index grid holds one z half at a time for b = 32 (plus the last plane of the first)
     const uint32_t nh = L == 5 ? 2u : 1u;
-    // label output keeps 8 children per open level-(L-1) cell instead
+    // label output keeps 8 children per open level-(L-1) cell instead (b >= 4); b <= 32 then
+    // needs neither the index grid nor the kept plane
     const uint32_t cap_open = (L - 1u) & 1u ? s.list1_cap : s.list0_cap;  // open level-(L-1) cells
     const uint32_t cb_bytes = L >= 2 ? s.gt_bytes * 8u * cap_open : 0u;
-    s.fg_bytes = align16(all_shared ? cb_bytes : std::max(s.gt_bytes * b * b * b / nh, cb_bytes));
+    const bool cells_only = all_shared || (!paletted && !global && L >= 2);
+    s.fg_bytes = align16(cells_only ? cb_bytes : std::max(s.gt_bytes * b * b * b / nh, cb_bytes));
     s.fg_off = put(true, s.fg_bytes);
-    s.plane_off = put(false, nh == 2 ? align16(s.gt_bytes * b * b) : 0u);
+    s.plane_off = put(false, nh == 2 && !cells_only ? align16(s.gt_bytes * b * b) : 0u);
     // private palette copy (frees the stage early); byte grids: a power of two >= max_pal, zero
     // padded (indices are masked with pal_cap - 1, so any byte stays in bounds)
     uint32_t p2 = 16u;

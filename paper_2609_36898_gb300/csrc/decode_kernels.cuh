@@ -1087,15 +1087,24 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
 #pragma unroll
           for (auto& x : B.w) x = gb * rep;
         }
+        if constexpr (sizeof(GT) == 1) {
+          if (pal_copied) {  // zero-padded power-of-two palette copy: masked bytes index it
+            const uint32_t pm4 = pmask * 0x01010101u;
+#pragma unroll
+            for (uint32_t h = 0; h < 2; ++h) {
+              A.w[h] &= pm4;
+              B.w[h] &= pm4;
+            }
+          }
+        }
 #pragma unroll
         for (uint32_t row = 0; row < 4; ++row) {  // row = dy | dz << 1: children 2 row, 2 row + 1
           uint32_t* dst = o + (row & 1u) * b + (row >> 1) * b * b;
           if constexpr (sizeof(GT) == 1) {
-            if (pal_copied) {  // zero-padded power-of-two palette copy: masked bytes index it
+            if (pal_copied) {
               const uint32_t wa = A.w[row >> 1], wb = B.w[row >> 1], k = 2u * (row & 1u);
-              store16(dst, c.pal[__byte_perm(wa, 0u, 0x4440u | k) & pmask],
-                      c.pal[__byte_perm(wa, 0u, 0x4441u | k) & pmask], c.pal[__byte_perm(wb, 0u, 0x4440u | k) & pmask],
-                      c.pal[__byte_perm(wb, 0u, 0x4441u | k) & pmask]);
+              store16(dst, c.pal[__byte_perm(wa, 0u, 0x4440u | k)], c.pal[__byte_perm(wa, 0u, 0x4441u | k)],
+                      c.pal[__byte_perm(wb, 0u, 0x4440u | k)], c.pal[__byte_perm(wb, 0u, 0x4441u | k)]);
               continue;
             }
           }
