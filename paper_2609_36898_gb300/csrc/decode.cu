@@ -249,7 +249,7 @@ __device__ __forceinline__ void rans_symbols_item(const Params& P, const uint32_
     return w0 <= w1 && w1 <= nw;
   };
   bool ok = true;
-  if (P.lod < kPrefixMinLod) {
+  if (P.lod < P.v.prefix_lod) {
     uint32_t w0, w1;
     const uint32_t len = min(q, S - run * q), ns = min(len, 32u);
     const uint32_t x0 = lane < ns ? rec[4u + 32u * run + lane] : (1u << 16);
@@ -562,7 +562,7 @@ uint32_t symbol_warps(uint32_t count, uint32_t sms) {
 
 // Warps per item of the rANS symbol kernels: one per run of the records (1 at a coarse level of
 // detail, where one warp walks the runs up to the level).
-uint32_t symbol_wpi(const Params& P) { return P.lod < kPrefixMinLod ? runs_k(P.v.flags) : 1u; }
+uint32_t symbol_wpi(const Params& P) { return P.lod < P.v.prefix_lod ? runs_k(P.v.flags) : 1u; }
 
 bool launch_symbols(const Params& P, uint8_t* ws, uint32_t base, uint32_t count, uint32_t smem, uint32_t sms,
                     cudaStream_t s) {

@@ -34,12 +34,6 @@ struct Params {
                           // (min(n, *n_dev) items; nullptr: n), for work sized on the device
 };
 
-// From this level of detail on, the rANS symbol kernel decodes only the stream's prefix up to the
-// level needed (levels 0 .. L - lod) and the reconstruction parses that prefix (level 0 needs the
-// whole stream). At level 1 the prefix is still about a quarter of the stream and the gain is a few
-// percent (32^3 bricks of the 512^3 workload: 0.258 -> 0.246 ms for 4096 bricks).
-constexpr uint32_t kPrefixMinLod = 1;
-
 // Items of a launch of a persistent schedule.
 __device__ __forceinline__ uint32_t launch_items(const Params& P) {
   return P.n_dev ? min(P.n, *P.n_dev) : P.n;
@@ -1377,7 +1371,7 @@ __device__ __forceinline__ ItemSrc item_src(const Params& P, uint32_t item, uint
     const uint32_t ns = head_words(S, runs_k(P.v.flags));
     s.head_bytes = (16u + 4u * ns + 4u * np + 15u) & ~15u;
     s.stream = reinterpret_cast<const uint32_t*>(P.ws + (size_t)(item - P.ws_item0) * P.v.sm.ws_stride);
-    s.S_use = P.lod >= kPrefixMinLod ? min(s.stream[P.v.sm.ws_stride / 4u - 1u], S) : 0u;  // the slot's last word
+    s.S_use = P.lod >= P.v.prefix_lod ? min(s.stream[P.v.sm.ws_stride / 4u - 1u], S) : 0u;  // the slot's last word
     s.stream_bytes = ((((s.S_use ? s.S_use : S) + 1u) >> 1) + 15u) & ~15u;
   } else {
     s.head_bytes = (e - a) * 4u;

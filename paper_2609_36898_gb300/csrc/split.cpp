@@ -335,6 +335,7 @@ vc_status vc_load_compressed_split(const void* host_bytes, size_t nbytes, int de
   }
   v->dv.sm = sl;
   v->sm_pal = sl_pal;
+  v->dv.prefix_lod = kPrefixMinLodSplit;  // level 1 reads the coarse records whole
   if (cudaMemcpy(v->d_flags, full.bflags.data(), full.n_bricks, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();
     vc_release(h);

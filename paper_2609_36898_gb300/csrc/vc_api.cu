@@ -300,6 +300,7 @@ vc_status vc_load_compressed(const void* host_bytes, size_t nbytes, int device, 
   v->dv.op_mask = op_mask;
   v->dv.coder = coder;
   v->dv.flags = flags;
+  v->dv.prefix_lod = kPrefixMinLod;
   v->dv.sm = sl;
   v->sm_pal = sl_pal;
   *out = reinterpret_cast<vc_volume*>(v);
