@@ -415,17 +415,24 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   // (and for packed palette indices, whose finest level is a 64^3 index grid) the large regions
   // (node operations, delta values, cursor masks, the finest grid) live in a global scratch slice
   // per block, the rest in shared memory when it fits (attempt 0), else everything in the slice
-  // (attempt 1); see SmemLayout::gscratch
+  // (attempt 1); see SmemLayout::gscratch. In attempt 0 the shared memory left over (up to a
+  // 1024-thread block's share of the multiprocessor) takes whole large regions back, the most
+  // read first: the children (or finest grid), the node operations, the cursor masks, the delta
+  // values (SmemLayout::big_sm).
   const bool global = L >= 6;
   SmemLayout s{};
   uint32_t o = 0, og = 0;  // shared / global scratch bytes placed
-  for (int attempt = global && !paletted ? -1 : 0; attempt < (global ? 2 : 1); ++attempt) {
+  uint32_t nodes_bytes = 0, dlist_bytes = 0, mask_bytes = 0;
+  auto build = [&](int attempt, uint32_t big) {
     s = SmemLayout{};
+    s.big_sm = big;
     o = 0;
     og = 0;
     const bool all_shared = attempt < 0, all_global = attempt == 1;
-    auto put = [&](bool large, uint32_t bytes) -> uint32_t {  // offset of a region of `bytes`
-      uint32_t& c = global && !all_shared && (large || all_global) ? og : o;
+    // offset of a region of `bytes`; region: 0 for the small ones, else its SmemLayout::big_sm bit
+    auto put = [&](uint32_t region, uint32_t bytes) -> uint32_t {
+      const bool in_global = global && !all_shared && (all_global || (region && !(big & region)));
+      uint32_t& c = in_global ? og : o;
       const uint32_t at = c;
       c += bytes;
       return at;
@@ -435,25 +442,28 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
     const uint32_t ncells = ((1u << (3 * L)) - 1u) / 7u;  // levels 0..L-1
     // misc: words 0..15 (flags, items, mbarriers), 16..47 warp totals, then 5 (NT / 32) + 5 words
     // of scan scratch
-    s.misc_off = put(false, align16(4u * (48u + 5u * (threads / 32u) + 5u)));
+    s.misc_off = put(0u, align16(4u * (48u + 5u * (threads / 32u) + 5u)));
     // a single stage may alias the regions a brick fills only after its parse (see stage_alias)
     const bool pal_always_copied = s.gt_bytes == 1 || v.max_pal <= 1024u;
     const bool may_alias = nstage == 1 && pal_always_copied && !global;
     // node operations: written by the parse; bricks without delta operations use their staged
     // symbols directly, or a copy here when the stage is aliased
     s.nodes_words = (v.max_nodes + 7u) / 8u + 4u;
-    s.nodes_off = put(true, (v.max_delta || may_alias) ? align16(4 * s.nodes_words) : 0u);
+    nodes_bytes = (v.max_delta || may_alias) ? align16(4 * s.nodes_words) : 0u;
+    s.nodes_off = put(kBigNodes, nodes_bytes);
     s.dlist_cap = v.max_delta;
-    s.dlist_off = put(true, align16(4 * (v.max_delta ? v.max_delta : 1u)));
+    dlist_bytes = align16(4 * (v.max_delta ? v.max_delta : 1u));
+    s.dlist_off = put(kBigDelta, dlist_bytes);
     // cursor masks (2 u32 masks + 2 prefixes per word of 32 nodes), level grids, stop bytes and
     // rank lists: one contiguous span unless b = 64
     s.nwords = (v.max_nodes + 31u) / 32u + 2u;
-    s.mask_off = put(true, align16((global ? 16 : 12) * s.nwords));
-    s.g_off = put(false, align16(s.gt_bytes * (ncells + 7u)));  // level 1 starts at cell 8 (alignment)
+    mask_bytes = align16((global ? 16 : 12) * s.nwords);
+    s.mask_off = put(kBigMasks, mask_bytes);
+    s.g_off = put(0u, align16(s.gt_bytes * (ncells + 7u)));  // level 1 starts at cell 8 (alignment)
     // per level l >= 1 below L, one byte per level-(l-1) cell: its children's stop-0 bits
     uint32_t ns_bytes = 0;
     for (uint32_t l = 1; l < L; ++l) ns_bytes += ((1u << (3 * (l - 1))) + 3u) & ~3u;
-    s.ns_off = put(false, align16(ns_bytes ? ns_bytes : 1u));
+    s.ns_off = put(0u, align16(ns_bytes ? ns_bytes : 1u));
     // the stop-0 cells of each level by rank, two buffers (even / odd levels); a level's stop-0
     // cells have 8 emitted children each, so there are at most max_nodes / 8 of them
     uint32_t cap[2] = {1u, 1u};
@@ -461,7 +471,7 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
       cap[l & 1u] = std::max(cap[l & 1u], std::min(1u << (3 * l), v.max_nodes / 8u + 1u));
     s.list0_cap = (cap[0] + 7u) & ~7u;
     s.list1_cap = cap[1];
-    s.list_off = put(false, align16(2u * (s.list0_cap + cap[1])));
+    s.list_off = put(0u, align16(2u * (s.list0_cap + cap[1])));
     // the finest index grid holds one z half at a time for b = 32 (plus the last plane of the first)
     const uint32_t nh = L == 5 ? 2u : 1u;
     // label output keeps 8 children per open level-(L-1) cell instead (b >= 4); b <= 32 then
@@ -470,24 +480,50 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
     const uint32_t cb_bytes = L >= 2 ? s.gt_bytes * 8u * cap_open : 0u;
     const bool cells_only = all_shared || (!paletted && !global && L >= 2);
     s.fg_bytes = align16(cells_only ? cb_bytes : std::max(s.gt_bytes * b * b * b / nh, cb_bytes));
-    s.fg_off = put(true, s.fg_bytes);
-    s.plane_off = put(false, nh == 2 && !cells_only ? align16(s.gt_bytes * b * b) : 0u);
+    s.fg_off = put(kBigFg, s.fg_bytes);
+    s.plane_off = put(0u, nh == 2 && !cells_only ? align16(s.gt_bytes * b * b) : 0u);
     // private palette copy (frees the stage early); byte grids: a power of two >= max_pal, zero
     // padded (indices are masked with pal_cap - 1, so any byte stays in bounds)
     uint32_t p2 = 16u;
     while (p2 < v.max_pal) p2 <<= 1;
     s.pal_cap = s.gt_bytes == 1 ? p2 : (v.max_pal <= 1024u ? v.max_pal : 0u);
-    s.pal_off = put(false, align16(4u * s.pal_cap));
-    s.rank_off = put(false, align16(2u * std::max(1u, (1u << (3 * (L - 1))) / 32u)));
+    s.pal_off = put(0u, align16(4u * s.pal_cap));
+    s.rank_off = put(0u, align16(2u * std::max(1u, (1u << (3 * (L - 1))) / 32u)));
     // the queue of open cells with palette reads: the rank list of level L-2, no longer read then
     s.pq_off = s.list_off + (L & 1u ? 2u * s.list0_cap : 0u);
     s.pq_cap = L & 1u ? s.list1_cap : s.list0_cap;
     // per warp a queue of up to 32 x 7 neighbour marks; the node operations, delta values and
-    // cursor masks are no longer read when the queues are filled
-    // (b = 64: the same span, in the scratch slice)
+    // cursor masks are no longer read when the queues are filled: the queues go over that span
+    // while it is one piece of memory (b = 64: in the scratch slice), else over the node
+    // operations' region when it is large enough, else into a region of their own
     const uint32_t mq_bytes = 224u * (threads / 32u);
+    const bool span_whole = !global || all_shared || all_global || (big & (kBigNodes | kBigDelta | kBigMasks)) == 0u;
     const uint32_t dead_span = s.mask_off + (global ? 16u : 12u) * s.nwords - s.nodes_off;
-    s.mq_off = dead_span >= mq_bytes ? s.nodes_off : put(global, align16(mq_bytes));
+    if (span_whole && dead_span >= mq_bytes) {
+      s.mq_off = s.nodes_off;
+      if (big & kBigNodes) s.big_sm |= kBigQueues;
+    } else if (nodes_bytes >= mq_bytes) {
+      s.mq_off = s.nodes_off;
+      if (big & kBigNodes) s.big_sm |= kBigQueues;
+    } else {
+      s.mq_off = put(kBigQueues, align16(mq_bytes));
+    }
+  };
+  for (int attempt = global && !paletted ? -1 : 0; attempt < (global ? 2 : 1); ++attempt) {
+    build(attempt, 0u);
+    if (global && attempt == 0 && o + 64u <= (uint32_t)optin) {
+      uint32_t left = std::min<uint32_t>((uint32_t)optin, (uint32_t)optin * threads / 1024u) - 64u;
+      left = left > o ? left - o : 0u;
+      uint32_t big = 0;
+      const uint32_t cand[4][2] = {{kBigFg, s.fg_bytes}, {kBigNodes, nodes_bytes}, {kBigMasks, mask_bytes},
+                                   {kBigDelta, dlist_bytes}};
+      for (const auto& c : cand)
+        if (c[1] && c[1] <= left) {
+          big |= c[0];
+          left -= c[1];
+        }
+      if (big) build(attempt, big);
+    }
     if (!global || o + 64u <= (uint32_t)optin) break;  // (+ the kernel's static shared words)
   }
   if (global && o + 64u > (uint32_t)optin) return VC_ERR_UNSUPPORTED;

@@ -499,6 +499,8 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   uint32_t* wtot = misc + 16;      // NW warp totals (words 16..47)
   uint32_t* scan_tmp = misc + 48;  // 5 NW + 5 words (48..255), 8-byte aligned
 
+  // large regions: the scratch slice (gm), or shared memory for those the layout put there (b = 64)
+  auto big = [&](uint32_t bit) -> unsigned char* { return (L >= 6 && (SL.big_sm & bit)) ? sm : gm; };
   const uint32_t n_pal = head[0], S_rec = head[1], nd = head[3];
   const bool truncated = S_use != 0u && S_use < S_rec;
   const uint32_t S = truncated ? S_use : S_rec;
@@ -517,14 +519,14 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   }
   c.op_mask = P.v.op_mask;
   c.s_err = s_err;
-  uint32_t* dlist = reinterpret_cast<uint32_t*>(gm + SL.dlist_off);
+  uint32_t* dlist = reinterpret_cast<uint32_t*>(big(kBigDelta) + SL.dlist_off);
   c.dlist = dlist;
   c.dlist_cap = nd < SL.dlist_cap ? nd : SL.dlist_cap;
 
   // 1. operations per node
   if (nd == 0 && SL.stage_alias) {
     // the symbols are the operations; copied out of the stage, which step 2 overwrites
-    uint32_t* nodes = reinterpret_cast<uint32_t*>(gm + SL.nodes_off);
+    uint32_t* nodes = reinterpret_cast<uint32_t*>(big(kBigNodes) + SL.nodes_off);
     const uint32_t nw = min((S + 7u) / 8u + 2u, SL.nodes_words);
     for (uint32_t i = tid; i < nw; i += NT) nodes[i] = sw[i];
     c.nodes = nodes;
@@ -534,9 +536,9 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     c.nodes = sw;
     c.n_nodes = S;
   } else {
-    uint32_t* nodes = reinterpret_cast<uint32_t*>(gm + SL.nodes_off);
+    uint32_t* nodes = reinterpret_cast<uint32_t*>(big(kBigNodes) + SL.nodes_off);
     // the finest grid's region is idle during the parse: it keeps the per-word automaton masks
-    uint32_t* wst = ((S + 7u) >> 3) * 4u <= SL.wst_bytes ? reinterpret_cast<uint32_t*>(gm + SL.wst_off) : nullptr;
+    uint32_t* wst = ((S + 7u) >> 3) * 4u <= SL.wst_bytes ? reinterpret_cast<uint32_t*>(big(kBigFg) + SL.wst_off) : nullptr;
     const ParseOut po = parse_stream<NT, (L >= 6)>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap, scan_tmp, wst, s_err,
                                                    short_delta);
     c.nodes = nodes;
@@ -549,7 +551,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   }
 
   // 2. palette-cursor masks and prefix counts (32 nodes per word)
-  uint32_t* adv_mask = reinterpret_cast<uint32_t*>(gm + SL.mask_off);
+  uint32_t* adv_mask = reinterpret_cast<uint32_t*>(big(kBigMasks) + SL.mask_off);
   uint32_t* del_mask = adv_mask + SL.nwords;
   // prefix counts: 16 bits while a brick has fewer than 2^16 nodes (b <= 32), 32 bits beyond
   using Pre = typename std::conditional<(L >= 6), uint32_t, uint16_t>::type;
@@ -598,7 +600,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
   const bool no_stop = (P.v.flags & kFlagNoStop) != 0;
   constexpr uint32_t b = 1u << L;
   const bool finest = Lout == (uint32_t)L;
-  GT* fg = reinterpret_cast<GT*>(gm + SL.fg_off);
+  GT* fg = reinterpret_cast<GT*>(big(kBigFg) + SL.fg_off);
 
   // the 8 children (nodes j0 .. j0+7) of a stop-0 cell with index gp at coordinates (px, py, pz):
   // palette indices or neighbour marks into v, returns the children emitted with stop bit 0
@@ -929,7 +931,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
       const uint32_t* ns32 = reinterpret_cast<const uint32_t*>(NS + nsofs_prev);
       uint16_t* rpre = reinterpret_cast<uint16_t*>(sm + SL.rank_off);  // rank of the first open cell of each 32
       const uint16_t* plist = lists[(L - 1u) & 1u];
-      GT* cb = reinterpret_cast<GT*>(gm + SL.fg_off);
+      GT* cb = reinterpret_cast<GT*>(big(kBigFg) + SL.fg_off);
       // rank of open cell m (bit m of ns32 set)
       auto rank_of = [&](uint32_t m, uint32_t w) -> uint32_t {
         return rpre[m >> 5] + __popc(w & ((1u << (m & 31u)) - 1u));
@@ -999,7 +1001,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
       // twice more: the chain is followed); cells that are not open hold their level-grid value.
       // Marks are replaced in place: a chain that meets a replaced value stops there, with the
       // same result.
-      uint8_t* mq = gm + SL.mq_off + 224u * warp;
+      uint8_t* mq = big(kBigQueues) + SL.mq_off + 224u * warp;
       for (uint32_t r0 = warp * 32u; r0 < npar; r0 += NT) {
         const uint32_t r = r0 + lane;
         const uint32_t mm = r < npar ? mark_bits<GT>(load_cells8<GT>(cb + 8u * r)) : 0u;

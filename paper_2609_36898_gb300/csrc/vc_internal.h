@@ -58,6 +58,8 @@ constexpr uint32_t kRing = 3u;            // pipelined schedule: workspace slots
 // records of a detail split hold levels 0 .. L - 1 only: level 1 needs them whole, so their
 // prefix decode starts at level 2.
 constexpr uint32_t kPrefixMinLod = 1;
+// SmemLayout::big_sm: large regions of a b = 64 layout placed in shared memory
+constexpr uint32_t kBigNodes = 1u, kBigDelta = 2u, kBigMasks = 4u, kBigFg = 8u, kBigQueues = 16u;
 constexpr uint32_t kPrefixMinLodSplit = 2;
 
 // Byte offsets of the reconstruction kernel's shared-memory regions (one brick per block).
@@ -100,6 +102,8 @@ struct SmemLayout {
   uint32_t total;
   uint32_t gscratch;     // 0: the regions are in shared memory; else b = 64: they are in a global
                          // scratch slice of this many bytes per thread block (no shared memory)
+  uint32_t big_sm;       // b = 64 with a scratch slice: the large regions in shared memory instead
+                         // (kBig* bits; the others are in the slice)
   // rANS symbol kernel
   uint32_t ws_stride;    // bytes of decoded symbols per request item (workspace)
   uint32_t a_buf;        // per-warp coded-word buffer bytes
