@@ -407,18 +407,21 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
                          bool paletted) {
   const uint32_t L = v.L;
   if (!schedule_supported(L, threads) || nstage < 1 || nstage > 2) return VC_ERR_UNSUPPORTED;
-  int optin = 0;
-  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
+  int optin = 0, per_sm = 0, reserved = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device) != cudaSuccess)
     return VC_ERR_CUDA;
   // b = 64 bricks: with label output the finest level needs only the open cells' children, so
   // every region may fit one block's shared memory (attempt -1; no scratch slice); otherwise
   // (and for packed palette indices, whose finest level is a 64^3 index grid) the large regions
   // (node operations, delta values, cursor masks, the finest grid) live in a global scratch slice
   // per block, the rest in shared memory when it fits (attempt 0), else everything in the slice
-  // (attempt 1); see SmemLayout::gscratch. In attempt 0 the shared memory left over (up to a
-  // 1024-thread block's share of the multiprocessor) takes whole large regions back, the most
-  // read first: the children (or finest grid), the node operations, the cursor masks, the delta
-  // values (SmemLayout::big_sm).
+  // (attempt 1); see SmemLayout::gscratch. In attempt 0 the shared memory left over takes whole
+  // large regions back, the most read first: the children (or finest grid), the node operations,
+  // the cursor masks, the delta values (SmemLayout::big_sm); up to the block's share of the
+  // multiprocessor when 1024 / threads blocks are resident (as many as 64 registers a thread
+  // allow), so that the fill costs no occupancy.
   const bool global = L >= 6;
   SmemLayout s{};
   uint32_t o = 0, og = 0;  // shared / global scratch bytes placed
@@ -512,7 +515,8 @@ vc_status compute_layout(const Volume& v, int device, uint32_t threads, uint32_t
   for (int attempt = global && !paletted ? -1 : 0; attempt < (global ? 2 : 1); ++attempt) {
     build(attempt, 0u);
     if (global && attempt == 0 && o + 64u <= (uint32_t)optin) {
-      uint32_t left = std::min<uint32_t>((uint32_t)optin, (uint32_t)optin * threads / 1024u) - 64u;
+      const uint32_t share = (uint32_t)per_sm / std::max(1u, 1024u / threads) - (uint32_t)reserved;
+      uint32_t left = std::min<uint32_t>((uint32_t)optin, share) - 64u;
       left = left > o ? left - o : 0u;
       uint32_t big = 0;
       const uint32_t cand[4][2] = {{kBigFg, s.fg_bytes}, {kBigNodes, nodes_bytes}, {kBigMasks, mask_bytes},
