@@ -102,6 +102,45 @@ def test_b64_thread_counts_and_grid_sizes(ragged, threads, blocks_per_sm):
         vol.release()
 
 
+@pytest.fixture(scope="module")
+def dense():
+    """128 x 128 x 64 voxels of ~19-voxel cells: 4 bricks of 64^3 with up to ~98k nodes each, too
+    many for every region of a brick to fit one block's shared memory."""
+    return synth.fill(synth.small(dims=(128, 128, 64), seed=66, grid=16, diameter=19.0, bg=0.1))
+
+
+@pytest.mark.parametrize("threads", [1024, 512, 256])
+def test_b64_scratch_layout_with_regions_in_shared_memory(dense, threads):
+    """Bricks beyond the all-in-shared-memory layout keep their large regions in a scratch slice,
+    and the shared memory a block leaves over takes some of them back (1024 threads: children and
+    node operations; 512: delta values; 256: none): every brick, label and packed-index output,
+    levels 0 and 1, grid and batched schedules, 1 and 4 rANS runs, against the oracle."""
+    for flags in (0, oracle.runs_flag(4)):
+        enc = vc.vc_encode_volume(dense, 6, op_mask=0x7F, coder=1, flags=flags)
+        n = oracle.header(enc)["n_bricks"]
+        assert max(len(oracle.brick_nodes(enc, i)) for i in range(n)) > 60000
+        vol = vc.Volume(enc)
+        try:
+            vc.vc_volume_set_schedule(vol.handle, threads, 1, 0)
+            for lod in (0, 1):
+                ref = oracle_bricks(enc, range(n), lod)
+                for mode in ("grid", "batched"):
+                    out, st = decode(vol, list(range(n)), lod, mode)
+                    assert st[0] == 0, (threads, flags, lod, mode, st)
+                    assert np.array_equal(out.reshape(ref.shape), ref), (threads, flags, lod, mode)
+            out, st = decode(vol, list(range(n)), 0, "grid", paletted=True)
+            assert st[0] == 0
+            _, bits, per = vc.vc_volume_slot_words(vol.handle, 0, True)
+            v = np.arange(64 ** 3)
+            for i in range(n):
+                pal = oracle.brick_record(enc, i)["palette"]
+                w = out[i][v // per].astype(np.uint64)
+                idx = ((w >> (bits * (v % per)).astype(np.uint64)) & ((1 << bits) - 1)).astype(np.int64)
+                assert np.array_equal(pal[idx].reshape(64, 64, 64), oracle.decode_brick(enc, i, 0)), (threads, flags, i)
+        finally:
+            vol.release()
+
+
 @pytest.mark.parametrize("coder", [0, 1])
 def test_b64_16bit_index_grids(coder):
     """2^3 cubes of distinct labels: 32768 labels per 64^3 brick (16-bit grids, palettes read from
