@@ -299,10 +299,11 @@ bool release_frame(void* handle) {
   if (!f || f->kind != kHandleFrame) return false;
   int prev = -1;
   cudaGetDevice(&prev);
-  if (prev != f->v->device) cudaSetDevice(f->v->device);
+  const int device = f->v->device;  // f is gone after free_frame
+  if (prev != device) cudaSetDevice(device);
   cudaDeviceSynchronize();
   free_frame(f);
-  if (prev >= 0 && prev != f->v->device) cudaSetDevice(prev);
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
   return true;
 }
 
