@@ -541,9 +541,12 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     uint32_t* wst = ((S + 7u) >> 3) * 4u <= SL.wst_bytes ? reinterpret_cast<uint32_t*>(big(kBigFg) + SL.wst_off) : nullptr;
     const ParseOut po = parse_stream<NT, (L >= 6)>(sw, S, nodes, SL.nodes_words, dlist, c.dlist_cap, scan_tmp, wst, s_err,
                                                    short_delta);
+    // a stream whose delta count is off may claim more nodes than the layout holds (it is sized
+    // for the volume's largest S - n_delta): flagged, and cut to what the regions hold
+    const uint32_t ncap = 32u * (SL.nwords - 2u);
     c.nodes = nodes;
-    c.n_nodes = po.n_nodes;
-    if (truncated ? po.n_delta > nd : po.n_delta != nd) set_err(s_err, VC_ERR_CORRUPT);
+    c.n_nodes = min(po.n_nodes, ncap);
+    if ((truncated ? po.n_delta > nd : po.n_delta != nd) || po.n_nodes > ncap) set_err(s_err, VC_ERR_CORRUPT);
     // delta values from their entries, one delta operation per thread (visible after the barriers
     // of step 2)
     for (uint32_t d = tid; d < c.dlist_cap; d += NT) dlist[d] = read_delta(sw, dlist[d], S, short_delta);
@@ -896,8 +899,13 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
       while (open8) {
         const uint32_t o = __ffs(open8) - 1u;
         open8 &= open8 - 1u;
-        if (base < lcap) list_cur[base] = (uint16_t)(8u * p + o);
-        else set_err(s_err, VC_ERR_CORRUPT);
+        if (base < lcap) {
+          list_cur[base] = (uint16_t)(8u * p + o);
+        } else {  // cut: the cell counts as stopped from here on, so that every cell of the next
+                  // levels is still written (inherited) and the stop bits match the ranks
+          set_err(s_err, VC_ERR_CORRUPT);
+          NSl[p] &= (uint8_t)~(1u << o);
+        }
         ++base;
       }
     }

@@ -245,6 +245,35 @@ def test_host_entry_point_matches_device_path(small_volume):
         vol.release()
 
 
+def test_garbage_coded_words_in_every_record_are_reported_not_faulted():
+    """Random bytes in place of every record's coded words (headers, states and palettes intact):
+    every brick decodes from garbage symbols, whose parse claims node and stop-0 counts no brick of
+    the volume has (rank lists cut, node counts beyond the layout, neighbour chains through cells
+    left unset). Every schedule and three levels of detail report VC_ERR_CORRUPT without a fault,
+    and the intact volume decodes to the oracle afterwards in the same context."""
+    V = synth.fill(synth.small(dims=(128, 128, 96), seed=12, grid=16, diameter=19.0, bg=0.1))
+    enc = vc.vc_encode_volume(V, 5, op_mask=0x7F, coder=1)
+    h = oracle.header(enc)
+    n = h["n_bricks"]
+    rec_off = (128 + 4 * (n + 1) + 15) & ~15
+    lib = oracle._load()
+    rng = np.random.default_rng(8)
+    bad = enc.copy()
+    for i in range(n):
+        r = oracle.brick_record(enc, i)
+        hw = int(lib.oracle_head_words(1, 0, r["n_sym"]))
+        at = rec_off + 4 * r["offset_words"] + 16 + 4 * hw + 4 * r["n_pal"]
+        bad[at: at + r["coded_bytes"]] = rng.integers(0, 256, r["coded_bytes"], dtype=np.uint8)
+    for lod in (0, 1, 2):
+        for mode in ("grid", "batched", "pipelined"):
+            _, st = gpu_decode(bad, np.arange(n), lod, mode)
+            assert st[0] == vc.VC_ERR_CORRUPT, (lod, mode, st)
+    torch.cuda.synchronize()
+    out, st = gpu_decode(enc, np.arange(n), 0, "grid")
+    assert st[0] == 0
+    assert np.array_equal(out, oracle_bricks(enc, np.arange(n), 0))
+
+
 # ------------------------------------------------------------------ brute force
 
 def _tiny_bricks():
