@@ -639,6 +639,10 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
       const uint32_t w = j0 >> 5, lt = (1u << (j0 & 31u)) - 1u;
       const uint32_t k0 = adv_pre[w] + __popc(adv_mask[w] & lt);
       const uint32_t dd0 = del_pre[w] + __popc(del_mask[w] & lt);
+      // the group's cursor stays within the palette: its advances read entries k0 .. k0 + na - 1,
+      // last / delta children read below the cursor (a corrupt cursor may run past the palette,
+      // and an index out of range could pass for a neighbour mark)
+      bad |= k0 + (uint32_t)__popc(adv8) > n_pal;
 #pragma unroll
       for (uint32_t o = 0; o < 8; ++o) {
         if ((m_pal >> o) & 1u) {
@@ -646,7 +650,6 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
           const uint32_t below = (1u << o) - 1u;
           const uint32_t k = k0 + __popc(adv8 & below);
           if (op == OP_ADV) {
-            bad |= k >= n_pal;
             v[o] = k;
           } else if (op == OP_LAST) {
             bad |= k == 0u;
@@ -700,31 +703,34 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
     const uint32_t k0 = adv_pre[w] + __popc(adv_mask[w] & lt);
     const uint32_t dd0 = del_pre[w] + __popc(del_mask[w] & lt);
     const uint32_t na0 = (adv[0] * 0x01010101u) >> 24, nd0 = (del[0] * 0x01010101u) >> 24;
+    // Both paths below check that the cursor stays within the palette: an advance reads entry
+    // k < |P|, last / delta children read below the cursor k <= |P| (a corrupt cursor may run
+    // past the palette, and an index out of range could pass for a neighbour mark).
     const uint32_t ndel = nd0 + ((del[1] * 0x01010101u) >> 24);
     bool bytewise = false;
     if constexpr (sizeof(GT) == 1) bytewise = ndel <= 4u;
     if (bytewise) {
-      // 8-bit grids: indices and the cursor stay below 252 in a valid brick, so all eight
-      // children are computed bytewise: k per byte, the group's delta values by byte permutation
-      // (up to four of them; more in one group take the loop below)
+      // 8-bit grids: the cursor stays below 252 (checked next, in full width: it also keeps every
+      // cursor byte of the bytewise computation from wrapping), so all eight children are
+      // computed bytewise: k per byte, the group's delta values by byte permutation (up to four
+      // of them; more in one group take the loop below)
       const uint32_t K[2] = {k0 * 0x01010101u + adv[0] * 0x01010100u,
                              (k0 + na0) * 0x01010101u + adv[1] * 0x01010100u};
       const uint32_t Dp[2] = {del[0] * 0x01010100u, nd0 * 0x01010101u + del[1] * 0x01010100u};
+      bad |= k0 + na0 + ((adv[1] * 0x01010101u) >> 24) > n_pal;  // the cursor after the group <= |P|
       uint32_t d4 = 0u;
 #pragma unroll
       for (uint32_t i = 0; i < 4; ++i) {
         const uint32_t di = dd0 + i;
         if (i < ndel) d4 |= (di < c.dlist_cap ? min(dlist[di], 255u) : 0u) << (8u * i);
       }
-      const uint32_t np4 = n_pal * 0x01010101u;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         uint32_t t = Dp[h] | (Dp[h] >> 4);
         t &= 0x00FF00FFu;
         const uint32_t sel = (t | (t >> 8)) & 0xFFFFu;  // byte i of Dp -> nibble i
-        const uint32_t delm = del[h] * 0xFFu, advm = adv[h] * 0xFFu, lstm = lst[h] * 0xFFu;
+        const uint32_t delm = del[h] * 0xFFu, lstm = lst[h] * 0xFFu;
         const uint32_t D = __byte_perm(d4, 0u, sel) & delm;
-        bad |= (~__vcmpltu4(K[h], np4) & advm) != 0u;                    // advance: k < |P|
         bad |= (__vcmpeq4(K[h], 0u) & lstm) != 0u;                        // last: k >= 1
         bad |= ((__vcmpeq4(D, 0u) | __vcmpgtu4(D, K[h])) & delm) != 0u;   // delta: 1 <= delta <= k
         const uint32_t idx = K[h] - lst[h] - D;
@@ -743,7 +749,6 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
         const uint32_t k = k0 + __popc(adv8 & below);
         uint32_t idx;
         if (op == OP_ADV) {
-          bad |= k >= n_pal;
           idx = k;
         } else if (op == OP_LAST) {
           bad |= k == 0u;
@@ -755,6 +760,7 @@ __device__ void decode_brick(const Params& P, const uint32_t* head, const uint32
           idx = k - delta;
         }
         set_cell<GT>(v, o, idx & (sizeof(GT) == 1 ? 0xFFu : 0xFFFFu));
+        bad |= k + ((adv8 >> o) & 1u) > n_pal;  // advance: k < |P|; last / delta: k <= |P|
       }
     }
   };

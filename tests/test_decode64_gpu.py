@@ -141,6 +141,42 @@ def test_b64_scratch_layout_with_regions_in_shared_memory(dense, threads):
             vol.release()
 
 
+@pytest.mark.parametrize("which", ["ragged", "dense"])
+def test_b64_garbage_coded_words_are_reported_not_faulted(which, ragged, dense):
+    """Random bytes in place of every record's coded words (headers, states, run starts and
+    palettes intact), in both layouts (everything in shared memory; a scratch slice with some
+    regions in shared memory) and with 1 and 4 rANS runs: every schedule at levels 0 and 1
+    reports VC_ERR_CORRUPT without a fault, and the intact volume decodes to the oracle afterwards."""
+    V = ragged if which == "ragged" else dense
+    lib = oracle._load()
+    rng = np.random.default_rng(9)
+    for flags in (0, oracle.runs_flag(4)):
+        enc = vc.vc_encode_volume(V, 6, op_mask=0x7F, coder=1, flags=flags)
+        n = oracle.header(enc)["n_bricks"]
+        rec_off = (128 + 4 * (n + 1) + 15) & ~15
+        bad = enc.copy()
+        for i in range(n):
+            r = oracle.brick_record(enc, i)
+            hw = int(lib.oracle_head_words(1, flags, r["n_sym"]))
+            at = rec_off + 4 * r["offset_words"] + 16 + 4 * hw + 4 * r["n_pal"]
+            bad[at: at + r["coded_bytes"]] = rng.integers(0, 256, r["coded_bytes"], dtype=np.uint8)
+        vol = vc.Volume(bad)
+        try:
+            for lod in (0, 1):
+                for mode in ("grid", "batched"):
+                    _, st = decode(vol, list(range(n)), lod, mode)
+                    assert st[0] == vc.VC_ERR_CORRUPT, (which, flags, lod, mode, st)
+        finally:
+            vol.release()
+        good = vc.Volume(enc)
+        try:
+            out, st = decode(good, list(range(n)), 0, "grid")
+            assert st[0] == 0
+            assert np.array_equal(out.reshape(n, 64, 64, 64), oracle_bricks(enc, range(n), 0))
+        finally:
+            good.release()
+
+
 @pytest.mark.parametrize("coder", [0, 1])
 def test_b64_16bit_index_grids(coder):
     """2^3 cubes of distinct labels: 32768 labels per 64^3 brick (16-bit grids, palettes read from
