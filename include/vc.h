@@ -20,7 +20,9 @@
  *   - Decode errors found on the device are reported through a caller-owned status buffer
  *     (VC_STATUS_WORDS int32 words): word 0 = first error code (0 if none; the first writer wins),
  *     word 1 = index of the request item that raised it, words 2..3 = library scratch (the work
- *     counter of the batched decoder, reset by each call). The kernels never trap.
+ *     counter of the batched decoder, reset by each call). The kernels never trap, and a corrupt
+ *     record (any byte of its operation stream, symbol words or states) is reported, never read
+ *     or written past the regions its decode uses; its output slot then holds unspecified labels.
  *
  * ------------------------------------------------------------------------------------------
  * Byte format ("VCZ1", all integers little endian). The paper fixes the operations, the
